@@ -1,0 +1,166 @@
+"""FP64 CPU oracle of the signature-kernel PDE solve — TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA product path never imports it
+and shares no code with it (only the seeded input generators are common).
+
+The arithmetic lives in ``sigk_oracle.c`` (plain C, float64, no FMA
+contraction), which follows Sec. 3.1 of the paper: the explicit
+finite-difference scheme on the dyadically refined grid P_lambda with the
+refined increment inner product 2^(-2 lambda) <dx_p, dy_q>, boundary value 1,
+and the kernel read at the terminal corner.  ``mmd2`` is the unbiased MMD
+estimator named in Sec. 3.1.1, written as the usual U-statistic.
+
+Pins (tests/test_oracle_pins.py) tie it to closed forms, brute-force truncated
+signatures, invariants and finite differences.  Every function is pinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int64)
+_i64 = ctypes.c_int64
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.oracle_sigk_pair.restype = ctypes.c_double
+        L.oracle_sigk_pair.argtypes = [_dp, _i64, _dp, _i64, _i64, ctypes.c_int]
+        L.oracle_sigk_pairs.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, ctypes.c_int, _dp]
+        L.oracle_sigk_gram.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _i64, ctypes.c_int, _dp]
+        L.oracle_sigk_pairs_varlen.argtypes = [_dp, _ip, _dp, _ip, _i64, _i64, ctypes.c_int, _dp]
+        L.oracle_sigk_pair_grad.restype = ctypes.c_double
+        L.oracle_sigk_pair_grad.argtypes = [_dp, _i64, _dp, _i64, _i64, ctypes.c_int,
+                                            ctypes.c_double, _dp, _dp]
+        L.oracle_sigk_pairs_grad.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, ctypes.c_int,
+                                             _dp, _dp, _dp]
+        L.oracle_sigk_gram_grad.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _i64, ctypes.c_int,
+                                            _dp, _dp, _dp]
+        L.oracle_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def sigkernel(x, y, dyadic_order: int) -> float:
+    """k_{x,y} on P_lambda for one pair; x: [L,d], y: [M,d]."""
+    x, xp = _d(x)
+    y, yp = _d(y)
+    assert x.ndim == 2 and y.ndim == 2 and x.shape[1] == y.shape[1]
+    return float(lib().oracle_sigk_pair(xp, x.shape[0], yp, y.shape[0], x.shape[1],
+                                        int(dyadic_order)))
+
+
+def pairs(X, Y, dyadic_order: int):
+    """out[b] = k(X_b, Y_b); X: [B,L,d], Y: [B,M,d]."""
+    X, xp = _d(X)
+    Y, yp = _d(Y)
+    B, L, d = X.shape
+    out = np.empty(B)
+    lib().oracle_sigk_pairs(xp, yp, B, L, Y.shape[1], d, int(dyadic_order),
+                            out.ctypes.data_as(_dp))
+    return out
+
+
+def gram(X, Y, dyadic_order: int):
+    """out[i,j] = k(X_i, Y_j)."""
+    X, xp = _d(X)
+    Y, yp = _d(Y)
+    Bx, L, d = X.shape
+    By, M, _ = Y.shape
+    out = np.empty((Bx, By))
+    lib().oracle_sigk_gram(xp, yp, Bx, By, L, M, d, int(dyadic_order), out.ctypes.data_as(_dp))
+    return out
+
+
+def pairs_varlen(Xp, x_off, Yp, y_off, dyadic_order: int):
+    """Pairs of uneven lengths, packed as [sum L, d] with offsets [B+1]."""
+    Xp, xp = _d(Xp)
+    Yp, yp = _d(Yp)
+    xo = np.ascontiguousarray(x_off, dtype=np.int64)
+    yo = np.ascontiguousarray(y_off, dtype=np.int64)
+    B = xo.shape[0] - 1
+    out = np.empty(B)
+    lib().oracle_sigk_pairs_varlen(xp, xo.ctypes.data_as(_ip), yp, yo.ctypes.data_as(_ip), B,
+                                   Xp.shape[1], int(dyadic_order), out.ctypes.data_as(_dp))
+    return out
+
+
+def sigkernel_grad(x, y, dyadic_order: int, gout: float = 1.0):
+    """(k, dk/dx, dk/dy) for one pair (reverse-mode of the discrete scheme)."""
+    x, xp = _d(x)
+    y, yp = _d(y)
+    dx = np.zeros_like(x)
+    dy = np.zeros_like(y)
+    k = lib().oracle_sigk_pair_grad(xp, x.shape[0], yp, y.shape[0], x.shape[1],
+                                    int(dyadic_order), float(gout), dx.ctypes.data_as(_dp),
+                                    dy.ctypes.data_as(_dp))
+    return float(k), dx, dy
+
+
+def pairs_grad(X, Y, dyadic_order: int, gout):
+    X, xp = _d(X)
+    Y, yp = _d(Y)
+    g, gp = _d(gout)
+    dX = np.zeros_like(X)
+    dY = np.zeros_like(Y)
+    B, L, d = X.shape
+    lib().oracle_sigk_pairs_grad(xp, yp, B, L, Y.shape[1], d, int(dyadic_order), gp,
+                                 dX.ctypes.data_as(_dp), dY.ctypes.data_as(_dp))
+    return dX, dY
+
+
+def gram_grad(X, Y, dyadic_order: int, gout, want_dx: bool = True, want_dy: bool = True):
+    X, xp = _d(X)
+    Y, yp = _d(Y)
+    g, gp = _d(gout)
+    Bx, L, d = X.shape
+    By, M, _ = Y.shape
+    dX = np.zeros_like(X) if want_dx else None
+    dY = np.zeros_like(Y) if want_dy else None
+    lib().oracle_sigk_gram_grad(xp, yp, Bx, By, L, M, d, int(dyadic_order), gp,
+                                dX.ctypes.data_as(_dp) if want_dx else None,
+                                dY.ctypes.data_as(_dp) if want_dy else None)
+    return dX, dY
+
+
+def mmd2(X, Y, dyadic_order: int) -> float:
+    """Unbiased MMD^2 estimator (Sec. 3.1.1 names it; U-statistic form):
+    1/(m(m-1)) sum_{i!=j} k(x_i,x_j) + 1/(n(n-1)) sum_{i!=j} k(y_i,y_j)
+    - 2/(mn) sum_{i,j} k(x_i,y_j)."""
+    m, n = X.shape[0], Y.shape[0]
+    Kxx = gram(X, X, dyadic_order)
+    Kyy = gram(Y, Y, dyadic_order)
+    Kxy = gram(X, Y, dyadic_order)
+    sxx = Kxx.sum() - np.trace(Kxx)
+    syy = Kyy.sum() - np.trace(Kyy)
+    return float(sxx / (m * (m - 1)) + syy / (n * (n - 1)) - 2.0 * Kxy.sum() / (m * n))
+
+
+def mmd2_grad_x(X, Y, dyadic_order: int):
+    """d MMD^2 / dX for the estimator above (X appears in Kxx twice and in Kxy)."""
+    m, n = X.shape[0], Y.shape[0]
+    gxx = np.full((m, m), 1.0 / (m * (m - 1)))
+    np.fill_diagonal(gxx, 0.0)
+    dXa, dXb = gram_grad(X, X, dyadic_order, gxx)
+    gxy = np.full((m, n), -2.0 / (m * n))
+    dXc, _ = gram_grad(X, Y, dyadic_order, gxy, want_dy=False)
+    return dXa + dXb + dXc
