@@ -1,0 +1,349 @@
+"""Benchmark of the signature-kernel PDE solve on GB300.
+
+One step = one pass of the whole hot path over one batch: the Gram matrix of
+256 x 256 pairs of 128-point, 8-channel time-augmented random walks at dyadic
+order 2 (xi ~ N(0, 1/(L d))), FP32 recurrence: increments, coarse-cell
+coefficients, the anti-diagonal sweep of 508 x 508 refined cells per pair,
+and the corner values, all inside one kernel launch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` is refined grid cells per second over
+the whole job (inputs resident in HBM, L2 flushed between timed steps);
+`e2e` is the same metric through the public API with the inputs copied from
+pinned host memory and the Gram read back every step.  `--impl reference`
+times the FP64 CPU oracle on this host's cores on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PDE grid cells/s and kernel pairs/s at stated rel err vs FP64 oracle; % FP32 FMA peak"
+WORKLOAD = "gram 256x256, L=M=128, d=8 time-augmented random walks, dyadic order 2, fp32 recurrence"
+BX = BY = 256
+L = M = 128
+D = 8
+LAM = 2
+NI = (L - 1) << LAM
+NJ = (M - 1) << LAM
+CELLS_PER_PAIR = NI * NJ
+COARSE_PER_PAIR = (L - 1) * (M - 1)
+FLOP_PER_CELL = 3           # add, multiply, add of the printed scheme (h precomputed per coarse cell)
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB of L2
+
+
+def peaks():
+    p = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+    return p
+
+
+def fp32_peak_tflops(sms: int):
+    """FP32 FMA peak: SMs x 128 lanes x 2 flop x max SM clock."""
+    p = peaks()
+    mhz = float(p.get("sm_max_mhz", 2070.0))
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, mhz, ("measured" if "sm_max_mhz" in p else "fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_inputs(rank: int):
+    from paper_2006_14794_gb300 import inputs
+    w = inputs.gram_256(seed=inputs.SEEDS[2] + 1000 * rank)
+    X32, X64 = inputs.f32(w["X"])
+    Y32, Y64 = inputs.f32(w["Y"])
+    return X32, Y32, X64, Y64
+
+
+def oracle_sample_rate(X64, Y64, budget_s: float):
+    """Oracle cells/s on this host's cores: whole rows of the Gram, until the
+    time budget is spent (at least one row)."""
+    import oracle
+    t0 = time.perf_counter()
+    rows = 0
+    while True:
+        oracle.gram(X64[rows:rows + 1], Y64, LAM)
+        rows += 1
+        if time.perf_counter() - t0 >= budget_s or rows == BX:
+            break
+    dt = time.perf_counter() - t0
+    pairs = rows * BY
+    return pairs * CELLS_PER_PAIR / dt, pairs, dt, oracle.num_threads()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    _, _, X64, Y64 = make_inputs(0)
+    vals = []
+    budget = float(os.environ.get("SIGK_REF_STEP_SECONDS", "8"))
+    for _ in range(args.warmup):
+        oracle_sample_rate(X64, Y64, 0.5)
+    samples = []
+    for _ in range(args.steps):
+        rate, pairs, dt, cores = oracle_sample_rate(X64, Y64, budget)
+        vals.append(rate)
+        samples.append(pairs)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * BX * BY * CELLS_PER_PAIR / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+        "pairs_per_s": value / CELLS_PER_PAIR,
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d of 65536 pairs (whole Gram rows) per step, ~%gs each" % (
+                             min(samples), budget)},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2006_14794_gb300 import sigk
+    sigk.lib()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    X32, Y32, X64, Y64 = make_inputs(rank)
+    Xd = torch.from_numpy(X32).to(dev)
+    Yd = torch.from_numpy(Y32).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- warm-up (also the parity sample)
+    out = None
+    for _ in range(max(args.warmup, 3)):
+        out = sigk.gram(Xd, Yd, LAM)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: inputs resident, L2 flushed before each step
+    st = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local if ws > 1 else 0)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(st)
+        out = sigk.gram(Xd, Yd, LAM)
+        ev[i][1].record(st)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells_step = BX * BY * CELLS_PER_PAIR
+    value = ws * cells_step / (ms * 1e-3)
+
+    # ---- end to end through the public API, host buffers (pinned)
+    Xh = torch.from_numpy(X32).pin_memory()
+    Yh = torch.from_numpy(Y32).pin_memory()
+    Oh = torch.empty(BX, BY, dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, args.steps)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for i in range(e2e_steps):
+        xd = Xh.to(dev, non_blocking=True)
+        yd = Yh.to(dev, non_blocking=True)
+        o = sigk.gram(xd, yd, LAM)
+        Oh.copy_(o, non_blocking=True)
+    e1.record(st)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = ws * cells_step / (e2e_ms * 1e-3)
+
+    # ---- parity of the timed output with the oracle on sampled entries
+    line = None
+    if rank == 0:
+        import oracle
+        got = out.cpu().numpy()
+        rng = np.random.default_rng(11)
+        idx = rng.integers(0, BX, size=(48, 2))
+        ref = np.array([oracle.sigkernel(X64[i], Y64[j], LAM) for i, j in idx])
+        g = got[idx[:, 0], idx[:, 1]]
+        rel = float(np.max(np.abs(g - ref) / np.maximum(np.abs(ref), 1e-3)))
+
+        peak_tf, mhz, peak_src = fp32_peak_tflops(sms)
+        flop = BX * BY * (CELLS_PER_PAIR * FLOP_PER_CELL + COARSE_PER_PAIR * 2 * D)
+        achieved_tf = flop / (ms * 1e-3) / 1e12
+
+        # plain FP64 per-pair GPU sweep on the same workload (comparison baseline)
+        f64 = None
+        if not args.skip_fp64:
+            Xd64 = torch.from_numpy(X64).to(dev)
+            Yd64 = torch.from_numpy(Y64).to(dev)
+            sigk.gram(Xd64[:8], Yd64[:8], LAM)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            o64 = sigk.gram(Xd64, Yd64, LAM)
+            b.record(st)
+            torch.cuda.synchronize(dev)
+            ms64 = a.elapsed_time(b)
+            rel64 = float(np.max(np.abs(o64.cpu().numpy()[idx[:, 0], idx[:, 1]] - ref) /
+                                 np.maximum(np.abs(ref), 1e-3)))
+            f64 = {"value": cells_step / (ms64 * 1e-3), "unit": "cells/s", "ms_per_step": ms64,
+                   "rel_err_vs_oracle": rel64, "kernel": "plain per-pair anti-diagonal FP64"}
+
+        cpu = None
+        if not args.skip_cpu:
+            rate, pairs, dt, cores = oracle_sample_rate(X64, Y64, args.cpu_seconds)
+            cpu = {"value": rate, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                   "sample": "%d of 65536 pairs (whole Gram rows), %.1f s" % (pairs, dt)}
+
+        line = {
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_step": BX * BY,
+                       "cells_per_pair": CELLS_PER_PAIR, "l2": "flushed (256 MB write) before each step",
+                       "parallelism": "dp%d (independent Gram per GPU)" % ws},
+            "pairs_per_s": value / CELLS_PER_PAIR,
+            "rel_err_vs_oracle": rel,
+            "fp32_fma_peak_frac": achieved_tf / peak_tf,
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": None,
+                         "peak_source": "%s SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s max SM clock)" % (
+                             sms, mhz, peak_src),
+                         "work": "3 flop per refined cell + 2d flop per coarse cell"},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": "cells/s",
+                    "h2d_bytes_per_step": int(X32.nbytes + Y32.nbytes),
+                    "d2h_bytes_per_step": int(BX * BY * 4), "ms_per_step": e2e_ms},
+            "gpu_launches": args.steps,
+            "wall_s_timed_region": t_wall,
+            "fp64_plain_gpu": f64,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

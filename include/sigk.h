@@ -1,0 +1,153 @@
+/*
+ * sigk.h — C ABI of libsigk: the signature kernel of two streams, computed
+ * as the solution of its Goursat PDE on a dyadically refined grid.
+ *
+ * Paper: C. Salvi, T. Cass, J. Foster, T. Lyons, W. Yang, "The Signature
+ * Kernel is the solution of a Goursat PDE" (arXiv 2006.14794).
+ *
+ *   k_{x,y}(s,t) = <S(x)_s, S(y)_t>                      (Def. "signature kernel")
+ *   d^2 k / ds dt = <x'_s, y'_t> k,  k(u,.) = k(.,v) = 1  (Thm. "PDE")
+ *
+ * solved with the explicit finite-difference scheme of Sec. 3.1 on the grid
+ * P_lambda, which splits every cell of the sample grid into
+ * 2^lambda x 2^lambda cells (Def. of P_lambda).  On piecewise-linear paths the
+ * refined increment inner product is 2^(-2 lambda) <dx_p, dy_q> (remark after
+ * the scheme):
+ *
+ *   k(i+1,j+1) = k(i+1,j) + k(i,j+1) - k(i,j)
+ *                + 1/2 <dx, dy> (k(i+1,j) + k(i,j+1)),   k(0,.) = k(.,0) = 1,
+ *
+ * and the kernel is the value at the terminal corner.  A path of L points
+ * x_0..x_{L-1} in R^d gives L-1 increments; rows of P_lambda refine x
+ * (Ni = 2^lambda (L-1)), columns refine y (Nj = 2^lambda (M-1)).
+ *
+ * Conventions for every call:
+ *  - Every pointer is caller-owned DEVICE memory, row-major and contiguous
+ *    (paths [B, L, d]; outputs [B] or [Bx, By]); 4-byte (f32) or 8-byte (f64)
+ *    alignment.  Offsets of the uneven-length calls are device int64 arrays.
+ *  - Calls are asynchronous on `stream` (0 = the legacy default stream).
+ *    Argument errors are detected on the host, return an error code and
+ *    launch nothing.  CUDA launch errors return SIGK_ECUDA.
+ *  - A call needing scratch memory takes it from the caller-provided
+ *    workspace `ws` of `ws_bytes` bytes; size it with sigk_workspace_bytes.
+ *    Calls whose workspace size is 0 accept ws = NULL.
+ *  - L = 1 or M = 1 (a single point) is valid and gives k = 1.  B = 0 is
+ *    valid and launches nothing.  d >= 1.  0 <= dyadic_order <= 8.
+ *  - NaN or Inf inputs propagate to the outputs; nothing traps.
+ *  - Time augmentation and path scaling are the caller's job.
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef SIGK_H
+#define SIGK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIGK_OK = 0,
+    SIGK_EINVAL = 1,        /* bad argument (null pointer, negative size, ...) */
+    SIGK_ENOMEM_WS = 2,     /* workspace missing or smaller than required      */
+    SIGK_ECUDA = 3,         /* a CUDA call failed (launch error, bad device)   */
+    SIGK_ETIMEOUT = 4,      /* a device-side bounded wait expired              */
+    SIGK_EUNSUPPORTED = 5   /* valid but unsupported (dyadic order > 8, ...)   */
+} sigk_status;
+
+typedef enum { SIGK_F32 = 0, SIGK_F64 = 1 } sigk_dtype;   /* storage AND arithmetic */
+
+/* Recurrence form.  AUTO = the register-chained difference form for f32 and
+ * the paper's plain form for f64.  PLAIN = one thread block per pair sweeping
+ * the grid's anti-diagonals with the scheme as printed (f64) or its
+ * difference form (f32): the baseline the chained kernel is measured against. */
+typedef enum { SIGK_REC_AUTO = 0, SIGK_REC_CHAIN = 1, SIGK_REC_PLAIN = 2 } sigk_rec;
+
+typedef struct {
+    int rec;          /* sigk_rec; 0 = auto                                   */
+    int symmetric;    /* gram only: X == Y and Bx == By; fills the lower
+                         triangle by mirroring the upper one                  */
+    int reserved[6];  /* must be 0                                            */
+} sigk_opts;          /* a NULL pointer means all-zero (automatic) options    */
+
+typedef enum {
+    SIGK_OP_PAIRS = 0, SIGK_OP_GRAM = 1, SIGK_OP_PAIRS_VARLEN = 2,
+    SIGK_OP_PAIRS_BACKWARD = 3, SIGK_OP_GRAM_BACKWARD = 4
+} sigk_op;
+
+/* Bytes of device workspace the call `op` needs for these sizes (B_or_Bx is
+ * B for pair calls; By is ignored for them).  For SIGK_OP_PAIRS_VARLEN pass
+ * L = M = the longest path length.  Returns 0 when no workspace is needed.
+ * Never fails; nonsense sizes give 0. */
+size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int64_t M,
+                            int64_t d, int dyadic_order, int dtype, const sigk_opts *opts);
+
+/* out[b] = k(X_b, Y_b), b < B.   X: [B, L, d], Y: [B, M, d], out: [B].
+ * Defines: Def. "signature kernel" + the explicit scheme of Sec. 3.1. */
+int sigk_pairs(const void *X, const void *Y, int64_t B, int64_t L, int64_t M, int64_t d,
+               int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *ws,
+               size_t ws_bytes, void *stream);
+
+/* out[i * By + j] = k(X_i, Y_j).   X: [Bx, L, d], Y: [By, M, d], out: [Bx, By].
+ * The Gram matrices used by the paper's kernel methods (Sec. 5). */
+int sigk_gram(const void *X, const void *Y, int64_t Bx, int64_t By, int64_t L, int64_t M,
+              int64_t d, int dyadic_order, int dtype, const sigk_opts *opts, void *out,
+              void *ws, size_t ws_bytes, void *stream);
+
+/* Pairs of uneven lengths.  Path b of X is rows x_off[b] .. x_off[b+1]-1 of
+ * Xp [sum L, d]; likewise Y.  x_off, y_off: device int64 [B+1], nondecreasing,
+ * x_off[0] = 0.  max_len: an upper bound on every path length (host value).
+ * out: [B].  Same scheme as sigk_pairs, per pair. */
+int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp,
+                      const int64_t *y_off, int64_t B, int64_t d, int64_t max_len,
+                      int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *ws,
+                      size_t ws_bytes, void *stream);
+
+/* Reverse-mode derivative of sigk_pairs: dX[b] = grad_out[b] dk_b/dX_b and
+ * dY[b] = grad_out[b] dk_b/dY_b (either output may be NULL to skip it).
+ * The paper states no gradient; this is the exact derivative of the discrete
+ * scheme (adjoint sweep from the terminal corner, then the chain rule through
+ * <dx_p, dy_q>).  grad_out: [B]; dX: [B, L, d]; dY: [B, M, d] (overwritten). */
+int sigk_pairs_backward(const void *grad_out, const void *X, const void *Y, int64_t B,
+                        int64_t L, int64_t M, int64_t d, int dyadic_order, int dtype,
+                        const sigk_opts *opts, void *dX, void *dY, void *ws, size_t ws_bytes,
+                        void *stream);
+
+/* Reverse-mode derivative of sigk_gram: dX[i] = sum_j grad_out[i,j] dk_ij/dX_i,
+ * dY[j] = sum_i grad_out[i,j] dk_ij/dY_j (either may be NULL).
+ * grad_out: [Bx, By].  dX, dY overwritten. */
+int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64_t Bx,
+                       int64_t By, int64_t L, int64_t M, int64_t d, int dyadic_order,
+                       int dtype, const sigk_opts *opts, void *dX, void *dY, void *ws,
+                       size_t ws_bytes, void *stream);
+
+/* The unbiased MMD^2 estimator between two batches (Sec. 3.1.1 names it; the
+ * U-statistic form) from the three Gram matrices:
+ *   out[0] = sum_{i!=j} Kxx_ij / (m(m-1)) + sum_{i!=j} Kyy_ij / (n(n-1))
+ *            - 2 sum_{i,j} Kxy_ij / (mn).
+ * Kxx [m,m], Kyy [n,n], Kxy [m,n]; out: one element.  m, n >= 2. */
+int sigk_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n,
+              int dtype, void *out, void *stream);
+
+/* Gradient of sigk_mmd2 with respect to the three Gram matrices, scaled by
+ * the scalar grad (device, one element): writes gKxx [m,m], gKyy [n,n],
+ * gKxy [m,n] (any may be NULL). */
+int sigk_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *gKxx,
+                       void *gKyy, void *gKxy, void *stream);
+
+/* Status word of the last call that used workspace `ws` on `stream`:
+ * synchronises the stream, then returns SIGK_OK or SIGK_ETIMEOUT (a bounded
+ * device wait expired).  SIGK_OK when ws is NULL. */
+int sigk_stream_status(void *stream, void *ws);
+
+/* Static description of a status code (never NULL). */
+const char *sigk_strerror(int status);
+
+/* Library version, e.g. "sigk 0.1 sm_103a". */
+const char *sigk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIGK_H */

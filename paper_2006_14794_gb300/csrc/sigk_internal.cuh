@@ -1,0 +1,98 @@
+// Internal declarations shared by the libsigk CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sigk.h"
+
+namespace sigk {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// How a flat pair index maps to (row path, column path, output slots).
+// The grid's rows refine the "A" path and its columns the "B" path.
+enum PairMode { PM_PAIRS = 0, PM_GRAM = 1, PM_GRAM_SYM = 2, PM_VARLEN = 3 };
+
+struct PairSrc {
+    int mode;
+    const void *A;          // row paths
+    const void *B;          // column paths
+    const int64_t *a_off;   // varlen offsets (rows of A), [n+1]
+    const int64_t *b_off;
+    int64_t nb;             // gram: number of B paths (columns of the enumeration)
+    int64_t La, Lb;         // uniform lengths (ignored for varlen)
+    int64_t d;
+    int64_t out_si, out_sj; // gram: out index = i*out_si + j*out_sj
+};
+
+struct PairRef {
+    int64_t a_row0, la;     // first point row of the A path, and its length
+    int64_t b_row0, lb;
+    int64_t out0, out1;     // output slots (out1 = -1 when only one)
+};
+
+// Upper-triangle enumeration (i <= j) of an n x n symmetric Gram matrix.
+__host__ __device__ inline void sym_index(int64_t k, int64_t n, int64_t &i, int64_t &j) {
+    // row i holds n - i entries, starting at off(i) = i*n - i*(i-1)/2
+    double nn = (double)n;
+    double disc = (2.0 * nn + 1.0) * (2.0 * nn + 1.0) - 8.0 * (double)k;
+    int64_t ii = (int64_t)((2.0 * nn + 1.0 - sqrt(disc > 0 ? disc : 0.0)) * 0.5);
+    if (ii < 0) ii = 0;
+    if (ii > n - 1) ii = n - 1;
+    while (ii > 0 && ii * n - ii * (ii - 1) / 2 > k) --ii;
+    while (ii + 1 < n && (ii + 1) * n - (ii + 1) * ii / 2 <= k) ++ii;
+    i = ii;
+    j = ii + (k - (ii * n - ii * (ii - 1) / 2));
+}
+
+__host__ __device__ inline PairRef pair_ref(const PairSrc &s, int64_t k) {
+    PairRef r;
+    r.out1 = -1;
+    if (s.mode == PM_PAIRS) {
+        r.a_row0 = k * s.La; r.la = s.La;
+        r.b_row0 = k * s.Lb; r.lb = s.Lb;
+        r.out0 = k;
+    } else if (s.mode == PM_GRAM) {
+        int64_t i = k / s.nb, j = k - (k / s.nb) * s.nb;
+        r.a_row0 = i * s.La; r.la = s.La;
+        r.b_row0 = j * s.Lb; r.lb = s.Lb;
+        r.out0 = i * s.out_si + j * s.out_sj;
+    } else if (s.mode == PM_GRAM_SYM) {
+        int64_t i, j;
+        sym_index(k, s.nb, i, j);
+        r.a_row0 = i * s.La; r.la = s.La;
+        r.b_row0 = j * s.Lb; r.lb = s.Lb;
+        r.out0 = i * s.nb + j;
+        r.out1 = (i != j) ? j * s.nb + i : -1;
+    } else {
+        r.a_row0 = s.a_off[k]; r.la = s.a_off[k + 1] - s.a_off[k];
+        r.b_row0 = s.b_off[k]; r.lb = s.b_off[k + 1] - s.b_off[k];
+        r.out0 = k;
+    }
+    return r;
+}
+
+// ---- launchers (each returns a cudaError_t) --------------------------------
+
+struct ChainPlan {
+    int R, lam, D4;         // rows per lane, dyadic order, channel float4 chunks
+    int Tper, vpad, vtop;   // period (refined columns incl. virtual), pads
+    int NQ, NQV;            // coarse columns incl. virtual, virtual ones
+    int nby, nbx, nout;     // per-warp column / row increment buffers, output slots
+    int yunits, xunits;     // their sizes (float4 units)
+    int warp_units;         // shared memory per warp (float4 units)
+    int64_t ppw;            // pairs per warp
+    int grid, smem_bytes;
+};
+
+// Returns false when the chained kernel has no instance for these sizes.
+bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p);
+cudaError_t launch_chain_f32(const PairSrc &src, const ChainPlan &p, int64_t n_pairs,
+                             float *out, cudaStream_t st);
+
+cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype, void *out,
+                         cudaStream_t st);
+
+cudaError_t launch_fill_one(void *out, int64_t n, int dtype, cudaStream_t st);
+
+}  // namespace sigk

@@ -1,0 +1,190 @@
+"""Thin Python binding of libsigk (include/sigk.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module
+only checks tensors, allocates outputs with PyTorch, and passes device
+pointers and the current CUDA stream through ``ctypes``.  Importing it does
+not need a GPU; calling it needs the built ``libsigk.so`` and fails loudly when
+it is missing (there is no CPU fallback).
+
+Names follow the C ABI: ``pairs``, ``gram``, ``pairs_varlen``,
+``pairs_backward``, ``gram_backward``, ``mmd2``; the autograd wrappers are
+``SigKernelPairs``, ``SigKernelGram`` and ``mmd2_loss``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+SIGK_OK, SIGK_EINVAL, SIGK_ENOMEM_WS, SIGK_ECUDA, SIGK_ETIMEOUT, SIGK_EUNSUPPORTED = range(6)
+SIGK_F32, SIGK_F64 = 0, 1
+REC_AUTO, REC_CHAIN, REC_PLAIN = 0, 1, 2
+OP_PAIRS, OP_GRAM, OP_PAIRS_VARLEN, OP_PAIRS_BACKWARD, OP_GRAM_BACKWARD = range(5)
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+class SigkOpts(ctypes.Structure):
+    _fields_ = [("rec", _int), ("symmetric", _int), ("reserved", _int * 6)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every symbol include/sigk.h declares
+SIGNATURES = [
+    ("sigk_workspace_bytes", ctypes.c_size_t,
+     [_int, _i64, _i64, _i64, _i64, _i64, _int, _int, _vp]),
+    ("sigk_pairs", _int, [_vp, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp, _vp, _vp,
+                          ctypes.c_size_t, _vp]),
+    ("sigk_gram", _int, [_vp, _vp, _i64, _i64, _i64, _i64, _i64, _int, _int, _vp, _vp, _vp,
+                         ctypes.c_size_t, _vp]),
+    ("sigk_pairs_varlen", _int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _int, _int, _vp, _vp,
+                                 _vp, ctypes.c_size_t, _vp]),
+    ("sigk_pairs_backward", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp, _vp,
+                                   _vp, _vp, ctypes.c_size_t, _vp]),
+    ("sigk_gram_backward", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _int, _int, _vp,
+                                  _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    ("sigk_mmd2", _int, [_vp, _vp, _vp, _i64, _i64, _int, _vp, _vp]),
+    ("sigk_mmd2_backward", _int, [_vp, _i64, _i64, _int, _vp, _vp, _vp, _vp]),
+    ("sigk_stream_status", _int, [_vp, _vp]),
+    ("sigk_strerror", ctypes.c_char_p, [_int]),
+    ("sigk_version", ctypes.c_char_p, []),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """The loaded libsigk.so.  Builds it in-tree when missing (needs nvcc)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError("libsigk.so is not built: %s" % path)
+            _build.build()
+        L = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SigkError(RuntimeError):
+    pass
+
+
+def _check(status: int, what: str):
+    if status != SIGK_OK:
+        msg = lib().sigk_strerror(status).decode()
+        raise SigkError("%s failed: %s (status %d)" % (what, msg, status))
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return SIGK_F32
+    if t.dtype == torch.float64:
+        return SIGK_F64
+    raise TypeError("sigk works on float32 or float64 tensors, got %s" % t.dtype)
+
+
+def _dev(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor (libsigk has no CPU path)" % name)
+    return t.contiguous()
+
+
+def _stream(dev) -> int:
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _opts(rec: int = REC_AUTO, symmetric: bool = False):
+    o = SigkOpts()
+    o.rec = int(rec)
+    o.symmetric = 1 if symmetric else 0
+    return o
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _workspace(op, b, b2, L, M, d, lam, dt, o, device):
+    n = lib().sigk_workspace_bytes(op, b, b2, L, M, d, lam, dt, ctypes.byref(o))
+    if n == 0:
+        return None, 0
+    return torch.empty(n, dtype=torch.uint8, device=device), n
+
+
+def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO) -> torch.Tensor:
+    """out[b] = k(X_b, Y_b).  X: [B, L, d], Y: [B, M, d] (same dtype, same CUDA device)."""
+    X, Y = _dev(X, "X"), _dev(Y, "Y")
+    if X.dim() != 3 or Y.dim() != 3 or X.shape[0] != Y.shape[0] or X.shape[2] != Y.shape[2]:
+        raise ValueError("pairs wants X [B,L,d] and Y [B,M,d]")
+    if X.dtype != Y.dtype:
+        raise TypeError("X and Y must share a dtype")
+    B, L, d = X.shape
+    M = Y.shape[1]
+    dt = _dtype_code(X)
+    out = torch.empty(B, dtype=X.dtype, device=X.device)
+    o = _opts(rec)
+    ws, nws = _workspace(OP_PAIRS, B, 0, L, M, d, dyadic_order, dt, o, X.device)
+    _check(lib().sigk_pairs(X.data_ptr(), Y.data_ptr(), B, L, M, d, int(dyadic_order), dt,
+                            ctypes.byref(o), out.data_ptr(), _ptr(ws), nws, _stream(X.device)),
+           "sigk_pairs")
+    return out
+
+
+def gram(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO,
+         symmetric: bool = False) -> torch.Tensor:
+    """out[i, j] = k(X_i, Y_j).  With symmetric=True, Y must be X and only the
+    upper triangle is solved (then mirrored)."""
+    X, Y = _dev(X, "X"), _dev(Y, "Y")
+    if X.dim() != 3 or Y.dim() != 3 or X.shape[2] != Y.shape[2]:
+        raise ValueError("gram wants X [Bx,L,d] and Y [By,M,d]")
+    if X.dtype != Y.dtype:
+        raise TypeError("X and Y must share a dtype")
+    Bx, L, d = X.shape
+    By, M = Y.shape[0], Y.shape[1]
+    dt = _dtype_code(X)
+    out = torch.empty(Bx, By, dtype=X.dtype, device=X.device)
+    o = _opts(rec, symmetric)
+    ws, nws = _workspace(OP_GRAM, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
+    _check(lib().sigk_gram(X.data_ptr(), Y.data_ptr(), Bx, By, L, M, d, int(dyadic_order), dt,
+                           ctypes.byref(o), out.data_ptr(), _ptr(ws), nws, _stream(X.device)),
+           "sigk_gram")
+    return out
+
+
+def pairs_varlen(Xp: torch.Tensor, x_off: torch.Tensor, Yp: torch.Tensor, y_off: torch.Tensor,
+                 dyadic_order: int, max_len: int, rec: int = REC_AUTO) -> torch.Tensor:
+    """Pairs of uneven lengths: Xp [sum L, d] with int64 offsets x_off [B+1] (on the GPU)."""
+    Xp, Yp = _dev(Xp, "Xp"), _dev(Yp, "Yp")
+    x_off, y_off = _dev(x_off, "x_off"), _dev(y_off, "y_off")
+    if x_off.dtype != torch.int64 or y_off.dtype != torch.int64:
+        raise TypeError("offsets must be int64")
+    B = x_off.shape[0] - 1
+    d = Xp.shape[1]
+    dt = _dtype_code(Xp)
+    out = torch.empty(B, dtype=Xp.dtype, device=Xp.device)
+    o = _opts(rec)
+    ws, nws = _workspace(OP_PAIRS_VARLEN, B, 0, max_len, max_len, d, dyadic_order, dt, o,
+                         Xp.device)
+    _check(lib().sigk_pairs_varlen(Xp.data_ptr(), x_off.data_ptr(), Yp.data_ptr(),
+                                   y_off.data_ptr(), B, d, int(max_len), int(dyadic_order), dt,
+                                   ctypes.byref(o), out.data_ptr(), _ptr(ws), nws,
+                                   _stream(Xp.device)), "sigk_pairs_varlen")
+    return out
+
+
+def version() -> str:
+    return lib().sigk_version().decode()

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/sigk.h declares; host-side argument checks reject bad calls before any
+CUDA work (so these run without a GPU)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sigk.h")
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="needs nvcc to build libsigk.so")
+
+
+def declared_symbols():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sigk_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def libsigk():
+    from paper_2006_14794_gb300 import sigk
+    return sigk.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("sigk_pairs", "sigk_gram", "sigk_pairs_varlen", "sigk_pairs_backward",
+                 "sigk_gram_backward", "sigk_workspace_bytes", "sigk_stream_status",
+                 "sigk_strerror", "sigk_mmd2", "sigk_mmd2_backward"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libsigk):
+    from paper_2006_14794_gb300 import sigk
+    for name in declared_symbols():
+        assert hasattr(libsigk, name), name
+    bound = {n for n, _, _ in sigk.SIGNATURES}
+    assert set(declared_symbols()) == bound
+
+
+def test_exported_symbols_are_c_linkage():
+    from paper_2006_14794_gb300 import build
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (sigk_[a-z0-9_]+)\b", out))
+    assert set(declared_symbols()) <= exported
+
+
+def test_version_and_strerror(libsigk):
+    assert b"sm_103a" in libsigk.sigk_version()
+    for s in range(6):
+        assert libsigk.sigk_strerror(s)
+    assert libsigk.sigk_strerror(99) == b"unknown status"
+
+
+def test_argument_checks_need_no_gpu(libsigk):
+    from paper_2006_14794_gb300 import sigk
+    o = sigk.SigkOpts()
+    P = ctypes.c_void_p(16)   # never dereferenced: the checks fail first
+    # negative batch, zero channels, bad dtype, too-high dyadic order, reserved opts
+    assert libsigk.sigk_pairs(P, P, -1, 4, 4, 2, 0, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EINVAL
+    assert libsigk.sigk_pairs(P, P, 3, 4, 4, 0, 0, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EINVAL
+    assert libsigk.sigk_pairs(P, P, 3, 4, 4, 2, 0, 7, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EINVAL
+    assert libsigk.sigk_pairs(P, P, 3, 4, 4, 2, 9, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EUNSUPPORTED
+    assert libsigk.sigk_pairs(P, P, 3, 4, 4, 2, -1, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EINVAL
+    assert libsigk.sigk_pairs(None, P, 3, 4, 4, 2, 1, 0, None, P, None, 0, None) == sigk.SIGK_EINVAL
+    o.reserved[2] = 1
+    assert libsigk.sigk_gram(P, P, 2, 2, 4, 4, 2, 0, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EINVAL
+    o2 = sigk.SigkOpts(); o2.symmetric = 1
+    assert libsigk.sigk_gram(P, P, 2, 3, 4, 4, 2, 0, 0, ctypes.byref(o2), P, None, 0, None) == sigk.SIGK_EINVAL
+    # empty batches are valid and launch nothing
+    assert libsigk.sigk_pairs(None, None, 0, 4, 4, 2, 0, 0, None, None, None, 0, None) == sigk.SIGK_OK
+    assert libsigk.sigk_gram(None, None, 0, 5, 4, 4, 2, 0, 0, None, None, None, 0, None) == sigk.SIGK_OK
