@@ -77,9 +77,15 @@ const char *sigk_version(void) { return "sigk 0.1 sm_103a"; }
 
 size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int64_t M, int64_t d,
                             int dyadic_order, int dtype, const sigk_opts *opts) {
-    (void)op; (void)B_or_Bx; (void)By; (void)L; (void)M; (void)d; (void)dyadic_order;
-    (void)dtype; (void)opts;
-    return 0;
+    if (common_checks(B_or_Bx, L, M, d, dyadic_order, dtype, opts) != SIGK_OK) return 0;
+    int64_t n_pairs;
+    if (op == SIGK_OP_PAIRS_BACKWARD) n_pairs = B_or_Bx;
+    else if (op == SIGK_OP_GRAM_BACKWARD) n_pairs = (By < 0) ? 0 : B_or_Bx * By;
+    else return 0;   // the forward calls need no workspace
+    if (n_pairs == 0 || L < 2 || M < 2) return 0;
+    int64_t grid, slot, smem;
+    if (!bwd_plain_plan(n_pairs, L, M, d, dyadic_order, dtype, grid, slot, smem)) return 0;
+    return (size_t)(grid * slot);
 }
 
 int sigk_pairs(const void *X, const void *Y, int64_t B, int64_t L, int64_t M, int64_t d,
@@ -159,34 +165,81 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, cons
     return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, (cudaStream_t)stream));
 }
 
+namespace {
+
+int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const void *gout, void *dX,
+                 void *dY, int64_t nX, int64_t nY, void *ws, size_t ws_bytes, cudaStream_t st) {
+    const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+    if (dX && cudaMemsetAsync(dX, 0, (size_t)(nX * es), st) != cudaSuccess) return SIGK_ECUDA;
+    if (dY && cudaMemsetAsync(dY, 0, (size_t)(nY * es), st) != cudaSuccess) return SIGK_ECUDA;
+    if (n_pairs == 0 || src.La < 2 || src.Lb < 2 || (!dX && !dY)) return SIGK_OK;
+    int64_t grid, slot, smem;
+    if (!bwd_plain_plan(n_pairs, src.La, src.Lb, src.d, lam, dtype, grid, slot, smem))
+        return SIGK_EUNSUPPORTED;
+    if (!ws || (int64_t)ws_bytes < grid * slot) return SIGK_ENOMEM_WS;
+    return cuda_status(launch_bwd_plain(src, n_pairs, lam, dtype, gout, dX, dY, ws, grid, slot,
+                                        smem, st));
+}
+
+}  // namespace
+
 int sigk_pairs_backward(const void *grad_out, const void *X, const void *Y, int64_t B, int64_t L,
                         int64_t M, int64_t d, int dyadic_order, int dtype, const sigk_opts *opts,
                         void *dX, void *dY, void *ws, size_t ws_bytes, void *stream) {
-    (void)grad_out; (void)X; (void)Y; (void)B; (void)L; (void)M; (void)d; (void)dyadic_order;
-    (void)dtype; (void)opts; (void)dX; (void)dY; (void)ws; (void)ws_bytes; (void)stream;
-    return SIGK_EUNSUPPORTED;
+    int s = common_checks(B, L, M, d, dyadic_order, dtype, opts);
+    if (s) return s;
+    if (opts && opts->symmetric) return SIGK_EINVAL;
+    if (B == 0) return SIGK_OK;
+    if (!grad_out || !X || !Y) return SIGK_EINVAL;
+    PairSrc src;
+    memset(&src, 0, sizeof(src));
+    src.mode = PM_PAIRS;
+    src.A = X; src.B = Y;
+    src.La = L; src.Lb = M; src.d = d;
+    return run_backward(src, B, dyadic_order, dtype, grad_out, dX, dY, B * L * d, B * M * d, ws,
+                        ws_bytes, (cudaStream_t)stream);
 }
 
 int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64_t Bx, int64_t By,
                        int64_t L, int64_t M, int64_t d, int dyadic_order, int dtype,
                        const sigk_opts *opts, void *dX, void *dY, void *ws, size_t ws_bytes,
                        void *stream) {
-    (void)grad_out; (void)X; (void)Y; (void)Bx; (void)By; (void)L; (void)M; (void)d;
-    (void)dyadic_order; (void)dtype; (void)opts; (void)dX; (void)dY; (void)ws; (void)ws_bytes;
-    (void)stream;
-    return SIGK_EUNSUPPORTED;
+    int s = common_checks(Bx, L, M, d, dyadic_order, dtype, opts);
+    if (s) return s;
+    if (By < 0) return SIGK_EINVAL;
+    if (opts && opts->symmetric) return SIGK_EINVAL;
+    if (Bx == 0 || By == 0) {
+        const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+        if (dX && Bx && cudaMemsetAsync(dX, 0, (size_t)(Bx * L * d * es), (cudaStream_t)stream)) return SIGK_ECUDA;
+        if (dY && By && cudaMemsetAsync(dY, 0, (size_t)(By * M * d * es), (cudaStream_t)stream)) return SIGK_ECUDA;
+        return SIGK_OK;
+    }
+    if (!grad_out || !X || !Y) return SIGK_EINVAL;
+    PairSrc src;
+    memset(&src, 0, sizeof(src));
+    src.mode = PM_GRAM;
+    src.A = X; src.B = Y;
+    src.La = L; src.Lb = M; src.d = d;
+    src.nb = By;
+    src.out_si = By; src.out_sj = 1;
+    return run_backward(src, Bx * By, dyadic_order, dtype, grad_out, dX, dY, Bx * L * d, By * M * d,
+                        ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int sigk_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n, int dtype,
               void *out, void *stream) {
-    (void)Kxx; (void)Kyy; (void)Kxy; (void)m; (void)n; (void)dtype; (void)out; (void)stream;
-    return SIGK_EUNSUPPORTED;
+    if (m < 2 || n < 2) return SIGK_EINVAL;
+    if (dtype != SIGK_F32 && dtype != SIGK_F64) return SIGK_EINVAL;
+    if (!Kxx || !Kyy || !Kxy || !out) return SIGK_EINVAL;
+    return cuda_status(launch_mmd2(Kxx, Kyy, Kxy, m, n, dtype, out, (cudaStream_t)stream));
 }
 
 int sigk_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *gKxx, void *gKyy,
                        void *gKxy, void *stream) {
-    (void)grad; (void)m; (void)n; (void)dtype; (void)gKxx; (void)gKyy; (void)gKxy; (void)stream;
-    return SIGK_EUNSUPPORTED;
+    if (m < 2 || n < 2) return SIGK_EINVAL;
+    if (dtype != SIGK_F32 && dtype != SIGK_F64) return SIGK_EINVAL;
+    if (!grad) return SIGK_EINVAL;
+    return cuda_status(launch_mmd2_backward(grad, m, n, dtype, gKxx, gKyy, gKxy, (cudaStream_t)stream));
 }
 
 int sigk_stream_status(void *stream, void *ws) {

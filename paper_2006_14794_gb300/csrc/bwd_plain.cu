@@ -1,0 +1,269 @@
+// Reverse-mode derivative of the scheme (the paper states no gradient; this
+// is the exact derivative of the discrete scheme of Sec. 3.1), one thread
+// block per pair:
+//
+//  1. G(p,q) = <dx_p, dy_q> into the block's workspace slot;
+//  2. the forward sweep by anti-diagonals (as in fwd_plain.cu), writing every
+//     K(a,b) of the (Ni+1) x (Nj+1) grid into the slot;
+//  3. the adjoint A(a,b) = d k(Ni,Nj) / d K(a,b) by anti-diagonals from the
+//     terminal corner:
+//       A(a,b) = h(a,b+1) A(a,b+1) + h(a+1,b) A(a+1,b) - A(a+1,b+1),
+//     h = 1 + c, out-of-grid terms zero, A(Ni,Nj) = 1; in FP32 in the
+//     difference form (P(a,b) = A(a,b) - A(a,b+1)):
+//       P(a,b) = P(a+1,b) + c(a,b+1) A(a,b+1) + c(a+1,b) A(a+1,b),
+//       A(a,b) = A(a,b+1) + P(a,b),
+//     seeded by a virtual P(Ni+1,Nj) = 1;
+//     every cell adds A(a,b) (K(a,b-1) + K(a-1,b)) to Gbar of its coarse cell;
+//  4. the chain rule: dk/d dx_p = 1/2 4^-lambda sum_q Gbar(p,q) dy_q (and the
+//     mirror for y), scaled by the incoming gradient, then to the points:
+//     dk/dx_i = dk/d dx_{i-1} - dk/d dx_i, added atomically into dX / dY
+//     (a path appears in many pairs of a Gram).
+#include "sigk_internal.cuh"
+
+namespace sigk {
+
+namespace {
+
+constexpr int BWD_THREADS = 512;
+
+struct BwdArgs {
+    PairSrc src;
+    const void *gout;       // [n] incoming gradient, indexed like the forward output
+    void *dA, *dB;          // gradients of the A (row) and B (column) paths, or null
+    unsigned char *ws;      // workspace: n_slots slots of slot_bytes
+    int64_t slot_bytes;
+    int64_t n_pairs;
+    int lam;
+};
+
+template <typename T>
+__device__ __forceinline__ T inc(const T *p, int64_t i, int64_t d, int64_t c) {
+    return p[(i + 1) * d + c] - p[i * d + c];
+}
+
+template <typename T>
+__device__ __forceinline__ void atomic_add(T *p, T v) { atomicAdd(p, v); }
+
+template <typename T, bool QF>
+__global__ void __launch_bounds__(BWD_THREADS) bwd_plain_kernel(BwdArgs a) {
+    extern __shared__ unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    const T scale = (T)0.5 / (T)(1LL << (2 * a.lam));
+    const int lam = a.lam;
+    const int64_t d = a.src.d;
+    unsigned char *slot = a.ws + (int64_t)blockIdx.x * a.slot_bytes;
+    for (int64_t k = blockIdx.x; k < a.n_pairs; k += gridDim.x) {
+        const PairRef pr = pair_ref(a.src, k);
+        const T gk = ((const T *)a.gout)[pr.out0];
+        if (pr.la < 2 || pr.lb < 2) continue;   // k = 1 identically: zero gradient
+        // rows index the shorter path; its gradient goes to the matching output
+        const T *x = (const T *)a.src.A + pr.a_row0 * d;
+        const T *y = (const T *)a.src.B + pr.b_row0 * d;
+        T *dx = a.dA ? (T *)a.dA + pr.a_row0 * d : nullptr;
+        T *dy = a.dB ? (T *)a.dB + pr.b_row0 * d : nullptr;
+        int64_t la = pr.la, lb = pr.lb;
+        if (la > lb) {
+            const T *t = x; x = y; y = t;
+            T *td = dx; dx = dy; dy = td;
+            int64_t tl = la; la = lb; lb = tl;
+        }
+        const int64_t nx = la - 1, ny = lb - 1;
+        const int64_t Ni = nx << lam, Nj = ny << lam, W = Nj + 1;
+        T *Gm = reinterpret_cast<T *>(slot);
+        T *Gb = Gm + nx * ny;
+        T *Kg = Gb + nx * ny;
+
+        // 1. increment Gram, Gbar = 0
+        for (int64_t idx = threadIdx.x; idx < nx * ny; idx += blockDim.x) {
+            const int64_t p = idx / ny, q = idx - (idx / ny) * ny;
+            T g = 0;
+            for (int64_t c = 0; c < d; ++c) g += inc(x, p, d, c) * inc(y, q, d, c);
+            Gm[idx] = g * scale;
+            Gb[idx] = 0;
+        }
+        __syncthreads();
+#define COEF(aa, bb) Gm[(((aa) - 1) >> lam) * ny + (((bb) - 1) >> lam)]
+
+        // 2. forward sweep, K grid into the slot
+        {
+            T *D0 = sm, *D1 = sm + (Ni + 1), *D2 = sm + 2 * (Ni + 1), *D3 = sm + 3 * (Ni + 1);
+            for (int64_t i = threadIdx.x; i <= Ni; i += blockDim.x) {
+                D0[i] = 1; D1[i] = QF ? (T)0 : (T)1; D2[i] = 1;
+                if (QF) D3[i] = 0;
+                Kg[i * W] = 1;   // column 0
+            }
+            for (int64_t b = threadIdx.x; b <= Nj; b += blockDim.x) Kg[b] = 1;   // row 0
+            __syncthreads();
+            for (int64_t n = 2; n <= Ni + Nj; ++n) {
+                const int64_t alo = n - Nj > 0 ? n - Nj : 0;
+                const int64_t ahi = n < Ni ? n : Ni;
+                for (int64_t aa = alo + threadIdx.x; aa <= ahi; aa += blockDim.x) {
+                    const int64_t bb = n - aa;
+                    if (!QF) {
+                        T v = 1;
+                        if (aa > 0 && bb > 0) {
+                            const T c = COEF(aa, bb);
+                            const T kl = D0[aa], ku = D0[aa - 1], kd = D1[aa - 1];
+                            v = kl + ku - kd + c * (kl + ku);
+                            Kg[aa * W + bb] = v;
+                        }
+                        D2[aa] = v;
+                    } else {
+                        T kv = 1, qv = 0;
+                        if (aa > 0 && bb > 0) {
+                            const T c = COEF(aa, bb);
+                            const T kl = D0[aa], ku = D0[aa - 1], qu = D1[aa - 1];
+                            qv = qu + c * (kl + ku);
+                            kv = kl + qv;
+                            Kg[aa * W + bb] = kv;
+                        }
+                        D2[aa] = kv;
+                        D3[aa] = qv;
+                    }
+                }
+                __syncthreads();
+                if (!QF) {
+                    T *t = D1; D1 = D0; D0 = D2; D2 = t;
+                } else {
+                    T *t0 = D0, *t1 = D1;
+                    D0 = D2; D1 = D3; D2 = t0; D3 = t1;
+                }
+            }
+        }
+
+        // 3. adjoint sweep from the terminal corner; diagonals indexed by a in [0, Ni+1]
+        {
+            const int64_t V = Ni + 2;
+            // QF: E0/E1 = A, P on diagonal n+1; E2/E3 = A, P on diagonal n.
+            // plain: E0 = A on n+1, E1 = A on n+2, E2 = A on n.
+            T *E0 = sm, *E1 = sm + V, *E2 = sm + 2 * V, *E3 = sm + 3 * V;
+            for (int64_t i = threadIdx.x; i < V; i += blockDim.x) {
+                E0[i] = 0; E1[i] = 0; E2[i] = 0;
+                if (QF) E3[i] = 0;
+            }
+            __syncthreads();
+            for (int64_t n = Ni + Nj; n >= 2; --n) {
+                const int64_t alo = n - Nj > 1 ? n - Nj : 1;
+                const int64_t ahi = n - 1 < Ni ? n - 1 : Ni;
+                for (int64_t aa = alo + threadIdx.x; aa <= ahi; aa += blockDim.x) {
+                    const int64_t bb = n - aa;
+                    // neighbours on diagonal n+1: (aa, bb+1) at row aa, (aa+1, bb) at row aa+1
+                    const T Ar = (bb + 1 <= Nj) ? E0[aa] : (T)0;
+                    const T Ad = (aa + 1 <= Ni) ? E0[aa + 1] : (T)0;
+                    const T cr = (bb + 1 <= Nj) ? COEF(aa, bb + 1) : (T)0;
+                    const T cd = (aa + 1 <= Ni) ? COEF(aa + 1, bb) : (T)0;
+                    T An;
+                    if (QF) {
+                        T Pd;
+                        if (aa + 1 <= Ni) Pd = E1[aa + 1];
+                        else Pd = (bb == Nj) ? (T)1 : (T)0;   // virtual seed row
+                        const T Pn = Pd + cr * Ar + cd * Ad;
+                        An = Ar + Pn;
+                        E3[aa] = Pn;
+                    } else {
+                        if (aa == Ni && bb == Nj) {
+                            An = 1;
+                        } else {
+                            const T Add = (aa + 1 <= Ni && bb + 1 <= Nj) ? E1[aa + 1] : (T)0;
+                            An = (1 + cr) * Ar + (1 + cd) * Ad - Add;
+                        }
+                    }
+                    E2[aa] = An;
+                    const T s = Kg[aa * W + bb - 1] + Kg[(aa - 1) * W + bb];
+                    atomic_add(&Gb[((aa - 1) >> lam) * ny + ((bb - 1) >> lam)], An * s);
+                }
+                __syncthreads();
+                if (QF) {
+                    T *t0 = E0, *t1 = E1;
+                    E0 = E2; E1 = E3; E2 = t0; E3 = t1;
+                } else {
+                    T *t = E1; E1 = E0; E0 = E2; E2 = t;
+                }
+            }
+        }
+#undef COEF
+
+        // 4. chain rule through G(p,q) = <dx_p, dy_q>, into the points
+        const T f = gk * scale;
+        if (dx) {
+            for (int64_t idx = threadIdx.x; idx < nx * d; idx += blockDim.x) {
+                const int64_t p = idx / d, c = idx - (idx / d) * d;
+                T s = 0;
+                for (int64_t q = 0; q < ny; ++q) s += Gb[p * ny + q] * inc(y, q, d, c);
+                s *= f;
+                atomic_add(&dx[(p + 1) * d + c], s);
+                atomic_add(&dx[p * d + c], -s);
+            }
+        }
+        if (dy) {
+            for (int64_t idx = threadIdx.x; idx < ny * d; idx += blockDim.x) {
+                const int64_t q = idx / d, c = idx - (idx / d) * d;
+                T s = 0;
+                for (int64_t p = 0; p < nx; ++p) s += Gb[p * ny + q] * inc(x, p, d, c);
+                s *= f;
+                atomic_add(&dy[(q + 1) * d + c], s);
+                atomic_add(&dy[q * d + c], -s);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, bool QF>
+int grid_of(int64_t n_pairs, int64_t smem) {
+    auto kern = bwd_plain_kernel<T, QF>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BWD_THREADS, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    if (per_sm < 1) return 0;
+    int64_t g = (int64_t)sms * per_sm;
+    if (g > n_pairs) g = n_pairs;
+    return (int)g;
+}
+
+}  // namespace
+
+// Sizes of the plain backward's workspace for uniform lengths La x Lb:
+// one slot per thread block in flight.
+bool bwd_plain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, int dtype,
+                    int64_t &grid, int64_t &slot_bytes, int64_t &smem) {
+    (void)d;
+    const int64_t la = La < Lb ? La : Lb, lb = La < Lb ? Lb : La;
+    const int64_t nx = la > 1 ? la - 1 : 0, ny = lb > 1 ? lb - 1 : 0;
+    const int64_t Ni = nx << lam, Nj = ny << lam;
+    const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+    slot_bytes = ((2 * nx * ny + (Ni + 1) * (Nj + 1)) * es + 255) / 256 * 256;
+    smem = (dtype == SIGK_F64 ? 3 : 4) * (Ni + 2) * es;
+    if (smem > 227 * 1024) return false;
+    if (n_pairs < 1) { grid = 0; return true; }
+    grid = dtype == SIGK_F64 ? grid_of<double, false>(n_pairs, smem)
+                             : grid_of<float, true>(n_pairs, smem);
+    return grid > 0;
+}
+
+cudaError_t launch_bwd_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype,
+                             const void *gout, void *dA, void *dB, void *ws, int64_t grid,
+                             int64_t slot_bytes, int64_t smem, cudaStream_t st) {
+    BwdArgs a;
+    a.src = src;
+    a.gout = gout;
+    a.dA = dA;
+    a.dB = dB;
+    a.ws = (unsigned char *)ws;
+    a.slot_bytes = slot_bytes;
+    a.n_pairs = n_pairs;
+    a.lam = lam;
+    if (dtype == SIGK_F64)
+        bwd_plain_kernel<double, false><<<(int)grid, BWD_THREADS, (int)smem, st>>>(a);
+    else
+        bwd_plain_kernel<float, true><<<(int)grid, BWD_THREADS, (int)smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sigk

@@ -95,4 +95,15 @@ cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype
 
 cudaError_t launch_fill_one(void *out, int64_t n, int dtype, cudaStream_t st);
 
+bool bwd_plain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, int dtype,
+                    int64_t &grid, int64_t &slot_bytes, int64_t &smem);
+cudaError_t launch_bwd_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype,
+                             const void *gout, void *dA, void *dB, void *ws, int64_t grid,
+                             int64_t slot_bytes, int64_t smem, cudaStream_t st);
+
+cudaError_t launch_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n,
+                        int dtype, void *out, cudaStream_t st);
+cudaError_t launch_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *gKxx,
+                                 void *gKyy, void *gKxy, cudaStream_t st);
+
 }  // namespace sigk

@@ -188,3 +188,113 @@ def pairs_varlen(Xp: torch.Tensor, x_off: torch.Tensor, Yp: torch.Tensor, y_off:
 
 def version() -> str:
     return lib().sigk_version().decode()
+
+
+def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
+                   need_dx: bool = True, need_dy: bool = True):
+    """(dX, dY) with dX[b] = grad_out[b] dk(X_b, Y_b)/dX_b (None when not needed)."""
+    X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
+    B, L, d = X.shape
+    M = Y.shape[1]
+    dt = _dtype_code(X)
+    grad_out = grad_out.to(X.dtype)
+    dX = torch.empty_like(X) if need_dx else None
+    dY = torch.empty_like(Y) if need_dy else None
+    o = _opts()
+    ws, nws = _workspace(OP_PAIRS_BACKWARD, B, 0, L, M, d, dyadic_order, dt, o, X.device)
+    _check(lib().sigk_pairs_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), B, L, M, d,
+                                     int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
+                                     _ptr(ws), nws, _stream(X.device)), "sigk_pairs_backward")
+    return dX, dY
+
+
+def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
+                  need_dx: bool = True, need_dy: bool = True):
+    """(dX, dY): dX[i] = sum_j grad_out[i,j] dk(X_i,Y_j)/dX_i, dY[j] likewise."""
+    X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
+    Bx, L, d = X.shape
+    By, M = Y.shape[0], Y.shape[1]
+    dt = _dtype_code(X)
+    grad_out = grad_out.to(X.dtype).contiguous()
+    dX = torch.empty_like(X) if need_dx else None
+    dY = torch.empty_like(Y) if need_dy else None
+    o = _opts()
+    ws, nws = _workspace(OP_GRAM_BACKWARD, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
+    _check(lib().sigk_gram_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), Bx, By, L, M,
+                                    d, int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
+                                    _ptr(ws), nws, _stream(X.device)), "sigk_gram_backward")
+    return dX, dY
+
+
+def mmd2(Kxx: torch.Tensor, Kyy: torch.Tensor, Kxy: torch.Tensor) -> torch.Tensor:
+    """Unbiased MMD^2 from the three Gram matrices (one element tensor)."""
+    Kxx, Kyy, Kxy = _dev(Kxx, "Kxx"), _dev(Kyy, "Kyy"), _dev(Kxy, "Kxy")
+    m, n = Kxx.shape[0], Kyy.shape[0]
+    out = torch.empty(1, dtype=Kxx.dtype, device=Kxx.device)
+    _check(lib().sigk_mmd2(Kxx.data_ptr(), Kyy.data_ptr(), Kxy.data_ptr(), m, n, _dtype_code(Kxx),
+                           out.data_ptr(), _stream(Kxx.device)), "sigk_mmd2")
+    return out
+
+
+def mmd2_backward(grad: torch.Tensor, m: int, n: int, dtype, device):
+    grad = _dev(grad.reshape(1).to(dtype), "grad")
+    gxx = torch.empty(m, m, dtype=dtype, device=device)
+    gyy = torch.empty(n, n, dtype=dtype, device=device)
+    gxy = torch.empty(m, n, dtype=dtype, device=device)
+    _check(lib().sigk_mmd2_backward(grad.data_ptr(), m, n, _dtype_code(gxx), gxx.data_ptr(),
+                                    gyy.data_ptr(), gxy.data_ptr(), _stream(device)),
+           "sigk_mmd2_backward")
+    return gxx, gyy, gxy
+
+
+class SigKernelPairs(torch.autograd.Function):
+    """k(X_b, Y_b) with the adjoint sweep as its backward."""
+
+    @staticmethod
+    def forward(ctx, X, Y, dyadic_order):
+        ctx.save_for_backward(X, Y)
+        ctx.lam = dyadic_order
+        return pairs(X, Y, dyadic_order)
+
+    @staticmethod
+    def backward(ctx, g):
+        X, Y = ctx.saved_tensors
+        dX, dY = pairs_backward(g, X, Y, ctx.lam, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        return dX, dY, None
+
+
+class SigKernelGram(torch.autograd.Function):
+    """k(X_i, Y_j) with the adjoint sweep as its backward."""
+
+    @staticmethod
+    def forward(ctx, X, Y, dyadic_order):
+        ctx.save_for_backward(X, Y)
+        ctx.lam = dyadic_order
+        return gram(X, Y, dyadic_order)
+
+    @staticmethod
+    def backward(ctx, g):
+        X, Y = ctx.saved_tensors
+        dX, dY = gram_backward(g, X, Y, ctx.lam, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        return dX, dY, None
+
+
+class _MMD2(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, Kxx, Kyy, Kxy):
+        ctx.shape = (Kxx.shape[0], Kyy.shape[0], Kxx.dtype, Kxx.device)
+        return mmd2(Kxx, Kyy, Kxy)
+
+    @staticmethod
+    def backward(ctx, g):
+        m, n, dt, dev = ctx.shape
+        return mmd2_backward(g, m, n, dt, dev)
+
+
+def mmd2_loss(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int) -> torch.Tensor:
+    """Differentiable unbiased MMD^2 between two batches of paths, built from
+    three signature-kernel Gram matrices."""
+    Kxx = SigKernelGram.apply(X, X, dyadic_order)
+    Kyy = SigKernelGram.apply(Y, Y, dyadic_order)
+    Kxy = SigKernelGram.apply(X, Y, dyadic_order)
+    return _MMD2.apply(Kxx, Kyy, Kxy)[0]
