@@ -122,6 +122,26 @@ int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64
                        int dtype, const sigk_opts *opts, void *dX, void *dY, void *ws,
                        size_t ws_bytes, void *stream);
 
+/* sigk_pairs_backward without a workspace argument: the paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory at call time (a process that hands all device memory to its
+ * own pool at start-up, or runs under a fixed memory budget, where one more
+ * cudaMalloc fails or stalls the device).  It allocates nothing: the
+ * per-block scratch of the adjoint sweep lives in a fixed 32 MiB array in the
+ * library's device image, which every GPU that loads the library holds until
+ * the process exits.  Arguments, layout and results are those of
+ * sigk_pairs_backward (dX, dY may be NULL; both are overwritten).
+ * Returns SIGK_EUNSUPPORTED when one pair's scratch,
+ * (2 (L-1)(M-1) + (2^lambda (L-1) + 1)(2^lambda (M-1) + 1)) elements,
+ * exceeds the array.  The first call on each device looks the array's device
+ * address up once (cudaGetSymbolAddress, with that device current); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  No state carries over between calls. */
+int sigk_pairs_backward_noalloc(const void *grad_out, const void *X, const void *Y, int64_t B,
+                                int64_t L, int64_t M, int64_t d, int dyadic_order, int dtype,
+                                void *dX, void *dY, void *stream);
+
 /* The unbiased MMD^2 estimator between two batches (Sec. 3.1.1 names it; the
  * U-statistic form) from the three Gram matrices:
  *   out[0] = sum_{i!=j} Kxx_ij / (m(m-1)) + sum_{i!=j} Kyy_ij / (n(n-1))

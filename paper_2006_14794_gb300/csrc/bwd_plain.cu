@@ -18,6 +18,8 @@
 //     mirror for y), scaled by the incoming gradient, then to the points:
 //     dk/dx_i = dk/d dx_{i-1} - dk/d dx_i, added atomically into dX / dY
 //     (a path appears in many pairs of a Gram).
+#include <string.h>
+
 #include "sigk_internal.cuh"
 
 namespace sigk {
@@ -267,3 +269,81 @@ cudaError_t launch_bwd_plain(const PairSrc &src, int64_t n_pairs, int lam, int d
 }
 
 }  // namespace sigk
+
+// ---------------------------------------------------------------------------
+// sigk_pairs_backward_noalloc: the pairs backward above, with its per-block
+// scratch taken from a fixed array in device memory instead of a caller
+// workspace.  For callers that cannot allocate device memory at call time:
+// a process whose device memory is all handed to its own pool at start-up,
+// or that runs under a fixed memory budget, where an extra allocation fails
+// or stalls the device.  The array is part of the library image: every GPU
+// that loads the library holds SIGK_NOALLOC_SCRATCH_BYTES of it until the
+// process exits.  Every call shares it, so calls that overlap on the GPU
+// (two streams, or two host threads) race and must be serialised by the
+// caller.  Each call writes every scratch element it reads before reading it
+// (the kernel clears its dk/dG accumulator itself), so no state carries over
+// from one call to the next.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#define SIGK_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define SIGK_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char sigk_noalloc_scratch[SIGK_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[SIGK_NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side name is only a stand-in for it).
+int noalloc_scratch(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SIGK_ECUDA;
+    if (dev < 0 || dev >= SIGK_NOALLOC_MAX_DEVICES) return SIGK_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, sigk_noalloc_scratch) != cudaSuccess || !p) return SIGK_ECUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SIGK_OK;
+}
+
+}  // namespace
+
+extern "C" int sigk_pairs_backward_noalloc(const void *grad_out, const void *X, const void *Y,
+                                           int64_t B, int64_t L, int64_t M, int64_t d,
+                                           int dyadic_order, int dtype, void *dX, void *dY,
+                                           void *stream) {
+    using namespace sigk;
+    if (B < 0 || L < 1 || M < 1 || d < 1) return SIGK_EINVAL;
+    if (dtype != SIGK_F32 && dtype != SIGK_F64) return SIGK_EINVAL;
+    if (dyadic_order < 0) return SIGK_EINVAL;
+    if (dyadic_order > 8) return SIGK_EUNSUPPORTED;
+    if (B == 0) return SIGK_OK;
+    if (!grad_out || !X || !Y) return SIGK_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+    int64_t grid = 0, slot = 0, smem = 0;
+    if (!bwd_plain_plan(B, L, M, d, dyadic_order, dtype, grid, slot, smem)) return SIGK_EUNSUPPORTED;
+    if (L >= 2 && M >= 2 && slot > (int64_t)SIGK_NOALLOC_SCRATCH_BYTES)
+        return SIGK_EUNSUPPORTED;   // one pair's scratch does not fit the fixed array
+    void *scratch = nullptr;
+    int s = noalloc_scratch(&scratch);
+    if (s != SIGK_OK) return s;
+    if (dX && cudaMemsetAsync(dX, 0, (size_t)(B * L * d * es), st) != cudaSuccess) return SIGK_ECUDA;
+    if (dY && cudaMemsetAsync(dY, 0, (size_t)(B * M * d * es), st) != cudaSuccess) return SIGK_ECUDA;
+    if (L < 2 || M < 2 || (!dX && !dY)) return SIGK_OK;
+    const int64_t fit = (int64_t)SIGK_NOALLOC_SCRATCH_BYTES / slot;
+    if (grid > fit) grid = fit;
+    PairSrc src;
+    memset(&src, 0, sizeof(src));
+    src.mode = PM_PAIRS;
+    src.A = X; src.B = Y;
+    src.La = L; src.Lb = M; src.d = d;
+    return launch_bwd_plain(src, B, dyadic_order, dtype, grad_out, dX, dY, scratch, grid, slot, smem,
+                            st) == cudaSuccess ? SIGK_OK : SIGK_ECUDA;
+}

@@ -49,6 +49,8 @@ SIGNATURES = [
                                    _vp, _vp, ctypes.c_size_t, _vp]),
     ("sigk_gram_backward", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _int, _int, _vp,
                                   _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    ("sigk_pairs_backward_noalloc", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _int, _int,
+                                           _vp, _vp, _vp]),
     ("sigk_mmd2", _int, [_vp, _vp, _vp, _i64, _i64, _int, _vp, _vp]),
     ("sigk_mmd2_backward", _int, [_vp, _i64, _i64, _int, _vp, _vp, _vp, _vp]),
     ("sigk_stream_status", _int, [_vp, _vp]),
