@@ -58,17 +58,30 @@ typedef enum {
 
 typedef enum { SIGK_F32 = 0, SIGK_F64 = 1 } sigk_dtype;   /* storage AND arithmetic */
 
-/* Recurrence form.  AUTO = the register-chained difference form for f32 and
- * the paper's plain form for f64.  PLAIN = one thread block per pair sweeping
- * the grid's anti-diagonals with the scheme as printed (f64) or its
- * difference form (f32): the baseline the chained kernel is measured against. */
+/* Recurrence form and schedule.
+ *  CHAIN: the register-resident wavefront in the difference form of the
+ *    scheme: for pairs of equal lengths whose refined rows fit one warp
+ *    (2^lambda (L-1) <= 512 for the shorter path) each warp solves a chain
+ *    of pairs; otherwise (long or uneven pairs, wide d) the strip path: the
+ *    grid is cut into 512-row (f32) or 256-row (f64) strips solved by warps
+ *    of a persistent kernel that hand bottom rows on behind bounded waits,
+ *    with the coarse-cell coefficients formed first by a separate kernel.
+ *    It needs workspace (sigk_workspace_bytes) and dyadic_order <= 3.
+ *  PLAIN: one thread block per pair sweeping the anti-diagonals, the scheme
+ *    as printed (f64) or its difference form (f32): the baseline.
+ *  AUTO: CHAIN for f32 (PLAIN when CHAIN has no instance), PLAIN for f64. */
 typedef enum { SIGK_REC_AUTO = 0, SIGK_REC_CHAIN = 1, SIGK_REC_PLAIN = 2 } sigk_rec;
 
 typedef struct {
     int rec;          /* sigk_rec; 0 = auto                                   */
     int symmetric;    /* gram only: X == Y and Bx == By; fills the lower
                          triangle by mirroring the upper one                  */
-    int reserved[6];  /* must be 0                                            */
+    int fault_inject; /* test only, 0 otherwise: 1 makes the first strip of
+                         the first pair of the strip path never publish its
+                         bottom row, so the strip below waits out its bounded
+                         wait (~1 s) and sigk_stream_status reports
+                         SIGK_ETIMEOUT; nothing faults on the device          */
+    int reserved[5];  /* must be 0                                            */
 } sigk_opts;          /* a NULL pointer means all-zero (automatic) options    */
 
 typedef enum {
@@ -156,9 +169,11 @@ int sigk_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int6
 int sigk_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *gKxx,
                        void *gKyy, void *gKxy, void *stream);
 
-/* Status word of the last call that used workspace `ws` on `stream`:
- * synchronises the stream, then returns SIGK_OK or SIGK_ETIMEOUT (a bounded
- * device wait expired).  SIGK_OK when ws is NULL. */
+/* Status word of the last strip-path call that used workspace `ws` on
+ * `stream`: synchronises the stream, then returns SIGK_OK or SIGK_ETIMEOUT
+ * (a bounded device wait expired; that call's results are meaningless).
+ * SIGK_OK when ws is NULL.  Only meaningful after a call that took the strip
+ * path (it needed workspace). */
 int sigk_stream_status(void *stream, void *ws);
 
 /* Static description of a status code (never NULL). */

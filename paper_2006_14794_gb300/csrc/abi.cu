@@ -13,7 +13,8 @@ bool opts_ok(const sigk_opts *o) {
     if (!o) return true;
     if (o->rec < SIGK_REC_AUTO || o->rec > SIGK_REC_PLAIN) return false;
     if (o->symmetric != 0 && o->symmetric != 1) return false;
-    for (int i = 0; i < 6; ++i)
+    if (o->fault_inject != 0 && o->fault_inject != 1) return false;
+    for (int i = 0; i < 5; ++i)
         if (o->reserved[i] != 0) return false;
     return true;
 }
@@ -36,25 +37,83 @@ int cuda_status(cudaError_t e) {
     return SIGK_ECUDA;
 }
 
-// Solve n_pairs pairs described by `src` (uniform lengths La x Lb).
-int run_uniform(PairSrc src, int64_t n_pairs, int lam, int dtype, int rec, void *out,
-                cudaStream_t st) {
-    if (n_pairs == 0) return SIGK_OK;
-    if (src.La < 2 || src.Lb < 2) return cuda_status(launch_fill_one(out, n_pairs, dtype, st));
-    if (dtype == SIGK_F32 && rec != SIGK_REC_PLAIN) {
-        // the chained kernel wants the shorter path on the rows (k(x,y) = k(y,x));
-        // sigk_gram already orders its batches, pairs are swapped here
-        PairSrc s2 = src;
-        if (s2.mode == PM_PAIRS && s2.La > s2.Lb) {
-            const void *t = s2.A; s2.A = s2.B; s2.B = t;
-            int64_t tl = s2.La; s2.La = s2.Lb; s2.Lb = tl;
-        }
-        ChainPlan p;
-        if (chain_plan(n_pairs, s2.La, s2.Lb, s2.d, lam, p))
-            return cuda_status(launch_chain_f32(s2, p, n_pairs, (float *)out, st));
-        if (rec == SIGK_REC_CHAIN) return SIGK_EUNSUPPORTED;
+// Bounded device waits of the strip path: ~1 s at the GB300's 2.07 GHz clock.
+constexpr long long WAIT_CYCLES = 2000000000LL;
+// Largest workspace the strip path asks for; bigger batches run in pieces.
+constexpr int64_t STRIP_WS_CAP = 8LL << 30;
+
+int fault_of(const sigk_opts *o) { return o ? o->fault_inject : 0; }
+
+// Pairs per strip-path launch and the workspace that needs.
+void strip_batch(int64_t n, int64_t la, int64_t lb, int lam, int dtype, int64_t &nb, int64_t &bytes) {
+    nb = n;
+    bytes = strip_workspace_bytes(nb, la, lb, lam, dtype);
+    while (nb > 1 && bytes > STRIP_WS_CAP) {
+        nb = (nb + 1) / 2;
+        bytes = strip_workspace_bytes(nb, la, lb, lam, dtype);
     }
-    return cuda_status(launch_plain(src, n_pairs, lam, dtype, out, st));
+}
+
+enum Path { P_FILL, P_CHAIN, P_STRIP, P_PLAIN };
+
+Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, ChainPlan *cp) {
+    if (src.La < 2 || src.Lb < 2) return P_FILL;
+    if (rec == SIGK_REC_PLAIN) return P_PLAIN;
+    if (dtype == SIGK_F64 && rec != SIGK_REC_CHAIN) return P_PLAIN;
+    if (dtype == SIGK_F32) {
+        int64_t la = src.La, lb = src.Lb;
+        if (src.mode == PM_PAIRS && la > lb) { int64_t t = la; la = lb; lb = t; }
+        ChainPlan p;
+        if (chain_plan(n, la, lb, src.d, lam, p)) {
+            if (cp) *cp = p;
+            return P_CHAIN;
+        }
+    }
+    if (strip_supported(lam, src.d, dtype)) return P_STRIP;
+    return rec == SIGK_REC_CHAIN ? P_FILL /* unsupported */ : P_PLAIN;
+}
+
+int run_strip(PairSrc src, int64_t n, int lam, int dtype, int64_t la, int64_t lb, const sigk_opts *opts,
+              void *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+    int64_t nb, need;
+    strip_batch(n, la, lb, lam, dtype, nb, need);
+    if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        PairSrc s = src;
+        s.kbase = src.kbase + k0;
+        const int64_t m = n - k0 < nb ? n - k0 : nb;
+        cudaError_t e = launch_strip(s, m, lam, dtype, ws, out, WAIT_CYCLES,
+                                     k0 == 0 ? fault_of(opts) : 0, st, la, lb);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return SIGK_OK;
+}
+
+// Solve n_pairs pairs described by `src` (uniform lengths La x Lb).
+int run_uniform(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opts *opts,
+                void *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (n_pairs == 0) return SIGK_OK;
+    const int rec = rec_of(opts);
+    ChainPlan p;
+    switch (choose_uniform(src, n_pairs, lam, dtype, rec, &p)) {
+        case P_FILL:
+            if (src.La < 2 || src.Lb < 2) return cuda_status(launch_fill_one(out, n_pairs, dtype, st));
+            return SIGK_EUNSUPPORTED;
+        case P_CHAIN: {
+            // the chained kernel wants the shorter path on the rows (k(x,y) = k(y,x));
+            // sigk_gram already orders its batches, pairs are swapped here
+            PairSrc s2 = src;
+            if (s2.mode == PM_PAIRS && s2.La > s2.Lb) {
+                const void *t = s2.A; s2.A = s2.B; s2.B = t;
+                int64_t tl = s2.La; s2.La = s2.Lb; s2.Lb = tl;
+            }
+            return cuda_status(launch_chain_f32(s2, p, n_pairs, (float *)out, st));
+        }
+        case P_STRIP:
+            return run_strip(src, n_pairs, lam, dtype, src.La, src.Lb, opts, out, ws, ws_bytes, st);
+        default:
+            return cuda_status(launch_plain(src, n_pairs, lam, dtype, out, st));
+    }
 }
 
 }  // namespace
@@ -79,19 +138,40 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
                             int dyadic_order, int dtype, const sigk_opts *opts) {
     if (common_checks(B_or_Bx, L, M, d, dyadic_order, dtype, opts) != SIGK_OK) return 0;
     int64_t n_pairs;
-    if (op == SIGK_OP_PAIRS_BACKWARD) n_pairs = B_or_Bx;
-    else if (op == SIGK_OP_GRAM_BACKWARD) n_pairs = (By < 0) ? 0 : B_or_Bx * By;
-    else return 0;   // the forward calls need no workspace
+    if (op == SIGK_OP_PAIRS || op == SIGK_OP_PAIRS_VARLEN || op == SIGK_OP_PAIRS_BACKWARD)
+        n_pairs = B_or_Bx;
+    else if (op == SIGK_OP_GRAM || op == SIGK_OP_GRAM_BACKWARD)
+        n_pairs = (By < 0) ? 0 : (opts && opts->symmetric ? B_or_Bx * (B_or_Bx + 1) / 2 : B_or_Bx * By);
+    else
+        return 0;
     if (n_pairs == 0 || L < 2 || M < 2) return 0;
-    int64_t grid, slot, smem;
-    if (!bwd_plain_plan(n_pairs, L, M, d, dyadic_order, dtype, grid, slot, smem)) return 0;
-    return (size_t)(grid * slot);
+    if (op == SIGK_OP_PAIRS_BACKWARD || op == SIGK_OP_GRAM_BACKWARD) {
+        int64_t grid, slot, smem;
+        if (!bwd_plain_plan(n_pairs, L, M, d, dyadic_order, dtype, grid, slot, smem)) return 0;
+        return (size_t)(grid * slot);
+    }
+    int64_t nb, need;
+    if (op == SIGK_OP_PAIRS_VARLEN) {
+        const int rec = rec_of(opts);
+        const bool strip = strip_supported(dyadic_order, d, dtype) &&
+                           (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN);
+        if (!strip) return 0;
+        strip_batch(n_pairs, L, M, dyadic_order, dtype, nb, need);
+        return (size_t)need;
+    }
+    PairSrc src;
+    memset(&src, 0, sizeof(src));
+    src.mode = op == SIGK_OP_PAIRS ? PM_PAIRS : PM_GRAM;
+    src.La = L; src.Lb = M; src.d = d;
+    if (src.mode == PM_GRAM && L > M) { src.La = M; src.Lb = L; }
+    if (choose_uniform(src, n_pairs, dyadic_order, dtype, rec_of(opts), nullptr) != P_STRIP) return 0;
+    strip_batch(n_pairs, L, M, dyadic_order, dtype, nb, need);
+    return (size_t)need;
 }
 
 int sigk_pairs(const void *X, const void *Y, int64_t B, int64_t L, int64_t M, int64_t d,
                int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *ws,
                size_t ws_bytes, void *stream) {
-    (void)ws; (void)ws_bytes;
     int s = common_checks(B, L, M, d, dyadic_order, dtype, opts);
     if (s) return s;
     if (opts && opts->symmetric) return SIGK_EINVAL;
@@ -102,13 +182,12 @@ int sigk_pairs(const void *X, const void *Y, int64_t B, int64_t L, int64_t M, in
     src.mode = PM_PAIRS;
     src.A = X; src.B = Y;
     src.La = L; src.Lb = M; src.d = d;
-    return run_uniform(src, B, dyadic_order, dtype, rec_of(opts), out, (cudaStream_t)stream);
+    return run_uniform(src, B, dyadic_order, dtype, opts, out, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int sigk_gram(const void *X, const void *Y, int64_t Bx, int64_t By, int64_t L, int64_t M,
               int64_t d, int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *ws,
               size_t ws_bytes, void *stream) {
-    (void)ws; (void)ws_bytes;
     int s = common_checks(Bx, L, M, d, dyadic_order, dtype, opts);
     if (s) return s;
     if (By < 0) return SIGK_EINVAL;
@@ -124,7 +203,7 @@ int sigk_gram(const void *X, const void *Y, int64_t Bx, int64_t By, int64_t L, i
         src.A = X; src.B = X;
         src.La = L; src.Lb = L;
         src.nb = Bx;
-        return run_uniform(src, Bx * (Bx + 1) / 2, dyadic_order, dtype, rec_of(opts), out,
+        return run_uniform(src, Bx * (Bx + 1) / 2, dyadic_order, dtype, opts, out, ws, ws_bytes,
                            (cudaStream_t)stream);
     }
     src.mode = PM_GRAM;
@@ -141,20 +220,18 @@ int sigk_gram(const void *X, const void *Y, int64_t Bx, int64_t By, int64_t L, i
         src.nb = Bx;
         src.out_si = 1; src.out_sj = By;
     }
-    return run_uniform(src, Bx * By, dyadic_order, dtype, rec_of(opts), out, (cudaStream_t)stream);
+    return run_uniform(src, Bx * By, dyadic_order, dtype, opts, out, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, const int64_t *y_off,
                       int64_t B, int64_t d, int64_t max_len, int dyadic_order, int dtype,
                       const sigk_opts *opts, void *out, void *ws, size_t ws_bytes, void *stream) {
-    (void)ws; (void)ws_bytes;
     int s = common_checks(B, max_len < 1 ? 1 : max_len, 1, d, dyadic_order, dtype, opts);
     if (s) return s;
     if (max_len < 1) return SIGK_EINVAL;
     if (opts && opts->symmetric) return SIGK_EINVAL;
     if (B == 0) return SIGK_OK;
     if (!Xp || !Yp || !x_off || !y_off || !out) return SIGK_EINVAL;
-    if (opts && opts->rec == SIGK_REC_CHAIN) return SIGK_EUNSUPPORTED;
     PairSrc src;
     memset(&src, 0, sizeof(src));
     src.mode = PM_VARLEN;
@@ -162,6 +239,13 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, cons
     src.a_off = x_off; src.b_off = y_off;
     src.La = max_len; src.Lb = max_len;
     src.d = d;
+    const int rec = rec_of(opts);
+    const bool strip = strip_supported(dyadic_order, d, dtype) &&
+                       (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN);
+    if (strip)
+        return run_strip(src, B, dyadic_order, dtype, max_len, max_len, opts, out, ws, ws_bytes,
+                         (cudaStream_t)stream);
+    if (rec == SIGK_REC_CHAIN) return SIGK_EUNSUPPORTED;
     return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, (cudaStream_t)stream));
 }
 
@@ -243,9 +327,11 @@ int sigk_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *
 }
 
 int sigk_stream_status(void *stream, void *ws) {
-    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SIGK_ECUDA;
-    (void)ws;
-    return SIGK_OK;
+    if (!ws) return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? SIGK_OK : SIGK_ECUDA;
+    int st = 0;
+    const int r = read_status_word(ws, (cudaStream_t)stream, &st);
+    if (r != SIGK_OK) return r;
+    return st == SIGK_ETIMEOUT ? SIGK_ETIMEOUT : SIGK_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,530 @@
+// Forward sweep for long or uneven pairs: the grid of each pair is cut into
+// horizontal strips of 32*R refined rows; a persistent kernel hands strips to
+// warps in pair order from an atomic counter, and the strips of one pair form
+// a wavefront across warps (Sec. 3.1.1's anti-diagonal parallelism carried
+// from one warp to the next): each strip publishes its bottom row in chunks of
+// CW columns behind release flags, and the strip below consumes them.
+//
+// Inside a strip the work is laid out as in the chained kernel: lane l holds
+// rows R*l .. R*l+R-1, row r of lane l works on column t - R*l - r + 1 at step
+// t, and the scheme runs in its difference form
+//   Q(a,b) = Q(a-1,b) + c (K(a,b-1) + K(a-1,b)),  K(a,b) = K(a,b-1) + Q(a,b),
+// c = 1/2 4^-lambda <dx_p, dy_q> (Sec. 3.1, scheme and remark).
+//
+// Coefficients: a separate kernel forms every coarse-cell coefficient c(p,q)
+// once and stores each strip's coefficients anti-diagonal-major, d(n, P) =
+// c(p, n - P) for the strip's coarse rows P: at window n every group of every
+// lane of the warp needs exactly diagonal n (the skew of the wavefront makes
+// p + q the same for all of them), so a lane reads its NG coefficients as
+// contiguous vectors and the warp reads one contiguous slice.  Virtual rows
+// (above a pair's first row, padding the first strip) and columns outside the
+// grid have c = 0, which keeps K = 1 and Q = 0 exactly there.
+//
+// Waits are bounded: a consumer that does not see its chunk within
+// `wait_cycles` records SIGK_ETIMEOUT in the status word and carries on
+// (its result is then meaningless and the call reports the timeout).
+#include <string.h>
+
+#include "sigk_internal.cuh"
+
+namespace sigk {
+
+namespace {
+
+constexpr int STRIP_WARPS = 2;   // warps per CTA
+constexpr int CW = 32;           // columns per published chunk of a bottom row
+
+// ---- planning: per-pair sizes and offsets, computed on the device ----------
+
+struct PairPlan {
+    int64_t a_row0, b_row0;  // first point row of the row path and column path
+    int64_t c_off;           // start of this pair's coefficient blocks (elements)
+    int64_t bnd_off;         // start of its bottom-row buffers (elements)
+    int64_t flag_off;        // start of its chunk flags
+    int64_t strip_base;      // global index of its first strip
+    int64_t out0, out1;
+    int ni, nj;              // refined rows / columns
+    int nx, ny;              // coarse rows / columns
+    int ns, pad;             // strips, virtual refined rows above the first
+    int nw;                  // windows (coefficient diagonals) per strip
+    int swap;                // 1: the rows refine the B path (src.B), columns the A path
+};
+
+template <int R, int LAM>
+__global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *totals) {
+    constexpr int S = 1 << LAM;
+    constexpr int TH = 32 * R;
+    constexpr int CP = 32 * (R / S);
+    __shared__ int64_t part[4][1024];
+    // pass 1: per-pair shape
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const PairRef pr = pair_ref(src, k);
+        PairPlan p;
+        // rows refine the longer path: more strips, more warps per pair
+        const bool swap = pr.lb > pr.la;
+        const int64_t la = swap ? pr.lb : pr.la, lb = swap ? pr.la : pr.lb;
+        p.a_row0 = swap ? pr.b_row0 : pr.a_row0;
+        p.b_row0 = swap ? pr.a_row0 : pr.b_row0;
+        p.out0 = pr.out0;
+        p.out1 = pr.out1;
+        p.swap = swap ? 1 : 0;
+        p.nx = la > 1 ? (int)(la - 1) : 0;
+        p.ny = lb > 1 ? (int)(lb - 1) : 0;
+        p.ni = p.nx << LAM;
+        p.nj = p.ny << LAM;
+        p.ns = (p.nx > 0 && p.ny > 0) ? (p.ni + TH - 1) / TH : 0;
+        p.pad = p.ns * TH - p.ni;
+        p.nw = ((p.nj + TH - 2) >> LAM) + 2;
+        p.c_off = (int64_t)p.ns * p.nw * CP;        // sizes for now, offsets after the scan
+        p.bnd_off = p.ns > 0 ? (int64_t)(p.ns - 1) * p.nj * 2 : 0;
+        p.flag_off = p.ns > 0 ? p.ns - 1 : 0;
+        p.strip_base = p.ns;
+        plan[k] = p;
+    }
+    __syncthreads();
+    // pass 2: exclusive scans of the four sizes, in chunks of blockDim
+    int64_t run[4] = {0, 0, 0, 0};
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t k = base + threadIdx.x;
+        int64_t v[4] = {0, 0, 0, 0};
+        if (k < n) {
+            v[0] = plan[k].c_off;
+            v[1] = plan[k].bnd_off;
+            v[2] = plan[k].flag_off;
+            v[3] = plan[k].strip_base;
+        }
+        for (int j = 0; j < 4; ++j) part[j][threadIdx.x] = v[j];
+        __syncthreads();
+        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+            int64_t t[4];
+            for (int j = 0; j < 4; ++j)
+                t[j] = (int)threadIdx.x >= off ? part[j][threadIdx.x - off] : 0;
+            __syncthreads();
+            for (int j = 0; j < 4; ++j) part[j][threadIdx.x] += t[j];
+            __syncthreads();
+        }
+        if (k < n) {
+            plan[k].c_off = run[0] + part[0][threadIdx.x] - v[0];
+            plan[k].bnd_off = run[1] + part[1][threadIdx.x] - v[1];
+            plan[k].flag_off = run[2] + part[2][threadIdx.x] - v[2];
+            plan[k].strip_base = run[3] + part[3][threadIdx.x] - v[3];
+        }
+        for (int j = 0; j < 4; ++j) run[j] += part[j][blockDim.x - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 4; ++j) totals[j] = run[j];
+}
+
+// ---- coefficients: each strip's anti-diagonal-major block -----------------
+// One CTA computes 64 diagonals x 64 strip rows at a time; each thread a 4 x 4
+// block of (diagonal, row), whose 4 rows and 7 columns come from shared
+// memory as float4 channel vectors.
+
+constexpr int GT = 64;
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> { using type = float4; };
+template <>
+struct Vec4<double> { using type = double4; };
+
+template <typename T, int R, int LAM>
+__global__ void __launch_bounds__(256) coef_kernel(PairSrc src, const PairPlan *plan,
+                                                   int64_t n_pairs, const int64_t *totals,
+                                                   T *cbuf) {
+    constexpr int S = 1 << LAM;
+    constexpr int NG = R / S;
+    constexpr int CP = 32 * NG;      // coarse rows per strip (incl. virtual)
+    using V4 = typename Vec4<T>::type;
+    extern __shared__ unsigned char smraw[];
+    const int64_t d = src.d;
+    const int D4 = (int)((d + 3) / 4);
+    const int RS = D4 + 1;   // row stride in V4 units (padding against bank conflicts)
+    V4 *sx = reinterpret_cast<V4 *>(smraw);          // GT rows of dx
+    V4 *sy = sx + GT * RS;                            // 2*GT-1 rows of dy
+    const T scale = (T)0.5 / (T)(1LL << (2 * LAM));
+    const int64_t total_strips = totals[3];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int64_t gs = blockIdx.x; gs < total_strips; gs += gridDim.x) {
+        // the pair of this strip: last plan with strip_base <= gs
+        int64_t lo = 0, hi = n_pairs - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (plan[mid].strip_base <= gs) lo = mid; else hi = mid - 1;
+        }
+        const PairPlan pp = plan[lo];
+        const int s = (int)(gs - pp.strip_base);
+        // a_row0 / b_row0 are offsets into the row / column path's own array
+        const T *x = (const T *)(pp.swap ? src.B : src.A) + pp.a_row0 * d;
+        const T *y = (const T *)(pp.swap ? src.A : src.B) + pp.b_row0 * d;
+        T *blk = cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
+        const int prow0 = s * CP - (pp.pad >> LAM);   // real coarse row of strip row 0
+        for (int W0 = 0; W0 < pp.nw; W0 += GT) {
+            for (int P0 = 0; P0 < CP; P0 += GT) {
+                __syncthreads();
+                // stage dx rows P0 .. P0+GT-1 and dy rows q = W - P in [W0-P0-GT+1, W0-P0+GT-1]
+                for (int u = threadIdx.x; u < GT * D4; u += blockDim.x) {
+                    const int i = u / D4, c4 = u - (u / D4) * D4;
+                    const int p = prow0 + P0 + i;
+                    T v[4] = {0, 0, 0, 0};
+                    if (p >= 0 && p < pp.nx)
+                        for (int e = 0; e < 4; ++e) {
+                            const int64_t c = c4 * 4 + e;
+                            if (c < d) v[e] = x[(p + 1) * d + c] - x[p * d + c];
+                        }
+                    V4 w; w.x = v[0]; w.y = v[1]; w.z = v[2]; w.w = v[3];
+                    sx[i * RS + c4] = w;
+                }
+                const int q0 = W0 - P0 - (GT - 1);
+                for (int u = threadIdx.x; u < (2 * GT - 1) * D4; u += blockDim.x) {
+                    const int i = u / D4, c4 = u - (u / D4) * D4;
+                    const int q = q0 + i;
+                    T v[4] = {0, 0, 0, 0};
+                    if (q >= 0 && q < pp.ny)
+                        for (int e = 0; e < 4; ++e) {
+                            const int64_t c = c4 * 4 + e;
+                            if (c < d) v[e] = y[(q + 1) * d + c] - y[q * d + c];
+                        }
+                    V4 w; w.x = v[0]; w.y = v[1]; w.z = v[2]; w.w = v[3];
+                    sy[i * RS + c4] = w;
+                }
+                __syncthreads();
+                // thread block: diagonals W0 + 4tx + i, rows P0 + 4ty + j
+                T acc[4][4];
+                for (int i = 0; i < 4; ++i)
+                    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+                for (int c4 = 0; c4 < D4; ++c4) {
+                    V4 xv[4], yv[7];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) xv[j] = sx[(4 * ty + j) * RS + c4];
+#pragma unroll
+                    for (int m = 0; m < 7; ++m) {
+                        // q - q0 = (W0 + 4tx + i) - (P0 + 4ty + j) - q0, i - j = m - 3
+                        yv[m] = sy[(4 * tx - 4 * ty + m - 3 + (GT - 1)) * RS + c4];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const V4 a = xv[j], b = yv[i - j + 3];
+                            acc[i][j] += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+                        }
+                }
+                for (int i = 0; i < 4; ++i) {
+                    const int W = W0 + 4 * tx + i;
+                    if (W >= pp.nw) continue;
+                    for (int j = 0; j < 4; ++j) {
+                        const int P = P0 + 4 * ty + j;
+                        if (P >= CP) continue;
+                        const int p = prow0 + P, q = W - P;
+                        const bool ok = p >= 0 && p < pp.nx && q >= 0 && q < pp.ny;
+                        blk[(int64_t)W * CP + P] = ok ? acc[i][j] * scale : (T)0;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---- the persistent strip sweep --------------------------------------------
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T>
+struct StripArgs {
+    PairSrc src;
+    const PairPlan *plan;
+    const int64_t *totals;
+    int64_t n_pairs;
+    const T *cbuf;
+    T *bnd;
+    int *flags;
+    int *counter;
+    int *status;
+    T *out;
+    long long wait_cycles;
+    int fault_inject;   // 1: the first strip of the first pair never publishes
+};
+
+template <typename T, int R, int LAM>
+__global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a) {
+    constexpr int S = 1 << LAM;
+    constexpr int NG = R / S;
+    constexpr int CP = 32 * NG;
+    constexpr int TH = 32 * R;
+    static_assert(R % S == 0, "whole coarse rows per lane");
+    __shared__ T topbuf[STRIP_WARPS][CW * 2];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    T *tb = topbuf[warp];
+    const int64_t total_strips = a.totals[3];
+
+    for (;;) {
+        int64_t gs = 0;
+        if (lane == 0) gs = atomicAdd((unsigned long long *)a.counter, 1ULL);
+        gs = __shfl_sync(FULL, gs, 0);
+        if (gs >= total_strips) break;
+        int64_t lo = 0, hi = a.n_pairs - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (a.plan[mid].strip_base <= gs) lo = mid; else hi = mid - 1;
+        }
+        const PairPlan pp = a.plan[lo];
+        const int s = (int)(gs - pp.strip_base);
+        const int nj = pp.nj;
+        const T *blk = a.cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
+        const T *top = s > 0 ? a.bnd + pp.bnd_off + (int64_t)(s - 1) * nj * 2 : nullptr;
+        T *bot = s < pp.ns - 1 ? a.bnd + pp.bnd_off + (int64_t)s * nj * 2 : nullptr;
+        const int *ftop = s > 0 ? a.flags + pp.flag_off + (s - 1) : nullptr;
+        int *fbot = s < pp.ns - 1 ? a.flags + pp.flag_off + s : nullptr;
+        const bool mute = a.fault_inject && lo == 0 && s == 0;
+        const int nchunk = (nj + CW - 1) / CW;
+        const int tend = nj + TH - 1;   // steps until the last row leaves column nj
+
+        T K[R], Q[R], cn[NG], co[NG], cx[NG];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { K[r] = 1; Q[r] = 0; }
+#pragma unroll
+        for (int g = 0; g < NG; ++g) { cn[g] = 0; co[g] = 0; cx[g] = blk[lane * NG + g]; }
+        T pK = 1, pQ = 0;
+        bool timed_out = false;
+
+        for (int w = 0; w * S < tend; ++w) {
+            // coefficients of diagonal w (prefetched), prefetch diagonal w + 1
+#pragma unroll
+            for (int g = 0; g < NG; ++g) { co[g] = cn[g]; cn[g] = cx[g]; }
+            if (w + 1 < pp.nw) {
+#pragma unroll
+                for (int g = 0; g < NG; ++g) cx[g] = blk[(int64_t)(w + 1) * CP + lane * NG + g];
+            }
+#pragma unroll
+            for (int jj = 0; jj < S; ++jj) {
+                const int t = w * S + jj;
+                if (t >= tend) break;
+                if (top && (t % CW) == 0 && t < nj) {
+                    // stage the top row's chunk t/CW (columns t+1 .. t+CW) once published
+                    const int need = t / CW + 1;
+                    if (!timed_out) {
+                        const long long t0 = clock64();
+                        while (ld_acquire(ftop) < need) {
+                            if (clock64() - t0 > a.wait_cycles) {
+                                timed_out = true;
+                                if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
+                                break;
+                            }
+                            __nanosleep(200);
+                        }
+                    }
+                    __syncwarp();
+                    for (int u = lane; u < CW * 2; u += 32) {
+                        const int col = t + u / 2;   // zero-based column
+                        tb[u] = col < nj ? top[(int64_t)col * 2 + (u & 1)] : (T)0;
+                    }
+                    __syncwarp();
+                }
+                // lane 0's row 0 is at column t + 1 now
+                if (lane == 0 && top) {
+                    if (t < nj) { pK = tb[(t % CW) * 2]; pQ = tb[(t % CW) * 2 + 1]; }
+                }
+                T shK = 0, shQ = 0;
+#pragma unroll
+                for (int r = R - 1; r >= 0; --r) {
+                    const int g = r / S, sr = r % S;
+                    const T c = (jj >= sr) ? cn[g] : co[g];
+                    const T kl = K[r];
+                    const T ku = r > 0 ? K[r > 0 ? r - 1 : 0] : pK;
+                    const T qu = r > 0 ? Q[r > 0 ? r - 1 : 0] : pQ;
+                    const T qn = qu + c * (kl + ku);
+                    K[r] = kl + qn;
+                    Q[r] = qn;
+                    if (r == R - 1) {
+                        shK = __shfl_up_sync(FULL, K[r], 1);
+                        shQ = __shfl_up_sync(FULL, Q[r], 1);
+                        if (lane == 31 && bot && !mute) {
+                            const int col = t - (TH - 1);   // zero-based column of the last row
+                            if (col >= 0 && col < nj) {
+                                bot[(int64_t)col * 2] = K[r];
+                                bot[(int64_t)col * 2 + 1] = Q[r];
+                                if ((col + 1) % CW == 0 || col + 1 == nj) {
+                                    __threadfence();
+                                    st_release(fbot, (col + CW) / CW);
+                                }
+                            }
+                        }
+                    }
+                }
+                if (lane == 0) {
+                    if (!top) { pK = 1; pQ = 0; }
+                } else {
+                    pK = shK;
+                    pQ = shQ;
+                }
+            }
+        }
+        if (s == pp.ns - 1 && lane == 31) {
+            a.out[pp.out0] = K[R - 1];
+            if (pp.out1 >= 0) a.out[pp.out1] = K[R - 1];
+        }
+    }
+}
+
+template <typename T>
+__global__ void strip_trivial_kernel(PairSrc src, int64_t n, T *out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const PairRef pr = pair_ref(src, k);
+        if (pr.la < 2 || pr.lb < 2) {
+            out[pr.out0] = (T)1;
+            if (pr.out1 >= 0) out[pr.out1] = (T)1;
+        }
+    }
+}
+
+}  // namespace
+
+// ---- host side --------------------------------------------------------------
+
+// Workspace layout (bytes, each part 256-aligned):
+//   status (int) | counter (u64) | totals (4 x i64) | plan [n] | flags [nflags]
+//   | coefficients [ncoef] | bottom rows [nbnd]
+struct StripLayout {
+    int64_t plan, flags, coef, bnd, total;
+};
+
+static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
+
+// Upper bounds from the longest path length (exact for uniform lengths).
+static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R, int lam,
+                                int64_t es) {
+    const int64_t S = 1LL << lam, TH = 32LL * R, CP = 32LL * (R / S);
+    const int64_t lx = max_la > max_lb ? max_la : max_lb, ly = max_la > max_lb ? max_lb : max_la;
+    const int64_t ni = (lx - 1) * S, nj = (ly - 1) * S;
+    const int64_t ns = (ni + TH - 1) / TH;
+    const int64_t nw = ((nj + TH - 2) >> lam) + 2;
+    StripLayout L;
+    int64_t off = 256 + 256 + 256;
+    L.plan = off;
+    off += al256(n * (int64_t)sizeof(PairPlan));
+    L.flags = off;
+    off += al256(n * (ns > 1 ? ns - 1 : 0) * 4 + 4);
+    L.coef = off;
+    off += al256(n * ns * nw * CP * es);
+    L.bnd = off;
+    off += al256(n * (ns > 1 ? ns - 1 : 0) * nj * 2 * es + es);
+    L.total = off;
+    return L;
+}
+
+static int strip_R(int dtype, int lam) {
+    (void)lam;
+    return dtype == SIGK_F64 ? 8 : 16;
+}
+
+// dyadic orders 0..3, and channel counts whose coefficient tile fits shared
+// memory (d <= 64 in f64, 128 in f32)
+bool strip_supported(int lam, int64_t d, int dtype) {
+    if (lam < 0 || lam > 3 || d < 1) return false;
+    const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+    return (3 * GT - 1) * ((d + 3) / 4 + 1) * 4 * es <= 200 * 1024;
+}
+
+int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype) {
+    if (lam < 0 || lam > 3 || n <= 0) return 0;
+    const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+    return strip_layout(n, max_la, max_lb, strip_R(dtype, lam), lam, es).total;
+}
+
+template <typename T, int R, int LAM>
+static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *out,
+                                  long long wait_cycles, int fault_inject, cudaStream_t st,
+                                  int64_t max_la, int64_t max_lb) {
+    const StripLayout L = strip_layout(n, max_la, max_lb, R, LAM, (int64_t)sizeof(T));
+    unsigned char *w = (unsigned char *)ws;
+    int *status = (int *)w;
+    int *counter = (int *)(w + 256);
+    int64_t *totals = (int64_t *)(w + 512);
+    PairPlan *plan = (PairPlan *)(w + L.plan);
+    int *flags = (int *)(w + L.flags);
+    T *cbuf = (T *)(w + L.coef);
+    T *bnd = (T *)(w + L.bnd);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w, 0, 768, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(flags, 0, (size_t)(L.coef - L.flags), st)) != cudaSuccess) return e;
+    strip_trivial_kernel<T><<<64, 256, 0, st>>>(src, n, out);
+    plan_kernel<R, LAM><<<1, 1024, 0, st>>>(src, n, plan, totals);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    {
+        const int D4 = (int)((src.d + 3) / 4);
+        const int smem = (GT + 2 * GT - 1) * (D4 + 1) * 4 * (int)sizeof(T);
+        auto ck = coef_kernel<T, R, LAM>;
+        if ((e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+            cudaSuccess)
+            return e;
+        ck<<<sms * 4, 256, smem, st>>>(src, plan, n, totals, cbuf);
+    }
+    StripArgs<T> a;
+    a.src = src;
+    a.plan = plan;
+    a.totals = totals;
+    a.n_pairs = n;
+    a.cbuf = cbuf;
+    a.bnd = bnd;
+    a.flags = flags;
+    a.counter = counter;
+    a.status = status;
+    a.out = out;
+    a.wait_cycles = wait_cycles;
+    a.fault_inject = fault_inject;
+    auto sk = strip_kernel<T, R, LAM>;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk, STRIP_WARPS * 32, 0)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // every CTA resident at once: a strip only ever waits on an earlier strip,
+    // which some resident warp holds
+    sk<<<sms * per_sm, STRIP_WARPS * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void *ws, void *out,
+                         long long wait_cycles, int fault_inject, cudaStream_t st, int64_t max_la,
+                         int64_t max_lb) {
+    if (n <= 0) return cudaSuccess;
+    if (dtype == SIGK_F64) {
+        switch (lam) {
+            case 0: return launch_strip_t<double, 8, 0>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+            case 1: return launch_strip_t<double, 8, 1>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+            case 2: return launch_strip_t<double, 8, 2>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+            case 3: return launch_strip_t<double, 8, 3>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+        }
+    } else {
+        switch (lam) {
+            case 0: return launch_strip_t<float, 16, 0>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+            case 1: return launch_strip_t<float, 16, 1>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+            case 2: return launch_strip_t<float, 16, 2>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+            case 3: return launch_strip_t<float, 16, 3>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+int read_status_word(void *ws, cudaStream_t st, int *status) {
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SIGK_ECUDA;
+    if (cudaMemcpy(status, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SIGK_ECUDA;
+    return SIGK_OK;
+}
+
+}  // namespace sigk

@@ -23,6 +23,7 @@ struct PairSrc {
     int64_t La, Lb;         // uniform lengths (ignored for varlen)
     int64_t d;
     int64_t out_si, out_sj; // gram: out index = i*out_si + j*out_sj
+    int64_t kbase;          // pair k of a launch is pair kbase + k of the call
 };
 
 struct PairRef {
@@ -47,6 +48,7 @@ __host__ __device__ inline void sym_index(int64_t k, int64_t n, int64_t &i, int6
 
 __host__ __device__ inline PairRef pair_ref(const PairSrc &s, int64_t k) {
     PairRef r;
+    k += s.kbase;
     r.out1 = -1;
     if (s.mode == PM_PAIRS) {
         r.a_row0 = k * s.La; r.la = s.La;
@@ -100,6 +102,13 @@ bool bwd_plain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam,
 cudaError_t launch_bwd_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype,
                              const void *gout, void *dA, void *dB, void *ws, int64_t grid,
                              int64_t slot_bytes, int64_t smem, cudaStream_t st);
+
+bool strip_supported(int lam, int64_t d, int dtype);
+int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype);
+cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void *ws, void *out,
+                         long long wait_cycles, int fault_inject, cudaStream_t st, int64_t max_la,
+                         int64_t max_lb);
+int read_status_word(void *ws, cudaStream_t st, int *status);
 
 cudaError_t launch_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n,
                         int dtype, void *out, cudaStream_t st);

@@ -30,7 +30,7 @@ _int = ctypes.c_int
 
 
 class SigkOpts(ctypes.Structure):
-    _fields_ = [("rec", _int), ("symmetric", _int), ("reserved", _int * 6)]
+    _fields_ = [("rec", _int), ("symmetric", _int), ("fault_inject", _int), ("reserved", _int * 5)]
 
 
 _lib = None
@@ -109,11 +109,20 @@ def _stream(dev) -> int:
     return torch.cuda.current_stream(dev).cuda_stream
 
 
-def _opts(rec: int = REC_AUTO, symmetric: bool = False):
+def _opts(rec: int = REC_AUTO, symmetric: bool = False, fault_inject: bool = False):
     o = SigkOpts()
     o.rec = int(rec)
     o.symmetric = 1 if symmetric else 0
+    o.fault_inject = 1 if fault_inject else 0
     return o
+
+
+def _status(ws, device):
+    """Reads the workspace status word after the stream drains; raises on a
+    device-side timeout."""
+    if ws is None:
+        return
+    _check(lib().sigk_stream_status(_stream(device), ws.data_ptr()), "device status")
 
 
 def _ptr(t):
@@ -127,8 +136,11 @@ def _workspace(op, b, b2, L, M, d, lam, dt, o, device):
     return torch.empty(n, dtype=torch.uint8, device=device), n
 
 
-def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO) -> torch.Tensor:
-    """out[b] = k(X_b, Y_b).  X: [B, L, d], Y: [B, M, d] (same dtype, same CUDA device)."""
+def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO,
+          check_status: bool = False, fault_inject: bool = False) -> torch.Tensor:
+    """out[b] = k(X_b, Y_b).  X: [B, L, d], Y: [B, M, d] (same dtype, same CUDA device).
+    check_status: synchronise and raise SigkError if a bounded device wait
+    expired (strip path only).  fault_inject: test switch of sigk_opts."""
     X, Y = _dev(X, "X"), _dev(Y, "Y")
     if X.dim() != 3 or Y.dim() != 3 or X.shape[0] != Y.shape[0] or X.shape[2] != Y.shape[2]:
         raise ValueError("pairs wants X [B,L,d] and Y [B,M,d]")
@@ -138,16 +150,18 @@ def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AU
     M = Y.shape[1]
     dt = _dtype_code(X)
     out = torch.empty(B, dtype=X.dtype, device=X.device)
-    o = _opts(rec)
+    o = _opts(rec, fault_inject=fault_inject)
     ws, nws = _workspace(OP_PAIRS, B, 0, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_pairs(X.data_ptr(), Y.data_ptr(), B, L, M, d, int(dyadic_order), dt,
                             ctypes.byref(o), out.data_ptr(), _ptr(ws), nws, _stream(X.device)),
            "sigk_pairs")
+    if check_status:
+        _status(ws, X.device)
     return out
 
 
 def gram(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO,
-         symmetric: bool = False) -> torch.Tensor:
+         symmetric: bool = False, check_status: bool = False) -> torch.Tensor:
     """out[i, j] = k(X_i, Y_j).  With symmetric=True, Y must be X and only the
     upper triangle is solved (then mirrored)."""
     X, Y = _dev(X, "X"), _dev(Y, "Y")
@@ -164,11 +178,14 @@ def gram(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUT
     _check(lib().sigk_gram(X.data_ptr(), Y.data_ptr(), Bx, By, L, M, d, int(dyadic_order), dt,
                            ctypes.byref(o), out.data_ptr(), _ptr(ws), nws, _stream(X.device)),
            "sigk_gram")
+    if check_status:
+        _status(ws, X.device)
     return out
 
 
 def pairs_varlen(Xp: torch.Tensor, x_off: torch.Tensor, Yp: torch.Tensor, y_off: torch.Tensor,
-                 dyadic_order: int, max_len: int, rec: int = REC_AUTO) -> torch.Tensor:
+                 dyadic_order: int, max_len: int, rec: int = REC_AUTO, check_status: bool = False,
+                 fault_inject: bool = False) -> torch.Tensor:
     """Pairs of uneven lengths: Xp [sum L, d] with int64 offsets x_off [B+1] (on the GPU)."""
     Xp, Yp = _dev(Xp, "Xp"), _dev(Yp, "Yp")
     x_off, y_off = _dev(x_off, "x_off"), _dev(y_off, "y_off")
@@ -178,13 +195,15 @@ def pairs_varlen(Xp: torch.Tensor, x_off: torch.Tensor, Yp: torch.Tensor, y_off:
     d = Xp.shape[1]
     dt = _dtype_code(Xp)
     out = torch.empty(B, dtype=Xp.dtype, device=Xp.device)
-    o = _opts(rec)
+    o = _opts(rec, fault_inject=fault_inject)
     ws, nws = _workspace(OP_PAIRS_VARLEN, B, 0, max_len, max_len, d, dyadic_order, dt, o,
                          Xp.device)
     _check(lib().sigk_pairs_varlen(Xp.data_ptr(), x_off.data_ptr(), Yp.data_ptr(),
                                    y_off.data_ptr(), B, d, int(max_len), int(dyadic_order), dt,
                                    ctypes.byref(o), out.data_ptr(), _ptr(ws), nws,
                                    _stream(Xp.device)), "sigk_pairs_varlen")
+    if check_status:
+        _status(ws, Xp.device)
     return out
 
 

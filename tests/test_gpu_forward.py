@@ -182,6 +182,7 @@ def test_varlen_pairs_match_oracle():
 
 
 def test_chain_requested_but_unsupported_is_an_error():
-    X = to_dev(np.zeros((2, 5, 40)))   # 40 channels: no chained instance
+    # dyadic order 4: neither the chained kernel nor the strip path has an instance
+    X = to_dev(np.zeros((2, 5, 40)))
     with pytest.raises(S().SigkError):
-        S().pairs(X, X, 0, rec=S().REC_CHAIN)
+        S().pairs(X, X, 4, rec=S().REC_CHAIN)

@@ -1,0 +1,89 @@
+"""The strip path (persistent strip wavefront with bounded waits, coarse-cell
+coefficients formed by their own kernel): parity with the FP64 oracle on long,
+uneven and wide pairs, and its failure detection."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2006_14794_gb300 import inputs
+from tests.gpu_util import need_gpu, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+    from paper_2006_14794_gb300 import sigk
+    sigk.lib()
+
+
+def S():
+    from paper_2006_14794_gb300 import sigk
+    return sigk
+
+
+@pytest.mark.parametrize("lam,L,M,d", [
+    (0, 700, 300, 3),     # 699 rows: two strips, the first with virtual rows
+    (1, 400, 520, 8),     # rows refine the longer (second) path
+    (2, 150, 160, 4),
+    (3, 70, 90, 5),
+    (1, 120, 130, 32),    # wide d: no chained instance
+    (0, 1600, 40, 2),     # many strips, narrow grid
+])
+def test_strip_pairs_match_oracle(lam, L, M, d):
+    B = 5
+    X32, X64 = inputs.f32(inputs.random_paths(1100 + lam, B, L, d, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(1200 + lam, B, M, d, time_channel=True))
+    ref = oracle.pairs(X64, Y64, lam)
+    got = S().pairs(to_dev(X32), to_dev(Y32), lam, check_status=True).cpu().numpy()
+    assert rel_err(got, ref) <= 1e-5
+    g64 = S().pairs(to_dev(X64, torch.float64), to_dev(Y64, torch.float64), lam, rec=S().REC_CHAIN,
+                    check_status=True).cpu().numpy()
+    assert rel_err(g64, ref) <= 1e-11
+
+
+def test_strip_gram_uneven_batches():
+    lam = 1
+    X32, X64 = inputs.f32(inputs.random_paths(1300, 4, 300, 6, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(1301, 3, 270, 6, time_channel=True))
+    ref = oracle.gram(X64, Y64, lam)
+    got = S().gram(to_dev(X32), to_dev(Y32), lam, check_status=True).cpu().numpy()
+    assert rel_err(got, ref) <= 1e-5
+    got = S().gram(to_dev(Y32), to_dev(X32), lam, check_status=True).cpu().numpy()
+    assert rel_err(got, ref.T) <= 1e-5
+
+
+def test_strip_varlen_with_degenerate_pairs():
+    rng = np.random.default_rng(14)
+    lens_x = [1, 2, 17, 700, 33, 1, 300]
+    lens_y = [5, 1, 2, 40, 600, 9, 300]
+    d = 3
+    xs = [inputs.random_paths(1400 + i, 1, L, d)[0] for i, L in enumerate(lens_x)]
+    ys = [inputs.random_paths(1500 + i, 1, M, d)[0] for i, M in enumerate(lens_y)]
+    xo = np.concatenate([[0], np.cumsum(lens_x)]).astype(np.int64)
+    yo = np.concatenate([[0], np.cumsum(lens_y)]).astype(np.int64)
+    X32, X64 = inputs.f32(np.concatenate(xs))
+    Y32, Y64 = inputs.f32(np.concatenate(ys))
+    for lam in (0, 1, 2):
+        ref = oracle.pairs_varlen(X64, xo, Y64, yo, lam)
+        got = S().pairs_varlen(to_dev(X32), torch.as_tensor(xo).cuda(), to_dev(Y32),
+                               torch.as_tensor(yo).cuda(), lam, max_len=700,
+                               check_status=True).cpu().numpy()
+        assert rel_err(got, ref) <= 1e-5
+        assert got[0] == 1.0 and got[1] == 1.0 and got[5] == 1.0
+
+
+def test_injected_fault_is_reported_as_timeout():
+    # the first strip of the first pair never publishes its bottom row: the
+    # strip below waits out its bounded wait (~1 s) and the call reports
+    # SIGK_ETIMEOUT; the context stays usable
+    X = to_dev(inputs.random_paths(1600, 2, 1100, 3))
+    with pytest.raises(S().SigkError) as e:
+        S().pairs(X, X, 0, check_status=True, fault_inject=True)
+    assert "timed out" in str(e.value)
+    # the next call on the same context is fine
+    ref = oracle.pairs(X.double().cpu().numpy(), X.double().cpu().numpy(), 0)
+    got = S().pairs(X, X, 0, check_status=True).cpu().numpy()
+    assert rel_err(got, ref) <= 1e-5
