@@ -352,6 +352,162 @@ def run_gpu(args):
     return 0
 
 
+# ---- other workloads (parity cases of the test suite, measured here on request) ----
+
+def _extra_setup(name):
+    """(description, step(), cells per step, flop per step, oracle-sample fn, h2d/d2h info)."""
+    import torch
+    from paper_2006_14794_gb300 import inputs, sigk
+    import oracle
+    if name == "uneven4096":
+        w = inputs.uneven_pairs()
+        lam = w["dyadic_order"]
+        X32, X64 = inputs.f32(w["Xp"])
+        Y32, Y64 = inputs.f32(w["Yp"])
+        xo, yo = w["x_off"], w["y_off"]
+        lx, ly = xo[1:] - xo[:-1], yo[1:] - yo[:-1]
+        cells = int(np.sum(((lx - 1) << lam) * ((ly - 1) << lam)))
+        coarse = int(np.sum((lx - 1) * (ly - 1)))
+        Xd, Yd = torch.from_numpy(X32).cuda(), torch.from_numpy(Y32).cuda()
+        xod, yod = torch.as_tensor(xo).cuda(), torch.as_tensor(yo).cuda()
+
+        def step():
+            return sigk.pairs_varlen(Xd, xod, Yd, yod, lam, max_len=512)
+
+        def host_step(hx, hy, hxo, hyo, ho):
+            o = sigk.pairs_varlen(hx.cuda(non_blocking=True), hxo.cuda(non_blocking=True),
+                                  hy.cuda(non_blocking=True), hyo.cuda(non_blocking=True), lam, max_len=512)
+            ho.copy_(o, non_blocking=True)
+
+        def oracle_rate(budget):
+            t0 = time.perf_counter(); done = 0; cc = 0
+            while time.perf_counter() - t0 < budget and done < 4096:
+                b = np.arange(done, min(done + 64, 4096))
+                sub_x = np.concatenate([X64[xo[i]:xo[i + 1]] for i in b])
+                sub_y = np.concatenate([Y64[yo[i]:yo[i + 1]] for i in b])
+                sxo = np.concatenate([[0], np.cumsum(lx[b])]); syo = np.concatenate([[0], np.cumsum(ly[b])])
+                oracle.pairs_varlen(sub_x, sxo, sub_y, syo, lam)
+                cc += int(np.sum(((lx[b] - 1) << lam) * ((ly[b] - 1) << lam))); done = b[-1] + 1
+            return cc / (time.perf_counter() - t0), "%d of 4096 pairs" % done
+        host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
+                torch.as_tensor(xo).pin_memory(), torch.as_tensor(yo).pin_memory(),
+                torch.empty(4096).pin_memory())
+        return ("4096 pairs, L,M ~ U{16..512}, d=16 walks, dyadic order 1, fp32", step, cells,
+                3 * cells + 2 * 16 * coarse, oracle_rate, host_step, host,
+                X32.nbytes + Y32.nbytes + xo.nbytes + yo.nbytes, 4096 * 4)
+    if name.startswith("long64"):
+        lam = int(name[-1])
+        w = inputs.long_pairs()
+        X32, X64 = inputs.f32(w["X"])
+        Y32, Y64 = inputs.f32(w["Y"])
+        n = (4095 << lam)
+        cells = 64 * n * n
+        Xd, Yd = torch.from_numpy(X32).cuda(), torch.from_numpy(Y32).cuda()
+
+        def step():
+            return sigk.pairs(Xd, Yd, lam)
+
+        def host_step(hx, hy, ho):
+            o = sigk.pairs(hx.cuda(non_blocking=True), hy.cuda(non_blocking=True), lam)
+            ho.copy_(o, non_blocking=True)
+
+        def oracle_rate(budget):
+            t0 = time.perf_counter()
+            oracle.pairs(X64[:1], Y64[:1], lam)
+            return n * n / (time.perf_counter() - t0), "1 of 64 pairs (single thread: one pair)"
+        host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
+                torch.empty(64).pin_memory())
+        return ("64 pairs, L=M=4096, d=64 time-augmented walks, dyadic order %d, fp32" % lam, step,
+                cells, 3 * cells + 2 * 64 * 64 * 4095 * 4095, oracle_rate, host_step, host,
+                X32.nbytes + Y32.nbytes, 64 * 4)
+    if name == "mmd128":
+        w = inputs.mmd_batches()
+        lam = w["dyadic_order"]
+        X32, X64 = inputs.f32(w["X"])
+        Y32, Y64 = inputs.f32(w["Y"])
+        npairs = 128 * 128 * 3
+        cells = npairs * (510 * 510)
+        Yd = torch.from_numpy(Y32).cuda()
+        Xd = torch.from_numpy(X32).cuda()
+
+        def step():
+            X = Xd.clone().requires_grad_(True)
+            v = sigk.mmd2_loss(X, Yd, lam)
+            v.backward()
+            return X.grad
+
+        def host_step(hx, hy, hg):
+            X = hx.cuda(non_blocking=True).requires_grad_(True)
+            v = sigk.mmd2_loss(X, hy.cuda(non_blocking=True), lam)
+            v.backward()
+            hg.copy_(X.grad, non_blocking=True)
+
+        def oracle_rate(budget):
+            t0 = time.perf_counter()
+            oracle.gram(X64[:4], Y64, lam)
+            return 4 * 128 * 510 * 510 / (time.perf_counter() - t0), "4 x 128 pairs of Kxy (forward only)"
+        host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
+                torch.empty(X32.shape).pin_memory())
+        return ("MMD^2 128 vs 128, L=256, d=32 walks + drift, dyadic order 1, loss + dL/dX, fp32 "
+                "(value counts the forward cells of Kxx, Kyy, Kxy as full 128x128 Grams)", step, cells,
+                3 * cells, oracle_rate, host_step, host, X32.nbytes + Y32.nbytes, X32.nbytes)
+    raise SystemExit("unknown workload " + name)
+
+
+def run_extra(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2006_14794_gb300 import sigk
+    sigk.lib()
+    desc, step, cells, flop, oracle_rate, host_step, host, h2d, d2h = _extra_setup(args.workload)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(st)
+        step()
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        host_step(*host)
+    e1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    props = torch.cuda.get_device_properties(0)
+    peak_tf, mhz, src = fp32_peak_tflops(props.multi_processor_count)
+    ach = flop / (ms * 1e-3) / 1e12
+    rate, sample = oracle_rate(args.cpu_seconds)
+    import oracle
+    line = {
+        "metric": METRIC, "value": cells / (ms * 1e-3), "unit": "cells/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "l2": "flushed (256 MB write) before each step"},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": ach / peak_tf, "traffic": None,
+                     "note": "whole call (all of its kernels) over CUDA events"},
+        "clocks": clk,
+        "e2e": {"value": cells / (e2e_ms * 1e-3), "unit": "cells/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+        "cpu_baseline": {"value": rate, "unit": "cells/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -361,11 +517,15 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", default="gram256",
+                    choices=["gram256", "uneven4096", "long64_l0", "long64_l1", "mmd128"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "gram256":
+        return run_extra(args)
     return run_gpu(args)
 
 

@@ -45,12 +45,15 @@ constexpr int64_t STRIP_WS_CAP = 8LL << 30;
 int fault_of(const sigk_opts *o) { return o ? o->fault_inject : 0; }
 
 // Pairs per strip-path launch and the workspace that needs.
-void strip_batch(int64_t n, int64_t la, int64_t lb, int lam, int dtype, int64_t &nb, int64_t &bytes) {
+void strip_batch(const PairSrc &src, int64_t n, int64_t la, int64_t lb, int lam, int dtype,
+                 int64_t &nb, int64_t &bytes) {
+    int64_t ra, rb;
+    src_rows(src, n, ra, rb);
     nb = n;
-    bytes = strip_workspace_bytes(nb, la, lb, lam, dtype);
+    bytes = strip_workspace_bytes(nb, la, lb, lam, dtype, ra, rb, src.d);
     while (nb > 1 && bytes > STRIP_WS_CAP) {
         nb = (nb + 1) / 2;
-        bytes = strip_workspace_bytes(nb, la, lb, lam, dtype);
+        bytes = strip_workspace_bytes(nb, la, lb, lam, dtype, ra, rb, src.d);
     }
 }
 
@@ -75,15 +78,16 @@ Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, 
 
 int run_strip(PairSrc src, int64_t n, int lam, int dtype, int64_t la, int64_t lb, const sigk_opts *opts,
               void *out, void *ws, size_t ws_bytes, cudaStream_t st) {
-    int64_t nb, need;
-    strip_batch(n, la, lb, lam, dtype, nb, need);
+    int64_t nb, need, ra, rb;
+    strip_batch(src, n, la, lb, lam, dtype, nb, need);
+    src_rows(src, n, ra, rb);
     if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         PairSrc s = src;
         s.kbase = src.kbase + k0;
         const int64_t m = n - k0 < nb ? n - k0 : nb;
         cudaError_t e = launch_strip(s, m, lam, dtype, ws, out, WAIT_CYCLES,
-                                     k0 == 0 ? fault_of(opts) : 0, st, la, lb);
+                                     k0 == 0 ? fault_of(opts) : 0, st, la, lb, ra, rb);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return SIGK_OK;
@@ -156,16 +160,31 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         const bool strip = strip_supported(dyadic_order, d, dtype) &&
                            (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN);
         if (!strip) return 0;
-        strip_batch(n_pairs, L, M, dyadic_order, dtype, nb, need);
+        PairSrc vs;
+        memset(&vs, 0, sizeof(vs));
+        vs.mode = PM_VARLEN;
+        vs.La = L; vs.Lb = M; vs.d = d;
+        strip_batch(vs, n_pairs, L, M, dyadic_order, dtype, nb, need);
         return (size_t)need;
     }
     PairSrc src;
     memset(&src, 0, sizeof(src));
-    src.mode = op == SIGK_OP_PAIRS ? PM_PAIRS : PM_GRAM;
-    src.La = L; src.Lb = M; src.d = d;
-    if (src.mode == PM_GRAM && L > M) { src.La = M; src.Lb = L; }
+    src.d = d;
+    if (op == SIGK_OP_PAIRS) {
+        src.mode = PM_PAIRS;
+        src.La = L; src.Lb = M;
+    } else if (opts && opts->symmetric) {
+        src.mode = PM_GRAM_SYM;
+        src.La = L; src.Lb = L;
+        src.nb = B_or_Bx;
+    } else {
+        // the same orientation sigk_gram picks
+        src.mode = PM_GRAM;
+        src.La = L <= M ? L : M; src.Lb = L <= M ? M : L;
+        src.nb = L <= M ? By : B_or_Bx;
+    }
     if (choose_uniform(src, n_pairs, dyadic_order, dtype, rec_of(opts), nullptr) != P_STRIP) return 0;
-    strip_batch(n_pairs, L, M, dyadic_order, dtype, nb, need);
+    strip_batch(src, n_pairs, src.La, src.Lb, dyadic_order, dtype, nb, need);
     return (size_t)need;
 }
 

@@ -116,10 +116,31 @@ __global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *tot
         for (int j = 0; j < 4; ++j) totals[j] = run[j];
 }
 
+// ---- increments: dx_r = x_{r+1} - x_r for every point row r of a path array,
+// stored at row r (the last row of each path is never read), channels padded
+// to a multiple of 4 with zeros so that a row is a run of 16-byte vectors.
+
+template <typename T>
+__global__ void inc_kernel(const T *pts, int64_t rows, const int64_t *rows_dev, int64_t d,
+                           int64_t D4, T *inc) {
+    // rows_dev: the exact row count of a packed array (its last offset), when
+    // the host only knows an upper bound
+    if (rows_dev && *rows_dev < rows) rows = *rows_dev;
+    const int64_t total = rows * D4 * 4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / (D4 * 4), c = i - (i / (D4 * 4)) * (D4 * 4);
+        inc[i] = (c < d && r + 1 < rows) ? pts[(r + 1) * d + c] - pts[r * d + c] : (T)0;
+    }
+}
+
 // ---- coefficients: each strip's anti-diagonal-major block -----------------
-// One CTA computes 64 diagonals x 64 strip rows at a time; each thread a 4 x 4
-// block of (diagonal, row), whose 4 rows and 7 columns come from shared
-// memory as float4 channel vectors.
+// One CTA computes 64 diagonals x 64 strip rows at a time; thread (tx, ty)
+// computes rows P0 + tx + 16 j and diagonals W0 + ty + 16 i (i, j < 4): its
+// 16 outputs need 4 row-path and 7 column-path increment vectors (the column
+// q = W - P depends on i - j only), read from shared memory as 4-channel
+// vectors; adjacent threads read adjacent rows, which an odd row stride keeps
+// free of bank conflicts, and store adjacent outputs.
 
 constexpr int GT = 64;
 
@@ -133,7 +154,7 @@ struct Vec4<double> { using type = double4; };
 template <typename T, int R, int LAM>
 __global__ void __launch_bounds__(256) coef_kernel(PairSrc src, const PairPlan *plan,
                                                    int64_t n_pairs, const int64_t *totals,
-                                                   T *cbuf) {
+                                                   const T *incA, const T *incB, T *cbuf) {
     constexpr int S = 1 << LAM;
     constexpr int NG = R / S;
     constexpr int CP = 32 * NG;      // coarse rows per strip (incl. virtual)
@@ -141,7 +162,7 @@ __global__ void __launch_bounds__(256) coef_kernel(PairSrc src, const PairPlan *
     extern __shared__ unsigned char smraw[];
     const int64_t d = src.d;
     const int D4 = (int)((d + 3) / 4);
-    const int RS = D4 + 1;   // row stride in V4 units (padding against bank conflicts)
+    const int RS = D4 | 1;   // odd row stride in V4 units: conflict-free row-adjacent reads
     V4 *sx = reinterpret_cast<V4 *>(smraw);          // GT rows of dx
     V4 *sy = sx + GT * RS;                            // 2*GT-1 rows of dy
     const T scale = (T)0.5 / (T)(1LL << (2 * LAM));
@@ -157,66 +178,75 @@ __global__ void __launch_bounds__(256) coef_kernel(PairSrc src, const PairPlan *
         const PairPlan pp = plan[lo];
         const int s = (int)(gs - pp.strip_base);
         // a_row0 / b_row0 are offsets into the row / column path's own array
-        const T *x = (const T *)(pp.swap ? src.B : src.A) + pp.a_row0 * d;
-        const T *y = (const T *)(pp.swap ? src.A : src.B) + pp.b_row0 * d;
+        const V4 *x = reinterpret_cast<const V4 *>(pp.swap ? incB : incA) + pp.a_row0 * D4;
+        const V4 *y = reinterpret_cast<const V4 *>(pp.swap ? incA : incB) + pp.b_row0 * D4;
         T *blk = cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
         const int prow0 = s * CP - (pp.pad >> LAM);   // real coarse row of strip row 0
         for (int W0 = 0; W0 < pp.nw; W0 += GT) {
             for (int P0 = 0; P0 < CP; P0 += GT) {
+                // a tile whose rows are all virtual or whose columns q = W - P all
+                // fall outside the grid holds zeros only
+                const int plo = prow0 + P0 > 0 ? prow0 + P0 : 0;
+                const int phi = prow0 + P0 + GT - 1 < pp.nx - 1 ? prow0 + P0 + GT - 1 : pp.nx - 1;
+                const int qlo = W0 - (P0 + GT - 1), qhi = W0 + GT - 1 - P0;
+                if (plo > phi || qhi < 0 || qlo >= pp.ny) {
+                    for (int u = threadIdx.x; u < GT * GT; u += blockDim.x) {
+                        const int W = W0 + u / GT, P = P0 + (u % GT);
+                        if (W < pp.nw && P < CP) blk[(int64_t)W * CP + P] = (T)0;
+                    }
+                    continue;
+                }
                 __syncthreads();
                 // stage dx rows P0 .. P0+GT-1 and dy rows q = W - P in [W0-P0-GT+1, W0-P0+GT-1]
                 for (int u = threadIdx.x; u < GT * D4; u += blockDim.x) {
                     const int i = u / D4, c4 = u - (u / D4) * D4;
                     const int p = prow0 + P0 + i;
-                    T v[4] = {0, 0, 0, 0};
-                    if (p >= 0 && p < pp.nx)
-                        for (int e = 0; e < 4; ++e) {
-                            const int64_t c = c4 * 4 + e;
-                            if (c < d) v[e] = x[(p + 1) * d + c] - x[p * d + c];
-                        }
-                    V4 w; w.x = v[0]; w.y = v[1]; w.z = v[2]; w.w = v[3];
+                    V4 w;
+                    if (p >= 0 && p < pp.nx) w = x[(int64_t)p * D4 + c4];
+                    else { w.x = 0; w.y = 0; w.z = 0; w.w = 0; }
                     sx[i * RS + c4] = w;
                 }
                 const int q0 = W0 - P0 - (GT - 1);
                 for (int u = threadIdx.x; u < (2 * GT - 1) * D4; u += blockDim.x) {
                     const int i = u / D4, c4 = u - (u / D4) * D4;
                     const int q = q0 + i;
-                    T v[4] = {0, 0, 0, 0};
-                    if (q >= 0 && q < pp.ny)
-                        for (int e = 0; e < 4; ++e) {
-                            const int64_t c = c4 * 4 + e;
-                            if (c < d) v[e] = y[(q + 1) * d + c] - y[q * d + c];
-                        }
-                    V4 w; w.x = v[0]; w.y = v[1]; w.z = v[2]; w.w = v[3];
+                    V4 w;
+                    if (q >= 0 && q < pp.ny) w = y[(int64_t)q * D4 + c4];
+                    else { w.x = 0; w.y = 0; w.z = 0; w.w = 0; }
                     sy[i * RS + c4] = w;
                 }
                 __syncthreads();
-                // thread block: diagonals W0 + 4tx + i, rows P0 + 4ty + j
+                // thread (tx, ty): rows P0 + tx + 16 j, diagonals W0 + ty + 16 i
                 T acc[4][4];
                 for (int i = 0; i < 4; ++i)
                     for (int j = 0; j < 4; ++j) acc[i][j] = 0;
                 for (int c4 = 0; c4 < D4; ++c4) {
                     V4 xv[4], yv[7];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) xv[j] = sx[(4 * ty + j) * RS + c4];
+                    for (int j = 0; j < 4; ++j) xv[j] = sx[(tx + 16 * j) * RS + c4];
 #pragma unroll
                     for (int m = 0; m < 7; ++m) {
-                        // q - q0 = (W0 + 4tx + i) - (P0 + 4ty + j) - q0, i - j = m - 3
-                        yv[m] = sy[(4 * tx - 4 * ty + m - 3 + (GT - 1)) * RS + c4];
+                        // q - q0 = (ty + 16 i) - (tx + 16 j) + GT - 1, with i - j = m - 3
+                        yv[m] = sy[(ty - tx + 16 * (m - 3) + (GT - 1)) * RS + c4];
                     }
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const V4 a = xv[j], b = yv[i - j + 3];
-                            acc[i][j] += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+                            T t = acc[i][j];
+                            t = fma(a.x, b.x, t);
+                            t = fma(a.y, b.y, t);
+                            t = fma(a.z, b.z, t);
+                            t = fma(a.w, b.w, t);
+                            acc[i][j] = t;
                         }
                 }
                 for (int i = 0; i < 4; ++i) {
-                    const int W = W0 + 4 * tx + i;
+                    const int W = W0 + ty + 16 * i;
                     if (W >= pp.nw) continue;
                     for (int j = 0; j < 4; ++j) {
-                        const int P = P0 + 4 * ty + j;
+                        const int P = P0 + tx + 16 * j;
                         if (P >= CP) continue;
                         const int p = prow0 + P, q = W - P;
                         const bool ok = p >= 0 && p < pp.nx && q >= 0 && q < pp.ny;
@@ -256,6 +286,30 @@ struct StripArgs {
     int fault_inject;   // 1: the first strip of the first pair never publishes
 };
 
+constexpr int NRING = 8;   // coefficient diagonals in flight per warp
+
+// Each lane copies its own NG coefficients of a diagonal into the warp's ring
+// (cp.async, so the copy needs no registers), NRING - 1 diagonals ahead.
+template <typename T, int NG>
+__device__ __forceinline__ void ring_fetch(T *slot, const T *src) {
+    constexpr int BYTES = NG * (int)sizeof(T);
+    constexpr int CH = BYTES >= 16 ? 16 : BYTES;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
+#pragma unroll
+    for (int o = 0; o < BYTES; o += CH) {
+        if (CH == 16)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + o),
+                         "l"((const char *)src + o) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst + o),
+                         "l"((const char *)src + o), "n"(CH) : "memory");
+    }
+}
+
+__device__ __forceinline__ void ring_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void ring_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <typename T, int R, int LAM>
 __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a) {
     constexpr int S = 1 << LAM;
@@ -264,6 +318,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
     constexpr int TH = 32 * R;
     static_assert(R % S == 0, "whole coarse rows per lane");
     __shared__ T topbuf[STRIP_WARPS][CW * 2];
+    __shared__ __align__(16) T ring[STRIP_WARPS][NRING][CP];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     T *tb = topbuf[warp];
@@ -291,22 +346,33 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
         const int nchunk = (nj + CW - 1) / CW;
         const int tend = nj + TH - 1;   // steps until the last row leaves column nj
 
-        T K[R], Q[R], cn[NG], co[NG], cx[NG];
+        T K[R], Q[R], cn[NG], co[NG];
 #pragma unroll
         for (int r = 0; r < R; ++r) { K[r] = 1; Q[r] = 0; }
 #pragma unroll
-        for (int g = 0; g < NG; ++g) { cn[g] = 0; co[g] = 0; cx[g] = blk[lane * NG + g]; }
+        for (int g = 0; g < NG; ++g) { cn[g] = 0; co[g] = 0; }
         T pK = 1, pQ = 0;
         bool timed_out = false;
+        // fill the ring with diagonals 0 .. NRING-2 (one commit group each)
+#pragma unroll
+        for (int k = 0; k < NRING - 1; ++k) {
+            if (k < pp.nw) ring_fetch<T, NG>(&ring[warp][k][lane * NG], blk + (int64_t)k * CP + lane * NG);
+            ring_commit();
+        }
 
         for (int w = 0; w * S < tend; ++w) {
-            // coefficients of diagonal w (prefetched), prefetch diagonal w + 1
-#pragma unroll
-            for (int g = 0; g < NG; ++g) { co[g] = cn[g]; cn[g] = cx[g]; }
-            if (w + 1 < pp.nw) {
-#pragma unroll
-                for (int g = 0; g < NG; ++g) cx[g] = blk[(int64_t)(w + 1) * CP + lane * NG + g];
+            // diagonal w + NRING - 1 into the slot diagonal w - 1 used; then
+            // diagonal w has landed (at most NRING - 1 newer groups in flight)
+            {
+                const int k = w + NRING - 1;
+                if (k < pp.nw)
+                    ring_fetch<T, NG>(&ring[warp][k % NRING][lane * NG], blk + (int64_t)k * CP + lane * NG);
+                ring_commit();
+                ring_wait<NRING - 1>();
             }
+            const T *cw = &ring[warp][w % NRING][lane * NG];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) { co[g] = cn[g]; cn[g] = cw[g]; }
 #pragma unroll
             for (int jj = 0; jj < S; ++jj) {
                 const int t = w * S + jj;
@@ -371,6 +437,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                 }
             }
         }
+        ring_wait<0>();
         if (s == pp.ns - 1 && lane == 31) {
             a.out[pp.out0] = K[R - 1];
             if (pp.out1 >= 0) a.out[pp.out1] = K[R - 1];
@@ -398,14 +465,14 @@ __global__ void strip_trivial_kernel(PairSrc src, int64_t n, T *out) {
 //   status (int) | counter (u64) | totals (4 x i64) | plan [n] | flags [nflags]
 //   | coefficients [ncoef] | bottom rows [nbnd]
 struct StripLayout {
-    int64_t plan, flags, coef, bnd, total;
+    int64_t plan, flags, coef, bnd, incA, incB, total;
 };
 
 static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
 
 // Upper bounds from the longest path length (exact for uniform lengths).
 static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R, int lam,
-                                int64_t es) {
+                                int64_t es, int64_t rowsA, int64_t rowsB, int64_t D4) {
     const int64_t S = 1LL << lam, TH = 32LL * R, CP = 32LL * (R / S);
     const int64_t lx = max_la > max_lb ? max_la : max_lb, ly = max_la > max_lb ? max_lb : max_la;
     const int64_t ni = (lx - 1) * S, nj = (ly - 1) * S;
@@ -421,6 +488,10 @@ static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R
     off += al256(n * ns * nw * CP * es);
     L.bnd = off;
     off += al256(n * (ns > 1 ? ns - 1 : 0) * nj * 2 * es + es);
+    L.incA = off;
+    off += al256(rowsA * D4 * 4 * es);
+    L.incB = off;
+    off += al256(rowsB * D4 * 4 * es);
     L.total = off;
     return L;
 }
@@ -438,17 +509,20 @@ bool strip_supported(int lam, int64_t d, int dtype) {
     return (3 * GT - 1) * ((d + 3) / 4 + 1) * 4 * es <= 200 * 1024;
 }
 
-int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype) {
+int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype,
+                              int64_t rowsA, int64_t rowsB, int64_t d) {
     if (lam < 0 || lam > 3 || n <= 0) return 0;
     const int64_t es = dtype == SIGK_F64 ? 8 : 4;
-    return strip_layout(n, max_la, max_lb, strip_R(dtype, lam), lam, es).total;
+    return strip_layout(n, max_la, max_lb, strip_R(dtype, lam), lam, es, rowsA, rowsB, (d + 3) / 4)
+        .total;
 }
 
 template <typename T, int R, int LAM>
 static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *out,
                                   long long wait_cycles, int fault_inject, cudaStream_t st,
-                                  int64_t max_la, int64_t max_lb) {
-    const StripLayout L = strip_layout(n, max_la, max_lb, R, LAM, (int64_t)sizeof(T));
+                                  int64_t max_la, int64_t max_lb, int64_t rowsA, int64_t rowsB) {
+    const int64_t D4 = (src.d + 3) / 4;
+    const StripLayout L = strip_layout(n, max_la, max_lb, R, LAM, (int64_t)sizeof(T), rowsA, rowsB, D4);
     unsigned char *w = (unsigned char *)ws;
     int *status = (int *)w;
     int *counter = (int *)(w + 256);
@@ -457,10 +531,26 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     int *flags = (int *)(w + L.flags);
     T *cbuf = (T *)(w + L.coef);
     T *bnd = (T *)(w + L.bnd);
+    T *incA = (T *)(w + L.incA);
+    T *incB = (T *)(w + L.incB);
     cudaError_t e;
     if ((e = cudaMemsetAsync(w, 0, 768, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(flags, 0, (size_t)(L.coef - L.flags), st)) != cudaSuccess) return e;
     strip_trivial_kernel<T><<<64, 256, 0, st>>>(src, n, out);
+    {
+        const bool packed = src.mode == PM_VARLEN;
+        const int64_t na = rowsA * D4 * 4, nbv = rowsB * D4 * 4;
+        int ga = (int)((na + 255) / 256 < 4096 ? (na + 255) / 256 : 4096);
+        int gb = (int)((nbv + 255) / 256 < 4096 ? (nbv + 255) / 256 : 4096);
+        if (ga < 1) ga = 1;
+        if (gb < 1) gb = 1;
+        // the offsets' last entry is the exact row count of a packed array
+        const int64_t nall = src.kbase + n;
+        inc_kernel<T><<<ga, 256, 0, st>>>((const T *)src.A, rowsA, packed ? src.a_off + nall : nullptr,
+                                          src.d, D4, incA);
+        inc_kernel<T><<<gb, 256, 0, st>>>((const T *)src.B, rowsB, packed ? src.b_off + nall : nullptr,
+                                          src.d, D4, incB);
+    }
     plan_kernel<R, LAM><<<1, 1024, 0, st>>>(src, n, plan, totals);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -472,7 +562,7 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
         if ((e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
             cudaSuccess)
             return e;
-        ck<<<sms * 4, 256, smem, st>>>(src, plan, n, totals, cbuf);
+        ck<<<sms * 4, 256, smem, st>>>(src, plan, n, totals, incA, incB, cbuf);
     }
     StripArgs<T> a;
     a.src = src;
@@ -501,21 +591,21 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
 
 cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void *ws, void *out,
                          long long wait_cycles, int fault_inject, cudaStream_t st, int64_t max_la,
-                         int64_t max_lb) {
+                         int64_t max_lb, int64_t rowsA, int64_t rowsB) {
     if (n <= 0) return cudaSuccess;
     if (dtype == SIGK_F64) {
         switch (lam) {
-            case 0: return launch_strip_t<double, 8, 0>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb);
-            case 1: return launch_strip_t<double, 8, 1>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb);
-            case 2: return launch_strip_t<double, 8, 2>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb);
-            case 3: return launch_strip_t<double, 8, 3>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+            case 0: return launch_strip_t<double, 8, 0>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
+            case 1: return launch_strip_t<double, 8, 1>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
+            case 2: return launch_strip_t<double, 8, 2>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
+            case 3: return launch_strip_t<double, 8, 3>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
         }
     } else {
         switch (lam) {
-            case 0: return launch_strip_t<float, 16, 0>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb);
-            case 1: return launch_strip_t<float, 16, 1>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb);
-            case 2: return launch_strip_t<float, 16, 2>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb);
-            case 3: return launch_strip_t<float, 16, 3>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb);
+            case 0: return launch_strip_t<float, 16, 0>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
+            case 1: return launch_strip_t<float, 16, 1>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
+            case 2: return launch_strip_t<float, 16, 2>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
+            case 3: return launch_strip_t<float, 16, 3>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
         }
     }
     return cudaErrorInvalidValue;

@@ -104,10 +104,21 @@ cudaError_t launch_bwd_plain(const PairSrc &src, int64_t n_pairs, int lam, int d
                              int64_t slot_bytes, int64_t smem, cudaStream_t st);
 
 bool strip_supported(int lam, int64_t d, int dtype);
-int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype);
+// rowsA / rowsB: point rows of the src.A / src.B arrays (an upper bound for
+// packed uneven paths, whose exact count the kernels read from the offsets)
+int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype,
+                              int64_t rowsA, int64_t rowsB, int64_t d);
 cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void *ws, void *out,
                          long long wait_cycles, int fault_inject, cudaStream_t st, int64_t max_la,
-                         int64_t max_lb);
+                         int64_t max_lb, int64_t rowsA, int64_t rowsB);
+
+// Point rows of the src.A and src.B arrays of a call of n_total pairs.
+inline void src_rows(const PairSrc &s, int64_t n_total, int64_t &ra, int64_t &rb) {
+    if (s.mode == PM_PAIRS) { ra = n_total * s.La; rb = n_total * s.Lb; }
+    else if (s.mode == PM_GRAM) { ra = (n_total / s.nb) * s.La; rb = s.nb * s.Lb; }
+    else if (s.mode == PM_GRAM_SYM) { ra = s.nb * s.La; rb = ra; }
+    else { ra = n_total * s.La; rb = n_total * s.Lb; }   // packed: upper bounds
+}
 int read_status_word(void *ws, cudaStream_t st, int *status);
 
 cudaError_t launch_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n,
