@@ -120,6 +120,68 @@ int run_uniform(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opt
     }
 }
 
+
+// The adjoint's path: the strip backward (f32 auto / chain, f64 chain), else
+// the plain one-block-per-pair backward.
+bool bwd_uses_strip(int lam, int64_t d, int dtype, int rec) {
+    if (!strip_supported(lam, d, dtype)) return false;
+    return dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN;
+}
+
+void bwd_strip_batch(const PairSrc &src, int64_t n, int lam, int dtype, int64_t &nb, int64_t &bytes) {
+    int64_t ra, rb;
+    src_rows(src, n, ra, rb);
+    nb = n;
+    bytes = strip_bwd_workspace_bytes(nb, src.La, src.Lb, lam, dtype, ra, rb, src.d);
+    while (nb > 1 && bytes > STRIP_WS_CAP) {
+        nb = (nb + 1) / 2;
+        bytes = strip_bwd_workspace_bytes(nb, src.La, src.Lb, lam, dtype, ra, rb, src.d);
+    }
+}
+
+int64_t backward_ws_bytes(const PairSrc &src, int64_t n, int lam, int dtype, int rec) {
+    if (n == 0 || src.La < 2 || src.Lb < 2) return 0;
+    if (bwd_uses_strip(lam, src.d, dtype, rec)) {
+        int64_t nb, need;
+        bwd_strip_batch(src, n, lam, dtype, nb, need);
+        return need;
+    }
+    int64_t grid, slot, smem;
+    if (!bwd_plain_plan(n, src.La, src.Lb, src.d, lam, dtype, grid, slot, smem)) return -1;
+    return grid * slot;
+}
+
+int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opts *opts,
+                 const void *gout, void *dX, void *dY, int64_t nX, int64_t nY, void *ws,
+                 size_t ws_bytes, cudaStream_t st) {
+    const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+    if (dX && cudaMemsetAsync(dX, 0, (size_t)(nX * es), st) != cudaSuccess) return SIGK_ECUDA;
+    if (dY && cudaMemsetAsync(dY, 0, (size_t)(nY * es), st) != cudaSuccess) return SIGK_ECUDA;
+    if (n_pairs == 0 || src.La < 2 || src.Lb < 2 || (!dX && !dY)) return SIGK_OK;
+    const int rec = rec_of(opts);
+    if (bwd_uses_strip(lam, src.d, dtype, rec)) {
+        int64_t nb, need, ra, rb;
+        bwd_strip_batch(src, n_pairs, lam, dtype, nb, need);
+        src_rows(src, n_pairs, ra, rb);
+        if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
+        for (int64_t k0 = 0; k0 < n_pairs; k0 += nb) {
+            PairSrc s = src;
+            s.kbase = k0;
+            const int64_t m = n_pairs - k0 < nb ? n_pairs - k0 : nb;
+            cudaError_t e = launch_strip_bwd(s, m, lam, dtype, ws, gout, dX, dY, WAIT_CYCLES, st,
+                                             src.La, src.Lb, ra, rb);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        return SIGK_OK;
+    }
+    int64_t grid, slot, smem;
+    if (!bwd_plain_plan(n_pairs, src.La, src.Lb, src.d, lam, dtype, grid, slot, smem))
+        return SIGK_EUNSUPPORTED;
+    if (!ws || (int64_t)ws_bytes < grid * slot) return SIGK_ENOMEM_WS;
+    return cuda_status(launch_bwd_plain(src, n_pairs, lam, dtype, gout, dX, dY, ws, grid, slot,
+                                        smem, st));
+}
+
 }  // namespace
 
 extern "C" {
@@ -150,9 +212,13 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         return 0;
     if (n_pairs == 0 || L < 2 || M < 2) return 0;
     if (op == SIGK_OP_PAIRS_BACKWARD || op == SIGK_OP_GRAM_BACKWARD) {
-        int64_t grid, slot, smem;
-        if (!bwd_plain_plan(n_pairs, L, M, d, dyadic_order, dtype, grid, slot, smem)) return 0;
-        return (size_t)(grid * slot);
+        PairSrc bs;
+        memset(&bs, 0, sizeof(bs));
+        bs.mode = op == SIGK_OP_PAIRS_BACKWARD ? PM_PAIRS : PM_GRAM;
+        bs.La = L; bs.Lb = M; bs.d = d;
+        bs.nb = By;
+        const int64_t need = backward_ws_bytes(bs, n_pairs, dyadic_order, dtype, rec_of(opts));
+        return need > 0 ? (size_t)need : 0;
     }
     int64_t nb, need;
     if (op == SIGK_OP_PAIRS_VARLEN) {
@@ -268,23 +334,6 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, cons
     return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, (cudaStream_t)stream));
 }
 
-namespace {
-
-int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const void *gout, void *dX,
-                 void *dY, int64_t nX, int64_t nY, void *ws, size_t ws_bytes, cudaStream_t st) {
-    const int64_t es = dtype == SIGK_F64 ? 8 : 4;
-    if (dX && cudaMemsetAsync(dX, 0, (size_t)(nX * es), st) != cudaSuccess) return SIGK_ECUDA;
-    if (dY && cudaMemsetAsync(dY, 0, (size_t)(nY * es), st) != cudaSuccess) return SIGK_ECUDA;
-    if (n_pairs == 0 || src.La < 2 || src.Lb < 2 || (!dX && !dY)) return SIGK_OK;
-    int64_t grid, slot, smem;
-    if (!bwd_plain_plan(n_pairs, src.La, src.Lb, src.d, lam, dtype, grid, slot, smem))
-        return SIGK_EUNSUPPORTED;
-    if (!ws || (int64_t)ws_bytes < grid * slot) return SIGK_ENOMEM_WS;
-    return cuda_status(launch_bwd_plain(src, n_pairs, lam, dtype, gout, dX, dY, ws, grid, slot,
-                                        smem, st));
-}
-
-}  // namespace
 
 int sigk_pairs_backward(const void *grad_out, const void *X, const void *Y, int64_t B, int64_t L,
                         int64_t M, int64_t d, int dyadic_order, int dtype, const sigk_opts *opts,
@@ -299,8 +348,8 @@ int sigk_pairs_backward(const void *grad_out, const void *X, const void *Y, int6
     src.mode = PM_PAIRS;
     src.A = X; src.B = Y;
     src.La = L; src.Lb = M; src.d = d;
-    return run_backward(src, B, dyadic_order, dtype, grad_out, dX, dY, B * L * d, B * M * d, ws,
-                        ws_bytes, (cudaStream_t)stream);
+    return run_backward(src, B, dyadic_order, dtype, opts, grad_out, dX, dY, B * L * d, B * M * d,
+                        ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64_t Bx, int64_t By,
@@ -325,8 +374,8 @@ int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64
     src.La = L; src.Lb = M; src.d = d;
     src.nb = By;
     src.out_si = By; src.out_sj = 1;
-    return run_backward(src, Bx * By, dyadic_order, dtype, grad_out, dX, dY, Bx * L * d, By * M * d,
-                        ws, ws_bytes, (cudaStream_t)stream);
+    return run_backward(src, Bx * By, dyadic_order, dtype, opts, grad_out, dX, dY, Bx * L * d,
+                        By * M * d, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int sigk_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n, int dtype,

@@ -48,6 +48,8 @@ struct PairPlan {
     int ns, pad;             // strips, virtual refined rows above the first
     int nw;                  // windows (coefficient diagonals) per strip
     int swap;                // 1: the rows refine the B path (src.B), columns the A path
+    int64_t s_off;           // backward: start of its per-cell sums K(a,b-1) + K(a-1,b)
+    int64_t g_off;           // backward: start of its dense dk/dG [nx][ny]
 };
 
 template <int R, int LAM>
@@ -55,7 +57,7 @@ __global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *tot
     constexpr int S = 1 << LAM;
     constexpr int TH = 32 * R;
     constexpr int CP = 32 * (R / S);
-    __shared__ int64_t part[4][1024];
+    __shared__ int64_t part[6][512];
     // pass 1: per-pair shape
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
         const PairRef pr = pair_ref(src, k);
@@ -79,28 +81,32 @@ __global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *tot
         p.bnd_off = p.ns > 0 ? (int64_t)(p.ns - 1) * p.nj * 2 : 0;
         p.flag_off = p.ns > 0 ? p.ns - 1 : 0;
         p.strip_base = p.ns;
+        p.s_off = (int64_t)p.ns * (p.nj + TH - 1) * TH;
+        p.g_off = (int64_t)p.nx * p.ny;
         plan[k] = p;
     }
     __syncthreads();
     // pass 2: exclusive scans of the four sizes, in chunks of blockDim
-    int64_t run[4] = {0, 0, 0, 0};
+    int64_t run[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t base = 0; base < n; base += blockDim.x) {
         const int64_t k = base + threadIdx.x;
-        int64_t v[4] = {0, 0, 0, 0};
+        int64_t v[6] = {0, 0, 0, 0, 0, 0};
         if (k < n) {
             v[0] = plan[k].c_off;
             v[1] = plan[k].bnd_off;
             v[2] = plan[k].flag_off;
             v[3] = plan[k].strip_base;
+            v[4] = plan[k].s_off;
+            v[5] = plan[k].g_off;
         }
-        for (int j = 0; j < 4; ++j) part[j][threadIdx.x] = v[j];
+        for (int j = 0; j < 6; ++j) part[j][threadIdx.x] = v[j];
         __syncthreads();
         for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-            int64_t t[4];
-            for (int j = 0; j < 4; ++j)
+            int64_t t[6];
+            for (int j = 0; j < 6; ++j)
                 t[j] = (int)threadIdx.x >= off ? part[j][threadIdx.x - off] : 0;
             __syncthreads();
-            for (int j = 0; j < 4; ++j) part[j][threadIdx.x] += t[j];
+            for (int j = 0; j < 6; ++j) part[j][threadIdx.x] += t[j];
             __syncthreads();
         }
         if (k < n) {
@@ -108,12 +114,14 @@ __global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *tot
             plan[k].bnd_off = run[1] + part[1][threadIdx.x] - v[1];
             plan[k].flag_off = run[2] + part[2][threadIdx.x] - v[2];
             plan[k].strip_base = run[3] + part[3][threadIdx.x] - v[3];
+            plan[k].s_off = run[4] + part[4][threadIdx.x] - v[4];
+            plan[k].g_off = run[5] + part[5][threadIdx.x] - v[5];
         }
-        for (int j = 0; j < 4; ++j) run[j] += part[j][blockDim.x - 1];
+        for (int j = 0; j < 6; ++j) run[j] += part[j][blockDim.x - 1];
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        for (int j = 0; j < 4; ++j) totals[j] = run[j];
+        for (int j = 0; j < 6; ++j) totals[j] = run[j];
 }
 
 // ---- increments: dx_r = x_{r+1} - x_r for every point row r of a path array,
@@ -284,6 +292,7 @@ struct StripArgs {
     T *out;
     long long wait_cycles;
     int fault_inject;   // 1: the first strip of the first pair never publishes
+    T *sums;            // backward: per-cell K(a,b-1) + K(a-1,b), [strip][step][lane][R]; or null
 };
 
 constexpr int NRING = 8;   // coefficient diagonals in flight per warp
@@ -403,6 +412,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                     if (t < nj) { pK = tb[(t % CW) * 2]; pQ = tb[(t % CW) * 2 + 1]; }
                 }
                 T shK = 0, shQ = 0;
+                T sum[R];
 #pragma unroll
                 for (int r = R - 1; r >= 0; --r) {
                     const int g = r / S, sr = r % S;
@@ -410,7 +420,8 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                     const T kl = K[r];
                     const T ku = r > 0 ? K[r > 0 ? r - 1 : 0] : pK;
                     const T qu = r > 0 ? Q[r > 0 ? r - 1 : 0] : pQ;
-                    const T qn = qu + c * (kl + ku);
+                    sum[r] = kl + ku;
+                    const T qn = qu + c * sum[r];
                     K[r] = kl + qn;
                     Q[r] = qn;
                     if (r == R - 1) {
@@ -429,6 +440,11 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                         }
                     }
                 }
+                if (a.sums) {
+                    T *dst = a.sums + pp.s_off + ((int64_t)s * tend + t) * TH + lane * R;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) dst[r] = sum[r];
+                }
                 if (lane == 0) {
                     if (!top) { pK = 1; pQ = 0; }
                 } else {
@@ -438,9 +454,231 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
             }
         }
         ring_wait<0>();
-        if (s == pp.ns - 1 && lane == 31) {
+        if (a.out && s == pp.ns - 1 && lane == 31) {
             a.out[pp.out0] = K[R - 1];
             if (pp.out1 >= 0) a.out[pp.out1] = K[R - 1];
+        }
+    }
+}
+
+
+// ---- the adjoint: the strip schedule run backwards in time -----------------
+// A(a,b) = d k(Ni,Nj) / d K(a,b) obeys (reverse mode of the scheme)
+//   P(a,b) = A(a,b) - A(a,b+1) = c(a,b+1) A(a,b+1) + V(a+1,b),
+//   V(a,b) = P(a,b) + c(a,b) A(a,b),
+// with A(.,Nj+1) = 0 and V(Ni+1,b) = [b = Nj] (the seed A(Ni,Nj) = 1).  Each
+// cell needs, from the step after it in the forward schedule, its own A and
+// coefficient and the row below's V, so running the forward schedule
+// backwards (rows ascending within a step, V passed up the lanes and, between
+// strips, through chunked buffers behind bounded waits, strips of a pair in
+// reverse order) has every input ready.  Each cell adds A(a,b) (K(a,b-1) +
+// K(a-1,b)), read back from the forward's store, to dk/dG of its coarse cell;
+// a group's coarse cell is complete at the end of the window whose diagonal
+// it sits on.
+
+template <typename T>
+struct AdjArgs {
+    const PairPlan *plan;
+    const int64_t *totals;
+    int64_t n_pairs;
+    const T *cbuf;
+    const T *sums;
+    T *vbuf;         // per pair, per strip boundary: V of the lower strip's first row [nj]
+    int *vflags;     // chunks of vbuf published, counted from the right
+    int *counter;
+    int *status;
+    T *gbar;         // dense dk/dG (unscaled), [nx][ny] per pair
+    long long wait_cycles;
+};
+
+template <typename T, int R, int LAM>
+__global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> a) {
+    constexpr int S = 1 << LAM;
+    constexpr int NG = R / S;
+    constexpr int CP = 32 * NG;
+    constexpr int TH = 32 * R;
+    __shared__ T belowbuf[STRIP_WARPS][CW];
+    __shared__ __align__(16) T ring[STRIP_WARPS][NRING][CP];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    T *bb = belowbuf[warp];
+    const int64_t total_strips = a.totals[3];
+
+    for (;;) {
+        int64_t gs = 0;
+        if (lane == 0) gs = atomicAdd((unsigned long long *)a.counter, 1ULL);
+        gs = __shfl_sync(FULL, gs, 0);
+        if (gs >= total_strips) break;
+        int64_t lo = 0, hi = a.n_pairs - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (a.plan[mid].strip_base <= gs) lo = mid; else hi = mid - 1;
+        }
+        const PairPlan pp = a.plan[lo];
+        const int s = pp.ns - 1 - (int)(gs - pp.strip_base);   // last strip first
+        const int nj = pp.nj;
+        const int tend = nj + TH - 1;
+        const int nwin = (tend + S - 1) / S;
+        const T *blk = a.cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
+        const T *sst = a.sums + pp.s_off + (int64_t)s * tend * TH;
+        const T *below = s < pp.ns - 1 ? a.vbuf + pp.bnd_off / 2 + (int64_t)s * nj : nullptr;
+        const int *fbelow = s < pp.ns - 1 ? a.vflags + pp.flag_off + s : nullptr;
+        T *above = s > 0 ? a.vbuf + pp.bnd_off / 2 + (int64_t)(s - 1) * nj : nullptr;
+        int *fabove = s > 0 ? a.vflags + pp.flag_off + (s - 1) : nullptr;
+        const int prow0 = s * CP - (pp.pad >> LAM);
+
+        T A[R], V[R], cp[R], cn[NG], co[NG], gN[NG], gO[NG];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { A[r] = 0; V[r] = 0; cp[r] = 0; }
+#pragma unroll
+        for (int g = 0; g < NG; ++g) { gN[g] = 0; gO[g] = 0; }
+        bool timed_out = false;
+        // the ring holds diagonals w - 1 (co) ... in descending order
+#pragma unroll
+        for (int k = 0; k < NRING - 1; ++k) {
+            const int dg = nwin - 1 - k;
+            if (dg >= 0 && dg < pp.nw)
+                ring_fetch<T, NG>(&ring[warp][(dg + NRING) % NRING][lane * NG], blk + (int64_t)dg * CP + lane * NG);
+            ring_commit();
+        }
+        ring_wait<NRING - 2>();   // diagonal nwin - 1 has landed
+        {
+            const T *cw = &ring[warp][(nwin - 1 + NRING) % NRING][lane * NG];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) co[g] = cw[g];
+        }
+        for (int w = nwin - 1; w >= 0; --w) {
+            // cn = diagonal w (was co), co = diagonal w - 1 (zero below 0)
+            {
+                const int k = w - (NRING - 1);
+                if (k >= 0)
+                    ring_fetch<T, NG>(&ring[warp][k % NRING][lane * NG], blk + (int64_t)k * CP + lane * NG);
+                ring_commit();
+                ring_wait<NRING - 2>();
+            }
+#pragma unroll
+            for (int g = 0; g < NG; ++g) cn[g] = co[g];
+            if (w >= 1) {
+                const T *cw = &ring[warp][(w - 1) % NRING][lane * NG];
+#pragma unroll
+                for (int g = 0; g < NG; ++g) co[g] = cw[g];
+            } else {
+#pragma unroll
+                for (int g = 0; g < NG; ++g) co[g] = 0;
+            }
+#pragma unroll
+            for (int jj = S - 1; jj >= 0; --jj) {
+                const int t = w * S + jj;
+                if (t >= tend) continue;
+                const int col31 = t - (TH - 1);   // zero-based column of the strip's last row
+                // V of the row below the strip for lane 31's last row
+                if (below && col31 >= 0 && col31 < nj && ((nj - 1 - col31) % CW) == 0) {
+                    const int need = (nj - 1 - col31) / CW + 1;
+                    if (!timed_out) {
+                        const long long t0 = clock64();
+                        while (ld_acquire(fbelow) < need) {
+                            if (clock64() - t0 > a.wait_cycles) {
+                                timed_out = true;
+                                if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
+                                break;
+                            }
+                            __nanosleep(200);
+                        }
+                    }
+                    __syncwarp();
+                    for (int u = lane; u < CW; u += 32) {
+                        const int c = col31 - u;   // columns col31, col31-1, ...
+                        bb[u] = c >= 0 ? below[c] : (T)0;
+                    }
+                    __syncwarp();
+                }
+                T vbel;
+                if (below)
+                    vbel = (col31 >= 0 && col31 < nj) ? bb[(nj - 1 - col31) % CW] : (T)0;
+                else
+                    vbel = (col31 == nj - 1) ? (T)1 : (T)0;   // seed: V(Ni+1, Nj) = 1
+                // the next lane's first row V, from the previous reverse step
+                const T vnext = __shfl_down_sync(FULL, V[0], 1);
+                const T *srow = sst + (int64_t)t * TH + lane * R;
+                T sm[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[r] = srow[r];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int g = r / S, sr = r % S;
+                    const T cown = (jj >= sr) ? cn[g] : co[g];
+                    const T vb = r < R - 1 ? V[r < R - 1 ? r + 1 : 0] : (lane == 31 ? vbel : vnext);
+                    const T P = vb + cp[r] * A[r];
+                    const T An = A[r] + P;
+                    V[r] = P + cown * An;
+                    A[r] = An;
+                    cp[r] = cown;
+                    if (jj >= sr) gN[g] += An * sm[r]; else gO[g] += An * sm[r];
+                }
+                // lane 0's first row is at column t: its V goes to the strip above
+                if (above && lane == 0 && t < nj) {
+                    above[t] = V[0];
+                    const int done = nj - t;
+                    if (done % CW == 0 || t == 0) {
+                        __threadfence();
+                        st_release(fabove, (done + CW - 1) / CW);
+                    }
+                }
+            }
+            // diagonal w is complete for every group of the lane
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const int p = prow0 + NG * lane + g, q = w - NG * lane - g;
+                if (p >= 0 && p < pp.nx && q >= 0 && q < pp.ny)
+                    a.gbar[pp.g_off + (int64_t)p * pp.ny + q] = gN[g];
+                gN[g] = gO[g];
+                gO[g] = 0;
+            }
+        }
+        ring_wait<0>();
+    }
+}
+
+// Chain rule through G(p,q) = <dx_p, dy_q>: dk/d dx_p = f sum_q Gbar(p,q) dy_q,
+// dk/d dy_q = f sum_p Gbar(p,q) dx_p (f = incoming gradient x 1/2 4^-lambda),
+// then to the points, atomically (a path appears in many pairs).
+template <typename T>
+__global__ void __launch_bounds__(256) grad_chain_kernel(PairSrc src, const PairPlan *plan,
+                                                         int64_t n_pairs, const T *gbar,
+                                                         const T *incA, const T *incB, const T *gout,
+                                                         T *dA, T *dB, T scale) {
+    const int64_t d = src.d;
+    const int64_t D4 = (d + 3) / 4;
+    for (int64_t k = blockIdx.x; k < n_pairs; k += gridDim.x) {
+        const PairPlan pp = plan[k];
+        if (pp.ns == 0) continue;
+        const T f = gout[pp.out0] * scale;
+        const T *G = gbar + pp.g_off;
+        const T *xi = (pp.swap ? incB : incA) + pp.a_row0 * D4 * 4;
+        const T *yi = (pp.swap ? incA : incB) + pp.b_row0 * D4 * 4;
+        T *gx = pp.swap ? dB : dA;
+        T *gy = pp.swap ? dA : dB;
+        if (gx) {
+            gx += pp.a_row0 * d;
+            for (int64_t u = threadIdx.x; u < (int64_t)pp.nx * d; u += blockDim.x) {
+                const int64_t p = u / d, c = u - (u / d) * d;
+                T acc = 0;
+                for (int q = 0; q < pp.ny; ++q) acc += G[p * pp.ny + q] * yi[(int64_t)q * D4 * 4 + c];
+                acc *= f;
+                atomicAdd(&gx[(p + 1) * d + c], acc);
+                atomicAdd(&gx[p * d + c], -acc);
+            }
+        }
+        if (gy) {
+            gy += pp.b_row0 * d;
+            for (int64_t u = threadIdx.x; u < (int64_t)pp.ny * d; u += blockDim.x) {
+                const int64_t q = u / d, c = u - (u / d) * d;
+                T acc = 0;
+                for (int p = 0; p < pp.nx; ++p) acc += G[(int64_t)p * pp.ny + q] * xi[(int64_t)p * D4 * 4 + c];
+                acc *= f;
+                atomicAdd(&gy[(q + 1) * d + c], acc);
+                atomicAdd(&gy[q * d + c], -acc);
+            }
         }
     }
 }
@@ -466,6 +704,8 @@ __global__ void strip_trivial_kernel(PairSrc src, int64_t n, T *out) {
 //   | coefficients [ncoef] | bottom rows [nbnd]
 struct StripLayout {
     int64_t plan, flags, coef, bnd, incA, incB, total;
+    // backward only
+    int64_t vflags, vbuf, sums, gbar;
 };
 
 static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
@@ -493,7 +733,36 @@ static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R
     L.incB = off;
     off += al256(rowsB * D4 * 4 * es);
     L.total = off;
+    L.vflags = L.vbuf = L.sums = L.gbar = 0;
     return L;
+}
+
+static StripLayout strip_layout_bwd(int64_t n, int64_t max_la, int64_t max_lb, int R, int lam,
+                                    int64_t es, int64_t rowsA, int64_t rowsB, int64_t D4) {
+    StripLayout L = strip_layout(n, max_la, max_lb, R, lam, es, rowsA, rowsB, D4);
+    const int64_t S = 1LL << lam, TH = 32LL * R;
+    const int64_t lx = max_la > max_lb ? max_la : max_lb, ly = max_la > max_lb ? max_lb : max_la;
+    const int64_t nx = lx - 1, ny = ly - 1, ni = nx * S, nj = ny * S;
+    const int64_t ns = (ni + TH - 1) / TH;
+    int64_t off = L.total;
+    L.vflags = off;
+    off += al256(n * (ns > 1 ? ns - 1 : 0) * 4 + 4);
+    L.vbuf = off;
+    off += al256(n * (ns > 1 ? ns - 1 : 0) * nj * es + es);
+    L.sums = off;
+    off += al256(n * ns * (nj + TH - 1) * TH * es);
+    L.gbar = off;
+    off += al256(n * nx * ny * es);
+    L.total = off;
+    return L;
+}
+
+int64_t strip_bwd_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype,
+                                  int64_t rowsA, int64_t rowsB, int64_t d) {
+    if (lam < 0 || lam > 3 || n <= 0) return 0;
+    const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+    const int R = dtype == SIGK_F64 ? 8 : 16;
+    return strip_layout_bwd(n, max_la, max_lb, R, lam, es, rowsA, rowsB, (d + 3) / 4).total;
 }
 
 static int strip_R(int dtype, int lam) {
@@ -551,7 +820,7 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
         inc_kernel<T><<<gb, 256, 0, st>>>((const T *)src.B, rowsB, packed ? src.b_off + nall : nullptr,
                                           src.d, D4, incB);
     }
-    plan_kernel<R, LAM><<<1, 1024, 0, st>>>(src, n, plan, totals);
+    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -577,6 +846,7 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     a.out = out;
     a.wait_cycles = wait_cycles;
     a.fault_inject = fault_inject;
+    a.sums = nullptr;
     auto sk = strip_kernel<T, R, LAM>;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk, STRIP_WARPS * 32, 0)) !=
@@ -587,6 +857,123 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     // which some resident warp holds
     sk<<<sms * per_sm, STRIP_WARPS * 32, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int R, int LAM>
+static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, const T *gout, T *dA,
+                                      T *dB, long long wait_cycles, cudaStream_t st, int64_t max_la,
+                                      int64_t max_lb, int64_t rowsA, int64_t rowsB) {
+    const int64_t D4 = (src.d + 3) / 4;
+    const StripLayout L = strip_layout_bwd(n, max_la, max_lb, R, LAM, (int64_t)sizeof(T), rowsA, rowsB, D4);
+    unsigned char *w = (unsigned char *)ws;
+    int *status = (int *)w;
+    int *counter = (int *)(w + 256);
+    int *counter2 = (int *)(w + 264);
+    int64_t *totals = (int64_t *)(w + 512);
+    PairPlan *plan = (PairPlan *)(w + L.plan);
+    T *incA = (T *)(w + L.incA);
+    T *incB = (T *)(w + L.incB);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w, 0, 768, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w + L.flags, 0, (size_t)(L.coef - L.flags), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w + L.vflags, 0, (size_t)(L.vbuf - L.vflags), st)) != cudaSuccess) return e;
+    {
+        const bool packed = src.mode == PM_VARLEN;
+        const int64_t na = rowsA * D4 * 4, nbv = rowsB * D4 * 4;
+        int ga = (int)((na + 255) / 256 < 4096 ? (na + 255) / 256 : 4096);
+        int gb = (int)((nbv + 255) / 256 < 4096 ? (nbv + 255) / 256 : 4096);
+        if (ga < 1) ga = 1;
+        if (gb < 1) gb = 1;
+        const int64_t nall = src.kbase + n;
+        inc_kernel<T><<<ga, 256, 0, st>>>((const T *)src.A, rowsA, packed ? src.a_off + nall : nullptr,
+                                          src.d, D4, incA);
+        inc_kernel<T><<<gb, 256, 0, st>>>((const T *)src.B, rowsB, packed ? src.b_off + nall : nullptr,
+                                          src.d, D4, incB);
+    }
+    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    {
+        const int smem = (GT + 2 * GT - 1) * ((int)D4 | 1) * 4 * (int)sizeof(T);
+        auto ck = coef_kernel<T, R, LAM>;
+        if ((e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+            return e;
+        ck<<<sms * 4, 256, smem, st>>>(src, plan, n, totals, incA, incB, (T *)(w + L.coef));
+    }
+    {
+        StripArgs<T> a;
+        a.src = src;
+        a.plan = plan;
+        a.totals = totals;
+        a.n_pairs = n;
+        a.cbuf = (const T *)(w + L.coef);
+        a.bnd = (T *)(w + L.bnd);
+        a.flags = (int *)(w + L.flags);
+        a.counter = counter;
+        a.status = status;
+        a.out = nullptr;
+        a.wait_cycles = wait_cycles;
+        a.fault_inject = 0;
+        a.sums = (T *)(w + L.sums);
+        auto sk = strip_kernel<T, R, LAM>;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk, STRIP_WARPS * 32, 0)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        sk<<<sms * per_sm, STRIP_WARPS * 32, 0, st>>>(a);
+    }
+    {
+        AdjArgs<T> a;
+        a.plan = plan;
+        a.totals = totals;
+        a.n_pairs = n;
+        a.cbuf = (const T *)(w + L.coef);
+        a.sums = (const T *)(w + L.sums);
+        a.vbuf = (T *)(w + L.vbuf);
+        a.vflags = (int *)(w + L.vflags);
+        a.counter = counter2;
+        a.status = status;
+        a.gbar = (T *)(w + L.gbar);
+        a.wait_cycles = wait_cycles;
+        auto ak = strip_adj_kernel<T, R, LAM>;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ak, STRIP_WARPS * 32, 0)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        ak<<<sms * per_sm, STRIP_WARPS * 32, 0, st>>>(a);
+    }
+    const T scale = (T)0.5 / (T)(1LL << (2 * LAM));
+    grad_chain_kernel<T><<<sms * 4, 256, 0, st>>>(src, plan, n, (const T *)(w + L.gbar), incA, incB,
+                                                  gout, dA, dB, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strip_bwd(const PairSrc &src, int64_t n, int lam, int dtype, void *ws,
+                             const void *gout, void *dA, void *dB, long long wait_cycles,
+                             cudaStream_t st, int64_t max_la, int64_t max_lb, int64_t rowsA,
+                             int64_t rowsB) {
+    if (n <= 0) return cudaSuccess;
+#define SIGK_BWD_CASE(T, RR, L)                                                                   \
+    return launch_strip_bwd_t<T, RR, L>(src, n, ws, (const T *)gout, (T *)dA, (T *)dB, wait_cycles, \
+                                        st, max_la, max_lb, rowsA, rowsB);
+    if (dtype == SIGK_F64) {
+        switch (lam) {
+            case 0: SIGK_BWD_CASE(double, 8, 0)
+            case 1: SIGK_BWD_CASE(double, 8, 1)
+            case 2: SIGK_BWD_CASE(double, 8, 2)
+            case 3: SIGK_BWD_CASE(double, 8, 3)
+        }
+    } else {
+        switch (lam) {
+            case 0: SIGK_BWD_CASE(float, 16, 0)
+            case 1: SIGK_BWD_CASE(float, 16, 1)
+            case 2: SIGK_BWD_CASE(float, 16, 2)
+            case 3: SIGK_BWD_CASE(float, 16, 3)
+        }
+    }
+#undef SIGK_BWD_CASE
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void *ws, void *out,

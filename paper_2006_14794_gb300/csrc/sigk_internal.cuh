@@ -120,6 +120,12 @@ inline void src_rows(const PairSrc &s, int64_t n_total, int64_t &ra, int64_t &rb
     else { ra = n_total * s.La; rb = n_total * s.Lb; }   // packed: upper bounds
 }
 int read_status_word(void *ws, cudaStream_t st, int *status);
+int64_t strip_bwd_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype,
+                                  int64_t rowsA, int64_t rowsB, int64_t d);
+cudaError_t launch_strip_bwd(const PairSrc &src, int64_t n, int lam, int dtype, void *ws,
+                             const void *gout, void *dA, void *dB, long long wait_cycles,
+                             cudaStream_t st, int64_t max_la, int64_t max_lb, int64_t rowsA,
+                             int64_t rowsB);
 
 cudaError_t launch_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n,
                         int dtype, void *out, cudaStream_t st);

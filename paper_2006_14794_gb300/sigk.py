@@ -212,7 +212,7 @@ def version() -> str:
 
 
 def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
-                   need_dx: bool = True, need_dy: bool = True):
+                   need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO):
     """(dX, dY) with dX[b] = grad_out[b] dk(X_b, Y_b)/dX_b (None when not needed)."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     B, L, d = X.shape
@@ -221,7 +221,7 @@ def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dya
     grad_out = grad_out.to(X.dtype)
     dX = torch.empty_like(X) if need_dx else None
     dY = torch.empty_like(Y) if need_dy else None
-    o = _opts()
+    o = _opts(rec)
     ws, nws = _workspace(OP_PAIRS_BACKWARD, B, 0, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_pairs_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), B, L, M, d,
                                      int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
@@ -230,7 +230,7 @@ def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dya
 
 
 def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
-                  need_dx: bool = True, need_dy: bool = True):
+                  need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO):
     """(dX, dY): dX[i] = sum_j grad_out[i,j] dk(X_i,Y_j)/dX_i, dY[j] likewise."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     Bx, L, d = X.shape
@@ -239,7 +239,7 @@ def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyad
     grad_out = grad_out.to(X.dtype).contiguous()
     dX = torch.empty_like(X) if need_dx else None
     dY = torch.empty_like(Y) if need_dy else None
-    o = _opts()
+    o = _opts(rec)
     ws, nws = _workspace(OP_GRAM_BACKWARD, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_gram_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), Bx, By, L, M,
                                     d, int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),

@@ -147,3 +147,23 @@ def test_workspace_too_small_is_an_error():
     r = lib.sigk_pairs_backward(g.data_ptr(), X.data_ptr(), X.data_ptr(), 2, 10, 10, 3, 1, 0,
                                 ctypes.byref(o), dX.data_ptr(), None, ws.data_ptr(), need - 1, st)
     assert r == S().SIGK_ENOMEM_WS
+
+
+@pytest.mark.parametrize("lam,L,M,d", [(0, 700, 300, 3), (1, 40, 25, 8), (2, 150, 160, 4), (3, 33, 70, 5)])
+def test_strip_backward_matches_oracle(lam, L, M, d):
+    # the strip path's adjoint (f32 by default, f64 on request), multi-strip
+    # pairs included, against the oracle's gradient and the plain backward
+    B = 3
+    X32, X64 = inputs.f32(inputs.random_paths(800 + lam, B, L, d, scale=2.0, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(900 + lam, B, M, d, scale=2.0, time_channel=True))
+    g = np.random.default_rng(6).normal(size=B)
+    rX, rY = oracle.pairs_grad(X64, Y64, lam, g)
+    dX, dY = S().pairs_backward(to_dev(g), to_dev(X32), to_dev(Y32), lam)
+    assert grad_err(dX.cpu(), rX) <= 1e-4
+    assert grad_err(dY.cpu(), rY) <= 1e-4
+    dX, dY = S().pairs_backward(to_dev(g, torch.float64), to_dev(X64, torch.float64),
+                                to_dev(Y64, torch.float64), lam, rec=S().REC_CHAIN)
+    assert grad_err(dX.cpu(), rX) <= 1e-10
+    assert grad_err(dY.cpu(), rY) <= 1e-10
+    pX, pY = S().pairs_backward(to_dev(g), to_dev(X32), to_dev(Y32), lam, rec=S().REC_PLAIN)
+    assert grad_err(pX.cpu(), rX) <= 1e-4
