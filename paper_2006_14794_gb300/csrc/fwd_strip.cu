@@ -641,43 +641,92 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
 
 // Chain rule through G(p,q) = <dx_p, dy_q>: dk/d dx_p = f sum_q Gbar(p,q) dy_q,
 // dk/d dy_q = f sum_p Gbar(p,q) dx_p (f = incoming gradient x 1/2 4^-lambda),
-// then to the points, atomically (a path appears in many pairs).
+// then to the points, atomically (a path appears in many pairs).  Both
+// contractions run on 64 x 64 tiles of Gbar staged in shared memory; thread
+// (t / 8, t % 8) owns rows t/8 and t/8 + 32 of the output tile and 4
+// channels of a 32-channel block.
+constexpr int CT = 64;
+
 template <typename T>
 __global__ void __launch_bounds__(256) grad_chain_kernel(PairSrc src, const PairPlan *plan,
                                                          int64_t n_pairs, const T *gbar,
                                                          const T *incA, const T *incB, const T *gout,
                                                          T *dA, T *dB, T scale) {
+    using V4 = typename Vec4<T>::type;
+    // rows padded by one element against bank conflicts, except in double
+    // precision, where the padding would pass the 48 KB static limit
+    constexpr int GP = sizeof(T) == 4 ? CT + 1 : CT;
+    __shared__ T Gs[CT][GP];
+    __shared__ V4 Vs[CT][8];
     const int64_t d = src.d;
     const int64_t D4 = (d + 3) / 4;
+    const int rt = threadIdx.x >> 3, ct = threadIdx.x & 7;
     for (int64_t k = blockIdx.x; k < n_pairs; k += gridDim.x) {
         const PairPlan pp = plan[k];
         if (pp.ns == 0) continue;
         const T f = gout[pp.out0] * scale;
         const T *G = gbar + pp.g_off;
-        const T *xi = (pp.swap ? incB : incA) + pp.a_row0 * D4 * 4;
-        const T *yi = (pp.swap ? incA : incB) + pp.b_row0 * D4 * 4;
+        const V4 *xi = reinterpret_cast<const V4 *>(pp.swap ? incB : incA) + pp.a_row0 * D4;
+        const V4 *yi = reinterpret_cast<const V4 *>(pp.swap ? incA : incB) + pp.b_row0 * D4;
         T *gx = pp.swap ? dB : dA;
         T *gy = pp.swap ? dA : dB;
-        if (gx) {
-            gx += pp.a_row0 * d;
-            for (int64_t u = threadIdx.x; u < (int64_t)pp.nx * d; u += blockDim.x) {
-                const int64_t p = u / d, c = u - (u / d) * d;
-                T acc = 0;
-                for (int q = 0; q < pp.ny; ++q) acc += G[p * pp.ny + q] * yi[(int64_t)q * D4 * 4 + c];
-                acc *= f;
-                atomicAdd(&gx[(p + 1) * d + c], acc);
-                atomicAdd(&gx[p * d + c], -acc);
-            }
-        }
-        if (gy) {
-            gy += pp.b_row0 * d;
-            for (int64_t u = threadIdx.x; u < (int64_t)pp.ny * d; u += blockDim.x) {
-                const int64_t q = u / d, c = u - (u / d) * d;
-                T acc = 0;
-                for (int p = 0; p < pp.nx; ++p) acc += G[(int64_t)p * pp.ny + q] * xi[(int64_t)p * D4 * 4 + c];
-                acc *= f;
-                atomicAdd(&gy[(q + 1) * d + c], acc);
-                atomicAdd(&gy[q * d + c], -acc);
+        for (int pass = 0; pass < 2; ++pass) {
+            // pass 0: rows p of dk/d dx, contracting over q; pass 1: rows q of dk/d dy over p
+            T *gout_pts = pass == 0 ? gx : gy;
+            if (!gout_pts) continue;
+            gout_pts += (pass == 0 ? pp.a_row0 : pp.b_row0) * d;
+            const int nrow = pass == 0 ? pp.nx : pp.ny, nred = pass == 0 ? pp.ny : pp.nx;
+            const V4 *other = pass == 0 ? yi : xi;
+            for (int r0 = 0; r0 < nrow; r0 += CT) {
+                for (int64_t cb = 0; cb < D4; cb += 8) {
+                    T acc[2][4];
+                    for (int i = 0; i < 2; ++i)
+                        for (int e = 0; e < 4; ++e) acc[i][e] = 0;
+                    for (int k0 = 0; k0 < nred; k0 += CT) {
+                        __syncthreads();
+                        // Gs[i][j] = Gbar(output row r0+i, reduction index k0+j)
+                        for (int u = threadIdx.x; u < CT * CT; u += blockDim.x) {
+                            const int i = u / CT, j = u % CT;
+                            const int orow = r0 + i, red = k0 + j;
+                            T v = 0;
+                            if (orow < nrow && red < nred)
+                                v = pass == 0 ? G[(int64_t)orow * pp.ny + red] : G[(int64_t)red * pp.ny + orow];
+                            Gs[i][j] = v;
+                        }
+                        for (int u = threadIdx.x; u < CT * 8; u += blockDim.x) {
+                            const int j = u / 8, c4 = u % 8;
+                            V4 v;
+                            v.x = 0; v.y = 0; v.z = 0; v.w = 0;
+                            if (k0 + j < nred && cb + c4 < D4) v = other[(int64_t)(k0 + j) * D4 + cb + c4];
+                            Vs[j][c4] = v;
+                        }
+                        __syncthreads();
+#pragma unroll 8
+                        for (int j = 0; j < CT; ++j) {
+                            const T g0 = Gs[rt][j], g1 = Gs[rt + 32][j];
+                            const V4 v = Vs[j][ct];
+                            acc[0][0] = fma(g0, v.x, acc[0][0]);
+                            acc[0][1] = fma(g0, v.y, acc[0][1]);
+                            acc[0][2] = fma(g0, v.z, acc[0][2]);
+                            acc[0][3] = fma(g0, v.w, acc[0][3]);
+                            acc[1][0] = fma(g1, v.x, acc[1][0]);
+                            acc[1][1] = fma(g1, v.y, acc[1][1]);
+                            acc[1][2] = fma(g1, v.z, acc[1][2]);
+                            acc[1][3] = fma(g1, v.w, acc[1][3]);
+                        }
+                    }
+                    for (int i = 0; i < 2; ++i) {
+                        const int orow = r0 + rt + 32 * i;
+                        if (orow >= nrow) continue;
+                        for (int e = 0; e < 4; ++e) {
+                            const int64_t c = (cb + ct) * 4 + e;
+                            if (c >= d) continue;
+                            const T v = acc[i][e] * f;
+                            atomicAdd(&gout_pts[(int64_t)(orow + 1) * d + c], v);
+                            atomicAdd(&gout_pts[(int64_t)orow * d + c], -v);
+                        }
+                    }
+                }
             }
         }
     }
