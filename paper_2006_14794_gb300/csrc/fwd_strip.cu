@@ -157,7 +157,7 @@ struct Vec4;
 template <>
 struct Vec4<float> { using type = float4; };
 template <>
-struct Vec4<double> { using type = double4; };
+struct Vec4<double> { using type = double4_32a; };
 
 template <typename T, int R, int LAM>
 __global__ void __launch_bounds__(256) coef_kernel(PairSrc src, const PairPlan *plan,
@@ -352,7 +352,6 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
         const int *ftop = s > 0 ? a.flags + pp.flag_off + (s - 1) : nullptr;
         int *fbot = s < pp.ns - 1 ? a.flags + pp.flag_off + s : nullptr;
         const bool mute = a.fault_inject && lo == 0 && s == 0;
-        const int nchunk = (nj + CW - 1) / CW;
         const int tend = nj + TH - 1;   // steps until the last row leaves column nj
 
         T K[R], Q[R], cn[NG], co[NG];
@@ -362,6 +361,28 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
         for (int g = 0; g < NG; ++g) { cn[g] = 0; co[g] = 0; }
         T pK = 1, pQ = 0;
         bool timed_out = false;
+        // the top row's next chunk, two values per lane, loaded a chunk ahead
+        T tn0 = 0, tn1 = 0;
+        auto fetch_top = [&](int c) {
+            if (!top || c * CW >= nj) return;
+            const int need = (c + 1) * CW < nj ? c + 1 : (nj + CW - 1) / CW;
+            if (!timed_out) {
+                const long long t0 = clock64();
+                while (ld_acquire(ftop) < need) {
+                    if (clock64() - t0 > a.wait_cycles) {
+                        timed_out = true;
+                        if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+            }
+            __syncwarp();
+            const int col = c * CW + lane;   // zero-based column of this lane's (K, Q)
+            tn0 = col < nj ? top[(int64_t)col * 2] : (T)0;
+            tn1 = col < nj ? top[(int64_t)col * 2 + 1] : (T)0;
+        };
+        fetch_top(0);
         // fill the ring with diagonals 0 .. NRING-2 (one commit group each)
 #pragma unroll
         for (int k = 0; k < NRING - 1; ++k) {
@@ -387,25 +408,12 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                 const int t = w * S + jj;
                 if (t >= tend) break;
                 if (top && (t % CW) == 0 && t < nj) {
-                    // stage the top row's chunk t/CW (columns t+1 .. t+CW) once published
-                    const int need = t / CW + 1;
-                    if (!timed_out) {
-                        const long long t0 = clock64();
-                        while (ld_acquire(ftop) < need) {
-                            if (clock64() - t0 > a.wait_cycles) {
-                                timed_out = true;
-                                if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
-                                break;
-                            }
-                            __nanosleep(200);
-                        }
-                    }
+                    // chunk t/CW (columns t+1 .. t+CW) was loaded one chunk ago:
+                    // publish it to the warp, then fetch the next one
+                    tb[2 * lane] = tn0;
+                    tb[2 * lane + 1] = tn1;
                     __syncwarp();
-                    for (int u = lane; u < CW * 2; u += 32) {
-                        const int col = t + u / 2;   // zero-based column
-                        tb[u] = col < nj ? top[(int64_t)col * 2 + (u & 1)] : (T)0;
-                    }
-                    __syncwarp();
+                    fetch_top(t / CW + 1);
                 }
                 // lane 0's row 0 is at column t + 1 now
                 if (lane == 0 && top) {
@@ -433,6 +441,8 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                                 bot[(int64_t)col * 2] = K[r];
                                 bot[(int64_t)col * 2 + 1] = Q[r];
                                 if ((col + 1) % CW == 0 || col + 1 == nj) {
+                                    // measured: a fence before the release store publishes
+                                    // faster than the release store alone
                                     __threadfence();
                                     st_release(fbot, (col + CW) / CW);
                                 }
@@ -491,17 +501,36 @@ struct AdjArgs {
     long long wait_cycles;
 };
 
+constexpr int NSR = 8;   // slots of the per-cell sums ring (adjoint)
+constexpr int PD = 4;    // steps the sums are fetched ahead (< (NRING - 1) steps)
+
+template <typename T, int R, int LAM>
+__host__ __device__ constexpr int adj_warp_elems() {
+    return NRING * 32 * (R >> LAM) + NSR * 32 * R + CW;
+}
+
+// The lane's R sums of one step, NSR-slot ring, 16-byte cp.async chunks.
+template <typename T, int R>
+__device__ __forceinline__ void sums_fetch(T *slot, const T *src) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
+#pragma unroll
+    for (int o = 0; o < R * (int)sizeof(T); o += 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + o),
+                     "l"((const char *)src + o) : "memory");
+}
+
 template <typename T, int R, int LAM>
 __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> a) {
     constexpr int S = 1 << LAM;
     constexpr int NG = R / S;
     constexpr int CP = 32 * NG;
     constexpr int TH = 32 * R;
-    __shared__ T belowbuf[STRIP_WARPS][CW];
-    __shared__ __align__(16) T ring[STRIP_WARPS][NRING][CP];
+    extern __shared__ __align__(16) unsigned char adj_smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    T *bb = belowbuf[warp];
+    T *ringc = reinterpret_cast<T *>(adj_smem) + (size_t)warp * adj_warp_elems<T, R, LAM>();
+    T *rings = ringc + NRING * CP;
+    T *bb = rings + NSR * 32 * R;
     const int64_t total_strips = a.totals[3];
 
     for (;;) {
@@ -533,33 +562,63 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
 #pragma unroll
         for (int g = 0; g < NG; ++g) { gN[g] = 0; gO[g] = 0; }
         bool timed_out = false;
-        // the ring holds diagonals w - 1 (co) ... in descending order
+
+        // the row below's V, chunks counted from the right; one value per lane,
+        // fetched a chunk ahead (c: chunk index from the right)
+        T vn = 0;
+        auto fetch_below = [&](int c) {
+            const int hi_col = nj - 1 - c * CW;   // rightmost column of chunk c
+            if (!below || hi_col < 0) return;
+            const int need = c + 1;
+            if (!timed_out) {
+                const long long t0 = clock64();
+                while (ld_acquire(fbelow) < need) {
+                    if (clock64() - t0 > a.wait_cycles) {
+                        timed_out = true;
+                        if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+            }
+            __syncwarp();
+            const int col = hi_col - lane;
+            vn = col >= 0 ? below[col] : (T)0;
+        };
+        fetch_below(0);
+
+        // one initial group: coefficient diagonals nwin-1 .. nwin-NRING+1 and
+        // the sums of steps tend-1 .. tend-PD; then one group per step
 #pragma unroll
         for (int k = 0; k < NRING - 1; ++k) {
             const int dg = nwin - 1 - k;
             if (dg >= 0 && dg < pp.nw)
-                ring_fetch<T, NG>(&ring[warp][(dg + NRING) % NRING][lane * NG], blk + (int64_t)dg * CP + lane * NG);
-            ring_commit();
+                ring_fetch<T, NG>(&ringc[((dg + NRING) % NRING) * CP + lane * NG], blk + (int64_t)dg * CP + lane * NG);
         }
-        ring_wait<NRING - 2>();   // diagonal nwin - 1 has landed
+#pragma unroll
+        for (int k = 0; k < PD; ++k) {
+            const int ts = tend - 1 - k;
+            if (ts >= 0) sums_fetch<T, R>(&rings[(ts % NSR) * 32 * R + lane * R], sst + (int64_t)ts * TH + lane * R);
+        }
+        ring_commit();
+        ring_wait<0>();
         {
-            const T *cw = &ring[warp][(nwin - 1 + NRING) % NRING][lane * NG];
+            const T *cw = &ringc[((nwin - 1 + NRING) % NRING) * CP + lane * NG];
 #pragma unroll
             for (int g = 0; g < NG; ++g) co[g] = cw[g];
         }
         for (int w = nwin - 1; w >= 0; --w) {
-            // cn = diagonal w (was co), co = diagonal w - 1 (zero below 0)
+            // diagonal w - (NRING - 1) joins this window's first group; diagonal
+            // w - 1 was fetched NRING - 1 windows (>= PD steps) ago and has landed
             {
                 const int k = w - (NRING - 1);
                 if (k >= 0)
-                    ring_fetch<T, NG>(&ring[warp][k % NRING][lane * NG], blk + (int64_t)k * CP + lane * NG);
-                ring_commit();
-                ring_wait<NRING - 2>();
+                    ring_fetch<T, NG>(&ringc[(k % NRING) * CP + lane * NG], blk + (int64_t)k * CP + lane * NG);
             }
 #pragma unroll
             for (int g = 0; g < NG; ++g) cn[g] = co[g];
             if (w >= 1) {
-                const T *cw = &ring[warp][(w - 1) % NRING][lane * NG];
+                const T *cw = &ringc[((w - 1) % NRING) * CP + lane * NG];
 #pragma unroll
                 for (int g = 0; g < NG; ++g) co[g] = cw[g];
             } else {
@@ -570,36 +629,25 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
             for (int jj = S - 1; jj >= 0; --jj) {
                 const int t = w * S + jj;
                 if (t >= tend) continue;
+                // this step's group: the sums of step t - PD
+                if (t - PD >= 0)
+                    sums_fetch<T, R>(&rings[((t - PD) % NSR) * 32 * R + lane * R], sst + (int64_t)(t - PD) * TH + lane * R);
+                ring_commit();
+                ring_wait<PD>();   // the sums of step t (fetched PD steps ago) have landed
                 const int col31 = t - (TH - 1);   // zero-based column of the strip's last row
-                // V of the row below the strip for lane 31's last row
                 if (below && col31 >= 0 && col31 < nj && ((nj - 1 - col31) % CW) == 0) {
-                    const int need = (nj - 1 - col31) / CW + 1;
-                    if (!timed_out) {
-                        const long long t0 = clock64();
-                        while (ld_acquire(fbelow) < need) {
-                            if (clock64() - t0 > a.wait_cycles) {
-                                timed_out = true;
-                                if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
-                                break;
-                            }
-                            __nanosleep(200);
-                        }
-                    }
+                    // chunk (nj-1-col31)/CW was fetched a chunk ago: publish, fetch the next
+                    bb[lane] = vn;
                     __syncwarp();
-                    for (int u = lane; u < CW; u += 32) {
-                        const int c = col31 - u;   // columns col31, col31-1, ...
-                        bb[u] = c >= 0 ? below[c] : (T)0;
-                    }
-                    __syncwarp();
+                    fetch_below((nj - 1 - col31) / CW + 1);
                 }
                 T vbel;
                 if (below)
                     vbel = (col31 >= 0 && col31 < nj) ? bb[(nj - 1 - col31) % CW] : (T)0;
                 else
                     vbel = (col31 == nj - 1) ? (T)1 : (T)0;   // seed: V(Ni+1, Nj) = 1
-                // the next lane's first row V, from the previous reverse step
                 const T vnext = __shfl_down_sync(FULL, V[0], 1);
-                const T *srow = sst + (int64_t)t * TH + lane * R;
+                const T *srow = &rings[(t % NSR) * 32 * R + lane * R];
                 T sm[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) sm[r] = srow[r];
@@ -620,6 +668,8 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
                     above[t] = V[0];
                     const int done = nj - t;
                     if (done % CW == 0 || t == 0) {
+                        // measured: a fence before the release store publishes faster
+                        // than the release store alone
                         __threadfence();
                         st_release(fabove, (done + CW - 1) / CW);
                     }
@@ -986,11 +1036,14 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         a.gbar = (T *)(w + L.gbar);
         a.wait_cycles = wait_cycles;
         auto ak = strip_adj_kernel<T, R, LAM>;
+        const int asmem = STRIP_WARPS * adj_warp_elems<T, R, LAM>() * (int)sizeof(T);
+        if ((e = cudaFuncSetAttribute(ak, cudaFuncAttributeMaxDynamicSharedMemorySize, asmem)) != cudaSuccess)
+            return e;
         int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ak, STRIP_WARPS * 32, 0)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ak, STRIP_WARPS * 32, asmem)) != cudaSuccess)
             return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        ak<<<sms * per_sm, STRIP_WARPS * 32, 0, st>>>(a);
+        ak<<<sms * per_sm, STRIP_WARPS * 32, asmem, st>>>(a);
     }
     const T scale = (T)0.5 / (T)(1LL << (2 * LAM));
     grad_chain_kernel<T><<<sms * 4, 256, 0, st>>>(src, plan, n, (const T *)(w + L.gbar), incA, incB,
