@@ -158,6 +158,18 @@ def oracle_sample_rate(X64, Y64, budget_s: float):
     return pairs * CELLS_PER_PAIR / dt, pairs, dt, oracle.num_threads()
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The slowest rank's time: every rank passes its own, every rank gets the max
+    (no-op without an initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -246,12 +258,7 @@ def run_gpu(args):
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), dev)
     cells_step = BX * BY * CELLS_PER_PAIR
     value = ws * cells_step / (ms * 1e-3)
 
@@ -270,12 +277,7 @@ def run_gpu(args):
         Oh.copy_(o, non_blocking=True)
     e1.record(st)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dev)
     e2e_value = ws * cells_step / (e2e_ms * 1e-3)
 
     # ---- parity of the timed output with the oracle on sampled entries
