@@ -782,6 +782,175 @@ __global__ void __launch_bounds__(256) grad_chain_kernel(PairSrc src, const Pair
     }
 }
 
+// ---- coefficients on the tensor cores (f32 paths, d >= 32) -----------------
+// The same blocks as coef_kernel, from warp-level TF32 MMAs (m16n8k8) with each
+// operand split x = hi + lo (hi = x rounded to TF32, lo = the remainder rounded
+// to TF32) and the product taken as hi*hi + hi*lo + lo*hi: the dropped lo*lo
+// term is below FP32 rounding, so the coefficients keep FP32 accuracy (a
+// single TF32 product would not: about 3e-4 relative per coefficient).  A
+// 64 x 64 anti-diagonal tile (diagonals W, rows P) needs c(p, q) on the
+// 64 x 128 rectangle p in [P0, P0+64), q in [W0-P0-63, W0-P0+65); eight warps
+// compute it as 32 x 32 pieces into shared memory, and the tile is read back
+// along its diagonals and stored contiguously.
+
+constexpr int TC_CS = 130;   // row stride of the rectangle (conflict-free diagonal reads)
+
+__device__ __forceinline__ unsigned to_tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__host__ __device__ inline int tc_stride(int64_t d) { return (int)(((d + 7) / 8) * 8 + 4); }
+
+template <int R, int LAM>
+__global__ void __launch_bounds__(256) coef_tc_kernel(PairSrc src, const PairPlan *plan,
+                                                      int64_t n_pairs, const int64_t *totals,
+                                                      const float *incA, const float *incB,
+                                                      float *cbuf) {
+    constexpr int S = 1 << LAM;
+    constexpr int NG = R / S;
+    constexpr int CP = 32 * NG;
+    extern __shared__ __align__(16) float tcs[];
+    const int64_t d = src.d;
+    const int D4 = (int)((d + 3) / 4);
+    const int d8 = (int)((d + 7) / 8) * 8;
+    const int XS = tc_stride(d);                 // = d8 + 4: 4 x odd, conflict-free fragment loads
+    unsigned *xh = reinterpret_cast<unsigned *>(tcs);   // 64 rows of dx, TF32 hi / lo
+    unsigned *xl = xh + 64 * XS;
+    unsigned *yh = xl + 64 * XS;                        // 64 new rows of dy, hi / lo
+    unsigned *yl = yh + 64 * XS;
+    float *cs = reinterpret_cast<float *>(yl + 64 * XS);   // rectangle ring: 64 x 128 columns
+    const float scale = 0.5f / (float)(1 << (2 * LAM));
+    const int64_t total_strips = totals[3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int pw = 32 * (warp >> 2), qw = 16 * (warp & 3);
+    for (int64_t gs = blockIdx.x; gs < total_strips; gs += gridDim.x) {
+        int64_t lo = 0, hi = n_pairs - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (plan[mid].strip_base <= gs) lo = mid; else hi = mid - 1;
+        }
+        const PairPlan pp = plan[lo];
+        const int s = (int)(gs - pp.strip_base);
+        const float4 *x = reinterpret_cast<const float4 *>(pp.swap ? incB : incA) + pp.a_row0 * D4;
+        const float4 *y = reinterpret_cast<const float4 *>(pp.swap ? incA : incB) + pp.b_row0 * D4;
+        float *blk = cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
+        const int prow0 = s * CP - (pp.pad >> LAM);
+        for (int P0 = 0; P0 < CP; P0 += 64) {
+            const bool rows_empty = prow0 + P0 + 63 < 0 || prow0 + P0 >= pp.nx;
+            __syncthreads();
+            // dx rows of this row block, split once
+            for (int u = threadIdx.x; u < 64 * (d8 / 4); u += blockDim.x) {
+                const int i = u / (d8 / 4), c4 = u - i * (d8 / 4);
+                const int p = prow0 + P0 + i;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (p >= 0 && p < pp.nx && c4 < D4) v = x[(int64_t)p * D4 + c4];
+                const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned h = to_tf32(e[k]);
+                    xh[i * XS + 4 * c4 + k] = h;
+                    xl[i * XS + 4 * c4 + k] = to_tf32(e[k] - __uint_as_float(h));
+                }
+            }
+            // rectangle column block j covers q in [P0-63+64(j-1)... ]: block of columns
+            // qb = W0 - P0 - 63 + 64 h, h = 0, 1; the ring keeps the two halves
+            int have = -1;   // half index (in units of 64 columns from q = -P0-63) computed last
+            for (int W0 = 0; W0 < pp.nw; W0 += 64) {
+                const int qlo = W0 - (P0 + 63), qhi = W0 + 63 - P0;
+                if (rows_empty || qhi < 0 || qlo >= pp.ny) {
+                    for (int u = threadIdx.x; u < 64 * 64; u += blockDim.x) {
+                        const int W = W0 + u / 64, P = P0 + (u % 64);
+                        if (W < pp.nw && P < CP) blk[(int64_t)W * CP + P] = 0.f;
+                    }
+                    continue;
+                }
+                // this tile needs halves hw = W0/64 and hw + 1 (columns q = -P0-63 + 64 h + c)
+                const int hw = W0 / 64;
+                for (int h = hw; h <= hw + 1; ++h) {
+                    if (h <= have) continue;
+                    __syncthreads();
+                    const int qb = -P0 - 63 + 64 * h;
+                    for (int u = threadIdx.x; u < 64 * (d8 / 4); u += blockDim.x) {
+                        const int i = u / (d8 / 4), c4 = u - i * (d8 / 4);
+                        const int q = qb + i;
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (q >= 0 && q < pp.ny && c4 < D4) v = y[(int64_t)q * D4 + c4];
+                        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const unsigned hh = to_tf32(e[k]);
+                            yh[i * XS + 4 * c4 + k] = hh;
+                            yl[i * XS + 4 * c4 + k] = to_tf32(e[k] - __uint_as_float(hh));
+                        }
+                    }
+                    __syncthreads();
+                    float acc[2][2][4];
+#pragma unroll
+                    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[mi][ni][e] = 0.f;
+                    for (int k0 = 0; k0 < d8; k0 += 8) {
+                        unsigned ah[2][4], al[2][4], bh[2][2], bl[2][2];
+#pragma unroll
+                        for (int mi = 0; mi < 2; ++mi) {
+                            const int r0 = (pw + 16 * mi + g) * XS + k0 + t, r1 = r0 + 8 * XS;
+                            ah[mi][0] = xh[r0]; ah[mi][1] = xh[r1]; ah[mi][2] = xh[r0 + 4]; ah[mi][3] = xh[r1 + 4];
+                            al[mi][0] = xl[r0]; al[mi][1] = xl[r1]; al[mi][2] = xl[r0 + 4]; al[mi][3] = xl[r1 + 4];
+                        }
+#pragma unroll
+                        for (int ni = 0; ni < 2; ++ni) {
+                            const int r = (qw + 8 * ni + g) * XS + k0 + t;
+                            bh[ni][0] = yh[r]; bh[ni][1] = yh[r + 4];
+                            bl[ni][0] = yl[r]; bl[ni][1] = yl[r + 4];
+                        }
+#pragma unroll
+                        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                            for (int ni = 0; ni < 2; ++ni) {
+                                mma_tf32(acc[mi][ni], al[mi], bh[ni]);
+                                mma_tf32(acc[mi][ni], ah[mi], bl[ni]);
+                                mma_tf32(acc[mi][ni], ah[mi], bh[ni]);
+                            }
+                    }
+                    const int cbase = 64 * (h & 1);
+#pragma unroll
+                    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                        for (int ni = 0; ni < 2; ++ni) {
+                            const int r = pw + 16 * mi + g, c = cbase + qw + 8 * ni + 2 * t;
+                            cs[r * TC_CS + c] = acc[mi][ni][0];
+                            cs[r * TC_CS + c + 1] = acc[mi][ni][1];
+                            cs[(r + 8) * TC_CS + c] = acc[mi][ni][2];
+                            cs[(r + 8) * TC_CS + c + 1] = acc[mi][ni][3];
+                        }
+                    have = h;
+                }
+                __syncthreads();
+                // the diagonal tile: (W, P) -> q = W - P = -P0-63 + 64 hw + (Wl - Pl + 63)
+                for (int u = threadIdx.x; u < 64 * 64; u += blockDim.x) {
+                    const int Pl = u % 64, Wl = u / 64;
+                    const int W = W0 + Wl, P = P0 + Pl;
+                    const int col = (64 * hw + Wl - Pl + 63) & 127;   // ring column
+                    if (W < pp.nw && P < CP) blk[(int64_t)W * CP + P] = cs[Pl * TC_CS + col] * scale;
+                }
+            }
+        }
+    }
+}
+
 template <typename T>
 __global__ void strip_trivial_kernel(PairSrc src, int64_t n, T *out) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -885,6 +1054,34 @@ int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam
         .total;
 }
 
+// The coefficient blocks: split-TF32 tensor-core MMAs for f32 with d >= 32,
+// the FMA contraction otherwise (f64, or too few channels: at d = 16 the FMA
+// kernel measured faster, 2.9 vs 3.2 ms on 4096 uneven pairs; at d = 64 the
+// MMAs win, 10.1 vs 13.0 ms on 64 pairs of 4096 points).
+template <typename T, int R, int LAM>
+static cudaError_t launch_coef(const PairSrc &src, const PairPlan *plan, int64_t n,
+                               const int64_t *totals, const T *incA, const T *incB, T *cbuf,
+                               int sms, cudaStream_t st) {
+    cudaError_t e;
+    if (sizeof(T) == 4 && src.d >= 32) {
+        const int XS = tc_stride(src.d);
+        const int smem = (4 * 64 * XS + 64 * TC_CS) * 4;
+        auto tk = coef_tc_kernel<R, LAM>;
+        if ((e = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+            return e;
+        tk<<<sms * 2, 256, smem, st>>>(src, plan, n, totals, (const float *)incA, (const float *)incB,
+                                       (float *)cbuf);
+        return cudaGetLastError();
+    }
+    const int D4 = (int)((src.d + 3) / 4);
+    const int smem = (GT + 2 * GT - 1) * (D4 | 1) * 4 * (int)sizeof(T);
+    auto ck = coef_kernel<T, R, LAM>;
+    if ((e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+        return e;
+    ck<<<sms * 4, 256, smem, st>>>(src, plan, n, totals, incA, incB, cbuf);
+    return cudaGetLastError();
+}
+
 template <typename T, int R, int LAM>
 static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *out,
                                   long long wait_cycles, int fault_inject, cudaStream_t st,
@@ -923,15 +1120,8 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    {
-        const int D4 = (int)((src.d + 3) / 4);
-        const int smem = (GT + 2 * GT - 1) * (D4 + 1) * 4 * (int)sizeof(T);
-        auto ck = coef_kernel<T, R, LAM>;
-        if ((e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
-            cudaSuccess)
-            return e;
-        ck<<<sms * 4, 256, smem, st>>>(src, plan, n, totals, incA, incB, cbuf);
-    }
+    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, cbuf, sms, st)) != cudaSuccess)
+        return e;
     StripArgs<T> a;
     a.src = src;
     a.plan = plan;
@@ -993,13 +1183,9 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    {
-        const int smem = (GT + 2 * GT - 1) * ((int)D4 | 1) * 4 * (int)sizeof(T);
-        auto ck = coef_kernel<T, R, LAM>;
-        if ((e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-            return e;
-        ck<<<sms * 4, 256, smem, st>>>(src, plan, n, totals, incA, incB, (T *)(w + L.coef));
-    }
+    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, (T *)(w + L.coef), sms, st)) !=
+        cudaSuccess)
+        return e;
     {
         StripArgs<T> a;
         a.src = src;

@@ -319,3 +319,37 @@ def mmd2_loss(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int) -> torch.Tens
     Kyy = SigKernelGram.apply(Y, Y, dyadic_order)
     Kxy = SigKernelGram.apply(X, Y, dyadic_order)
     return _MMD2.apply(Kxx, Kyy, Kxy)[0]
+
+
+class Graphed:
+    """One library call captured into a CUDA graph with static input and output
+    buffers: ``g = graphed(pairs_varlen, Xp, x_off, Yp, y_off, 1, max_len=512)``
+    then ``out = g(Xp2, x_off2, Yp2, y_off2)`` copies the new inputs into the
+    captured buffers (same shapes) and replays the whole call (its memsets,
+    planning, coefficient and sweep kernels) as one graph launch.  The
+    workspace is allocated once, inside the capture's memory pool."""
+
+    def __init__(self, fn, *args, **kwargs):
+        self.static_in = [a.clone() if isinstance(a, torch.Tensor) else a for a in args]
+        self.kwargs = kwargs
+        dev = next(a.device for a in args if isinstance(a, torch.Tensor))
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            for _ in range(2):   # warm-up outside the capture (attributes, module load)
+                fn(*self.static_in, **kwargs)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
+            self.static_out = fn(*self.static_in, **kwargs)
+
+    def __call__(self, *args):
+        for dst, src in zip(self.static_in, args):
+            if isinstance(dst, torch.Tensor):
+                dst.copy_(src, non_blocking=True)
+        self.graph.replay()
+        return self.static_out
+
+
+def graphed(fn, *args, **kwargs) -> Graphed:
+    return Graphed(fn, *args, **kwargs)

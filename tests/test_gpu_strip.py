@@ -87,3 +87,26 @@ def test_injected_fault_is_reported_as_timeout():
     ref = oracle.pairs(X.double().cpu().numpy(), X.double().cpu().numpy(), 0)
     got = S().pairs(X, X, 0, check_status=True).cpu().numpy()
     assert rel_err(got, ref) <= 1e-5
+
+
+def test_graph_captured_calls_replay_correctly():
+    # the uneven-length strip path (memsets, planning, coefficients, sweep) and
+    # the chained Gram, each captured once and replayed on new inputs
+    w = inputs.uneven_pairs(B=96, lo=20, hi=300, d=16)
+    lam = w["dyadic_order"]
+    X32, X64 = inputs.f32(w["Xp"])
+    Y32, Y64 = inputs.f32(w["Yp"])
+    xo = torch.as_tensor(w["x_off"]).cuda()
+    yo = torch.as_tensor(w["y_off"]).cuda()
+    Xd, Yd = to_dev(X32), to_dev(Y32)
+    g = S().graphed(S().pairs_varlen, Xd, xo, Yd, yo, lam, max_len=300)
+    ref = oracle.pairs_varlen(X64, w["x_off"], Y64, w["y_off"], lam)
+    assert rel_err(g(Xd, xo, Yd, yo).cpu().numpy(), ref) <= 1e-5
+    # new values, same shapes
+    X2 = Xd * 0.7
+    ref2 = oracle.pairs_varlen(X2.double().cpu().numpy(), w["x_off"], Y64, w["y_off"], lam)
+    assert rel_err(g(X2, xo, Yd, yo).cpu().numpy(), ref2) <= 1e-5
+    A32, A64 = inputs.f32(inputs.random_paths(1700, 9, 60, 8, time_channel=True))
+    B32, B64 = inputs.f32(inputs.random_paths(1701, 7, 60, 8, time_channel=True))
+    gg = S().graphed(S().gram, to_dev(A32), to_dev(B32), 2)
+    assert rel_err(gg(to_dev(A32), to_dev(B32)).cpu().numpy(), oracle.gram(A64, B64, 2)) <= 1e-5
