@@ -69,8 +69,10 @@ typedef enum { SIGK_F32 = 0, SIGK_F64 = 1 } sigk_dtype;   /* storage AND arithme
  *    It needs workspace (sigk_workspace_bytes) and dyadic_order <= 3.
  *  PLAIN: one thread block per pair sweeping the anti-diagonals, the scheme
  *    as printed (f64) or its difference form (f32): the baseline.
+ *  STRIP: the strip path even where the register chain would apply
+ *    (SIGK_EUNSUPPORTED where the strip path has no instance).
  *  AUTO: CHAIN for f32 (PLAIN when CHAIN has no instance), PLAIN for f64. */
-typedef enum { SIGK_REC_AUTO = 0, SIGK_REC_CHAIN = 1, SIGK_REC_PLAIN = 2 } sigk_rec;
+typedef enum { SIGK_REC_AUTO = 0, SIGK_REC_CHAIN = 1, SIGK_REC_PLAIN = 2, SIGK_REC_STRIP = 3 } sigk_rec;
 
 typedef struct {
     int rec;          /* sigk_rec; 0 = auto                                   */
@@ -81,7 +83,16 @@ typedef struct {
                          bottom row, so the strip below waits out its bounded
                          wait (~1 s) and sigk_stream_status reports
                          SIGK_ETIMEOUT; nothing faults on the device          */
-    int reserved[5];  /* must be 0                                            */
+    int rows_per_lane;/* schedule: refined rows per lane of the chained kernel
+                         (4, 8 or 16; 0 = the smallest that fits).  Where the
+                         chained kernel would run (f32, rec AUTO or CHAIN) a
+                         value without an instance for the shape gives
+                         SIGK_EUNSUPPORTED; other paths ignore it             */
+    int coef_path;    /* strip path coefficients: 0 auto (split-TF32 tensor
+                         cores for f32 with d >= 32), 1 FMA contraction,
+                         2 split-TF32 tensor cores (f32 only: f64 gives
+                         SIGK_EUNSUPPORTED); other paths ignore it            */
+    int reserved[3];  /* must be 0                                            */
 } sigk_opts;          /* a NULL pointer means all-zero (automatic) options    */
 
 typedef enum {

@@ -11,10 +11,14 @@ namespace {
 
 bool opts_ok(const sigk_opts *o) {
     if (!o) return true;
-    if (o->rec < SIGK_REC_AUTO || o->rec > SIGK_REC_PLAIN) return false;
+    if (o->rec < SIGK_REC_AUTO || o->rec > SIGK_REC_STRIP) return false;
     if (o->symmetric != 0 && o->symmetric != 1) return false;
     if (o->fault_inject != 0 && o->fault_inject != 1) return false;
-    for (int i = 0; i < 5; ++i)
+    if (o->rows_per_lane != 0 && o->rows_per_lane != 4 && o->rows_per_lane != 8 &&
+        o->rows_per_lane != 16)
+        return false;
+    if (o->coef_path < 0 || o->coef_path > 2) return false;
+    for (int i = 0; i < 3; ++i)
         if (o->reserved[i] != 0) return false;
     return true;
 }
@@ -28,6 +32,7 @@ int common_checks(int64_t B, int64_t L, int64_t M, int64_t d, int lam, int dtype
     if (!opts_ok(opts)) return SIGK_EINVAL;
     if (lam < 0) return SIGK_EINVAL;
     if (lam > 8) return SIGK_EUNSUPPORTED;
+    if (opts && opts->coef_path == 2 && dtype != SIGK_F32) return SIGK_EUNSUPPORTED;
     return SIGK_OK;
 }
 
@@ -43,6 +48,8 @@ constexpr long long WAIT_CYCLES = 2000000000LL;
 constexpr int64_t STRIP_WS_CAP = 8LL << 30;
 
 int fault_of(const sigk_opts *o) { return o ? o->fault_inject : 0; }
+int rows_of(const sigk_opts *o) { return o ? o->rows_per_lane : 0; }
+int coef_of(const sigk_opts *o) { return o ? o->coef_path : 0; }
 
 // Pairs per strip-path launch and the workspace that needs.
 void strip_batch(const PairSrc &src, int64_t n, int64_t la, int64_t lb, int lam, int dtype,
@@ -59,18 +66,21 @@ void strip_batch(const PairSrc &src, int64_t n, int64_t la, int64_t lb, int lam,
 
 enum Path { P_FILL, P_CHAIN, P_STRIP, P_PLAIN };
 
-Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, ChainPlan *cp) {
+Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, ChainPlan *cp,
+                    int rows_per_lane = 0) {
     if (src.La < 2 || src.Lb < 2) return P_FILL;
     if (rec == SIGK_REC_PLAIN) return P_PLAIN;
+    if (rec == SIGK_REC_STRIP) return strip_supported(lam, src.d, dtype) ? P_STRIP : P_FILL;
     if (dtype == SIGK_F64 && rec != SIGK_REC_CHAIN) return P_PLAIN;
     if (dtype == SIGK_F32) {
         int64_t la = src.La, lb = src.Lb;
         if (src.mode == PM_PAIRS && la > lb) { int64_t t = la; la = lb; lb = t; }
         ChainPlan p;
-        if (chain_plan(n, la, lb, src.d, lam, p)) {
+        if (chain_plan(n, la, lb, src.d, lam, p, rows_per_lane)) {
             if (cp) *cp = p;
             return P_CHAIN;
         }
+        if (rows_per_lane != 0) return P_FILL;   // the requested schedule has no instance
     }
     if (strip_supported(lam, src.d, dtype)) return P_STRIP;
     return rec == SIGK_REC_CHAIN ? P_FILL /* unsupported */ : P_PLAIN;
@@ -87,7 +97,7 @@ int run_strip(PairSrc src, int64_t n, int lam, int dtype, int64_t la, int64_t lb
         s.kbase = src.kbase + k0;
         const int64_t m = n - k0 < nb ? n - k0 : nb;
         cudaError_t e = launch_strip(s, m, lam, dtype, ws, out, WAIT_CYCLES,
-                                     k0 == 0 ? fault_of(opts) : 0, st, la, lb, ra, rb);
+                                     k0 == 0 ? fault_of(opts) : 0, st, la, lb, ra, rb, coef_of(opts));
         if (e != cudaSuccess) return cuda_status(e);
     }
     return SIGK_OK;
@@ -99,7 +109,7 @@ int run_uniform(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opt
     if (n_pairs == 0) return SIGK_OK;
     const int rec = rec_of(opts);
     ChainPlan p;
-    switch (choose_uniform(src, n_pairs, lam, dtype, rec, &p)) {
+    switch (choose_uniform(src, n_pairs, lam, dtype, rec, &p, rows_of(opts))) {
         case P_FILL:
             if (src.La < 2 || src.Lb < 2) return cuda_status(launch_fill_one(out, n_pairs, dtype, st));
             return SIGK_EUNSUPPORTED;
@@ -125,6 +135,7 @@ int run_uniform(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opt
 // the plain one-block-per-pair backward.
 bool bwd_uses_strip(int lam, int64_t d, int dtype, int rec) {
     if (!strip_supported(lam, d, dtype)) return false;
+    if (rec == SIGK_REC_STRIP) return true;
     return dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN;
 }
 
@@ -159,6 +170,7 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
     if (dY && cudaMemsetAsync(dY, 0, (size_t)(nY * es), st) != cudaSuccess) return SIGK_ECUDA;
     if (n_pairs == 0 || src.La < 2 || src.Lb < 2 || (!dX && !dY)) return SIGK_OK;
     const int rec = rec_of(opts);
+    if (rec == SIGK_REC_STRIP && !strip_supported(lam, src.d, dtype)) return SIGK_EUNSUPPORTED;
     if (bwd_uses_strip(lam, src.d, dtype, rec)) {
         int64_t nb, need, ra, rb;
         bwd_strip_batch(src, n_pairs, lam, dtype, nb, need);
@@ -169,7 +181,7 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
             s.kbase = k0;
             const int64_t m = n_pairs - k0 < nb ? n_pairs - k0 : nb;
             cudaError_t e = launch_strip_bwd(s, m, lam, dtype, ws, gout, dX, dY, WAIT_CYCLES, st,
-                                             src.La, src.Lb, ra, rb);
+                                             src.La, src.Lb, ra, rb, coef_of(opts));
             if (e != cudaSuccess) return cuda_status(e);
         }
         return SIGK_OK;
@@ -224,7 +236,8 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
     if (op == SIGK_OP_PAIRS_VARLEN) {
         const int rec = rec_of(opts);
         const bool strip = strip_supported(dyadic_order, d, dtype) &&
-                           (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN);
+                           (rec == SIGK_REC_STRIP ||
+                            (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN));
         if (!strip) return 0;
         PairSrc vs;
         memset(&vs, 0, sizeof(vs));
@@ -249,7 +262,8 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         src.La = L <= M ? L : M; src.Lb = L <= M ? M : L;
         src.nb = L <= M ? By : B_or_Bx;
     }
-    if (choose_uniform(src, n_pairs, dyadic_order, dtype, rec_of(opts), nullptr) != P_STRIP) return 0;
+    if (choose_uniform(src, n_pairs, dyadic_order, dtype, rec_of(opts), nullptr, rows_of(opts)) != P_STRIP)
+        return 0;
     strip_batch(src, n_pairs, src.La, src.Lb, dyadic_order, dtype, nb, need);
     return (size_t)need;
 }
@@ -326,11 +340,12 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, cons
     src.d = d;
     const int rec = rec_of(opts);
     const bool strip = strip_supported(dyadic_order, d, dtype) &&
-                       (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN);
+                       (rec == SIGK_REC_STRIP ||
+                        (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN));
     if (strip)
         return run_strip(src, B, dyadic_order, dtype, max_len, max_len, opts, out, ws, ws_bytes,
                          (cudaStream_t)stream);
-    if (rec == SIGK_REC_CHAIN) return SIGK_EUNSUPPORTED;
+    if (rec == SIGK_REC_CHAIN || rec == SIGK_REC_STRIP) return SIGK_EUNSUPPORTED;
     return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, (cudaStream_t)stream));
 }
 

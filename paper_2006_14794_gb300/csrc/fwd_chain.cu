@@ -308,7 +308,8 @@ int occupancy_of(int R, int lam, int D4, int smem) {
 
 }  // namespace
 
-bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p) {
+bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p,
+                int rows_per_lane) {
     if (La < 2 || Lb < 2 || lam > 3 || d < 1 || n_pairs < 1) return false;
     const int64_t S = 1LL << lam;
     const int64_t Ni = S * (La - 1), Nj = S * (Lb - 1);
@@ -317,7 +318,11 @@ bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, Cha
     if (D4 > 4) return false;
     int R = 0;
     for (int r : {4, 8, 16})
-        if (32 * r >= Ni && r >= 2 * S && has_instance(r, lam, D4)) { R = r; break; }
+        if ((rows_per_lane == 0 || rows_per_lane == r) && 32 * r >= Ni && r >= 2 * S &&
+            has_instance(r, lam, D4)) {
+            R = r;
+            break;
+        }
     if (R == 0) return false;
     const int64_t Tper = ((Nj + R - 1) / R) * R;
     if (Tper < 2 * R || Tper > (1 << 20)) return false;

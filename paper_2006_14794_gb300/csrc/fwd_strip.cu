@@ -1061,9 +1061,10 @@ int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam
 template <typename T, int R, int LAM>
 static cudaError_t launch_coef(const PairSrc &src, const PairPlan *plan, int64_t n,
                                const int64_t *totals, const T *incA, const T *incB, T *cbuf,
-                               int sms, cudaStream_t st) {
+                               int sms, cudaStream_t st, int coef_path) {
     cudaError_t e;
-    if (sizeof(T) == 4 && src.d >= 32) {
+    const bool tc = sizeof(T) == 4 && (coef_path == 2 || (coef_path == 0 && src.d >= 32));
+    if (tc) {
         const int XS = tc_stride(src.d);
         const int smem = (4 * 64 * XS + 64 * TC_CS) * 4;
         auto tk = coef_tc_kernel<R, LAM>;
@@ -1085,7 +1086,8 @@ static cudaError_t launch_coef(const PairSrc &src, const PairPlan *plan, int64_t
 template <typename T, int R, int LAM>
 static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *out,
                                   long long wait_cycles, int fault_inject, cudaStream_t st,
-                                  int64_t max_la, int64_t max_lb, int64_t rowsA, int64_t rowsB) {
+                                  int64_t max_la, int64_t max_lb, int64_t rowsA, int64_t rowsB,
+                                  int coef_path) {
     const int64_t D4 = (src.d + 3) / 4;
     const StripLayout L = strip_layout(n, max_la, max_lb, R, LAM, (int64_t)sizeof(T), rowsA, rowsB, D4);
     unsigned char *w = (unsigned char *)ws;
@@ -1120,7 +1122,7 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, cbuf, sms, st)) != cudaSuccess)
+    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, cbuf, sms, st, coef_path)) != cudaSuccess)
         return e;
     StripArgs<T> a;
     a.src = src;
@@ -1151,7 +1153,7 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
 template <typename T, int R, int LAM>
 static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, const T *gout, T *dA,
                                       T *dB, long long wait_cycles, cudaStream_t st, int64_t max_la,
-                                      int64_t max_lb, int64_t rowsA, int64_t rowsB) {
+                                      int64_t max_lb, int64_t rowsA, int64_t rowsB, int coef_path) {
     const int64_t D4 = (src.d + 3) / 4;
     const StripLayout L = strip_layout_bwd(n, max_la, max_lb, R, LAM, (int64_t)sizeof(T), rowsA, rowsB, D4);
     unsigned char *w = (unsigned char *)ws;
@@ -1183,7 +1185,8 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, (T *)(w + L.coef), sms, st)) !=
+    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, (T *)(w + L.coef), sms, st,
+                                    coef_path)) !=
         cudaSuccess)
         return e;
     {
@@ -1240,11 +1243,11 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
 cudaError_t launch_strip_bwd(const PairSrc &src, int64_t n, int lam, int dtype, void *ws,
                              const void *gout, void *dA, void *dB, long long wait_cycles,
                              cudaStream_t st, int64_t max_la, int64_t max_lb, int64_t rowsA,
-                             int64_t rowsB) {
+                             int64_t rowsB, int coef_path) {
     if (n <= 0) return cudaSuccess;
 #define SIGK_BWD_CASE(T, RR, L)                                                                   \
     return launch_strip_bwd_t<T, RR, L>(src, n, ws, (const T *)gout, (T *)dA, (T *)dB, wait_cycles, \
-                                        st, max_la, max_lb, rowsA, rowsB);
+                                        st, max_la, max_lb, rowsA, rowsB, coef_path);
     if (dtype == SIGK_F64) {
         switch (lam) {
             case 0: SIGK_BWD_CASE(double, 8, 0)
@@ -1266,21 +1269,21 @@ cudaError_t launch_strip_bwd(const PairSrc &src, int64_t n, int lam, int dtype, 
 
 cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void *ws, void *out,
                          long long wait_cycles, int fault_inject, cudaStream_t st, int64_t max_la,
-                         int64_t max_lb, int64_t rowsA, int64_t rowsB) {
+                         int64_t max_lb, int64_t rowsA, int64_t rowsB, int coef_path) {
     if (n <= 0) return cudaSuccess;
     if (dtype == SIGK_F64) {
         switch (lam) {
-            case 0: return launch_strip_t<double, 8, 0>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
-            case 1: return launch_strip_t<double, 8, 1>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
-            case 2: return launch_strip_t<double, 8, 2>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
-            case 3: return launch_strip_t<double, 8, 3>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
+            case 0: return launch_strip_t<double, 8, 0>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
+            case 1: return launch_strip_t<double, 8, 1>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
+            case 2: return launch_strip_t<double, 8, 2>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
+            case 3: return launch_strip_t<double, 8, 3>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
         }
     } else {
         switch (lam) {
-            case 0: return launch_strip_t<float, 16, 0>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
-            case 1: return launch_strip_t<float, 16, 1>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
-            case 2: return launch_strip_t<float, 16, 2>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
-            case 3: return launch_strip_t<float, 16, 3>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB);
+            case 0: return launch_strip_t<float, 16, 0>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
+            case 1: return launch_strip_t<float, 16, 1>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
+            case 2: return launch_strip_t<float, 16, 2>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
+            case 3: return launch_strip_t<float, 16, 3>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
         }
     }
     return cudaErrorInvalidValue;

@@ -88,7 +88,8 @@ struct ChainPlan {
 };
 
 // Returns false when the chained kernel has no instance for these sizes.
-bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p);
+bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p,
+                int rows_per_lane = 0);
 cudaError_t launch_chain_f32(const PairSrc &src, const ChainPlan &p, int64_t n_pairs,
                              float *out, cudaStream_t st);
 
@@ -110,7 +111,7 @@ int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam
                               int64_t rowsA, int64_t rowsB, int64_t d);
 cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void *ws, void *out,
                          long long wait_cycles, int fault_inject, cudaStream_t st, int64_t max_la,
-                         int64_t max_lb, int64_t rowsA, int64_t rowsB);
+                         int64_t max_lb, int64_t rowsA, int64_t rowsB, int coef_path);
 
 // Point rows of the src.A and src.B arrays of a call of n_total pairs.
 inline void src_rows(const PairSrc &s, int64_t n_total, int64_t &ra, int64_t &rb) {
@@ -125,7 +126,7 @@ int64_t strip_bwd_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int
 cudaError_t launch_strip_bwd(const PairSrc &src, int64_t n, int lam, int dtype, void *ws,
                              const void *gout, void *dA, void *dB, long long wait_cycles,
                              cudaStream_t st, int64_t max_la, int64_t max_lb, int64_t rowsA,
-                             int64_t rowsB);
+                             int64_t rowsB, int coef_path);
 
 cudaError_t launch_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n,
                         int dtype, void *out, cudaStream_t st);

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+from typing import NamedTuple, Optional, Union
 
 import torch
 
@@ -21,7 +22,8 @@ from . import build as _build
 
 SIGK_OK, SIGK_EINVAL, SIGK_ENOMEM_WS, SIGK_ECUDA, SIGK_ETIMEOUT, SIGK_EUNSUPPORTED = range(6)
 SIGK_F32, SIGK_F64 = 0, 1
-REC_AUTO, REC_CHAIN, REC_PLAIN = 0, 1, 2
+REC_AUTO, REC_CHAIN, REC_PLAIN, REC_STRIP = 0, 1, 2, 3
+COEF_AUTO, COEF_FMA, COEF_TC = 0, 1, 2
 OP_PAIRS, OP_GRAM, OP_PAIRS_VARLEN, OP_PAIRS_BACKWARD, OP_GRAM_BACKWARD = range(5)
 
 _vp = ctypes.c_void_p
@@ -30,7 +32,18 @@ _int = ctypes.c_int
 
 
 class SigkOpts(ctypes.Structure):
-    _fields_ = [("rec", _int), ("symmetric", _int), ("fault_inject", _int), ("reserved", _int * 5)]
+    _fields_ = [("rec", _int), ("symmetric", _int), ("fault_inject", _int),
+                ("rows_per_lane", _int), ("coef_path", _int), ("reserved", _int * 3)]
+
+
+class Schedule(NamedTuple):
+    """How a call is scheduled (the fields of sigk_opts that pick the kernels):
+    rec (REC_*), rows_per_lane of the chained kernel (4, 8, 16; 0 = smallest
+    that fits) and the strip path's coefficient kernel (COEF_*).  Every
+    schedule computes the same scheme; they differ in speed only."""
+    rec: int = REC_AUTO
+    rows_per_lane: int = 0
+    coef_path: int = COEF_AUTO
 
 
 _lib = None
@@ -82,13 +95,17 @@ def lib(build_if_missing: bool = True):
 
 
 class SigkError(RuntimeError):
-    pass
+    """A libsigk call returned an error; ``status`` is its sigk_status code."""
+
+    def __init__(self, msg: str, status: int = -1):
+        super().__init__(msg)
+        self.status = status
 
 
 def _check(status: int, what: str):
     if status != SIGK_OK:
         msg = lib().sigk_strerror(status).decode()
-        raise SigkError("%s failed: %s (status %d)" % (what, msg, status))
+        raise SigkError("%s failed: %s (status %d)" % (what, msg, status), status)
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -109,12 +126,28 @@ def _stream(dev) -> int:
     return torch.cuda.current_stream(dev).cuda_stream
 
 
-def _opts(rec: int = REC_AUTO, symmetric: bool = False, fault_inject: bool = False):
+def _opts(rec: int = REC_AUTO, symmetric: bool = False, fault_inject: bool = False,
+          schedule: Optional[Schedule] = None):
     o = SigkOpts()
     o.rec = int(rec)
+    if schedule is not None:
+        o.rec = int(schedule.rec)
+        o.rows_per_lane = int(schedule.rows_per_lane)
+        o.coef_path = int(schedule.coef_path)
     o.symmetric = 1 if symmetric else 0
     o.fault_inject = 1 if fault_inject else 0
     return o
+
+
+def _resolve(schedule, op, *shape_args):
+    """schedule may be None, a Schedule, or "tuned": look the shape up in the
+    tuner's cache (timing the candidates on a miss)."""
+    if isinstance(schedule, str):
+        if schedule != "tuned":
+            raise ValueError("schedule must be a Schedule, None or 'tuned'")
+        from . import tune
+        return tune.lookup(op, *shape_args)
+    return schedule
 
 
 def _status(ws, device):
@@ -137,10 +170,12 @@ def _workspace(op, b, b2, L, M, d, lam, dt, o, device):
 
 
 def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO,
-          check_status: bool = False, fault_inject: bool = False) -> torch.Tensor:
+          check_status: bool = False, fault_inject: bool = False,
+          schedule: Union[Schedule, str, None] = None) -> torch.Tensor:
     """out[b] = k(X_b, Y_b).  X: [B, L, d], Y: [B, M, d] (same dtype, same CUDA device).
     check_status: synchronise and raise SigkError if a bounded device wait
-    expired (strip path only).  fault_inject: test switch of sigk_opts."""
+    expired (strip path only).  fault_inject: test switch of sigk_opts.
+    schedule: a Schedule (overrides rec) or "tuned" (the tuner's choice)."""
     X, Y = _dev(X, "X"), _dev(Y, "Y")
     if X.dim() != 3 or Y.dim() != 3 or X.shape[0] != Y.shape[0] or X.shape[2] != Y.shape[2]:
         raise ValueError("pairs wants X [B,L,d] and Y [B,M,d]")
@@ -150,7 +185,8 @@ def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AU
     M = Y.shape[1]
     dt = _dtype_code(X)
     out = torch.empty(B, dtype=X.dtype, device=X.device)
-    o = _opts(rec, fault_inject=fault_inject)
+    schedule = _resolve(schedule, "pairs", X, Y, dyadic_order)
+    o = _opts(rec, fault_inject=fault_inject, schedule=schedule)
     ws, nws = _workspace(OP_PAIRS, B, 0, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_pairs(X.data_ptr(), Y.data_ptr(), B, L, M, d, int(dyadic_order), dt,
                             ctypes.byref(o), out.data_ptr(), _ptr(ws), nws, _stream(X.device)),
@@ -161,9 +197,10 @@ def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AU
 
 
 def gram(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO,
-         symmetric: bool = False, check_status: bool = False) -> torch.Tensor:
+         symmetric: bool = False, check_status: bool = False,
+         schedule: Union[Schedule, str, None] = None) -> torch.Tensor:
     """out[i, j] = k(X_i, Y_j).  With symmetric=True, Y must be X and only the
-    upper triangle is solved (then mirrored)."""
+    upper triangle is solved (then mirrored).  schedule: as for pairs."""
     X, Y = _dev(X, "X"), _dev(Y, "Y")
     if X.dim() != 3 or Y.dim() != 3 or X.shape[2] != Y.shape[2]:
         raise ValueError("gram wants X [Bx,L,d] and Y [By,M,d]")
@@ -173,7 +210,8 @@ def gram(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUT
     By, M = Y.shape[0], Y.shape[1]
     dt = _dtype_code(X)
     out = torch.empty(Bx, By, dtype=X.dtype, device=X.device)
-    o = _opts(rec, symmetric)
+    schedule = _resolve(schedule, "gram", X, Y, dyadic_order)
+    o = _opts(rec, symmetric, schedule=schedule)
     ws, nws = _workspace(OP_GRAM, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_gram(X.data_ptr(), Y.data_ptr(), Bx, By, L, M, d, int(dyadic_order), dt,
                            ctypes.byref(o), out.data_ptr(), _ptr(ws), nws, _stream(X.device)),
@@ -185,8 +223,10 @@ def gram(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUT
 
 def pairs_varlen(Xp: torch.Tensor, x_off: torch.Tensor, Yp: torch.Tensor, y_off: torch.Tensor,
                  dyadic_order: int, max_len: int, rec: int = REC_AUTO, check_status: bool = False,
-                 fault_inject: bool = False) -> torch.Tensor:
-    """Pairs of uneven lengths: Xp [sum L, d] with int64 offsets x_off [B+1] (on the GPU)."""
+                 fault_inject: bool = False,
+                 schedule: Union[Schedule, str, None] = None) -> torch.Tensor:
+    """Pairs of uneven lengths: Xp [sum L, d] with int64 offsets x_off [B+1] (on the GPU).
+    schedule: as for pairs."""
     Xp, Yp = _dev(Xp, "Xp"), _dev(Yp, "Yp")
     x_off, y_off = _dev(x_off, "x_off"), _dev(y_off, "y_off")
     if x_off.dtype != torch.int64 or y_off.dtype != torch.int64:
@@ -195,7 +235,8 @@ def pairs_varlen(Xp: torch.Tensor, x_off: torch.Tensor, Yp: torch.Tensor, y_off:
     d = Xp.shape[1]
     dt = _dtype_code(Xp)
     out = torch.empty(B, dtype=Xp.dtype, device=Xp.device)
-    o = _opts(rec, fault_inject=fault_inject)
+    schedule = _resolve(schedule, "pairs_varlen", Xp, x_off, Yp, y_off, dyadic_order, max_len)
+    o = _opts(rec, fault_inject=fault_inject, schedule=schedule)
     ws, nws = _workspace(OP_PAIRS_VARLEN, B, 0, max_len, max_len, d, dyadic_order, dt, o,
                          Xp.device)
     _check(lib().sigk_pairs_varlen(Xp.data_ptr(), x_off.data_ptr(), Yp.data_ptr(),
@@ -212,7 +253,8 @@ def version() -> str:
 
 
 def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
-                   need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO):
+                   need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
+                   schedule: Optional[Schedule] = None):
     """(dX, dY) with dX[b] = grad_out[b] dk(X_b, Y_b)/dX_b (None when not needed)."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     B, L, d = X.shape
@@ -221,7 +263,7 @@ def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dya
     grad_out = grad_out.to(X.dtype)
     dX = torch.empty_like(X) if need_dx else None
     dY = torch.empty_like(Y) if need_dy else None
-    o = _opts(rec)
+    o = _opts(rec, schedule=schedule)
     ws, nws = _workspace(OP_PAIRS_BACKWARD, B, 0, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_pairs_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), B, L, M, d,
                                      int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
@@ -230,7 +272,8 @@ def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dya
 
 
 def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
-                  need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO):
+                  need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
+                  schedule: Optional[Schedule] = None):
     """(dX, dY): dX[i] = sum_j grad_out[i,j] dk(X_i,Y_j)/dX_i, dY[j] likewise."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     Bx, L, d = X.shape
@@ -239,7 +282,7 @@ def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyad
     grad_out = grad_out.to(X.dtype).contiguous()
     dX = torch.empty_like(X) if need_dx else None
     dY = torch.empty_like(Y) if need_dy else None
-    o = _opts(rec)
+    o = _opts(rec, schedule=schedule)
     ws, nws = _workspace(OP_GRAM_BACKWARD, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_gram_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), Bx, By, L, M,
                                     d, int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
@@ -347,6 +390,11 @@ class Graphed:
         for dst, src in zip(self.static_in, args):
             if isinstance(dst, torch.Tensor):
                 dst.copy_(src, non_blocking=True)
+        self.graph.replay()
+        return self.static_out
+
+    def replay(self):
+        """Replays the captured call on the inputs already in the static buffers."""
         self.graph.replay()
         return self.static_out
 

@@ -76,3 +76,35 @@ def test_argument_checks_need_no_gpu(libsigk):
     # empty batches are valid and launch nothing
     assert libsigk.sigk_pairs(None, None, 0, 4, 4, 2, 0, 0, None, None, None, 0, None) == sigk.SIGK_OK
     assert libsigk.sigk_gram(None, None, 0, 5, 4, 4, 2, 0, 0, None, None, None, 0, None) == sigk.SIGK_OK
+
+
+def test_schedule_options_are_checked(libsigk):
+    from paper_2006_14794_gb300 import sigk
+    P = ctypes.c_void_p(16)
+
+    def call(dtype=0, **kw):
+        o = sigk.SigkOpts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return libsigk.sigk_pairs(P, P, 3, 4, 4, 2, 0, dtype, ctypes.byref(o), P, None, 0, None)
+
+    assert call(rows_per_lane=3) == sigk.SIGK_EINVAL
+    assert call(rows_per_lane=32) == sigk.SIGK_EINVAL
+    assert call(coef_path=3) == sigk.SIGK_EINVAL
+    assert call(coef_path=-1) == sigk.SIGK_EINVAL
+    assert call(rec=4) == sigk.SIGK_EINVAL
+    # the tensor-core coefficient kernel is f32 only
+    assert call(dtype=1, coef_path=2) == sigk.SIGK_EUNSUPPORTED
+
+
+def test_forced_strip_schedule_asks_for_workspace(libsigk):
+    from paper_2006_14794_gb300 import sigk
+    auto, strip = sigk.SigkOpts(), sigk.SigkOpts()
+    strip.rec = sigk.REC_STRIP
+    # 64 pairs of 33-point paths in f64: the default one-block-per-pair sweep
+    # needs no workspace, the strip path does
+    n_auto = libsigk.sigk_workspace_bytes(sigk.OP_PAIRS, 64, 0, 33, 33, 4, 1, 1, ctypes.byref(auto))
+    n_strip = libsigk.sigk_workspace_bytes(sigk.OP_PAIRS, 64, 0, 33, 33, 4, 1, 1, ctypes.byref(strip))
+    assert n_auto == 0 and n_strip > 0
+    # no strip instance above dyadic order 3: nothing to size
+    assert libsigk.sigk_workspace_bytes(sigk.OP_PAIRS, 64, 0, 33, 33, 4, 4, 1, ctypes.byref(strip)) == 0
