@@ -71,8 +71,15 @@ typedef enum { SIGK_F32 = 0, SIGK_F64 = 1 } sigk_dtype;   /* storage AND arithme
  *    as printed (f64) or its difference form (f32): the baseline.
  *  STRIP: the strip path even where the register chain would apply
  *    (SIGK_EUNSUPPORTED where the strip path has no instance).
+ *  BAND (f32, equal lengths, 2^lambda (L-1) <= 512 for the shorter path,
+ *    dyadic_order <= 3): the register chain reading coarse-cell coefficients
+ *    that a contraction kernel first writes into a banded buffer in the
+ *    workspace (4 bytes per coarse cell); CHAIN and AUTO take it for f32
+ *    pairs that fit a warp but are too wide (d > 16) for inline products.
  *  AUTO: CHAIN for f32 (PLAIN when CHAIN has no instance), PLAIN for f64. */
-typedef enum { SIGK_REC_AUTO = 0, SIGK_REC_CHAIN = 1, SIGK_REC_PLAIN = 2, SIGK_REC_STRIP = 3 } sigk_rec;
+typedef enum {
+    SIGK_REC_AUTO = 0, SIGK_REC_CHAIN = 1, SIGK_REC_PLAIN = 2, SIGK_REC_STRIP = 3, SIGK_REC_BAND = 4
+} sigk_rec;
 
 typedef struct {
     int rec;          /* sigk_rec; 0 = auto                                   */

@@ -11,7 +11,7 @@ namespace {
 
 bool opts_ok(const sigk_opts *o) {
     if (!o) return true;
-    if (o->rec < SIGK_REC_AUTO || o->rec > SIGK_REC_STRIP) return false;
+    if (o->rec < SIGK_REC_AUTO || o->rec > SIGK_REC_BAND) return false;
     if (o->symmetric != 0 && o->symmetric != 1) return false;
     if (o->fault_inject != 0 && o->fault_inject != 1) return false;
     if (o->rows_per_lane != 0 && o->rows_per_lane != 4 && o->rows_per_lane != 8 &&
@@ -64,22 +64,38 @@ void strip_batch(const PairSrc &src, int64_t n, int64_t la, int64_t lb, int lam,
     }
 }
 
-enum Path { P_FILL, P_CHAIN, P_STRIP, P_PLAIN };
+enum Path { P_FILL, P_CHAIN, P_BAND, P_STRIP, P_PLAIN };
+
+// Band-form pairs per launch and the workspace (the coefficient band) that needs.
+void band_batch(const BandPlan &bp, int64_t n, int64_t &nb, int64_t &bytes) {
+    nb = n;
+    bytes = band_bytes(bp, nb);
+    while (nb > 1 && bytes > STRIP_WS_CAP) {
+        nb = (nb + 1) / 2;
+        bytes = band_bytes(bp, nb);
+    }
+}
 
 Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, ChainPlan *cp,
-                    int rows_per_lane = 0) {
+                    int rows_per_lane = 0, BandPlan *bpo = nullptr) {
     if (src.La < 2 || src.Lb < 2) return P_FILL;
     if (rec == SIGK_REC_PLAIN) return P_PLAIN;
     if (rec == SIGK_REC_STRIP) return strip_supported(lam, src.d, dtype) ? P_STRIP : P_FILL;
+    if (rec == SIGK_REC_BAND && dtype != SIGK_F32) return P_FILL;
     if (dtype == SIGK_F64 && rec != SIGK_REC_CHAIN) return P_PLAIN;
     if (dtype == SIGK_F32) {
         int64_t la = src.La, lb = src.Lb;
         if (src.mode == PM_PAIRS && la > lb) { int64_t t = la; la = lb; lb = t; }
+        BandPlan bp;
+        const bool band = band_geometry(la, lb, lam, rows_per_lane, bp);
+        if (band && bpo) *bpo = bp;
+        if (rec == SIGK_REC_BAND) return band ? P_BAND : P_FILL;
         ChainPlan p;
         if (chain_plan(n, la, lb, src.d, lam, p, rows_per_lane)) {
             if (cp) *cp = p;
             return P_CHAIN;
         }
+        if (band) return P_BAND;
         if (rows_per_lane != 0) return P_FILL;   // the requested schedule has no instance
     }
     if (strip_supported(lam, src.d, dtype)) return P_STRIP;
@@ -109,7 +125,8 @@ int run_uniform(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opt
     if (n_pairs == 0) return SIGK_OK;
     const int rec = rec_of(opts);
     ChainPlan p;
-    switch (choose_uniform(src, n_pairs, lam, dtype, rec, &p, rows_of(opts))) {
+    BandPlan bp;
+    switch (choose_uniform(src, n_pairs, lam, dtype, rec, &p, rows_of(opts), &bp)) {
         case P_FILL:
             if (src.La < 2 || src.Lb < 2) return cuda_status(launch_fill_one(out, n_pairs, dtype, st));
             return SIGK_EUNSUPPORTED;
@@ -122,6 +139,24 @@ int run_uniform(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opt
                 int64_t tl = s2.La; s2.La = s2.Lb; s2.Lb = tl;
             }
             return cuda_status(launch_chain_f32(s2, p, n_pairs, (float *)out, st));
+        }
+        case P_BAND: {
+            PairSrc s2 = src;
+            if (s2.mode == PM_PAIRS && s2.La > s2.Lb) {
+                const void *t = s2.A; s2.A = s2.B; s2.B = t;
+                int64_t tl = s2.La; s2.La = s2.Lb; s2.Lb = tl;
+            }
+            int64_t nb, need;
+            band_batch(bp, n_pairs, nb, need);
+            if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
+            for (int64_t k0 = 0; k0 < n_pairs; k0 += nb) {
+                PairSrc s3 = s2;
+                s3.kbase = s2.kbase + k0;
+                const int64_t m = n_pairs - k0 < nb ? n_pairs - k0 : nb;
+                cudaError_t e = launch_band_f32(s3, bp, m, (float *)out, ws, st);
+                if (e != cudaSuccess) return cuda_status(e);
+            }
+            return SIGK_OK;
         }
         case P_STRIP:
             return run_strip(src, n_pairs, lam, dtype, src.La, src.Lb, opts, out, ws, ws_bytes, st);
@@ -262,8 +297,14 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         src.La = L <= M ? L : M; src.Lb = L <= M ? M : L;
         src.nb = L <= M ? By : B_or_Bx;
     }
-    if (choose_uniform(src, n_pairs, dyadic_order, dtype, rec_of(opts), nullptr, rows_of(opts)) != P_STRIP)
-        return 0;
+    BandPlan bp;
+    const Path path = choose_uniform(src, n_pairs, dyadic_order, dtype, rec_of(opts), nullptr,
+                                     rows_of(opts), &bp);
+    if (path == P_BAND) {
+        band_batch(bp, n_pairs, nb, need);
+        return (size_t)need;
+    }
+    if (path != P_STRIP) return 0;
     strip_batch(src, n_pairs, src.La, src.Lb, dyadic_order, dtype, nb, need);
     return (size_t)need;
 }
@@ -339,6 +380,7 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, cons
     src.La = max_len; src.Lb = max_len;
     src.d = d;
     const int rec = rec_of(opts);
+    if (rec == SIGK_REC_BAND) return SIGK_EUNSUPPORTED;   // the band form needs equal lengths
     const bool strip = strip_supported(dyadic_order, d, dtype) &&
                        (rec == SIGK_REC_STRIP ||
                         (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN));

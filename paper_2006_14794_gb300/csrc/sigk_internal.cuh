@@ -93,6 +93,20 @@ bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, Cha
 cudaError_t launch_chain_f32(const PairSrc &src, const ChainPlan &p, int64_t n_pairs,
                              float *out, cudaStream_t st);
 
+// The band form (fwd_band.cu): the row chain reading coefficients that a
+// contraction kernel formed beforehand into a banded buffer (the workspace).
+struct BandPlan {
+    int R, lam, NG;         // rows per lane, dyadic order, coarse rows per lane
+    int TperR;              // macro-steps per pair
+    int NQ, NQV, vrows;     // padded coarse columns, virtual columns, virtual coarse rows
+    int64_t slot_floats;    // floats per (pair, position) slot row: 32 lanes x NG x NG
+};
+// Geometry only (no device query); false when the band form has no instance.
+bool band_geometry(int64_t La, int64_t Lb, int lam, int rows_per_lane, BandPlan &p);
+int64_t band_bytes(const BandPlan &p, int64_t n_pairs);
+cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pairs, float *out,
+                            void *ws, cudaStream_t st);
+
 cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype, void *out,
                          cudaStream_t st);
 

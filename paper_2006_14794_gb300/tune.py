@@ -23,7 +23,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 import torch
 
 from . import sigk
-from .sigk import COEF_FMA, COEF_TC, REC_CHAIN, REC_PLAIN, REC_STRIP, Schedule
+from .sigk import COEF_FMA, COEF_TC, REC_BAND, REC_CHAIN, REC_PLAIN, REC_STRIP, Schedule
 
 _lock = threading.Lock()
 _mem: Dict[str, Schedule] = {}
@@ -45,11 +45,12 @@ def cache_path() -> str:
 
 def candidates(op: str, dtype: torch.dtype) -> List[Schedule]:
     """Schedules worth timing, roughly fastest-first so that slow ones are cut
-    short.  The uneven-length call has no chained form; f64 has no
-    tensor-core coefficient kernel."""
+    short.  The uneven-length call has no chained or band form; f64 has
+    neither those nor the tensor-core coefficient kernel."""
     c: List[Schedule] = []
     if op != "pairs_varlen" and dtype == torch.float32:
         c += [Schedule(REC_CHAIN, r, 0) for r in (4, 8, 16)]
+        c += [Schedule(REC_BAND, r, 0) for r in (4, 8, 16)]
     if dtype == torch.float32:
         c.append(Schedule(REC_STRIP, 0, COEF_TC))
     c.append(Schedule(REC_STRIP, 0, COEF_FMA))

@@ -92,7 +92,7 @@ def test_schedule_options_are_checked(libsigk):
     assert call(rows_per_lane=32) == sigk.SIGK_EINVAL
     assert call(coef_path=3) == sigk.SIGK_EINVAL
     assert call(coef_path=-1) == sigk.SIGK_EINVAL
-    assert call(rec=4) == sigk.SIGK_EINVAL
+    assert call(rec=5) == sigk.SIGK_EINVAL
     # the tensor-core coefficient kernel is f32 only
     assert call(dtype=1, coef_path=2) == sigk.SIGK_EUNSUPPORTED
 
@@ -108,3 +108,21 @@ def test_forced_strip_schedule_asks_for_workspace(libsigk):
     assert n_auto == 0 and n_strip > 0
     # no strip instance above dyadic order 3: nothing to size
     assert libsigk.sigk_workspace_bytes(sigk.OP_PAIRS, 64, 0, 33, 33, 4, 4, 1, ctypes.byref(strip)) == 0
+
+
+def test_band_schedule_is_f32_and_equal_length_only(libsigk):
+    from paper_2006_14794_gb300 import sigk
+    o = sigk.SigkOpts()
+    o.rec = sigk.REC_BAND
+    P = ctypes.c_void_p(16)
+    # f64 has no band form
+    assert libsigk.sigk_pairs(P, P, 3, 40, 40, 32, 1, 1, ctypes.byref(o), P, P, 1 << 30, None) == \
+        sigk.SIGK_EUNSUPPORTED
+    # neither have uneven lengths
+    assert libsigk.sigk_pairs_varlen(P, P, P, P, 3, 32, 40, 1, 0, ctypes.byref(o), P, P, 1 << 30, None) == \
+        sigk.SIGK_EUNSUPPORTED
+    # the band workspace: (pairs x macro-steps + 1) slot rows of 32 x NG^2 floats.
+    # 256-point paths at dyadic order 1: 510 refined rows -> 16 rows per lane,
+    # NG = 8 coarse rows per lane, 512 padded columns -> 32 macro-steps per pair
+    n = libsigk.sigk_workspace_bytes(sigk.OP_GRAM, 4, 5, 256, 256, 32, 1, 0, ctypes.byref(o))
+    assert n == 4 * (20 * 32 + 1) * 32 * 64

@@ -1,0 +1,103 @@
+"""The band form (coefficients formed by a contraction kernel into a banded
+buffer, read by the register chain): parity with the FP64 oracle through the C
+ABI, across every (rows per lane, dyadic order) instance, pair turnovers within
+a warp's chain, virtual rows and columns, both orientations, symmetric Grams,
+and the shapes of the 128 x 128 MMD workload."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2006_14794_gb300 import inputs
+from tests.gpu_util import need_gpu, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+    from paper_2006_14794_gb300 import sigk
+    sigk.lib()
+
+
+def S():
+    from paper_2006_14794_gb300 import sigk
+    return sigk
+
+
+def band(R):
+    return S().Schedule(S().REC_BAND, R, 0)
+
+
+@pytest.mark.parametrize("R,lam,L,M,d", [
+    (16, 1, 256, 256, 32),   # the MMD shape: 510 refined rows, 8 coarse rows per lane
+    (16, 1, 200, 300, 24),   # virtual rows (398 of 512) and virtual columns
+    (16, 2, 100, 77, 5),     # 4 coarse rows per lane
+    (16, 3, 60, 61, 3),      # 2 coarse rows per lane
+    (8, 0, 230, 256, 40),    # dyadic order 0, 8 coarse rows per lane
+    (8, 1, 129, 140, 17),
+    (8, 2, 40, 33, 9),
+    (4, 0, 100, 120, 64),
+    (4, 1, 60, 90, 33),
+])
+def test_band_gram_matches_oracle(R, lam, L, M, d):
+    # enough pairs that warps chain several of them (pair turnovers inside a warp)
+    Bx, By = 7, 9
+    X32, X64 = inputs.f32(inputs.random_paths(3100 + R + lam, Bx, L, d, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(3200 + R + lam, By, M, d, time_channel=True))
+    ref = oracle.gram(X64, Y64, lam)
+    got = S().gram(to_dev(X32), to_dev(Y32), lam, schedule=band(R)).cpu().numpy()
+    assert rel_err(got, ref) <= F32_TOL
+    # the other orientation (rows refine the shorter path either way)
+    got_t = S().gram(to_dev(Y32), to_dev(X32), lam, schedule=band(R)).cpu().numpy()
+    assert rel_err(got_t, ref.T) <= F32_TOL
+
+
+def test_band_pairs_both_orders_and_long_chains():
+    lam, d = 1, 32
+    B = 3000   # ~2-3 pairs per warp at 12 warps per SM
+    X32, X64 = inputs.f32(inputs.random_paths(3300, B, 40, d, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(3301, B, 35, d, time_channel=True))
+    ref = oracle.pairs(X64, Y64, lam)
+    got = S().pairs(to_dev(X32), to_dev(Y32), lam, schedule=band(16)).cpu().numpy()
+    assert rel_err(got, ref) <= F32_TOL
+    got2 = S().pairs(to_dev(Y32), to_dev(X32), lam, schedule=band(16)).cpu().numpy()
+    assert rel_err(got2, ref) <= F32_TOL
+
+
+def test_band_symmetric_gram():
+    lam, d = 1, 32
+    X32, X64 = inputs.f32(inputs.random_paths(3400, 11, 129, d, time_channel=True))
+    ref = oracle.gram(X64, X64, lam)
+    got = S().gram(to_dev(X32), to_dev(X32), lam, symmetric=True, schedule=band(8)).cpu().numpy()
+    assert rel_err(got, ref) <= F32_TOL
+    assert np.array_equal(got, got.T)
+
+
+def test_band_is_the_default_for_wide_short_pairs():
+    """d = 32 has no inline-product chain instance: AUTO takes the band form,
+    which needs workspace; its result equals the forced schedule's bit for bit."""
+    sigk = S()
+    lam, d = 1, 32
+    w = inputs.mmd_batches(B=6)
+    X32, X64 = inputs.f32(w["X"])
+    Y32, Y64 = inputs.f32(w["Y"])
+    auto = sigk.gram(to_dev(X32), to_dev(Y32), lam).cpu().numpy()
+    forced = sigk.gram(to_dev(X32), to_dev(Y32), lam, schedule=band(16)).cpu().numpy()
+    assert np.array_equal(auto, forced)
+    assert rel_err(auto, oracle.gram(X64, Y64, lam)) <= F32_TOL
+
+
+def test_band_refuses_what_it_cannot_do():
+    sigk = S()
+    X = to_dev(inputs.random_paths(3500, 2, 600, 4, time_channel=True))
+    with pytest.raises(sigk.SigkError) as ei:   # 599 rows do not fit a warp
+        sigk.pairs(X, X, 0, schedule=band(16))
+    assert ei.value.status == sigk.SIGK_EUNSUPPORTED
+    X64 = to_dev(inputs.random_paths(3501, 2, 60, 4, time_channel=True), torch.float64)
+    with pytest.raises(sigk.SigkError) as ei:
+        sigk.pairs(X64, X64, 1, schedule=band(16))
+    assert ei.value.status == sigk.SIGK_EUNSUPPORTED

@@ -12,12 +12,13 @@ from paper_2006_14794_gb300.sigk import COEF_FMA, COEF_TC, REC_CHAIN, REC_PLAIN,
 def test_candidates_cover_every_path():
     c32 = tune.candidates("gram", torch.float32)
     assert {s.rows_per_lane for s in c32 if s.rec == REC_CHAIN} == {4, 8, 16}
+    assert {s.rows_per_lane for s in c32 if s.rec == sigk.REC_BAND} == {4, 8, 16}
     assert Schedule(REC_STRIP, 0, COEF_TC) in c32 and Schedule(REC_STRIP, 0, COEF_FMA) in c32
     assert c32[-1].rec == REC_PLAIN
     c64 = tune.candidates("pairs", torch.float64)
-    assert all(s.rec != REC_CHAIN and s.coef_path != COEF_TC for s in c64)
+    assert all(s.rec not in (REC_CHAIN, sigk.REC_BAND) and s.coef_path != COEF_TC for s in c64)
     cv = tune.candidates("pairs_varlen", torch.float32)
-    assert all(s.rec != REC_CHAIN for s in cv)
+    assert all(s.rec not in (REC_CHAIN, sigk.REC_BAND) for s in cv)
 
 
 def test_pick_takes_the_fastest_that_ran():
