@@ -185,8 +185,41 @@ void bwd_strip_batch(const PairSrc &src, int64_t n, int lam, int dtype, int64_t 
     }
 }
 
-int64_t backward_ws_bytes(const PairSrc &src, int64_t n, int lam, int dtype, int rec) {
+// The band backward's orientation: rows refine the shorter path.  For a Gram
+// from sigk_gram_backward (A = X with out_si = nb, B = Y) the swap enumerates
+// (Y path, X path) like sigk_gram does.
+PairSrc band_orient(const PairSrc &src, int64_t n, bool &swapped) {
+    PairSrc o = src;
+    swapped = src.La > src.Lb;
+    if (!swapped) return o;
+    o.A = src.B; o.B = src.A;
+    o.La = src.Lb; o.Lb = src.La;
+    if (src.mode == PM_GRAM) {
+        o.nb = n / src.nb;            // the X paths are now the columns
+        o.out_si = 1;
+        o.out_sj = src.nb;
+    }
+    return o;
+}
+
+bool bwd_uses_band(const PairSrc &src, int lam, int dtype, int rec, int rows, BandPlan &bp) {
+    if (dtype != SIGK_F32 || rec == SIGK_REC_PLAIN || rec == SIGK_REC_STRIP) return false;
+    if (src.mode != PM_PAIRS && src.mode != PM_GRAM) return false;
+    const int64_t la = src.La < src.Lb ? src.La : src.Lb, lb = src.La < src.Lb ? src.Lb : src.La;
+    return band_geometry(la, lb, lam, rows, bp);
+}
+
+int64_t backward_ws_bytes(const PairSrc &src, int64_t n, int lam, int dtype, int rec, int rows = 0) {
     if (n == 0 || src.La < 2 || src.Lb < 2) return 0;
+    BandPlan bp;
+    if (bwd_uses_band(src, lam, dtype, rec, rows, bp)) {
+        bool sw;
+        const PairSrc o = band_orient(src, n, sw);
+        int64_t bytes;
+        band_bwd_batch(o, bp, n, STRIP_WS_CAP, bytes);
+        return bytes;
+    }
+    if (rec == SIGK_REC_BAND) return -1;
     if (bwd_uses_strip(lam, src.d, dtype, rec)) {
         int64_t nb, need;
         bwd_strip_batch(src, n, lam, dtype, nb, need);
@@ -206,6 +239,17 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
     if (n_pairs == 0 || src.La < 2 || src.Lb < 2 || (!dX && !dY)) return SIGK_OK;
     const int rec = rec_of(opts);
     if (rec == SIGK_REC_STRIP && !strip_supported(lam, src.d, dtype)) return SIGK_EUNSUPPORTED;
+    BandPlan bp;
+    if (bwd_uses_band(src, lam, dtype, rec, rows_of(opts), bp)) {
+        bool sw;
+        const PairSrc o = band_orient(src, n_pairs, sw);
+        int64_t bytes;
+        const int64_t nbp = band_bwd_batch(o, bp, n_pairs, STRIP_WS_CAP, bytes);
+        if (!ws || (int64_t)ws_bytes < bytes) return SIGK_ENOMEM_WS;
+        float *dA = (float *)(sw ? dY : dX), *dB = (float *)(sw ? dX : dY);
+        return cuda_status(launch_band_bwd_f32(o, bp, n_pairs, nbp, (const float *)gout, dA, dB, ws, st));
+    }
+    if (rec == SIGK_REC_BAND) return SIGK_EUNSUPPORTED;
     if (bwd_uses_strip(lam, src.d, dtype, rec)) {
         int64_t nb, need, ra, rb;
         bwd_strip_batch(src, n_pairs, lam, dtype, nb, need);
@@ -264,7 +308,7 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         bs.mode = op == SIGK_OP_PAIRS_BACKWARD ? PM_PAIRS : PM_GRAM;
         bs.La = L; bs.Lb = M; bs.d = d;
         bs.nb = By;
-        const int64_t need = backward_ws_bytes(bs, n_pairs, dyadic_order, dtype, rec_of(opts));
+        const int64_t need = backward_ws_bytes(bs, n_pairs, dyadic_order, dtype, rec_of(opts), rows_of(opts));
         return need > 0 ? (size_t)need : 0;
     }
     int64_t nb, need;

@@ -1,0 +1,1108 @@
+// Forward sweep, FP32, "band" form: the row-chain wavefront of fwd_chain.cu
+// (one warp solves a chain of pairs of equal shape, lane l owning refined rows
+// R*l .. R*l+R-1, the difference form Q(a,b) = Q(a-1,b) + c (K(a,b-1) +
+// K(a-1,b)), K(a,b) = K(a,b-1) + Q(a,b) of the scheme of Sec. 3.1), with the
+// coarse-cell coefficients c = 1/2 4^-lambda <dx_p, dy_q> (remark after the
+// scheme) formed beforehand by a contraction kernel instead of inside the
+// sweep.  That pays off when d is large: the sweep costs 3 operations per
+// refined cell, an inline dot product d / 4^lambda more.
+//
+// The coefficient buffer is laid out for the sweep ("band" layout).  In
+// macro-step pos of a pair (columns pos*NG .. pos*NG + NG - 1 of the padded
+// coarse grid, NG = R / 2^lambda coarse rows per lane), window w, group g of
+// lane l is at coarse cell (P, Q) = (l*NG + g, pos*NG + w - g).  Slot (pair,
+// pos, lane) holds these NG x NG values as [w][g]: in each window a lane reads
+// NG consecutive floats, and a warp reads 32 slots of one pair position, so
+// every load is a full 32-byte sector.  Cells with Q < 0 (pos = 0, w < g) are
+// the previous pair's last columns, which rows that have not turned over yet
+// still need: they are stored in the next pair's slot 0, so the chain reads
+// pair k's coefficients, tail included, from slots (k, 0 .. TperR - 1) and
+// (k + 1, 0).  Virtual rows and columns (padding, as in fwd_chain.cu) hold 0.
+#include <string.h>
+
+#include "sigk_internal.cuh"
+
+namespace sigk {
+
+namespace {
+
+constexpr int BAND_WARPS = 2;   // warps per CTA of the sweep
+constexpr int BC_THREADS = 256; // threads per CTA of the contraction
+constexpr int BC_DC = 32;       // channels staged per pass of the contraction
+
+struct BandCoefArgs {
+    PairSrc src;
+    int64_t n_pairs;      // pairs of this launch (slot rows 0 .. n_pairs)
+    int TperR, NQ, NQV, vrows;
+    float scale;          // 1/2 4^-lambda
+    float *band;
+};
+
+// Shared memory of the contraction: increments of one pair, channel-major.
+//   dx: [BC_DC][32*NG + 4]      row P (padded, virtual rows zero)
+//   dy: [BC_DC][ystride]        index Q + NG - 1 (zeros for Q < 0 and Q >= NQ)
+template <int NG>
+__host__ __device__ constexpr int bc_xstride() { return 32 * NG + 4; }
+__host__ __device__ inline int bc_ystride(int NQ, int NG) { return ((NQ + 2 * NG + 3) / 4) * 4 + 4; }
+
+// Position of row P of the staged row increments: with 8 rows per lane the
+// two 16-byte halves of a lane's rows are swapped for lanes 4..7 of every 8,
+// so the 8 lanes of a shared-memory phase read 8 distinct bank quads.
+template <int NG>
+__device__ __forceinline__ int bc_xpos(int P) {
+    if constexpr (NG == 8) return P ^ (((P >> 5) & 1) << 2);
+    else return P;
+}
+
+// One thread per slot (lane l, position pos) of the pair: the NG x NG cells
+// (l*NG + g, pos*NG + w - g), each a d-term dot product of increments.
+// Position TperR is the pair's tail (the cells with w < g there), written into
+// slot 0 of the next pair.  Each block takes a contiguous run of pairs, so
+// consecutive pairs of a Gram row share the row path and its staged
+// increments.
+template <int NG>
+__global__ void __launch_bounds__(BC_THREADS, 2) band_coef_kernel(BandCoefArgs a) {
+    extern __shared__ __align__(16) float bcs[];
+    constexpr int NPP = 32 * NG;
+    constexpr int XS = bc_xstride<NG>();
+    constexpr int SLOT = NG * NG;
+    const int YS = bc_ystride(a.NQ, NG);
+    float *dxs = bcs;
+    float *dys = bcs + BC_DC * XS;
+    const int64_t d = a.src.d;
+    const int nslots = 32 * (a.TperR + 1);
+    const int64_t per = (a.n_pairs + gridDim.x - 1) / gridDim.x;
+    const int64_t kbeg = (int64_t)blockIdx.x * per;
+    const int64_t kend = kbeg + per < a.n_pairs ? kbeg + per : a.n_pairs;
+    int64_t staged_x = -1;   // point row of the row path whose increments dxs holds (d <= BC_DC)
+    for (int64_t k = kbeg; k < kend; ++k) {
+        const PairRef pr = pair_ref(a.src, k);
+        const float *x = (const float *)a.src.A + pr.a_row0 * d;
+        const float *y = (const float *)a.src.B + pr.b_row0 * d;
+        const int nx = (int)pr.la - 1, ny = (int)pr.lb - 1;   // real coarse rows / columns
+        for (int base = 0; base < nslots; base += BC_THREADS) {
+            const int u = base + (int)threadIdx.x;
+            const int l = u & 31, pos = u >> 5;
+            float acc[NG][NG];
+#pragma unroll
+            for (int w = 0; w < NG; ++w)
+#pragma unroll
+                for (int g = 0; g < NG; ++g) acc[w][g] = 0.f;
+            for (int64_t c0 = 0; c0 < d; c0 += BC_DC) {
+                if (d > BC_DC || base == 0) {
+                    __syncthreads();
+                    // stage channels c0 .. c0 + BC_DC - 1 (consecutive threads take
+                    // consecutive channels of a row: coalesced loads)
+                    if (d > BC_DC || staged_x != pr.a_row0) {
+                        for (int v = threadIdx.x; v < BC_DC * NPP; v += BC_THREADS) {
+                            const int P = v / BC_DC, c = v - (v / BC_DC) * BC_DC;
+                            const int p = P - a.vrows;
+                            float e = 0.f;
+                            if (p >= 0 && p < nx && c0 + c < d)
+                                e = __ldg(x + (int64_t)(p + 1) * d + c0 + c) - __ldg(x + (int64_t)p * d + c0 + c);
+                            dxs[c * XS + bc_xpos<NG>(P)] = e;
+                        }
+                        staged_x = pr.a_row0;
+                    }
+                    for (int v = threadIdx.x; v < BC_DC * YS; v += BC_THREADS) {
+                        const int iq = v / BC_DC, c = v - (v / BC_DC) * BC_DC;
+                        const int q = iq - (NG - 1) - a.NQV;   // real column
+                        float e = 0.f;
+                        if (q >= 0 && q < ny && iq - (NG - 1) < a.NQ && c0 + c < d)
+                            e = __ldg(y + (int64_t)(q + 1) * d + c0 + c) - __ldg(y + (int64_t)q * d + c0 + c);
+                        dys[c * YS + iq] = e;
+                    }
+                    __syncthreads();
+                }
+                if (u < nslots) {
+                    const int cn = (int)(d - c0 < BC_DC ? d - c0 : BC_DC);
+#pragma unroll 2
+                    for (int c = 0; c < cn; ++c) {
+                        float xv[NG], yv[2 * NG];
+                        const float *xr = dxs + c * XS + l * NG;
+                        const float *yr = dys + c * YS + pos * NG;   // Q = pos*NG - (NG-1) + j
+                        if constexpr (NG >= 4) {
+                            const int sw = NG == 8 ? ((l >> 2) & 1) : 0;   // see bc_xpos
+#pragma unroll
+                            for (int h = 0; h < NG / 4; ++h) {
+                                const float4 v = *reinterpret_cast<const float4 *>(xr + 4 * (h ^ sw));
+                                xv[4 * h] = v.x; xv[4 * h + 1] = v.y; xv[4 * h + 2] = v.z; xv[4 * h + 3] = v.w;
+                            }
+#pragma unroll
+                            for (int h = 0; h < NG / 2; ++h) {
+                                const float4 v = *reinterpret_cast<const float4 *>(yr + 4 * h);
+                                yv[4 * h] = v.x; yv[4 * h + 1] = v.y; yv[4 * h + 2] = v.z; yv[4 * h + 3] = v.w;
+                            }
+                        } else {
+                            const float2 v = *reinterpret_cast<const float2 *>(xr);
+                            xv[0] = v.x; xv[1] = v.y;
+                            const float2 w0 = *reinterpret_cast<const float2 *>(yr);
+                            const float2 w1 = *reinterpret_cast<const float2 *>(yr + 2);
+                            yv[0] = w0.x; yv[1] = w0.y; yv[2] = w1.x; yv[3] = w1.y;
+                        }
+#pragma unroll
+                        for (int w = 0; w < NG; ++w)
+#pragma unroll
+                            for (int g = 0; g < NG; ++g)
+                                acc[w][g] = fmaf(xv[g], yv[w - g + NG - 1], acc[w][g]);
+                    }
+                }
+            }
+            if (u >= nslots) continue;
+            if (pos < a.TperR && pos > 0) {
+                float4 *dst = reinterpret_cast<float4 *>(a.band + (((k * a.TperR + pos) * 32) + l) * SLOT);
+                if constexpr (NG >= 4) {
+#pragma unroll
+                    for (int w = 0; w < NG; ++w)
+#pragma unroll
+                        for (int h = 0; h < NG / 4; ++h)
+                            dst[w * (NG / 4) + h] = make_float4(acc[w][4 * h] * a.scale, acc[w][4 * h + 1] * a.scale,
+                                                                acc[w][4 * h + 2] * a.scale, acc[w][4 * h + 3] * a.scale);
+                } else {
+                    dst[0] = make_float4(acc[0][0] * a.scale, acc[0][1] * a.scale, acc[1][0] * a.scale,
+                                         acc[1][1] * a.scale);
+                }
+            } else if (pos == 0) {
+                // the pair's own cells (w >= g); the cells w < g belong to the
+                // previous pair's block, which writes them (pair 0: zeros)
+                float *dst = a.band + ((k * a.TperR) * 32 + l) * SLOT;
+#pragma unroll
+                for (int w = 0; w < NG; ++w)
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        if (w >= g) dst[w * NG + g] = acc[w][g] * a.scale;
+                        else if (k == 0) dst[w * NG + g] = 0.f;
+                    }
+            } else {
+                // pos == TperR: the tail (w < g) into slot 0 of the next pair; after
+                // the last pair the slot has no owner, so its own cells are zeroed
+                float *dst = a.band + (((k + 1) * a.TperR) * 32 + l) * SLOT;
+#pragma unroll
+                for (int w = 0; w < NG; ++w)
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        if (w < g) dst[w * NG + g] = acc[w][g] * a.scale;
+                        else if (k == a.n_pairs - 1) dst[w * NG + g] = 0.f;
+                    }
+            }
+        }
+    }
+}
+
+struct BandArgs {
+    PairSrc src;
+    float *out;
+    const float *band;
+    int64_t n_pairs, ppw;
+    int TperR;
+    // what the adjoint needs to run the sweep backwards (null: forward only)
+    float *ckpt;     // [warp][nck][lane][2R]: (K, Q) of every row after each BAND_CK-th macro-step
+    float *exitk;    // [pair][lane][R]: K of each row on its pair's last column
+    float *botq;     // [warp][steps + 1]: Q of the warp's last row before each step
+    int nck;         // checkpoint slots per warp
+    int64_t bq_stride;
+};
+
+constexpr int BAND_CK = 8;   // macro-steps between checkpoints of the forward state
+
+template <int NG>
+__device__ __forceinline__ void load_window(float (&v)[NG], const float *p) {
+    if constexpr (NG == 8) {
+        const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+        const float4 b = __ldcs(reinterpret_cast<const float4 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else if constexpr (NG == 4) {
+        const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else {
+        const float2 a = __ldcs(reinterpret_cast<const float2 *>(p));
+        v[0] = a.x; v[1] = a.y;
+    }
+}
+
+// The sweep: fwd_chain.cu's chain_f32_kernel with its staging and dot
+// products replaced by one coefficient vector per window, prefetched one
+// macro-step ahead into the registers the window has just consumed.
+template <int R, int LAM, int MINB, bool SAVE>
+__global__ void __launch_bounds__(BAND_WARPS * 32, MINB) chain_band_kernel(BandArgs a) {
+    constexpr int S = 1 << LAM;
+    constexpr int NG = R / S;
+    constexpr int H = R / 2;
+    constexpr int NH = NG / 2;
+    constexpr int JOUT = R - 2;
+    constexpr int SLOT = NG * NG;
+    static_assert(R % S == 0 && NG % 2 == 0 && NG <= 8, "2, 4 or 8 coarse rows per lane");
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * BAND_WARPS + warp;
+    const int64_t k0 = gw * a.ppw;
+    if (k0 >= a.n_pairs) return;   // whole warp
+    const int np = (int)min(a.ppw, a.n_pairs - k0);
+    const int TperR = a.TperR;
+
+    float2 KP[H], QP[H];
+    float2 CN[NH], CO[NH];
+    float cb[NG][NG];   // this macro-step's coefficients [window][group]; refilled window by window
+#pragma unroll
+    for (int i = 0; i < H; ++i) { KP[i] = make_float2(1.f, 1.f); QP[i] = make_float2(0.f, 0.f); }
+#pragma unroll
+    for (int g = 0; g < NH; ++g) { CN[g] = make_float2(0.f, 0.f); CO[g] = CN[g]; }
+    float pK = 1.f, pQ = 0.f;
+
+    // slot of local pair kk at position pp, or null outside the chain (its
+    // first pair's rows before they start, and after the last pair except the
+    // slot that holds that pair's tail)
+    auto slot = [&](int kk, int pp) -> const float * {
+        if (kk < 0 || kk > np || (kk == np && pp != 0)) return nullptr;
+        return a.band + (((k0 + kk) * TperR + pp) * 32 + lane) * (int64_t)SLOT;
+    };
+
+    int kl = (lane == 0) ? 0 : -((lane + TperR - 1) / TperR);
+    int pos = -lane - kl * TperR;
+    {
+        const float *p0 = slot(kl, pos);
+#pragma unroll
+        for (int w = 0; w < NG; ++w) {
+            if (p0) load_window<NG>(cb[w], p0 + w * NG);
+            else
+#pragma unroll
+                for (int g = 0; g < NG; ++g) cb[w][g] = 0.f;
+        }
+    }
+    const int64_t total_m = (int64_t)np * TperR + 32;
+    float *bq = SAVE ? a.botq + gw * a.bq_stride : nullptr;
+    if (SAVE && lane == 31) bq[0] = 0.f;
+
+    for (int64_t m = 0; m < total_m; ++m) {
+        const bool trans = (pos == 0);
+        const float *pn = (pos + 1 == TperR) ? slot(kl + 1, 0) : slot(kl, pos + 1);
+        // exit states go to the pair the rows leave (kl - 1), when it is one of the chain's
+        float *ex = (SAVE && trans && kl >= 1 && kl <= np)
+                        ? a.exitk + ((k0 + kl - 1) * 32 + lane) * (int64_t)R : nullptr;
+
+#pragma unroll
+        for (int w = 0; w < NG; ++w) {
+#pragma unroll
+            for (int g = 0; g < NH; ++g) {
+                CO[g] = CN[g];
+                CN[g] = make_float2(cb[w][g], cb[w][g + NH]);
+            }
+            if (pn) load_window<NG>(cb[w], pn + w * NG);
+            else
+#pragma unroll
+                for (int g = 0; g < NG; ++g) cb[w][g] = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < S; ++jj) {
+                const int j = w * S + jj;
+                const float kH1 = KP[H - 1].x, qH1 = QP[H - 1].x;   // row H-1 before this step
+                float shK = 0.f, shQ = 0.f;
+#pragma unroll
+                for (int i = H - 1; i >= 0; --i) {
+                    const int g1 = i / S, s1 = i % S;   // row i; row i+H: group g1+NH, same s1
+                    if (jj == s1 && trans) {            // row starts its next pair now: k(.,0) = 1
+                        if (g1 == w) {
+                            if (ex) ex[i] = KP[i].x;
+                            KP[i].x = 1.f;
+                        }
+                        if (g1 + NH == w) {
+                            if (ex) ex[i + H] = KP[i].y;
+                            KP[i].y = 1.f;
+                        }
+                    }
+                    const float2 c = (jj >= s1) ? CN[g1] : CO[g1];
+                    float2 ku, qu;
+                    if (i > 0) {
+                        ku = KP[i > 0 ? i - 1 : 0];
+                        qu = QP[i > 0 ? i - 1 : 0];
+                    } else {
+                        ku = make_float2(pK, kH1);
+                        qu = make_float2(pQ, qH1);
+                    }
+                    const float2 sum = __fadd2_rn(KP[i], ku);
+                    const float2 qn = __ffma2_rn(c, sum, qu);
+                    KP[i] = __fadd2_rn(KP[i], qn);
+                    QP[i] = qn;
+                    if (i == H - 1) {
+                        shK = __shfl_up_sync(FULL, KP[i].y, 1);
+                        shQ = __shfl_up_sync(FULL, QP[i].y, 1);
+                        if (j == JOUT && trans && lane == 31) {
+                            const int kp = kl - 1;   // row R-1 just finished pair kp's last column
+                            if (kp >= 0 && kp < np && a.out) {
+                                const PairRef pr = pair_ref(a.src, k0 + kp);
+                                a.out[pr.out0] = KP[i].y;
+                                if (pr.out1 >= 0) a.out[pr.out1] = KP[i].y;
+                            }
+                        }
+                    }
+                }
+                if (SAVE && lane == 31) bq[m * R + j + 1] = QP[H - 1].y;
+                pK = (lane == 0) ? 1.f : shK;
+                pQ = (lane == 0) ? 0.f : shQ;
+            }
+        }
+        if (SAVE && ((m + 1) % BAND_CK == 0 || m == total_m - 1)) {
+            float4 *ck = reinterpret_cast<float4 *>(a.ckpt + ((gw * a.nck + m / BAND_CK) * 32 + lane) * (int64_t)(2 * R));
+#pragma unroll
+            for (int i = 0; i < H; i += 2) {
+                ck[i / 2] = make_float4(KP[i].x, KP[i].y, KP[i + 1].x, KP[i + 1].y);
+                ck[H / 2 + i / 2] = make_float4(QP[i].x, QP[i].y, QP[i + 1].x, QP[i + 1].y);
+            }
+        }
+        if (++pos == TperR) {
+            pos = 0;
+            ++kl;
+        }
+    }
+}
+
+template <int NG>
+cudaError_t launch_coef(const BandCoefArgs &a, int sms, cudaStream_t st) {
+    const int smem = (int)sizeof(float) * BC_DC * (bc_xstride<NG>() + bc_ystride(a.NQ, NG));
+    auto kern = band_coef_kernel<NG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BC_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t grid = (int64_t)sms * per_sm;
+    if (grid > a.n_pairs) grid = a.n_pairs;
+    kern<<<(int)grid, BC_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// (R, lambda) with R / 2^lambda in {2, 4, 8}; MINB as fwd_chain.cu
+#define SIGK_BAND_CASES(X) \
+    X(4, 0, 6) X(4, 1, 6) X(8, 0, 6) X(8, 1, 6) X(8, 2, 6) X(16, 1, 6) X(16, 2, 6) X(16, 3, 6)
+
+bool band_has_instance(int R, int lam) {
+#define X(r, l, mb) if (R == r && lam == l) return true;
+    SIGK_BAND_CASES(X)
+#undef X
+    return false;
+}
+
+template <int R, int LAM, int MINB>
+int band_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, chain_band_kernel<R, LAM, MINB, false>,
+                                                      BAND_WARPS * 32, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int band_occupancy_of(int R, int lam) {
+#define X(r, l, mb) if (R == r && lam == l) return band_occupancy<r, l, mb>();
+    SIGK_BAND_CASES(X)
+#undef X
+    return 0;
+}
+
+// ---- the adjoint: the band sweep run backwards in time ----------------------
+// The reverse mode of the difference form (as in the strip adjoint of
+// fwd_strip.cu): with A(a,b) = dk/dQ(a,b) and V(a,b) = P(a,b) + c(a,b) A(a,b),
+//   P(a,b) = c(a,b+1) A(a,b+1) + V(a+1,b),   A(a,b) = A(a,b+1) + P(a,b),
+// A(., Nj+1) = 0, V(Ni+1, b) = [b = Nj] g (g the incoming gradient), and
+// dk/dc(a,b) = A(a,b) (K(a,b-1) + K(a-1,b)).  Running the chain's schedule
+// backwards (rows ascending within a step) has every input ready, as in the
+// strip adjoint.  The sums K(a,b-1) + K(a-1,b) are not stored: the forward
+// step is undone in place,
+//   K(a,b-1) = K(a,b) - Q(a,b),   Q(a-1,b) = Q(a,b) - c(a,b) (K(a,b-1) + K(a-1,b)),
+// from the state after the step, exact up to rounding, with the state reset
+// to the forward's own every BAND_CK macro-steps (checkpoints), the K a row
+// had when it left its pair (exit states: the forward resets K to 1 there),
+// and the last row's Q before each step (it has no row below to recover it
+// from).  dk/dc is summed per coarse cell in registers and stored densely.
+
+struct BandAdjArgs {
+    PairSrc src;            // oriented: rows refine the A paths
+    const float *band;      // coefficients, band layout
+    const float *ckpt, *exitk, *botq;
+    int nck;
+    int64_t bq_stride;
+    const float *gout;      // incoming gradient, indexed like the forward's outputs
+    float *gbar;            // dk/dc (unscaled), dense
+    int64_t g_ld;           // floats per gbar row
+    int64_t a_first;        // first A path of this launch (rows of gbar count from it)
+    int gram;               // 1: gbar columns hold every B path (Gram), 0: one block per pair
+    int64_t n_pairs, ppw;
+    int TperR, NQ, NQV, vrows, nx, ny;
+};
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <int NBYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (NBYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(NBYTES) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int R, int LAM>
+__host__ __device__ constexpr int adj_warp_floats() {
+    return 2 * 32 * (R >> LAM) * (R >> LAM) + 2 * R;
+}
+
+template <int R, int LAM>
+__global__ void __launch_bounds__(BAND_WARPS * 32) chain_band_adj_kernel(BandAdjArgs a) {
+    constexpr int S = 1 << LAM;
+    constexpr int NG = R / S;
+    constexpr int H = R / 2;
+    constexpr int NH = NG / 2;
+    constexpr int JOUT = R - 2;
+    constexpr int SLOT = NG * NG;
+    constexpr int NCH = SLOT >= 4 ? SLOT / 4 : 1;   // 16-byte chunks of a lane's slot
+    extern __shared__ __align__(16) float adj_sm[];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * BAND_WARPS + warp;
+    const int64_t k0 = gw * a.ppw;
+    if (k0 >= a.n_pairs) return;
+    const int np = (int)min(a.ppw, a.n_pairs - k0);
+    const int TperR = a.TperR;
+    // per warp: two macro-steps of coefficient slots (lane-major, 16-byte
+    // chunks rotated by lane against bank conflicts) and of the last row's Q
+    float *ring = adj_sm + (size_t)warp * adj_warp_floats<R, LAM>();
+    float *bqs = ring + 2 * 32 * SLOT;
+    const float *bq = a.botq + gw * a.bq_stride;
+    auto chunk = [&](int c) { return NCH >= 8 ? (c ^ (lane & 7)) : (NCH >= 2 ? (c ^ (lane & (NCH - 1))) : c); };
+    auto lane_slot = [&](int buf) { return ring + ((size_t)buf * 32 + lane) * SLOT; };
+
+    auto locate = [&](int64_t m, int &kl, int &pos) {
+        const int64_t mm = m - lane;
+        int64_t q = mm >= 0 ? mm / TperR : -((-mm + TperR - 1) / TperR);
+        kl = (int)q;
+        pos = (int)(mm - q * TperR);
+    };
+    auto slot_ptr = [&](int kk, int pp) -> const float * {
+        if (kk < 0 || kk > np || (kk == np && pp != 0)) return nullptr;
+        return a.band + (((k0 + kk) * TperR + pp) * 32 + lane) * (int64_t)SLOT;
+    };
+    // window w of macro-step m into buffer m & 1 (zeros outside the chain)
+    auto fetch = [&](int64_t m, int w) {
+        int kk, pp;
+        locate(m, kk, pp);
+        const float *src = slot_ptr(kk, pp);
+        float *dst = lane_slot((int)(m & 1));
+        if constexpr (NG == 8) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float *dd = dst + 4 * chunk(2 * w + h);
+                if (src) cp_async<16>(dd, src + w * NG + 4 * h);
+                else *reinterpret_cast<float4 *>(dd) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else if constexpr (NG == 4) {
+            float *dd = dst + 4 * chunk(w);
+            if (src) cp_async<16>(dd, src + w * NG);
+            else *reinterpret_cast<float4 *>(dd) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            float *dd = dst + 2 * w;
+            if (src) cp_async<8>(dd, src + w * NG);
+            else *reinterpret_cast<float2 *>(dd) = make_float2(0.f, 0.f);
+        }
+        if (w == NG - 1 && lane == 31) {
+            float *bd = bqs + (m & 1) * R;
+#pragma unroll
+            for (int h = 0; h < R / 4; ++h) cp_async<16>(bd + 4 * h, bq + m * R + 4 * h);
+        }
+    };
+    auto read_window = [&](int buf, int w, float2 (&c)[NH]) {
+        const float *sl = lane_slot(buf);
+        float v[NG];
+        if constexpr (NG == 8) {
+            const float4 x0 = *reinterpret_cast<const float4 *>(sl + 4 * chunk(2 * w));
+            const float4 x1 = *reinterpret_cast<const float4 *>(sl + 4 * chunk(2 * w + 1));
+            v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+            v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+        } else if constexpr (NG == 4) {
+            const float4 x0 = *reinterpret_cast<const float4 *>(sl + 4 * chunk(w));
+            v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+        } else {
+            const float2 x0 = *reinterpret_cast<const float2 *>(sl + 2 * w);
+            v[0] = x0.x; v[1] = x0.y;
+        }
+#pragma unroll
+        for (int g = 0; g < NH; ++g) c[g] = make_float2(v[g], v[g + NH]);
+    };
+    // start of pair kk's dk/dc block in gbar
+    auto gbase = [&](int kk) -> int64_t {
+        const PairRef pr = pair_ref(a.src, k0 + kk);
+        const int64_t ia = pr.a_row0 / a.src.La - a.a_first;
+        const int64_t jb = a.gram ? pr.b_row0 / a.src.Lb : 0;
+        return ia * a.nx * a.g_ld + jb * a.ny;
+    };
+
+    float2 KP[H], QP[H], A[H], V[H], CP[H];
+    float2 gN[NH], gO[NH];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        A[i] = make_float2(0.f, 0.f); V[i] = A[i]; CP[i] = A[i];
+        KP[i] = make_float2(1.f, 1.f); QP[i] = A[i];
+    }
+#pragma unroll
+    for (int g = 0; g < NH; ++g) { gN[g] = make_float2(0.f, 0.f); gO[g] = gN[g]; }
+
+    const int64_t mlast = (int64_t)np * TperR + 31;
+#pragma unroll
+    for (int w = NG - 1; w >= 0; --w) {
+        fetch(mlast, w);
+        cp_commit();
+    }
+    int cached_kl = -1000000;
+    int64_t gb_cur = 0, gb_prev = 0;
+
+    for (int64_t m = mlast; m >= 0; --m) {
+        int kl, pos;
+        locate(m, kl, pos);
+        const bool trans = (pos == 0);
+        if ((m + 1) % BAND_CK == 0 || m == mlast) {
+            // the forward's state after macro-step m
+            const float4 *ck = reinterpret_cast<const float4 *>(
+                a.ckpt + ((gw * a.nck + m / BAND_CK) * 32 + lane) * (int64_t)(2 * R));
+#pragma unroll
+            for (int i = 0; i < H; i += 2) {
+                const float4 kk4 = ck[i / 2], qq4 = ck[H / 2 + i / 2];
+                KP[i] = make_float2(kk4.x, kk4.y); KP[i + 1] = make_float2(kk4.z, kk4.w);
+                QP[i] = make_float2(qq4.x, qq4.y); QP[i + 1] = make_float2(qq4.z, qq4.w);
+            }
+        }
+        if (kl != cached_kl) {
+            cached_kl = kl;
+            if (kl >= 0 && kl < np) gb_cur = gbase(kl);
+            if (kl >= 1 && kl <= np) gb_prev = gbase(kl - 1);
+        }
+        // rows turning over in this macro-step leave pair kl - 1 in reverse:
+        // their K there, and (lane 31) the pair's incoming gradient
+        float2 exK[H];
+        float gseed = 0.f;
+        const bool has_prev = trans && kl >= 1 && kl <= np;
+        if (has_prev) {
+            const float *ex = a.exitk + ((k0 + kl - 1) * 32 + lane) * (int64_t)R;
+#pragma unroll
+            for (int i = 0; i < H; ++i) exK[i] = make_float2(ex[i], ex[i + H]);
+            if (lane == 31) gseed = a.gout[pair_ref(a.src, k0 + kl - 1).out0];
+        } else {
+#pragma unroll
+            for (int i = 0; i < H; ++i) exK[i] = make_float2(1.f, 1.f);
+        }
+        const int buf = (int)(m & 1);
+
+#pragma unroll
+        for (int w = NG - 1; w >= 0; --w) {
+            if (m >= 1) fetch(m - 1, w);
+            cp_commit();
+            cp_wait<NG - 1>();   // window w - 1 of this macro-step (w = 0: window NG-1 of the one before)
+            float2 CN[NH], CO[NH];
+            read_window(buf, w, CN);
+            if (w > 0) read_window(buf, w - 1, CO);
+            else read_window(buf ^ 1, NG - 1, CO);
+
+#pragma unroll
+            for (int jj = S - 1; jj >= 0; --jj) {
+                const int j = w * S + jj;
+                const float qbot = bqs[buf * R + j];          // lane 31: its last row's Q before the step
+                const float vH = V[0].y;
+                float vd = __shfl_down_sync(FULL, V[0].x, 1);
+                if (lane == 31) vd = (has_prev && j == JOUT) ? gseed : 0.f;
+                // packed rows (H-1, R-1) first: their K before the step is the
+                // row above packed row 0's
+                float2 KlH = add2(KP[H - 1], neg2(QP[H - 1]));
+                float2 KpH = KlH;
+                {
+                    constexpr int g1 = (H - 1) / S, s1 = (H - 1) % S;
+                    if (trans && jj == s1) {
+                        if (g1 == w) { KlH.x = 1.f; KpH.x = exK[H - 1].x; }
+                        if (g1 + NH == w) { KlH.y = 1.f; KpH.y = exK[H - 1].y; }
+                    }
+                }
+                float pKs = __shfl_up_sync(FULL, KpH.y, 1);
+                if (lane == 0) pKs = 1.f;
+                float2 kprev = make_float2(pKs, KpH.x);
+                float2 t0 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < H; ++i) {
+                    const int g1 = i / S, s1 = i % S;
+                    float2 Kl, Kp;
+                    if (i == H - 1) {
+                        Kl = KlH;
+                        Kp = KpH;
+                    } else {
+                        Kl = add2(KP[i], neg2(QP[i]));
+                        Kp = Kl;
+                        if (trans && jj == s1) {
+                            if (g1 == w) { Kl.x = 1.f; Kp.x = exK[i].x; }
+                            if (g1 + NH == w) { Kl.y = 1.f; Kp.y = exK[i].y; }
+                        }
+                    }
+                    const float2 sum = add2(Kl, kprev);
+                    const float2 c = (jj >= s1) ? CN[g1] : CO[g1];
+                    const float2 tq = fma2(neg2(c), sum, QP[i]);   // Q before the step of the rows above
+                    if (i == 0) t0 = tq;
+                    else QP[i - 1] = tq;
+                    KP[i] = Kp;
+                    kprev = Kp;
+                    const float2 vb = (i < H - 1) ? V[i < H - 1 ? i + 1 : 0] : make_float2(vH, vd);
+                    const float2 P = fma2(CP[i], A[i], vb);
+                    const float2 An = add2(A[i], P);
+                    V[i] = fma2(c, An, P);
+                    if (jj >= s1) gN[g1] = fma2(An, sum, gN[g1]);
+                    else gO[g1] = fma2(An, sum, gO[g1]);
+                    A[i] = An;
+                    CP[i] = c;
+                    if (trans && jj == s1) {   // in reverse the row enters its previous pair: A(., Nj+1) = 0
+                        if (g1 == w) { A[i].x = 0.f; CP[i].x = 0.f; }
+                        if (g1 + NH == w) { A[i].y = 0.f; CP[i].y = 0.f; }
+                    }
+                }
+                float qd = __shfl_down_sync(FULL, t0.x, 1);
+                if (lane == 31) qd = qbot;
+                QP[H - 1] = make_float2(t0.y, qd);
+            }
+            // window w's cells are complete: (P, Q) = (lane*NG + g, pos*NG + w - g)
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const float v = g < NH ? gN[g].x : gN[g - NH].y;
+                const int Q = pos * NG + w - g;
+                const int own = Q >= 0 ? kl : kl - 1;
+                if (own >= 0 && own < np) {
+                    const int p = lane * NG + g - a.vrows, q = (Q >= 0 ? Q : Q + a.NQ) - a.NQV;
+                    if (p >= 0 && q >= 0)
+                        a.gbar[(own == kl ? gb_cur : gb_prev) + (int64_t)p * a.g_ld + q] = v;
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < NH; ++g) { gN[g] = gO[g]; gO[g] = make_float2(0.f, 0.f); }
+        }
+    }
+    cp_wait<0>();
+}
+
+// Real (unpadded) increments of paths: inc[(path * (L - 1) + p) * d + c].
+__global__ void band_inc_kernel(const float *pts, int64_t npaths, int64_t L, int64_t d, float *inc) {
+    const int64_t total = npaths * (L - 1) * d;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = v % d, row = v / d;
+        const int64_t path = row / (L - 1), p = row - path * (L - 1);
+        const float *x = pts + (path * L + p) * d + c;
+        inc[v] = x[d] - x[0];
+    }
+}
+
+// C (+)= G B per batch, G read as G[r * ld + k] (or G[k * ld + r] when
+// trans): the chain rule through G(p, q) = <dx_p, dy_q>, summed over the
+// other path's increments.  128 x 32 output tiles, 32-deep K slices staged
+// in shared memory, 4 x 4 outputs per thread.
+struct GemmArgs {
+    const float *G;
+    int64_t g_ld, g_bstride;
+    const float *Bm;
+    int64_t b_bstride;
+    float *C;
+    int64_t c_bstride;
+    int64_t M, K;
+    int N, trans, accumulate;
+};
+constexpr int GT_M = 128, GT_K = 32, GT_N = 32;
+
+__global__ void __launch_bounds__(256) band_gemm_kernel(GemmArgs a) {
+    __shared__ __align__(16) float Gs[GT_K][GT_M + 4];
+    __shared__ __align__(16) float Bs[GT_K][GT_N];
+    const int64_t b = blockIdx.z;
+    const float *G = a.G + b * a.g_bstride;
+    const float *Bm = a.Bm + b * a.b_bstride;
+    float *C = a.C + b * a.c_bstride;
+    const int64_t r0 = (int64_t)blockIdx.x * GT_M;
+    const int n0 = blockIdx.y * GT_N;
+    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jx = 0; jx < 4; ++jx) acc[i][jx] = 0.f;
+    for (int64_t k0 = 0; k0 < a.K; k0 += GT_K) {
+        __syncthreads();
+        if (!a.trans) {
+            for (int v = threadIdx.x; v < GT_M * GT_K; v += 256) {
+                const int rr = v / GT_K, kk = v % GT_K;
+                const int64_t r = r0 + rr, k = k0 + kk;
+                Gs[kk][rr] = (r < a.M && k < a.K) ? G[r * a.g_ld + k] : 0.f;
+            }
+        } else {
+            for (int v = threadIdx.x; v < GT_M * GT_K; v += 256) {
+                const int kk = v / GT_M, rr = v % GT_M;
+                const int64_t r = r0 + rr, k = k0 + kk;
+                Gs[kk][rr] = (r < a.M && k < a.K) ? G[k * a.g_ld + r] : 0.f;
+            }
+        }
+        for (int v = threadIdx.x; v < GT_K * GT_N; v += 256) {
+            const int kk = v / GT_N, nn = v % GT_N;
+            const int64_t k = k0 + kk;
+            const int n = n0 + nn;
+            Bs[kk][nn] = (k < a.K && n < a.N) ? Bm[k * a.N + n] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < GT_K; ++kk) {
+            const float4 g = *reinterpret_cast<const float4 *>(&Gs[kk][4 * ty]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][4 * tx]);
+            const float gg[4] = {g.x, g.y, g.z, g.w};
+            const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jx = 0; jx < 4; ++jx) acc[i][jx] = fmaf(gg[i], bb[jx], acc[i][jx]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + 4 * ty + i;
+        if (r >= a.M) continue;
+#pragma unroll
+        for (int jx = 0; jx < 4; ++jx) {
+            const int n = n0 + 4 * tx + jx;
+            if (n >= a.N) continue;
+            float *dst = C + r * a.N + n;
+            *dst = a.accumulate ? *dst + acc[i][jx] : acc[i][jx];
+        }
+    }
+}
+
+// Point gradients from increment gradients: x_p enters dx_{p-1} (+) and dx_p
+// (-), so dX[path][p] = scale (dinc[p-1] - dinc[p]) (terms outside 0..L-2
+// absent).  Overwrites dpts.
+__global__ void band_points_kernel(const float *dinc, int64_t npaths, int64_t L, int64_t d, float scale,
+                                   float *dpts) {
+    const int64_t total = npaths * L * d;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = v % d, row = v / d;
+        const int64_t path = row / L, p = row - path * L;
+        const float *di = dinc + path * (L - 1) * d + c;
+        const float lo = p >= 1 ? di[(p - 1) * d] : 0.f;
+        const float hi = p < L - 1 ? di[p * d] : 0.f;
+        dpts[v] = scale * (lo - hi);
+    }
+}
+
+}  // namespace
+
+bool band_geometry(int64_t La, int64_t Lb, int lam, int rows_per_lane, BandPlan &p) {
+    if (La < 2 || Lb < 2 || lam < 0 || lam > 3) return false;
+    const int64_t S = 1LL << lam;
+    const int64_t Ni = S * (La - 1), Nj = S * (Lb - 1);
+    int R = 0;
+    for (int r : {4, 8, 16})
+        if ((rows_per_lane == 0 || rows_per_lane == r) && 32 * r >= Ni && band_has_instance(r, lam)) {
+            R = r;
+            break;
+        }
+    if (R == 0) return false;
+    const int NG = R >> lam;
+    const int64_t Tper = ((Nj + R - 1) / R) * R;
+    if (Tper < 2 * R || Tper > (1 << 20)) return false;
+    p.R = R;
+    p.lam = lam;
+    p.NG = NG;
+    p.TperR = (int)(Tper / R);
+    p.NQ = (int)(Tper / S);
+    p.NQV = (int)((Tper - Nj) / S);
+    p.vrows = (int)((32 * R - Ni) / S);
+    p.slot_floats = (int64_t)32 * NG * NG;
+    return true;
+}
+
+int64_t band_bytes(const BandPlan &p, int64_t n_pairs) {
+    return (int64_t)sizeof(float) * (n_pairs * p.TperR + 1) * p.slot_floats;
+}
+
+cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pairs, float *out,
+                            void *ws, cudaStream_t st) {
+    if (n_pairs <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    BandCoefArgs c;
+    c.src = src;
+    c.n_pairs = n_pairs;
+    c.TperR = p.TperR;
+    c.NQ = p.NQ;
+    c.NQV = p.NQV;
+    c.vrows = p.vrows;
+    c.scale = 0.5f / (float)(1 << (2 * p.lam));
+    c.band = (float *)ws;
+    if (p.NG == 8) e = launch_coef<8>(c, sms, st);
+    else if (p.NG == 4) e = launch_coef<4>(c, sms, st);
+    else e = launch_coef<2>(c, sms, st);
+    if (e != cudaSuccess) return e;
+
+    const int per_sm = band_occupancy_of(p.R, p.lam);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t warps = (int64_t)sms * per_sm * BAND_WARPS;
+    BandArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = src;
+    a.out = out;
+    a.band = (const float *)ws;
+    a.n_pairs = n_pairs;
+    a.ppw = (n_pairs + warps - 1) / warps;
+    a.TperR = p.TperR;
+    const int64_t nwarps = (n_pairs + a.ppw - 1) / a.ppw;
+    const int grid = (int)((nwarps + BAND_WARPS - 1) / BAND_WARPS);
+#define X(r, l, mb)                                                          \
+    if (p.R == r && p.lam == l) {                                            \
+        chain_band_kernel<r, l, mb, false><<<grid, BAND_WARPS * 32, 0, st>>>(a); \
+        return cudaGetLastError();                                           \
+    }
+    SIGK_BAND_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sigk
+
+// ---- the band backward -------------------------------------------------------
+
+namespace sigk {
+
+namespace {
+
+template <int R, int LAM>
+cudaError_t launch_adj(const BandAdjArgs &a, int64_t nwarps, cudaStream_t st) {
+    const int smem = (int)sizeof(float) * BAND_WARPS * adj_warp_floats<R, LAM>();
+    auto kern = chain_band_adj_kernel<R, LAM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (nwarps + BAND_WARPS - 1) / BAND_WARPS;
+    kern<<<(int)grid, BAND_WARPS * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+int64_t up4(int64_t v) { return (v + 3) / 4 * 4; }
+
+// Float counts of the backward's workspace regions for a launch of nbp pairs
+// (Gram: whole rows of nb pairs).  Checkpoint and last-row regions are sized
+// for any pairs-per-warp split (they are checked against the actual split at
+// launch).
+struct BwdRegions {
+    int64_t band, gbar, ckpt, exitk, botq, incA, incB, dincA, dincB;
+    int64_t total() const { return band + gbar + ckpt + exitk + botq + incA + incB + dincA + dincB; }
+};
+
+BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
+    const int64_t nx = src.La - 1, ny = src.Lb - 1, d = src.d;
+    const bool gram = src.mode == PM_GRAM;
+    const int64_t nA = gram ? (nbp + src.nb - 1) / src.nb : nbp;
+    const int64_t nB = gram ? src.nb : nbp;
+    BwdRegions r;
+    r.band = up4(band_bytes(p, nbp) / (int64_t)sizeof(float));
+    r.gbar = up4(nA * nx * nB * ny);
+    if (!gram) r.gbar = up4(nbp * nx * ny);
+    r.ckpt = ((nbp + 1) * ((2 * (int64_t)p.TperR + 32 + BAND_CK) / BAND_CK) + 1) * 32 * 2 * p.R;
+    r.exitk = (nbp + 1) * 32 * (int64_t)p.R;
+    r.botq = up4((nbp + 1) * ((2 * (int64_t)p.TperR + 32) * p.R + 4));
+    r.incA = up4(nA * nx * d);
+    r.incB = up4(nB * ny * d);
+    r.dincA = r.incA;
+    r.dincB = r.incB;
+    return r;
+}
+
+}  // namespace
+
+int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t cap_bytes,
+                       int64_t &bytes) {
+    // whole Gram rows per launch: each launch owns its row paths' gradients
+    const int64_t unit = src.mode == PM_GRAM ? src.nb : 1;
+    int64_t units = (n + unit - 1) / unit;
+    int64_t nb = n;
+    bytes = bwd_regions(src, p, nb).total() * (int64_t)sizeof(float);
+    while (units > 1 && bytes > cap_bytes) {
+        units = (units + 1) / 2;
+        nb = units * unit < n ? units * unit : n;
+        bytes = bwd_regions(src, p, nb).total() * (int64_t)sizeof(float);
+    }
+    return nb;
+}
+
+cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t n, int64_t nbp,
+                                const float *gout, float *dA, float *dB, void *ws, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int per_sm = band_occupancy_of(p.R, p.lam);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const bool gram = src0.mode == PM_GRAM;
+    const int64_t nx = src0.La - 1, ny = src0.Lb - 1, d = src0.d;
+    const float scale = 0.5f / (float)(1 << (2 * p.lam));
+    const BwdRegions rg = bwd_regions(src0, p, nbp);
+    float *w = (float *)ws;
+    float *band = w;
+    float *gbar = band + rg.band;
+    float *ckpt = gbar + rg.gbar;
+    float *exitk = ckpt + rg.ckpt;
+    float *botq = exitk + rg.exitk;
+    float *incA = botq + rg.botq;
+    float *incB = incA + rg.incA;
+    float *dincA = incB + rg.incB;
+    float *dincB = dincA + rg.dincA;
+    const int64_t nBall = gram ? src0.nb : 0;
+    if (gram) {
+        // every column path is used by every launch: increments once, gradients summed
+        band_inc_kernel<<<sms * 4, 256, 0, st>>>((const float *)src0.B, nBall, src0.Lb, d, incB);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    for (int64_t kb = 0; kb < n; kb += nbp) {
+        const int64_t m = n - kb < nbp ? n - kb : nbp;
+        PairSrc src = src0;
+        src.kbase = src0.kbase + kb;
+        const int64_t a0 = gram ? src.kbase / src0.nb : src.kbase;   // first row path
+        const int64_t nA = gram ? m / src0.nb : m;
+        // 1. coefficients
+        BandCoefArgs c;
+        c.src = src;
+        c.n_pairs = m;
+        c.TperR = p.TperR;
+        c.NQ = p.NQ;
+        c.NQV = p.NQV;
+        c.vrows = p.vrows;
+        c.scale = scale;
+        c.band = band;
+        if (p.NG == 8) e = launch_coef<8>(c, sms, st);
+        else if (p.NG == 4) e = launch_coef<4>(c, sms, st);
+        else e = launch_coef<2>(c, sms, st);
+        if (e != cudaSuccess) return e;
+        // 2. the forward sweep, keeping what the adjoint needs
+        const int64_t warps = (int64_t)sms * per_sm * BAND_WARPS;
+        BandArgs f;
+        memset(&f, 0, sizeof(f));
+        f.src = src;
+        f.band = band;
+        f.n_pairs = m;
+        f.ppw = (m + warps - 1) / warps;
+        f.TperR = p.TperR;
+        const int64_t nwarps = (m + f.ppw - 1) / f.ppw;
+        const int64_t tm = f.ppw * p.TperR + 32;
+        f.nck = (int)((tm + BAND_CK - 1) / BAND_CK);
+        f.bq_stride = up4(tm * p.R + 1);
+        if (nwarps * f.nck * 32 * 2 * p.R > rg.ckpt || nwarps * f.bq_stride > rg.botq)
+            return cudaErrorInvalidValue;   // the workspace bound does not hold (cannot happen)
+        f.ckpt = ckpt;
+        f.exitk = exitk;
+        f.botq = botq;
+        const int fgrid = (int)((nwarps + BAND_WARPS - 1) / BAND_WARPS);
+        bool launched = false;
+#define X(r, l, mb)                                                              \
+        if (p.R == r && p.lam == l) {                                            \
+            chain_band_kernel<r, l, mb, true><<<fgrid, BAND_WARPS * 32, 0, st>>>(f); \
+            launched = true;                                                     \
+        }
+        SIGK_BAND_CASES(X)
+#undef X
+        if (!launched) return cudaErrorInvalidValue;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // 3. the adjoint sweep: dk/dc into gbar
+        BandAdjArgs ad;
+        ad.src = src;
+        ad.band = band;
+        ad.ckpt = ckpt;
+        ad.exitk = exitk;
+        ad.botq = botq;
+        ad.nck = f.nck;
+        ad.bq_stride = f.bq_stride;
+        ad.gout = gout;
+        ad.gbar = gbar;
+        ad.g_ld = gram ? nBall * ny : ny;
+        ad.a_first = a0;
+        ad.gram = gram ? 1 : 0;
+        ad.n_pairs = m;
+        ad.ppw = f.ppw;
+        ad.TperR = p.TperR;
+        ad.NQ = p.NQ;
+        ad.NQV = p.NQV;
+        ad.vrows = p.vrows;
+        ad.nx = (int)nx;
+        ad.ny = (int)ny;
+        launched = false;
+#define X(r, l, mb)                                                  \
+        if (p.R == r && p.lam == l) {                                \
+            if ((e = launch_adj<r, l>(ad, nwarps, st)) != cudaSuccess) return e; \
+            launched = true;                                         \
+        }
+        SIGK_BAND_CASES(X)
+#undef X
+        if (!launched) return cudaErrorInvalidValue;
+        // 4. increments of this launch's paths
+        band_inc_kernel<<<sms * 4, 256, 0, st>>>((const float *)src.A + a0 * src.La * d, nA, src.La, d, incA);
+        if (!gram)
+            band_inc_kernel<<<sms * 4, 256, 0, st>>>((const float *)src.B + src.kbase * src.Lb * d, m, src.Lb, d,
+                                                     incB);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // 5. chain rule: dinc_A = gbar inc_B, dinc_B (+)= gbar^T inc_A
+        GemmArgs g1;
+        g1.G = gbar;
+        g1.Bm = incB;
+        g1.C = dincA;
+        g1.N = (int)d;
+        g1.trans = 0;
+        g1.accumulate = 0;
+        GemmArgs g2 = g1;
+        g2.Bm = incA;
+        g2.C = dincB;
+        g2.trans = 1;
+        int64_t batches;
+        if (gram) {
+            batches = 1;
+            g1.g_ld = g2.g_ld = nBall * ny;
+            g1.g_bstride = g2.g_bstride = 0;
+            g1.b_bstride = g2.b_bstride = 0;
+            g1.c_bstride = g2.c_bstride = 0;
+            g1.M = nA * nx; g1.K = nBall * ny;
+            g2.M = nBall * ny; g2.K = nA * nx;
+            g2.accumulate = kb > 0 ? 1 : 0;
+        } else {
+            batches = m;
+            g1.g_ld = g2.g_ld = ny;
+            g1.g_bstride = g2.g_bstride = nx * ny;
+            g1.b_bstride = ny * d; g2.b_bstride = nx * d;
+            g1.c_bstride = nx * d; g2.c_bstride = ny * d;
+            g1.M = nx; g1.K = ny;
+            g2.M = ny; g2.K = nx;
+        }
+        const dim3 gd1((unsigned)((g1.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N), (unsigned)batches);
+        const dim3 gd2((unsigned)((g2.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N), (unsigned)batches);
+        if (dA) band_gemm_kernel<<<gd1, 256, 0, st>>>(g1);
+        if (dB) band_gemm_kernel<<<gd2, 256, 0, st>>>(g2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // 6. point gradients
+        if (dA)
+            band_points_kernel<<<sms * 4, 256, 0, st>>>(dincA, nA, src.La, d, scale, dA + a0 * src.La * d);
+        if (dB && !gram)
+            band_points_kernel<<<sms * 4, 256, 0, st>>>(dincB, m, src.Lb, d, scale, dB + src.kbase * src.Lb * d);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (dB && gram) {
+        band_points_kernel<<<sms * 4, 256, 0, st>>>(dincB, nBall, src0.Lb, d, scale, dB);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int64_t band_bwd_bytes(const PairSrc &src, const BandPlan &p, int64_t nbp) {
+    return bwd_regions(src, p, nbp).total() * (int64_t)sizeof(float);
+}
+
+}  // namespace sigk

@@ -158,7 +158,7 @@ def test_strip_backward_matches_oracle(lam, L, M, d):
     Y32, Y64 = inputs.f32(inputs.random_paths(900 + lam, B, M, d, scale=2.0, time_channel=True))
     g = np.random.default_rng(6).normal(size=B)
     rX, rY = oracle.pairs_grad(X64, Y64, lam, g)
-    dX, dY = S().pairs_backward(to_dev(g), to_dev(X32), to_dev(Y32), lam)
+    dX, dY = S().pairs_backward(to_dev(g), to_dev(X32), to_dev(Y32), lam, rec=S().REC_STRIP)
     assert grad_err(dX.cpu(), rX) <= 1e-4
     assert grad_err(dY.cpu(), rY) <= 1e-4
     dX, dY = S().pairs_backward(to_dev(g, torch.float64), to_dev(X64, torch.float64),

@@ -101,3 +101,71 @@ def test_band_refuses_what_it_cannot_do():
     with pytest.raises(sigk.SigkError) as ei:
         sigk.pairs(X64, X64, 1, schedule=band(16))
     assert ei.value.status == sigk.SIGK_EUNSUPPORTED
+
+
+# ------------------------------------------------------------------ backward
+
+def grad_err(got, ref):
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30))
+
+
+GRAD_TOL = 1e-4
+
+
+@pytest.mark.parametrize("R,lam,L,M,d", [
+    (16, 1, 256, 256, 32),   # the MMD shape
+    (16, 1, 120, 200, 24),   # virtual rows and columns
+    (16, 2, 70, 77, 5),
+    (16, 3, 40, 41, 3),
+    (8, 0, 230, 256, 40),
+    (8, 1, 100, 90, 17),     # rows refine the second path
+    (8, 2, 40, 33, 9),
+    (4, 0, 100, 120, 6),
+    (4, 1, 60, 70, 33),
+])
+def test_band_gram_backward_matches_oracle(R, lam, L, M, d):
+    """The reversible adjoint (forward state undone in place between
+    checkpoints) against the oracle's exact gradient, with pair turnovers
+    inside each warp's chain."""
+    Bx, By = 5, 6
+    X32, X64 = inputs.f32(inputs.random_paths(3600 + R + lam, Bx, L, d, scale=2.0, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(3700 + R + lam, By, M, d, scale=2.0, time_channel=True))
+    gout = np.random.default_rng(37).normal(size=(Bx, By))
+    rX, rY = oracle.gram_grad(X64, Y64, lam, gout)
+    s = S().Schedule(S().REC_BAND, R, 0)
+    dX, dY = S().gram_backward(to_dev(gout), to_dev(X32), to_dev(Y32), lam, schedule=s)
+    assert grad_err(dX.cpu(), rX) <= GRAD_TOL
+    assert grad_err(dY.cpu(), rY) <= GRAD_TOL
+    # only one side requested
+    dX1, none = S().gram_backward(to_dev(gout), to_dev(X32), to_dev(Y32), lam, need_dy=False, schedule=s)
+    assert none is None and torch.equal(dX1, dX)
+
+
+@pytest.mark.parametrize("L,M", [(60, 60), (80, 50), (33, 90)])
+def test_band_pairs_backward_matches_oracle(L, M):
+    lam, d, B = 1, 20, 700   # several pairs per warp
+    X32, X64 = inputs.f32(inputs.random_paths(3800 + L, B, L, d, scale=2.0, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(3900 + M, B, M, d, scale=2.0, time_channel=True))
+    g = np.random.default_rng(39).normal(size=B)
+    rX, rY = oracle.pairs_grad(X64, Y64, lam, g)
+    dX, dY = S().pairs_backward(to_dev(g), to_dev(X32), to_dev(Y32), lam, schedule=band(16))
+    assert grad_err(dX.cpu(), rX) <= GRAD_TOL
+    assert grad_err(dY.cpu(), rY) <= GRAD_TOL
+
+
+def test_band_backward_is_the_default_and_agrees_with_the_strip_adjoint():
+    sigk = S()
+    w = inputs.mmd_batches(B=5)
+    X32, X64 = inputs.f32(w["X"])
+    Y32, Y64 = inputs.f32(w["Y"])
+    gout = np.random.default_rng(40).normal(size=(5, 5))
+    auto = sigk.gram_backward(to_dev(gout), to_dev(X32), to_dev(Y32), 1)
+    band_ = sigk.gram_backward(to_dev(gout), to_dev(X32), to_dev(Y32), 1, schedule=band(16))
+    strip = sigk.gram_backward(to_dev(gout), to_dev(X32), to_dev(Y32), 1, rec=sigk.REC_STRIP)
+    for a_, b_, s_ in zip(auto, band_, strip):
+        assert torch.equal(a_, b_)
+        assert grad_err(a_.cpu(), s_.cpu()) <= GRAD_TOL
+    rX, rY = oracle.gram_grad(X64, Y64, 1, gout)
+    assert grad_err(auto[0].cpu(), rX) <= GRAD_TOL
+    assert grad_err(auto[1].cpu(), rY) <= GRAD_TOL
