@@ -429,11 +429,11 @@ struct BandAdjArgs {
     int gram;               // 1: gbar columns hold every B path (Gram), 0: one block per pair
     int64_t n_pairs, ppw;
     int TperR, NQ, NQV, vrows, nx, ny;
+    float *junk;            // 32 floats per warp: the target of stores that fall outside the grid
 };
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 template <int NBYTES>
 __device__ __forceinline__ void cp_async(void *dst, const void *src) {
@@ -453,7 +453,7 @@ __host__ __device__ constexpr int adj_warp_floats() {
 }
 
 template <int R, int LAM>
-__global__ void __launch_bounds__(BAND_WARPS * 32) chain_band_adj_kernel(BandAdjArgs a) {
+__global__ void __launch_bounds__(BAND_WARPS * 32, 6) chain_band_adj_kernel(BandAdjArgs a) {
     constexpr int S = 1 << LAM;
     constexpr int NG = R / S;
     constexpr int H = R / 2;
@@ -475,6 +475,7 @@ __global__ void __launch_bounds__(BAND_WARPS * 32) chain_band_adj_kernel(BandAdj
     float *ring = adj_sm + (size_t)warp * adj_warp_floats<R, LAM>();
     float *bqs = ring + 2 * 32 * SLOT;
     const float *bq = a.botq + gw * a.bq_stride;
+    float *junk = a.junk + gw * 32 + lane;
     auto chunk = [&](int c) { return NCH >= 8 ? (c ^ (lane & 7)) : (NCH >= 2 ? (c ^ (lane & (NCH - 1))) : c); };
     auto lane_slot = [&](int buf) { return ring + ((size_t)buf * 32 + lane) * SLOT; };
 
@@ -488,11 +489,9 @@ __global__ void __launch_bounds__(BAND_WARPS * 32) chain_band_adj_kernel(BandAdj
         if (kk < 0 || kk > np || (kk == np && pp != 0)) return nullptr;
         return a.band + (((k0 + kk) * TperR + pp) * 32 + lane) * (int64_t)SLOT;
     };
-    // window w of macro-step m into buffer m & 1 (zeros outside the chain)
-    auto fetch = [&](int64_t m, int w) {
-        int kk, pp;
-        locate(m, kk, pp);
-        const float *src = slot_ptr(kk, pp);
+    // window w of macro-step m (slot src, null outside the chain) into buffer m & 1;
+    // with window NG-1 also the last row's Q
+    auto fetch = [&](int64_t m, const float *src, int w) {
         float *dst = lane_slot((int)(m & 1));
         if constexpr (NG == 8) {
 #pragma unroll
@@ -542,29 +541,44 @@ __global__ void __launch_bounds__(BAND_WARPS * 32) chain_band_adj_kernel(BandAdj
         return ia * a.nx * a.g_ld + jb * a.ny;
     };
 
-    float2 KP[H], QP[H], A[H], V[H], CP[H];
+    // forward state as (K, -Q): undoing a step then needs no negation
+    float2 KP[H], QN[H], A[H], V[H];
     float2 gN[NH], gO[NH];
+    // coefficients of the window processed before (the next one in forward
+    // order): a row's coefficient one forward step later comes from these or
+    // from the current window's
+    float2 CNP[NH];
 #pragma unroll
     for (int i = 0; i < H; ++i) {
-        A[i] = make_float2(0.f, 0.f); V[i] = A[i]; CP[i] = A[i];
-        KP[i] = make_float2(1.f, 1.f); QP[i] = A[i];
+        A[i] = make_float2(0.f, 0.f); V[i] = A[i];
+        KP[i] = make_float2(1.f, 1.f); QN[i] = A[i];
     }
 #pragma unroll
-    for (int g = 0; g < NH; ++g) { gN[g] = make_float2(0.f, 0.f); gO[g] = gN[g]; }
+    for (int g = 0; g < NH; ++g) { gN[g] = make_float2(0.f, 0.f); gO[g] = gN[g]; CNP[g] = gN[g]; }
 
     const int64_t mlast = (int64_t)np * TperR + 31;
+    int kl, pos;   // this lane's pair and position at macro-step m, tracked backwards
+    locate(mlast, kl, pos);
+    {
+        const float *s0 = slot_ptr(kl, pos);
 #pragma unroll
-    for (int w = NG - 1; w >= 0; --w) {
-        fetch(mlast, w);
-        cp_commit();
+        for (int w = NG - 1; w >= 0; --w) {
+            fetch(mlast, s0, w);
+            cp_commit();
+        }
     }
     int cached_kl = -1000000;
-    int64_t gb_cur = 0, gb_prev = 0;
+    int64_t row_cur = 0, row_prev = 0;     // gbar address of (row lane*NG - vrows, column -NQV) of pairs kl, kl-1
+    const int gmin = a.vrows - lane * NG;  // groups g >= gmin are real rows
 
     for (int64_t m = mlast; m >= 0; --m) {
-        int kl, pos;
-        locate(m, kl, pos);
+        if (m != mlast && --pos < 0) {
+            pos = TperR - 1;
+            --kl;
+        }
         const bool trans = (pos == 0);
+        const float *sprev = nullptr;
+        if (m >= 1) sprev = pos > 0 ? slot_ptr(kl, pos - 1) : slot_ptr(kl - 1, TperR - 1);
         if ((m + 1) % BAND_CK == 0 || m == mlast) {
             // the forward's state after macro-step m
             const float4 *ck = reinterpret_cast<const float4 *>(
@@ -573,39 +587,45 @@ __global__ void __launch_bounds__(BAND_WARPS * 32) chain_band_adj_kernel(BandAdj
             for (int i = 0; i < H; i += 2) {
                 const float4 kk4 = ck[i / 2], qq4 = ck[H / 2 + i / 2];
                 KP[i] = make_float2(kk4.x, kk4.y); KP[i + 1] = make_float2(kk4.z, kk4.w);
-                QP[i] = make_float2(qq4.x, qq4.y); QP[i + 1] = make_float2(qq4.z, qq4.w);
+                QN[i] = make_float2(-qq4.x, -qq4.y); QN[i + 1] = make_float2(-qq4.z, -qq4.w);
             }
         }
+        const bool cur_ok = kl >= 0 && kl < np, prev_ok = kl >= 1 && kl <= np;
         if (kl != cached_kl) {
             cached_kl = kl;
-            if (kl >= 0 && kl < np) gb_cur = gbase(kl);
-            if (kl >= 1 && kl <= np) gb_prev = gbase(kl - 1);
+            const int64_t off = (int64_t)(lane * NG - a.vrows) * a.g_ld - a.NQV;
+            if (cur_ok) row_cur = gbase(kl) + off;
+            if (prev_ok) row_prev = gbase(kl - 1) + off + a.NQ;
         }
-        // rows turning over in this macro-step leave pair kl - 1 in reverse:
-        // their K there, and (lane 31) the pair's incoming gradient
-        float2 exK[H];
+        // rows turning over in this macro-step leave pair kl - 1 in reverse;
+        // lane 31 seeds that pair's incoming gradient at its corner
         float gseed = 0.f;
-        const bool has_prev = trans && kl >= 1 && kl <= np;
+        const bool has_prev = trans && prev_ok;
+        float exK[R];   // their K when they left it (rows 0 .. R-1)
+#pragma unroll
+        for (int i = 0; i < R; ++i) exK[i] = 1.f;
         if (has_prev) {
-            const float *ex = a.exitk + ((k0 + kl - 1) * 32 + lane) * (int64_t)R;
+            const float4 *ex = reinterpret_cast<const float4 *>(a.exitk + ((k0 + kl - 1) * 32 + lane) * (int64_t)R);
 #pragma unroll
-            for (int i = 0; i < H; ++i) exK[i] = make_float2(ex[i], ex[i + H]);
+            for (int i = 0; i < R / 4; ++i) {
+                const float4 v = ex[i];
+                exK[4 * i] = v.x; exK[4 * i + 1] = v.y; exK[4 * i + 2] = v.z; exK[4 * i + 3] = v.w;
+            }
             if (lane == 31) gseed = a.gout[pair_ref(a.src, k0 + kl - 1).out0];
-        } else {
-#pragma unroll
-            for (int i = 0; i < H; ++i) exK[i] = make_float2(1.f, 1.f);
         }
         const int buf = (int)(m & 1);
 
-#pragma unroll
+        // a runtime loop over the windows keeps the body within the instruction cache
+#pragma unroll 1
         for (int w = NG - 1; w >= 0; --w) {
-            if (m >= 1) fetch(m - 1, w);
+            if (m >= 1) fetch(m - 1, sprev, w);
             cp_commit();
             cp_wait<NG - 1>();   // window w - 1 of this macro-step (w = 0: window NG-1 of the one before)
             float2 CN[NH], CO[NH];
             read_window(buf, w, CN);
             if (w > 0) read_window(buf, w - 1, CO);
             else read_window(buf ^ 1, NG - 1, CO);
+            const int tw = has_prev ? w : -1;   // group whose rows turn over in this window
 
 #pragma unroll
             for (int jj = S - 1; jj >= 0; --jj) {
@@ -616,15 +636,11 @@ __global__ void __launch_bounds__(BAND_WARPS * 32) chain_band_adj_kernel(BandAdj
                 if (lane == 31) vd = (has_prev && j == JOUT) ? gseed : 0.f;
                 // packed rows (H-1, R-1) first: their K before the step is the
                 // row above packed row 0's
-                float2 KlH = add2(KP[H - 1], neg2(QP[H - 1]));
-                float2 KpH = KlH;
-                {
-                    constexpr int g1 = (H - 1) / S, s1 = (H - 1) % S;
-                    if (trans && jj == s1) {
-                        if (g1 == w) { KlH.x = 1.f; KpH.x = exK[H - 1].x; }
-                        if (g1 + NH == w) { KlH.y = 1.f; KpH.y = exK[H - 1].y; }
-                    }
-                }
+                constexpr int gH = (H - 1) / S, sH = (H - 1) % S;
+                const bool hx = jj == sH && tw == gH, hy = jj == sH && tw == gH + NH;
+                float2 KlH = add2(KP[H - 1], QN[H - 1]);
+                float2 KpH = make_float2(hx ? exK[H - 1] : KlH.x, hy ? exK[R - 1] : KlH.y);
+                KlH = make_float2(hx ? 1.f : KlH.x, hy ? 1.f : KlH.y);
                 float pKs = __shfl_up_sync(FULL, KpH.y, 1);
                 if (lane == 0) pKs = 1.f;
                 float2 kprev = make_float2(pKs, KpH.x);
@@ -632,56 +648,55 @@ __global__ void __launch_bounds__(BAND_WARPS * 32) chain_band_adj_kernel(BandAdj
 #pragma unroll
                 for (int i = 0; i < H; ++i) {
                     const int g1 = i / S, s1 = i % S;
+                    const bool px = jj == s1 && tw == g1, py = jj == s1 && tw == g1 + NH;
                     float2 Kl, Kp;
                     if (i == H - 1) {
                         Kl = KlH;
                         Kp = KpH;
                     } else {
-                        Kl = add2(KP[i], neg2(QP[i]));
+                        Kl = add2(KP[i], QN[i]);
                         Kp = Kl;
-                        if (trans && jj == s1) {
-                            if (g1 == w) { Kl.x = 1.f; Kp.x = exK[i].x; }
-                            if (g1 + NH == w) { Kl.y = 1.f; Kp.y = exK[i].y; }
+                        if (jj == s1) {
+                            Kp = make_float2(px ? exK[i] : Kl.x, py ? exK[i + H] : Kl.y);
+                            Kl = make_float2(px ? 1.f : Kl.x, py ? 1.f : Kl.y);
                         }
                     }
                     const float2 sum = add2(Kl, kprev);
                     const float2 c = (jj >= s1) ? CN[g1] : CO[g1];
-                    const float2 tq = fma2(neg2(c), sum, QP[i]);   // Q before the step of the rows above
+                    const float2 tq = fma2(c, sum, QN[i]);   // -Q before the step of the rows above
                     if (i == 0) t0 = tq;
-                    else QP[i - 1] = tq;
+                    else QN[i - 1] = tq;
                     KP[i] = Kp;
                     kprev = Kp;
                     const float2 vb = (i < H - 1) ? V[i < H - 1 ? i + 1 : 0] : make_float2(vH, vd);
-                    const float2 P = fma2(CP[i], A[i], vb);
-                    const float2 An = add2(A[i], P);
+                    // the row's coefficient one forward step later
+                    const float2 cp = (jj < S - 1) ? ((jj + 1 >= s1) ? CN[g1] : CO[g1])
+                                                   : (s1 == 0 ? CNP[g1] : CN[g1]);
+                    const float2 P = fma2(cp, A[i], vb);
+                    float2 An = add2(A[i], P);
                     V[i] = fma2(c, An, P);
                     if (jj >= s1) gN[g1] = fma2(An, sum, gN[g1]);
                     else gO[g1] = fma2(An, sum, gO[g1]);
+                    // in reverse the row enters its previous pair: A(., Nj+1) = 0
+                    if (jj == s1) An = make_float2(px ? 0.f : An.x, py ? 0.f : An.y);
                     A[i] = An;
-                    CP[i] = c;
-                    if (trans && jj == s1) {   // in reverse the row enters its previous pair: A(., Nj+1) = 0
-                        if (g1 == w) { A[i].x = 0.f; CP[i].x = 0.f; }
-                        if (g1 + NH == w) { A[i].y = 0.f; CP[i].y = 0.f; }
-                    }
                 }
                 float qd = __shfl_down_sync(FULL, t0.x, 1);
-                if (lane == 31) qd = qbot;
-                QP[H - 1] = make_float2(t0.y, qd);
+                if (lane == 31) qd = -qbot;
+                QN[H - 1] = make_float2(t0.y, qd);
             }
             // window w's cells are complete: (P, Q) = (lane*NG + g, pos*NG + w - g)
+            const int Q0 = pos * NG + w;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 const float v = g < NH ? gN[g].x : gN[g - NH].y;
-                const int Q = pos * NG + w - g;
-                const int own = Q >= 0 ? kl : kl - 1;
-                if (own >= 0 && own < np) {
-                    const int p = lane * NG + g - a.vrows, q = (Q >= 0 ? Q : Q + a.NQ) - a.NQV;
-                    if (p >= 0 && q >= 0)
-                        a.gbar[(own == kl ? gb_cur : gb_prev) + (int64_t)p * a.g_ld + q] = v;
-                }
+                const int Q = Q0 - g;
+                const bool ok = g >= gmin && (Q >= 0 ? (cur_ok && Q >= a.NQV) : prev_ok);
+                float *dst = a.gbar + (Q >= 0 ? row_cur : row_prev) + (int64_t)g * a.g_ld + Q;
+                *(ok ? dst : junk) = v;   // no branch: cells outside the grid go to the warp's junk slot
             }
 #pragma unroll
-            for (int g = 0; g < NH; ++g) { gN[g] = gO[g]; gO[g] = make_float2(0.f, 0.f); }
+            for (int g = 0; g < NH; ++g) { gN[g] = gO[g]; gO[g] = make_float2(0.f, 0.f); CNP[g] = CN[g]; }
         }
     }
     cp_wait<0>();
@@ -702,7 +717,9 @@ __global__ void band_inc_kernel(const float *pts, int64_t npaths, int64_t L, int
 // C (+)= G B per batch, G read as G[r * ld + k] (or G[k * ld + r] when
 // trans): the chain rule through G(p, q) = <dx_p, dy_q>, summed over the
 // other path's increments.  128 x 32 output tiles, 32-deep K slices staged
-// in shared memory, 4 x 4 outputs per thread.
+// in shared memory (the next slice is loaded into registers while the current
+// one is used), 4 x 4 outputs per thread; long K ranges are split across
+// blocks that add their partial tiles atomically into a zeroed C.
 struct GemmArgs {
     const float *G;
     int64_t g_ld, g_bstride;
@@ -711,47 +728,66 @@ struct GemmArgs {
     float *C;
     int64_t c_bstride;
     int64_t M, K;
-    int N, trans, accumulate;
+    int N, trans, ksplit;   // ksplit > 1 (one batch only): block ks writes its partial
+    float *partial;         // tile to partial[ks][M][N], summed by band_split_sum_kernel
 };
+constexpr int GEMM_MAX_SPLIT = 8;
 constexpr int GT_M = 128, GT_K = 32, GT_N = 32;
 
 __global__ void __launch_bounds__(256) band_gemm_kernel(GemmArgs a) {
     __shared__ __align__(16) float Gs[GT_K][GT_M + 4];
     __shared__ __align__(16) float Bs[GT_K][GT_N];
-    const int64_t b = blockIdx.z;
+    const int64_t b = blockIdx.z / a.ksplit;
+    const int ks = blockIdx.z - (int)b * a.ksplit;
     const float *G = a.G + b * a.g_bstride;
     const float *Bm = a.Bm + b * a.b_bstride;
     float *C = a.C + b * a.c_bstride;
     const int64_t r0 = (int64_t)blockIdx.x * GT_M;
     const int n0 = blockIdx.y * GT_N;
     const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+    // this block's K range, in whole slices
+    const int64_t nslice = (a.K + GT_K - 1) / GT_K;
+    const int64_t s_lo = nslice * ks / a.ksplit, s_hi = nslice * (ks + 1) / a.ksplit;
+    float gr[16], br[4];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int v = threadIdx.x + 256 * i;
+            int rr, kk;
+            if (!a.trans) { rr = v / GT_K; kk = v % GT_K; } else { kk = v / GT_M; rr = v % GT_M; }
+            const int64_t r = r0 + rr, k = k0 + kk;
+            gr[i] = (r < a.M && k < a.K) ? (a.trans ? G[k * a.g_ld + r] : G[r * a.g_ld + k]) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int v = threadIdx.x + 256 * i;
+            const int kk = v / GT_N, nn = v % GT_N;
+            const int64_t k = k0 + kk;
+            const int n = n0 + nn;
+            br[i] = (k < a.K && n < a.N) ? Bm[k * a.N + n] : 0.f;
+        }
+    };
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jx = 0; jx < 4; ++jx) acc[i][jx] = 0.f;
-    for (int64_t k0 = 0; k0 < a.K; k0 += GT_K) {
+    if (s_lo < s_hi) load(s_lo * GT_K);
+    for (int64_t sl = s_lo; sl < s_hi; ++sl) {
         __syncthreads();
-        if (!a.trans) {
-            for (int v = threadIdx.x; v < GT_M * GT_K; v += 256) {
-                const int rr = v / GT_K, kk = v % GT_K;
-                const int64_t r = r0 + rr, k = k0 + kk;
-                Gs[kk][rr] = (r < a.M && k < a.K) ? G[r * a.g_ld + k] : 0.f;
-            }
-        } else {
-            for (int v = threadIdx.x; v < GT_M * GT_K; v += 256) {
-                const int kk = v / GT_M, rr = v % GT_M;
-                const int64_t r = r0 + rr, k = k0 + kk;
-                Gs[kk][rr] = (r < a.M && k < a.K) ? G[k * a.g_ld + r] : 0.f;
-            }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int v = threadIdx.x + 256 * i;
+            if (!a.trans) Gs[v % GT_K][v / GT_K] = gr[i];
+            else Gs[v / GT_M][v % GT_M] = gr[i];
         }
-        for (int v = threadIdx.x; v < GT_K * GT_N; v += 256) {
-            const int kk = v / GT_N, nn = v % GT_N;
-            const int64_t k = k0 + kk;
-            const int n = n0 + nn;
-            Bs[kk][nn] = (k < a.K && n < a.N) ? Bm[k * a.N + n] : 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int v = threadIdx.x + 256 * i;
+            Bs[v / GT_N][v % GT_N] = br[i];
         }
         __syncthreads();
+        if (sl + 1 < s_hi) load((sl + 1) * GT_K);
 #pragma unroll 8
         for (int kk = 0; kk < GT_K; ++kk) {
             const float4 g = *reinterpret_cast<const float4 *>(&Gs[kk][4 * ty]);
@@ -772,9 +808,18 @@ __global__ void __launch_bounds__(256) band_gemm_kernel(GemmArgs a) {
         for (int jx = 0; jx < 4; ++jx) {
             const int n = n0 + 4 * tx + jx;
             if (n >= a.N) continue;
-            float *dst = C + r * a.N + n;
-            *dst = a.accumulate ? *dst + acc[i][jx] : acc[i][jx];
+            if (a.ksplit > 1) a.partial[((int64_t)ks * a.M + r) * a.N + n] = acc[i][jx];
+            else C[r * a.N + n] = acc[i][jx];
         }
+    }
+}
+
+// C = (add ? C : 0) + sum over the splits, in split order (deterministic).
+__global__ void band_split_sum_kernel(const float *partial, int ksplit, int64_t MN, int add, float *C) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < MN; v += (int64_t)gridDim.x * blockDim.x) {
+        float acc = add ? C[v] : 0.f;
+        for (int s = 0; s < ksplit; ++s) acc += partial[s * MN + v];
+        C[v] = acc;
     }
 }
 
@@ -896,8 +941,8 @@ int64_t up4(int64_t v) { return (v + 3) / 4 * 4; }
 // for any pairs-per-warp split (they are checked against the actual split at
 // launch).
 struct BwdRegions {
-    int64_t band, gbar, ckpt, exitk, botq, incA, incB, dincA, dincB;
-    int64_t total() const { return band + gbar + ckpt + exitk + botq + incA + incB + dincA + dincB; }
+    int64_t band, gbar, ckpt, exitk, botq, incA, incB, dincA, dincB, part, junk;
+    int64_t total() const { return band + gbar + ckpt + exitk + botq + incA + incB + dincA + dincB + part + junk; }
 };
 
 BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
@@ -916,6 +961,9 @@ BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
     r.incB = up4(nB * ny * d);
     r.dincA = r.incA;
     r.dincB = r.incB;
+    // split-K partial tiles of the Gram's contractions
+    r.part = gram ? up4((int64_t)GEMM_MAX_SPLIT * (nA * nx > nB * ny ? nA * nx : nB * ny) * d) : 0;
+    r.junk = (nbp + 1) * 32;
     return r;
 }
 
@@ -959,6 +1007,8 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
     float *incB = incA + rg.incA;
     float *dincA = incB + rg.incB;
     float *dincB = dincA + rg.dincA;
+    float *part = dincB + rg.dincB;
+    float *junk = part + rg.part;
     const int64_t nBall = gram ? src0.nb : 0;
     if (gram) {
         // every column path is used by every launch: increments once, gradients summed
@@ -1036,6 +1086,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         ad.vrows = p.vrows;
         ad.nx = (int)nx;
         ad.ny = (int)ny;
+        ad.junk = junk;
         launched = false;
 #define X(r, l, mb)                                                  \
         if (p.R == r && p.lam == l) {                                \
@@ -1058,7 +1109,6 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         g1.C = dincA;
         g1.N = (int)d;
         g1.trans = 0;
-        g1.accumulate = 0;
         GemmArgs g2 = g1;
         g2.Bm = incA;
         g2.C = dincB;
@@ -1072,7 +1122,6 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
             g1.c_bstride = g2.c_bstride = 0;
             g1.M = nA * nx; g1.K = nBall * ny;
             g2.M = nBall * ny; g2.K = nA * nx;
-            g2.accumulate = kb > 0 ? 1 : 0;
         } else {
             batches = m;
             g1.g_ld = g2.g_ld = ny;
@@ -1082,10 +1131,38 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
             g1.M = nx; g1.K = ny;
             g2.M = ny; g2.K = nx;
         }
-        const dim3 gd1((unsigned)((g1.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N), (unsigned)batches);
-        const dim3 gd2((unsigned)((g2.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N), (unsigned)batches);
-        if (dA) band_gemm_kernel<<<gd1, 256, 0, st>>>(g1);
-        if (dB) band_gemm_kernel<<<gd2, 256, 0, st>>>(g2);
+        // a Gram's contractions have long K ranges: split them to about four
+        // blocks per SM, the partial tiles summed in a fixed order.  The Gram's
+        // column-path gradients add up over launches.
+        auto split = [&](const GemmArgs &g) {
+            if (!gram) return 1;
+            const int64_t tiles = ((g.M + GT_M - 1) / GT_M) * ((d + GT_N - 1) / GT_N);
+            int64_t ksp = (4 * (int64_t)sms + tiles - 1) / tiles;
+            const int64_t nsl = (g.K + GT_K - 1) / GT_K;
+            if (ksp > nsl / 4) ksp = nsl / 4;
+            if (ksp > GEMM_MAX_SPLIT) ksp = GEMM_MAX_SPLIT;
+            return (int)(ksp < 1 ? 1 : ksp);
+        };
+        g1.ksplit = split(g1);
+        g2.ksplit = split(g2);
+        g1.partial = g2.partial = part;
+        const bool add_b = gram && kb > 0;
+        // the split sum writes dincB; an unsplit contraction that must add goes through it too
+        if (add_b && g2.ksplit == 1) g2.ksplit = 2;
+        const dim3 gd1((unsigned)((g1.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N),
+                       (unsigned)(batches * g1.ksplit));
+        const dim3 gd2((unsigned)((g2.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N),
+                       (unsigned)(batches * g2.ksplit));
+        if (dA) {
+            band_gemm_kernel<<<gd1, 256, 0, st>>>(g1);
+            if (g1.ksplit > 1)
+                band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g1.ksplit, g1.M * d, 0, dincA);
+        }
+        if (dB) {
+            band_gemm_kernel<<<gd2, 256, 0, st>>>(g2);
+            if (g2.ksplit > 1)
+                band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g2.ksplit, g2.M * d, add_b ? 1 : 0, dincB);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 6. point gradients
         if (dA)
