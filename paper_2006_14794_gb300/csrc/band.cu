@@ -54,6 +54,13 @@ __device__ __forceinline__ int bc_xpos(int P) {
     else return P;
 }
 
+// Order of the groups inside a window of a slot: g and g + NG/2 side by side
+// (the sweeps carry groups g and g + NG/2 as one float2).
+template <int NG>
+__host__ __device__ constexpr int band_gpos(int g) {
+    return g < NG / 2 ? 2 * g : 2 * (g - NG / 2) + 1;
+}
+
 // One thread per slot (lane l, position pos) of the pair: the NG x NG cells
 // (l*NG + g, pos*NG + w - g), each a d-term dot product of increments.
 // Position TperR is the pair's tail (the cells with w < g there), written into
@@ -156,8 +163,9 @@ __global__ void __launch_bounds__(BC_THREADS, 2) band_coef_kernel(BandCoefArgs a
                     for (int w = 0; w < NG; ++w)
 #pragma unroll
                         for (int h = 0; h < NG / 4; ++h)
-                            dst[w * (NG / 4) + h] = make_float4(acc[w][4 * h] * a.scale, acc[w][4 * h + 1] * a.scale,
-                                                                acc[w][4 * h + 2] * a.scale, acc[w][4 * h + 3] * a.scale);
+                            dst[w * (NG / 4) + h] = make_float4(
+                                acc[w][2 * h] * a.scale, acc[w][2 * h + NG / 2] * a.scale,
+                                acc[w][2 * h + 1] * a.scale, acc[w][2 * h + 1 + NG / 2] * a.scale);
                 } else {
                     dst[0] = make_float4(acc[0][0] * a.scale, acc[0][1] * a.scale, acc[1][0] * a.scale,
                                          acc[1][1] * a.scale);
@@ -170,8 +178,8 @@ __global__ void __launch_bounds__(BC_THREADS, 2) band_coef_kernel(BandCoefArgs a
                 for (int w = 0; w < NG; ++w)
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        if (w >= g) dst[w * NG + g] = acc[w][g] * a.scale;
-                        else if (k == 0) dst[w * NG + g] = 0.f;
+                        if (w >= g) dst[w * NG + band_gpos<NG>(g)] = acc[w][g] * a.scale;
+                        else if (k == 0) dst[w * NG + band_gpos<NG>(g)] = 0.f;
                     }
             } else {
                 // pos == TperR: the tail (w < g) into slot 0 of the next pair; after
@@ -181,8 +189,8 @@ __global__ void __launch_bounds__(BC_THREADS, 2) band_coef_kernel(BandCoefArgs a
                 for (int w = 0; w < NG; ++w)
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        if (w < g) dst[w * NG + g] = acc[w][g] * a.scale;
-                        else if (k == a.n_pairs - 1) dst[w * NG + g] = 0.f;
+                        if (w < g) dst[w * NG + band_gpos<NG>(g)] = acc[w][g] * a.scale;
+                        else if (k == a.n_pairs - 1) dst[w * NG + band_gpos<NG>(g)] = 0.f;
                     }
             }
         }
@@ -287,7 +295,7 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, MINB) chain_band_kernel(BandA
 #pragma unroll
             for (int g = 0; g < NH; ++g) {
                 CO[g] = CN[g];
-                CN[g] = make_float2(cb[w][g], cb[w][g + NH]);
+                CN[g] = make_float2(cb[w][2 * g], cb[w][2 * g + 1]);   // groups g, g + NH
             }
             if (pn) load_window<NG>(cb[w], pn + w * NG);
             else
@@ -531,7 +539,7 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, 6) chain_band_adj_kernel(Band
             v[0] = x0.x; v[1] = x0.y;
         }
 #pragma unroll
-        for (int g = 0; g < NH; ++g) c[g] = make_float2(v[g], v[g + NH]);
+        for (int g = 0; g < NH; ++g) c[g] = make_float2(v[2 * g], v[2 * g + 1]);   // groups g, g + NH
     };
     // start of pair kk's dk/dc block in gbar
     auto gbase = [&](int kk) -> int64_t {
