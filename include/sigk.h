@@ -147,7 +147,11 @@ int sigk_pairs_backward(const void *grad_out, const void *X, const void *Y, int6
 
 /* Reverse-mode derivative of sigk_gram: dX[i] = sum_j grad_out[i,j] dk_ij/dX_i,
  * dY[j] = sum_i grad_out[i,j] dk_ij/dY_j (either may be NULL).
- * grad_out: [Bx, By].  dX, dY overwritten. */
+ * grad_out: [Bx, By].  dX, dY overwritten.
+ * With opts->symmetric (X == Y: the caller passes the same paths, Bx == By,
+ * L == M, dY NULL): dX = d/dX sum_ij grad_out[i,j] k(X_i, X_j), the derivative
+ * through both arguments, from the pairs i <= j only (k(x,y) = k(y,x)).  f32
+ * only, and only where the band form applies (SIGK_EUNSUPPORTED otherwise). */
 int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64_t Bx,
                        int64_t By, int64_t L, int64_t M, int64_t d, int dyadic_order,
                        int dtype, const sigk_opts *opts, void *dX, void *dY, void *ws,

@@ -204,7 +204,7 @@ PairSrc band_orient(const PairSrc &src, int64_t n, bool &swapped) {
 
 bool bwd_uses_band(const PairSrc &src, int lam, int dtype, int rec, int rows, BandPlan &bp) {
     if (dtype != SIGK_F32 || rec == SIGK_REC_PLAIN || rec == SIGK_REC_STRIP) return false;
-    if (src.mode != PM_PAIRS && src.mode != PM_GRAM) return false;
+    if (src.mode != PM_PAIRS && src.mode != PM_GRAM && src.mode != PM_GRAM_SYM) return false;
     const int64_t la = src.La < src.Lb ? src.La : src.Lb, lb = src.La < src.Lb ? src.Lb : src.La;
     return band_geometry(la, lb, lam, rows, bp);
 }
@@ -219,7 +219,7 @@ int64_t backward_ws_bytes(const PairSrc &src, int64_t n, int lam, int dtype, int
         band_bwd_batch(o, bp, n, STRIP_WS_CAP, bytes);
         return bytes;
     }
-    if (rec == SIGK_REC_BAND) return -1;
+    if (rec == SIGK_REC_BAND || src.mode == PM_GRAM_SYM) return -1;
     if (bwd_uses_strip(lam, src.d, dtype, rec)) {
         int64_t nb, need;
         bwd_strip_batch(src, n, lam, dtype, nb, need);
@@ -249,7 +249,8 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
         float *dA = (float *)(sw ? dY : dX), *dB = (float *)(sw ? dX : dY);
         return cuda_status(launch_band_bwd_f32(o, bp, n_pairs, nbp, (const float *)gout, dA, dB, ws, st));
     }
-    if (rec == SIGK_REC_BAND) return SIGK_EUNSUPPORTED;
+    // the symmetric backward exists in the band form only
+    if (rec == SIGK_REC_BAND || src.mode == PM_GRAM_SYM) return SIGK_EUNSUPPORTED;
     if (bwd_uses_strip(lam, src.d, dtype, rec)) {
         int64_t nb, need, ra, rb;
         bwd_strip_batch(src, n_pairs, lam, dtype, nb, need);
@@ -308,6 +309,11 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         bs.mode = op == SIGK_OP_PAIRS_BACKWARD ? PM_PAIRS : PM_GRAM;
         bs.La = L; bs.Lb = M; bs.d = d;
         bs.nb = By;
+        if (op == SIGK_OP_GRAM_BACKWARD && opts && opts->symmetric) {
+            if (B_or_Bx != By || L != M) return 0;
+            bs.mode = PM_GRAM_SYM;
+            bs.nb = B_or_Bx;
+        }
         const int64_t need = backward_ws_bytes(bs, n_pairs, dyadic_order, dtype, rec_of(opts), rows_of(opts));
         return need > 0 ? (size_t)need : 0;
     }
@@ -460,7 +466,8 @@ int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64
     int s = common_checks(Bx, L, M, d, dyadic_order, dtype, opts);
     if (s) return s;
     if (By < 0) return SIGK_EINVAL;
-    if (opts && opts->symmetric) return SIGK_EINVAL;
+    const bool sym = opts && opts->symmetric;
+    if (sym && (Bx != By || L != M || dY)) return SIGK_EINVAL;
     if (Bx == 0 || By == 0) {
         const int64_t es = dtype == SIGK_F64 ? 8 : 4;
         if (dX && Bx && cudaMemsetAsync(dX, 0, (size_t)(Bx * L * d * es), (cudaStream_t)stream)) return SIGK_ECUDA;
@@ -475,6 +482,13 @@ int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64
     src.La = L; src.Lb = M; src.d = d;
     src.nb = By;
     src.out_si = By; src.out_sj = 1;
+    if (sym) {
+        src.mode = PM_GRAM_SYM;
+        src.B = X;
+        src.nb = Bx;
+        return run_backward(src, Bx * (Bx + 1) / 2, dyadic_order, dtype, opts, grad_out, dX, nullptr,
+                            Bx * L * d, 0, ws, ws_bytes, (cudaStream_t)stream);
+    }
     return run_backward(src, Bx * By, dyadic_order, dtype, opts, grad_out, dX, dY, Bx * L * d,
                         By * M * d, ws, ws_bytes, (cudaStream_t)stream);
 }

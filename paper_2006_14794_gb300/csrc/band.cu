@@ -619,7 +619,11 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, 6) chain_band_adj_kernel(Band
                 const float4 v = ex[i];
                 exK[4 * i] = v.x; exK[4 * i + 1] = v.y; exK[4 * i + 2] = v.z; exK[4 * i + 3] = v.w;
             }
-            if (lane == 31) gseed = a.gout[pair_ref(a.src, k0 + kl - 1).out0];
+            if (lane == 31) {
+                // a symmetric Gram's pair (i, j), i < j, stands for (j, i) too
+                const PairRef pr = pair_ref(a.src, k0 + kl - 1);
+                gseed = a.gout[pr.out0] + (pr.out1 >= 0 ? a.gout[pr.out1] : 0.f);
+            }
         }
         const int buf = (int)(m & 1);
 
@@ -738,6 +742,9 @@ struct GemmArgs {
     int64_t M, K;
     int N, trans, ksplit;   // ksplit > 1 (one batch only): block ks writes its partial
     float *partial;         // tile to partial[ks][M][N], summed by band_split_sum_kernel
+    // symmetric Gram (blocks of rb x cb, only blocks i <= j stored, the rest
+    // zero): skip the K slices that hold only blocks below the diagonal
+    int64_t tri_rb, tri_cb;  // 0: no skipping
 };
 constexpr int GEMM_MAX_SPLIT = 8;
 constexpr int GT_M = 128, GT_K = 32, GT_N = 32;
@@ -754,8 +761,17 @@ __global__ void __launch_bounds__(256) band_gemm_kernel(GemmArgs a) {
     const int n0 = blockIdx.y * GT_N;
     const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
     // this block's K range, in whole slices
-    const int64_t nslice = (a.K + GT_K - 1) / GT_K;
-    const int64_t s_lo = nslice * ks / a.ksplit, s_hi = nslice * (ks + 1) / a.ksplit;
+    int64_t kmin = 0, kmax = a.K;
+    if (a.tri_rb > 0) {
+        if (!a.trans) kmin = (r0 / a.tri_rb) * a.tri_cb;   // rows of block i: columns of blocks j >= i
+        else {                                           // columns of block j: rows of blocks i <= j
+            const int64_t rl = (r0 + GT_M - 1 < a.M ? r0 + GT_M - 1 : a.M - 1);
+            kmax = (rl / a.tri_cb + 1) * a.tri_rb;
+            if (kmax > a.K) kmax = a.K;
+        }
+    }
+    const int64_t sl0 = kmin / GT_K, nslice = (kmax + GT_K - 1) / GT_K - sl0;
+    const int64_t s_lo = sl0 + nslice * ks / a.ksplit, s_hi = sl0 + nslice * (ks + 1) / a.ksplit;
     float gr[16], br[4];
     auto load = [&](int64_t k0) {
 #pragma unroll
@@ -955,8 +971,9 @@ struct BwdRegions {
 
 BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
     const int64_t nx = src.La - 1, ny = src.Lb - 1, d = src.d;
-    const bool gram = src.mode == PM_GRAM;
-    const int64_t nA = gram ? (nbp + src.nb - 1) / src.nb : nbp;
+    const bool sym = src.mode == PM_GRAM_SYM;
+    const bool gram = src.mode == PM_GRAM || sym;
+    const int64_t nA = sym ? src.nb : gram ? (nbp + src.nb - 1) / src.nb : nbp;
     const int64_t nB = gram ? src.nb : nbp;
     BwdRegions r;
     r.band = up4(band_bytes(p, nbp) / (int64_t)sizeof(float));
@@ -979,6 +996,10 @@ BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
 
 int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t cap_bytes,
                        int64_t &bytes) {
+    if (src.mode == PM_GRAM_SYM) {   // one launch: every pair involves the same paths
+        bytes = bwd_regions(src, p, n).total() * (int64_t)sizeof(float);
+        return n;
+    }
     // whole Gram rows per launch: each launch owns its row paths' gradients
     const int64_t unit = src.mode == PM_GRAM ? src.nb : 1;
     int64_t units = (n + unit - 1) / unit;
@@ -1001,7 +1022,11 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int per_sm = band_occupancy_of(p.R, p.lam);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const bool gram = src0.mode == PM_GRAM;
+    // symmetric Gram: pairs (i, j), i <= j, of one batch; dA gets the
+    // derivative through both arguments (dB must be null)
+    const bool sym = src0.mode == PM_GRAM_SYM;
+    const bool gram = src0.mode == PM_GRAM || sym;
+    if (sym && (dB || nbp != n)) return cudaErrorInvalidValue;
     const int64_t nx = src0.La - 1, ny = src0.Lb - 1, d = src0.d;
     const float scale = 0.5f / (float)(1 << (2 * p.lam));
     const BwdRegions rg = bwd_regions(src0, p, nbp);
@@ -1027,8 +1052,10 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         const int64_t m = n - kb < nbp ? n - kb : nbp;
         PairSrc src = src0;
         src.kbase = src0.kbase + kb;
-        const int64_t a0 = gram ? src.kbase / src0.nb : src.kbase;   // first row path
-        const int64_t nA = gram ? m / src0.nb : m;
+        const int64_t a0 = sym ? 0 : gram ? src.kbase / src0.nb : src.kbase;   // first row path
+        const int64_t nA = sym ? src0.nb : gram ? m / src0.nb : m;
+        // blocks below the diagonal of a symmetric Gram's dk/dc stay zero
+        if (sym && cudaMemsetAsync(gbar, 0, sizeof(float) * rg.gbar, st) != cudaSuccess) return cudaErrorUnknown;
         // 1. coefficients
         BandCoefArgs c;
         c.src = src;
@@ -1113,10 +1140,12 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         // 5. chain rule: dinc_A = gbar inc_B, dinc_B (+)= gbar^T inc_A
         GemmArgs g1;
         g1.G = gbar;
-        g1.Bm = incB;
+        g1.Bm = sym ? incA : incB;
         g1.C = dincA;
         g1.N = (int)d;
         g1.trans = 0;
+        g1.tri_rb = sym ? nx : 0;
+        g1.tri_cb = sym ? ny : 0;
         GemmArgs g2 = g1;
         g2.Bm = incA;
         g2.C = dincB;
@@ -1154,8 +1183,9 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         g1.ksplit = split(g1);
         g2.ksplit = split(g2);
         g1.partial = g2.partial = part;
-        const bool add_b = gram && kb > 0;
-        // the split sum writes dincB; an unsplit contraction that must add goes through it too
+        const bool add_b = (gram && kb > 0) || sym;
+        if (sym) g2.C = dincA;   // column-role gradients of the same paths: add them to the row role's
+        // the split sum writes the result; an unsplit contraction that must add goes through it too
         if (add_b && g2.ksplit == 1) g2.ksplit = 2;
         const dim3 gd1((unsigned)((g1.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N),
                        (unsigned)(batches * g1.ksplit));
@@ -1166,10 +1196,10 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
             if (g1.ksplit > 1)
                 band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g1.ksplit, g1.M * d, 0, dincA);
         }
-        if (dB) {
+        if (dB || sym) {
             band_gemm_kernel<<<gd2, 256, 0, st>>>(g2);
             if (g2.ksplit > 1)
-                band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g2.ksplit, g2.M * d, add_b ? 1 : 0, dincB);
+                band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g2.ksplit, g2.M * d, add_b ? 1 : 0, g2.C);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 6. point gradients

@@ -273,16 +273,21 @@ def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dya
 
 def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
                   need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
-                  schedule: Optional[Schedule] = None):
-    """(dX, dY): dX[i] = sum_j grad_out[i,j] dk(X_i,Y_j)/dX_i, dY[j] likewise."""
+                  schedule: Optional[Schedule] = None, symmetric: bool = False):
+    """(dX, dY): dX[i] = sum_j grad_out[i,j] dk(X_i,Y_j)/dX_i, dY[j] likewise.
+    symmetric=True (Y is X): (dX, None) with dX the derivative of
+    sum_ij grad_out[i,j] k(X_i, X_j) through both arguments, from the pairs
+    i <= j only (f32, band form; SigkError with SIGK_EUNSUPPORTED otherwise)."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     Bx, L, d = X.shape
     By, M = Y.shape[0], Y.shape[1]
     dt = _dtype_code(X)
     grad_out = grad_out.to(X.dtype).contiguous()
+    if symmetric:
+        need_dx, need_dy = True, False
     dX = torch.empty_like(X) if need_dx else None
     dY = torch.empty_like(Y) if need_dy else None
-    o = _opts(rec, schedule=schedule)
+    o = _opts(rec, symmetric=symmetric, schedule=schedule)
     ws, nws = _workspace(OP_GRAM_BACKWARD, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_gram_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), Bx, By, L, M,
                                     d, int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
@@ -328,17 +333,27 @@ class SigKernelPairs(torch.autograd.Function):
 
 
 class SigKernelGram(torch.autograd.Function):
-    """k(X_i, Y_j) with the adjoint sweep as its backward."""
+    """k(X_i, Y_j) with the adjoint sweep as its backward.  Given the same
+    tensor twice (a Gram of X with itself) it solves only the pairs i <= j,
+    forward and (where the band form applies) backward."""
 
     @staticmethod
     def forward(ctx, X, Y, dyadic_order):
         ctx.save_for_backward(X, Y)
         ctx.lam = dyadic_order
-        return gram(X, Y, dyadic_order)
+        ctx.sym = X is Y
+        return gram(X, Y, dyadic_order, symmetric=ctx.sym)
 
     @staticmethod
     def backward(ctx, g):
         X, Y = ctx.saved_tensors
+        if ctx.sym and ctx.needs_input_grad[0] and ctx.needs_input_grad[1]:
+            try:
+                dX, _ = gram_backward(g, X, X, ctx.lam, symmetric=True)
+                return dX, None, None
+            except SigkError as e:
+                if e.status != SIGK_EUNSUPPORTED:
+                    raise
         dX, dY = gram_backward(g, X, Y, ctx.lam, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
         return dX, dY, None
 

@@ -169,3 +169,32 @@ def test_band_backward_is_the_default_and_agrees_with_the_strip_adjoint():
     rX, rY = oracle.gram_grad(X64, Y64, 1, gout)
     assert grad_err(auto[0].cpu(), rX) <= GRAD_TOL
     assert grad_err(auto[1].cpu(), rY) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("lam,L,d", [(1, 256, 32), (1, 100, 9), (2, 60, 5)])
+def test_band_symmetric_backward_matches_oracle(lam, L, d):
+    """Pairs i <= j only: the derivative through both arguments of a Gram of X
+    with itself, for a non-symmetric incoming gradient."""
+    sigk = S()
+    B = 7
+    X32, X64 = inputs.f32(inputs.random_paths(4100 + L, B, L, d, scale=2.0, time_channel=True))
+    gout = np.random.default_rng(41).normal(size=(B, B))
+    rX, rY = oracle.gram_grad(X64, X64, lam, gout)
+    dX, none = sigk.gram_backward(to_dev(gout), to_dev(X32), to_dev(X32), lam, symmetric=True)
+    assert none is None
+    assert grad_err(dX.cpu(), rX + rY) <= GRAD_TOL
+    # the symmetric forward and autograd through it
+    X = to_dev(X32).requires_grad_(True)
+    K = sigk.SigKernelGram.apply(X, X, lam)
+    assert rel_err(K.detach().cpu().numpy(), oracle.gram(X64, X64, lam)) <= F32_TOL
+    K.backward(to_dev(gout))
+    assert grad_err(X.grad.cpu(), rX + rY) <= GRAD_TOL
+
+
+def test_symmetric_backward_argument_checks():
+    sigk = S()
+    X = to_dev(inputs.random_paths(4200, 3, 20, 3))
+    Y = to_dev(inputs.random_paths(4201, 4, 20, 3))
+    with pytest.raises(sigk.SigkError) as ei:   # different batches
+        sigk.gram_backward(torch.ones(3, 4, device="cuda"), X, Y, 1, symmetric=True)
+    assert ei.value.status == sigk.SIGK_EINVAL
