@@ -95,10 +95,13 @@ typedef struct {
                          chained kernel would run (f32, rec AUTO or CHAIN) a
                          value without an instance for the shape gives
                          SIGK_EUNSUPPORTED; other paths ignore it             */
-    int coef_path;    /* strip path coefficients: 0 auto (split-TF32 tensor
-                         cores for f32 with d >= 32), 1 FMA contraction,
-                         2 split-TF32 tensor cores (f32 only: f64 gives
-                         SIGK_EUNSUPPORTED); other paths ignore it            */
+    int coef_path;    /* strip path coefficients: 0 auto (split-TF32 on the
+                         tcgen05 tensor cores for f32 with 32 <= d <= 64,
+                         warp-level MMAs for larger d, FMA otherwise), 1 FMA
+                         contraction, 2 split-TF32 warp-level MMAs (mma.sync),
+                         3 split-TF32 tcgen05 MMAs (d <= 64); 2 and 3 are f32
+                         only (f64 gives SIGK_EUNSUPPORTED); other paths
+                         ignore it                                            */
     int reserved[3];  /* must be 0                                            */
 } sigk_opts;          /* a NULL pointer means all-zero (automatic) options    */
 

@@ -17,7 +17,7 @@ bool opts_ok(const sigk_opts *o) {
     if (o->rows_per_lane != 0 && o->rows_per_lane != 4 && o->rows_per_lane != 8 &&
         o->rows_per_lane != 16)
         return false;
-    if (o->coef_path < 0 || o->coef_path > 2) return false;
+    if (o->coef_path < 0 || o->coef_path > 3) return false;
     for (int i = 0; i < 3; ++i)
         if (o->reserved[i] != 0) return false;
     return true;
@@ -32,7 +32,8 @@ int common_checks(int64_t B, int64_t L, int64_t M, int64_t d, int lam, int dtype
     if (!opts_ok(opts)) return SIGK_EINVAL;
     if (lam < 0) return SIGK_EINVAL;
     if (lam > 8) return SIGK_EUNSUPPORTED;
-    if (opts && opts->coef_path == 2 && dtype != SIGK_F32) return SIGK_EUNSUPPORTED;
+    if (opts && opts->coef_path >= 2 && dtype != SIGK_F32) return SIGK_EUNSUPPORTED;
+    if (opts && opts->coef_path == 3 && d > 64) return SIGK_EUNSUPPORTED;
     return SIGK_OK;
 }
 

@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include "sigk_internal.cuh"
+#include "tc5.cuh"
 
 namespace sigk {
 
@@ -951,6 +952,171 @@ __global__ void __launch_bounds__(256) coef_tc_kernel(PairSrc src, const PairPla
     }
 }
 
+// ---- coefficients on the fifth-generation tensor cores (tcgen05, f32, d <= 64) ----
+// The same blocks as coef_kernel: d(W, P) = c(prow0 + P, W - P) for W < nw,
+// P < CP.  A block of 128 threads takes a 128-row slice of a strip's coarse
+// rows (the row increments, pre-scaled by 1/2 4^-lambda, split into TF32 hi
+// and lo parts once) and walks the columns in chunks of 128: the chunk's
+// column increments are split and staged, one thread issues the split-TF32
+// MMAs (D in TMEM, 128 x 128 fp32), the warps read D back into a shared tile
+// and store it along its anti-diagonals (each diagonal W a contiguous run of
+// P).  Cells outside the grid are zero (zero increments).  Waits on the MMA
+// barrier are bounded: on expiry the block records SIGK_ETIMEOUT and stops.
+constexpr int TC5_M = 128, TC5_N = 128, TC5_SS = TC5_N + 2;   // shared tile stride: conflict-free diagonals
+constexpr int TC5_T = 256;                                     // threads: two per operand row
+
+__host__ __device__ inline int tc5_k(int64_t d) { return (int)(((d + 3) / 4 * 4 + 7) / 8 * 8); }
+inline int tc5_smem_bytes(int64_t d) { return 4 * TC5_M * tc5_k(d) * 4 + TC5_M * TC5_SS * 4; }
+
+// Half of a row (K/8 float4s from k4 = h * K/8) of increments into registers.
+__device__ __forceinline__ void tc5_fetch(float4 (&v)[8], const float4 *src, int h, int K, int k4n) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int k4 = h * (K / 8) + i;
+        v[i] = (src && i < K / 8 && k4 < k4n) ? __ldg(src + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+// ... split into TF32 hi and lo parts and stored into the K-major tiles.
+__device__ __forceinline__ void tc5_store(unsigned char *hi, unsigned char *lo, int r, int h, int K,
+                                          const float4 (&v)[8], float s) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i >= K / 8) break;
+        const int k4 = h * (K / 8) + i;
+        const float e[4] = {v[i].x * s, v[i].y * s, v[i].z * s, v[i].w * s};
+        uint4 hh, ll;
+        hh.x = tc5::tf32(e[0]); ll.x = tc5::tf32(e[0] - __uint_as_float(hh.x));
+        hh.y = tc5::tf32(e[1]); ll.y = tc5::tf32(e[1] - __uint_as_float(hh.y));
+        hh.z = tc5::tf32(e[2]); ll.z = tc5::tf32(e[2] - __uint_as_float(hh.z));
+        hh.w = tc5::tf32(e[3]); ll.w = tc5::tf32(e[3] - __uint_as_float(hh.w));
+        const int off = tc5::cm_off(r, 4 * k4, K);
+        *reinterpret_cast<uint4 *>(hi + off) = hh;
+        *reinterpret_cast<uint4 *>(lo + off) = ll;
+    }
+}
+
+template <int R, int LAM>
+__global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const PairPlan *plan, int64_t n_pairs,
+                                                           const int64_t *totals, const float *incA,
+                                                           const float *incB, float *cbuf, int *status,
+                                                           long long max_wait) {
+    constexpr int S = 1 << LAM;
+    constexpr int CP = 32 * (R / S);
+    constexpr int RB = CP >= TC5_M ? CP / TC5_M : 1;   // 128-row slices per strip
+    constexpr int NW = TC5_T / 32;
+    extern __shared__ __align__(1024) unsigned char tc5_sm[];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tmem_slot;
+    const int K = tc5_k(src.d);
+    const int D4 = (int)((src.d + 3) / 4);
+    unsigned char *ah = tc5_sm, *al = ah + TC5_M * K * 4;
+    unsigned char *bh = al + TC5_M * K * 4, *bl = bh + TC5_N * K * 4;
+    float *St = reinterpret_cast<float *>(bl + TC5_N * K * 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & (TC5_M - 1), half = tid >> 7;   // operand row and half of K this thread stages
+    const float scale = 0.5f / (float)(1 << (2 * LAM));
+    const unsigned idesc = tc5::idesc_tf32(TC5_M, TC5_N);
+
+    if (warp == 0) tc5::alloc(&tmem_slot, TC5_N);
+    if (tid == 0) tc5::mbar_init(&mbar);
+    tc5::fence_before();
+    __syncthreads();
+    tc5::fence_after();
+    const unsigned tmem = tmem_slot;
+    unsigned phase = 0;
+    bool failed = false;
+
+    const int64_t items = totals[3] * RB;
+    for (int64_t it = blockIdx.x; it < items && !failed; it += gridDim.x) {
+        const int64_t gs = it / RB;
+        const int rb = (int)(it - gs * RB);
+        int64_t lo = 0, hi = n_pairs - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (plan[mid].strip_base <= gs) lo = mid; else hi = mid - 1;
+        }
+        const PairPlan pp = plan[lo];
+        const int s = (int)(gs - pp.strip_base);
+        const float4 *x = reinterpret_cast<const float4 *>(pp.swap ? incB : incA) + pp.a_row0 * D4;
+        const float4 *y = reinterpret_cast<const float4 *>(pp.swap ? incA : incB) + pp.b_row0 * D4;
+        float *blk = cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
+        const int P0 = rb * TC5_M;
+        const int prow0 = s * CP - (pp.pad >> LAM) + P0;   // coarse row of slice row 0
+        const bool rows_empty = prow0 + TC5_M - 1 < 0 || prow0 >= pp.nx;
+        const int qfirst = -(P0 + TC5_M - 1), qlast = pp.nw - 1 - P0;   // column range of the slice's diagonals
+        auto col_ok = [&](int q0) { return !rows_empty && q0 + TC5_N - 1 >= 0 && q0 < pp.ny; };
+        float4 nb[8];   // the next chunk's column increments, fetched ahead
+        __syncthreads();
+        {
+            const int p = prow0 + row;
+            float4 av[8];
+            tc5_fetch(av, (!rows_empty && p >= 0 && p < pp.nx && P0 + row < CP) ? x + (int64_t)p * D4 : nullptr,
+                      half, K, D4);
+            tc5_store(ah, al, row, half, K, av, scale);
+            const int q = qfirst + row;
+            tc5_fetch(nb, (col_ok(qfirst) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr, half, K, D4);
+        }
+        for (int q0 = qfirst; q0 <= qlast; q0 += TC5_N) {
+            const bool zero = !col_ok(q0);
+            if (!zero) {
+                tc5_store(bh, bl, row, half, K, nb, 1.f);
+                tc5::fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    tc5::fence_after();
+                    tc5::gemm_split(tmem, ah, al, bh, bl, K, idesc, false);
+                    tc5::commit(&mbar);
+                }
+            }
+            // fetch the next chunk's column increments while the MMAs run
+            {
+                const int qn = q0 + TC5_N, q = qn + row;
+                tc5_fetch(nb, (qn <= qlast && col_ok(qn) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr,
+                          half, K, D4);
+            }
+            if (!zero) {
+                const bool ok = tc5::mbar_wait(&mbar, phase, max_wait);
+                if (__syncthreads_or(!ok)) {   // block-uniform
+                    failed = true;
+                    if (tid == 0) atomicExch(status, (int)SIGK_ETIMEOUT);
+                    break;
+                }
+                phase ^= 1;
+                tc5::fence_after();
+                // D into the shared tile: warp w reads TMEM lanes 32 (w % 4) .., columns 64 (w / 4) ..
+                const int r = (warp & 3) * 32 + lane, cb = (warp >> 2) * 64;
+#pragma unroll
+                for (int c0 = 0; c0 < 64; c0 += 32) {
+                    float v[32];
+                    tc5::ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(cb + c0), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) St[r * TC5_SS + cb + c0 + j] = v[j];
+                }
+                tc5::fence_before();
+            }
+            __syncthreads();
+            // diagonals W = q + P of this chunk: P in [W - q0 - 127, W - q0] within the slice
+            const int wlo = q0 + P0 > 0 ? q0 + P0 : 0;
+            const int whi = q0 + P0 + TC5_N + TC5_M - 2 < pp.nw - 1 ? q0 + P0 + TC5_N + TC5_M - 2 : pp.nw - 1;
+            for (int W = wlo + warp; W <= whi; W += NW) {
+                int plo = W - q0 - (TC5_N - 1), phi = W - q0;
+                if (plo < P0) plo = P0;
+                if (phi > P0 + TC5_M - 1) phi = P0 + TC5_M - 1;
+                if (phi > CP - 1) phi = CP - 1;
+                for (int P = plo + lane; P <= phi; P += 32)
+                    blk[(int64_t)W * CP + P] = zero ? 0.f : St[(P - P0) * TC5_SS + (W - P - q0)];
+            }
+            __syncthreads();
+        }
+    }
+    // after a timeout, give the outstanding MMAs another bounded wait before
+    // the accumulator is released
+    if (failed) tc5::mbar_wait(&mbar, phase, max_wait);
+    tc5::fence_before();
+    __syncthreads();
+    if (warp == 0) tc5::dealloc(tmem, TC5_N);
+}
+
 template <typename T>
 __global__ void strip_trivial_kernel(PairSrc src, int64_t n, T *out) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -1061,8 +1227,21 @@ int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam
 template <typename T, int R, int LAM>
 static cudaError_t launch_coef(const PairSrc &src, const PairPlan *plan, int64_t n,
                                const int64_t *totals, const T *incA, const T *incB, T *cbuf,
-                               int sms, cudaStream_t st, int coef_path) {
+                               int sms, cudaStream_t st, int coef_path, int *status) {
     cudaError_t e;
+    // tcgen05 for f32 with 32 <= d <= 64 (or on request, d <= 64); mma.sync
+    // split-TF32 on request (or d > 64); FMA otherwise
+    const bool tc5 = sizeof(T) == 4 && src.d <= 64 &&
+                     (coef_path == 3 || (coef_path == 0 && src.d >= 32));
+    if (tc5) {
+        const int smem = tc5_smem_bytes(src.d);
+        auto tk = coef_tc5_kernel<R, LAM>;
+        if ((e = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+            return e;
+        tk<<<sms, TC5_T, smem, st>>>(src, plan, n, totals, (const float *)incA, (const float *)incB,
+                                     (float *)cbuf, status, 1LL << 26);
+        return cudaGetLastError();
+    }
     const bool tc = sizeof(T) == 4 && (coef_path == 2 || (coef_path == 0 && src.d >= 32));
     if (tc) {
         const int XS = tc_stride(src.d);
@@ -1122,7 +1301,8 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, cbuf, sms, st, coef_path)) != cudaSuccess)
+    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, cbuf, sms, st, coef_path, status)) !=
+        cudaSuccess)
         return e;
     StripArgs<T> a;
     a.src = src;
@@ -1186,7 +1366,7 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, (T *)(w + L.coef), sms, st,
-                                    coef_path)) !=
+                                    coef_path, status)) !=
         cudaSuccess)
         return e;
     {

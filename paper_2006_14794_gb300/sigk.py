@@ -23,7 +23,7 @@ from . import build as _build
 SIGK_OK, SIGK_EINVAL, SIGK_ENOMEM_WS, SIGK_ECUDA, SIGK_ETIMEOUT, SIGK_EUNSUPPORTED = range(6)
 SIGK_F32, SIGK_F64 = 0, 1
 REC_AUTO, REC_CHAIN, REC_PLAIN, REC_STRIP, REC_BAND = 0, 1, 2, 3, 4
-COEF_AUTO, COEF_FMA, COEF_TC = 0, 1, 2
+COEF_AUTO, COEF_FMA, COEF_TC, COEF_TC5 = 0, 1, 2, 3
 OP_PAIRS, OP_GRAM, OP_PAIRS_VARLEN, OP_PAIRS_BACKWARD, OP_GRAM_BACKWARD = range(5)
 
 _vp = ctypes.c_void_p

@@ -23,7 +23,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 import torch
 
 from . import sigk
-from .sigk import COEF_FMA, COEF_TC, REC_BAND, REC_CHAIN, REC_PLAIN, REC_STRIP, Schedule
+from .sigk import COEF_FMA, COEF_TC, COEF_TC5, REC_BAND, REC_CHAIN, REC_PLAIN, REC_STRIP, Schedule
 
 _lock = threading.Lock()
 _mem: Dict[str, Schedule] = {}
@@ -52,6 +52,7 @@ def candidates(op: str, dtype: torch.dtype) -> List[Schedule]:
         c += [Schedule(REC_CHAIN, r, 0) for r in (4, 8, 16)]
         c += [Schedule(REC_BAND, r, 0) for r in (4, 8, 16)]
     if dtype == torch.float32:
+        c.append(Schedule(REC_STRIP, 0, COEF_TC5))
         c.append(Schedule(REC_STRIP, 0, COEF_TC))
     c.append(Schedule(REC_STRIP, 0, COEF_FMA))
     c.append(Schedule(REC_PLAIN, 0, 0))

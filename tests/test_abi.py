@@ -90,11 +90,15 @@ def test_schedule_options_are_checked(libsigk):
 
     assert call(rows_per_lane=3) == sigk.SIGK_EINVAL
     assert call(rows_per_lane=32) == sigk.SIGK_EINVAL
-    assert call(coef_path=3) == sigk.SIGK_EINVAL
+    assert call(coef_path=4) == sigk.SIGK_EINVAL
     assert call(coef_path=-1) == sigk.SIGK_EINVAL
     assert call(rec=5) == sigk.SIGK_EINVAL
-    # the tensor-core coefficient kernel is f32 only
+    # the tensor-core coefficient kernels are f32 only; the tcgen05 one takes d <= 64
     assert call(dtype=1, coef_path=2) == sigk.SIGK_EUNSUPPORTED
+    assert call(dtype=1, coef_path=3) == sigk.SIGK_EUNSUPPORTED
+    o = sigk.SigkOpts()
+    o.coef_path = 3
+    assert libsigk.sigk_pairs(P, P, 3, 4, 4, 65, 0, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EUNSUPPORTED
 
 
 def test_forced_strip_schedule_asks_for_workspace(libsigk):

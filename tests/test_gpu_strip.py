@@ -110,3 +110,25 @@ def test_graph_captured_calls_replay_correctly():
     B32, B64 = inputs.f32(inputs.random_paths(1701, 7, 60, 8, time_channel=True))
     gg = S().graphed(S().gram, to_dev(A32), to_dev(B32), 2)
     assert rel_err(gg(to_dev(A32), to_dev(B32)).cpu().numpy(), oracle.gram(A64, B64, 2)) <= 1e-5
+
+
+@pytest.mark.parametrize("lam,L,M,d", [
+    (0, 700, 300, 64),   # 512-row strips: four 128-row slices per strip
+    (1, 400, 520, 40),   # d not a multiple of 8: zero-padded K
+    (2, 150, 160, 32),
+    (3, 70, 90, 33),     # 64-row strips: half of a 128-row slice
+])
+def test_strip_tcgen05_coefficients_match_oracle(lam, L, M, d):
+    """Coefficients from split-TF32 tcgen05 MMAs (TMEM accumulators) against
+    the oracle, and against the FMA and warp-level MMA coefficient paths."""
+    sigk = S()
+    B = 3
+    X32, X64 = inputs.f32(inputs.random_paths(4300 + lam, B, L, d, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(4400 + lam, B, M, d, time_channel=True))
+    ref = oracle.pairs(X64, Y64, lam)
+    outs = {}
+    for coef in (sigk.COEF_TC5, sigk.COEF_TC, sigk.COEF_FMA):
+        s = sigk.Schedule(sigk.REC_STRIP, 0, coef)
+        outs[coef] = sigk.pairs(to_dev(X32), to_dev(Y32), lam, schedule=s, check_status=True).cpu().numpy()
+        assert rel_err(outs[coef], ref) <= 1e-5, coef
+    assert rel_err(outs[sigk.COEF_TC5], outs[sigk.COEF_FMA]) <= 2e-6
