@@ -90,11 +90,13 @@ typedef struct {
                          bottom row, so the strip below waits out its bounded
                          wait (~1 s) and sigk_stream_status reports
                          SIGK_ETIMEOUT; nothing faults on the device          */
-    int rows_per_lane;/* schedule: refined rows per lane of the chained kernel
-                         (4, 8 or 16; 0 = the smallest that fits).  Where the
-                         chained kernel would run (f32, rec AUTO or CHAIN) a
-                         value without an instance for the shape gives
-                         SIGK_EUNSUPPORTED; other paths ignore it             */
+    int rows_per_lane;/* schedule: refined rows per lane (4, 8 or 16; 0 =
+                         default).  Chained and band kernels: the band height
+                         32 x rows_per_lane (default the smallest that fits).
+                         Strip path (f32: 16 by default, 8 for dyadic order
+                         <= 2, 4 for <= 1; f64: 8): the strip height.  A value
+                         without an instance gives SIGK_EUNSUPPORTED; the
+                         plain path ignores it                                */
     int coef_path;    /* strip path coefficients: 0 auto (split-TF32 on the
                          tcgen05 tensor cores for f32 with 32 <= d <= 64,
                          warp-level MMAs for larger d, FMA otherwise), 1 FMA
@@ -102,7 +104,12 @@ typedef struct {
                          3 split-TF32 tcgen05 MMAs (d <= 64); 2 and 3 are f32
                          only (f64 gives SIGK_EUNSUPPORTED); other paths
                          ignore it                                            */
-    int reserved[3];  /* must be 0                                            */
+    int orient;       /* strip path: which path the rows refine.  0 auto (the
+                         shorter path from 1024 pairs per call on, else the
+                         longer), 1 the longer (more strips per pair: more
+                         warps on few pairs), 2 the shorter (fewer virtual
+                         rows and fill/drain steps per cell)                   */
+    int reserved[2];  /* must be 0                                            */
 } sigk_opts;          /* a NULL pointer means all-zero (automatic) options    */
 
 typedef enum {

@@ -18,7 +18,8 @@ bool opts_ok(const sigk_opts *o) {
         o->rows_per_lane != 16)
         return false;
     if (o->coef_path < 0 || o->coef_path > 3) return false;
-    for (int i = 0; i < 3; ++i)
+    if (o->orient < 0 || o->orient > 2) return false;
+    for (int i = 0; i < 2; ++i)
         if (o->reserved[i] != 0) return false;
     return true;
 }
@@ -51,17 +52,30 @@ constexpr int64_t STRIP_WS_CAP = 8LL << 30;
 int fault_of(const sigk_opts *o) { return o ? o->fault_inject : 0; }
 int rows_of(const sigk_opts *o) { return o ? o->rows_per_lane : 0; }
 int coef_of(const sigk_opts *o) { return o ? o->coef_path : 0; }
+// the strip path's rows per lane (its default, or the requested one)
+int strip_R_of(const sigk_opts *o, int dtype) {
+    const int r = rows_of(o);
+    return r != 0 ? r : (dtype == SIGK_F64 ? 8 : 16);
+}
+// rows refine the shorter path: on request, or by default with many pairs
+// in flight (parallelism then comes from the pairs, and fewer virtual rows
+// and fill/drain steps per cell win)
+int shorter_of(const sigk_opts *o, int64_t n_pairs) {
+    const int v = o ? o->orient : 0;
+    return v == 2 || (v == 0 && n_pairs >= 1024) ? 1 : 0;
+}
 
 // Pairs per strip-path launch and the workspace that needs.
 void strip_batch(const PairSrc &src, int64_t n, int64_t la, int64_t lb, int lam, int dtype,
-                 int64_t &nb, int64_t &bytes) {
+                 const sigk_opts *opts, int64_t &nb, int64_t &bytes) {
     int64_t ra, rb;
     src_rows(src, n, ra, rb);
+    const int R = strip_R_of(opts, dtype), sh = shorter_of(opts, n);
     nb = n;
-    bytes = strip_workspace_bytes(nb, la, lb, lam, dtype, ra, rb, src.d);
+    bytes = strip_workspace_bytes(nb, la, lb, lam, dtype, ra, rb, src.d, R, sh);
     while (nb > 1 && bytes > STRIP_WS_CAP) {
         nb = (nb + 1) / 2;
-        bytes = strip_workspace_bytes(nb, la, lb, lam, dtype, ra, rb, src.d);
+        bytes = strip_workspace_bytes(nb, la, lb, lam, dtype, ra, rb, src.d, R, sh);
     }
 }
 
@@ -81,7 +95,10 @@ Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, 
                     int rows_per_lane = 0, BandPlan *bpo = nullptr) {
     if (src.La < 2 || src.Lb < 2) return P_FILL;
     if (rec == SIGK_REC_PLAIN) return P_PLAIN;
-    if (rec == SIGK_REC_STRIP) return strip_supported(lam, src.d, dtype) ? P_STRIP : P_FILL;
+    if (rec == SIGK_REC_STRIP)
+        return strip_supported(lam, src.d, dtype) &&
+                       strip_has_R(rows_per_lane ? rows_per_lane : (dtype == SIGK_F64 ? 8 : 16), lam, dtype)
+                   ? P_STRIP : P_FILL;
     if (rec == SIGK_REC_BAND && dtype != SIGK_F32) return P_FILL;
     if (dtype == SIGK_F64 && rec != SIGK_REC_CHAIN) return P_PLAIN;
     if (dtype == SIGK_F32) {
@@ -106,15 +123,17 @@ Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, 
 int run_strip(PairSrc src, int64_t n, int lam, int dtype, int64_t la, int64_t lb, const sigk_opts *opts,
               void *out, void *ws, size_t ws_bytes, cudaStream_t st) {
     int64_t nb, need, ra, rb;
-    strip_batch(src, n, la, lb, lam, dtype, nb, need);
+    strip_batch(src, n, la, lb, lam, dtype, opts, nb, need);
     src_rows(src, n, ra, rb);
+    if (!strip_has_R(strip_R_of(opts, dtype), lam, dtype)) return SIGK_EUNSUPPORTED;
     if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         PairSrc s = src;
         s.kbase = src.kbase + k0;
         const int64_t m = n - k0 < nb ? n - k0 : nb;
         cudaError_t e = launch_strip(s, m, lam, dtype, ws, out, WAIT_CYCLES,
-                                     k0 == 0 ? fault_of(opts) : 0, st, la, lb, ra, rb, coef_of(opts));
+                                     k0 == 0 ? fault_of(opts) : 0, st, la, lb, ra, rb, coef_of(opts),
+                                     strip_R_of(opts, dtype), shorter_of(opts, n));
         if (e != cudaSuccess) return cuda_status(e);
     }
     return SIGK_OK;
@@ -329,7 +348,7 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         memset(&vs, 0, sizeof(vs));
         vs.mode = PM_VARLEN;
         vs.La = L; vs.Lb = M; vs.d = d;
-        strip_batch(vs, n_pairs, L, M, dyadic_order, dtype, nb, need);
+        strip_batch(vs, n_pairs, L, M, dyadic_order, dtype, opts, nb, need);
         return (size_t)need;
     }
     PairSrc src;
@@ -356,7 +375,7 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         return (size_t)need;
     }
     if (path != P_STRIP) return 0;
-    strip_batch(src, n_pairs, src.La, src.Lb, dyadic_order, dtype, nb, need);
+    strip_batch(src, n_pairs, src.La, src.Lb, dyadic_order, dtype, opts, nb, need);
     return (size_t)need;
 }
 

@@ -54,7 +54,7 @@ struct PairPlan {
 };
 
 template <int R, int LAM>
-__global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *totals) {
+__global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *totals, int shorter_rows) {
     constexpr int S = 1 << LAM;
     constexpr int TH = 32 * R;
     constexpr int CP = 32 * (R / S);
@@ -63,8 +63,10 @@ __global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *tot
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
         const PairRef pr = pair_ref(src, k);
         PairPlan p;
-        // rows refine the longer path: more strips, more warps per pair
-        const bool swap = pr.lb > pr.la;
+        // rows refine the longer path (more strips, more warps per pair) or,
+        // with many pairs in flight, the shorter one (fewer virtual rows and
+        // fill/drain steps per cell)
+        const bool swap = shorter_rows ? pr.la > pr.lb : pr.lb > pr.la;
         const int64_t la = swap ? pr.lb : pr.la, lb = swap ? pr.la : pr.lb;
         p.a_row0 = swap ? pr.b_row0 : pr.a_row0;
         p.b_row0 = swap ? pr.a_row0 : pr.b_row0;
@@ -1146,9 +1148,10 @@ static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
 
 // Upper bounds from the longest path length (exact for uniform lengths).
 static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R, int lam,
-                                int64_t es, int64_t rowsA, int64_t rowsB, int64_t D4) {
+                                int64_t es, int64_t rowsA, int64_t rowsB, int64_t D4, int shorter_rows = 0) {
     const int64_t S = 1LL << lam, TH = 32LL * R, CP = 32LL * (R / S);
-    const int64_t lx = max_la > max_lb ? max_la : max_lb, ly = max_la > max_lb ? max_lb : max_la;
+    int64_t lx = max_la > max_lb ? max_la : max_lb, ly = max_la > max_lb ? max_lb : max_la;
+    if (shorter_rows) { const int64_t t = lx; lx = ly; ly = t; }
     const int64_t ni = (lx - 1) * S, nj = (ly - 1) * S;
     const int64_t ns = (ni + TH - 1) / TH;
     const int64_t nw = ((nj + TH - 2) >> lam) + 2;
@@ -1199,9 +1202,11 @@ int64_t strip_bwd_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int
     return strip_layout_bwd(n, max_la, max_lb, R, lam, es, rowsA, rowsB, (d + 3) / 4).total;
 }
 
-static int strip_R(int dtype, int lam) {
-    (void)lam;
-    return dtype == SIGK_F64 ? 8 : 16;
+// rows per lane of the strip path's forward: f64 8; f32 16 by default, 8 or
+// 4 on request (a 256- or 128-row strip wastes less on short or uneven pairs)
+bool strip_has_R(int R, int lam, int dtype) {
+    if (dtype == SIGK_F64) return R == 8;
+    return R == 16 || (R == 8 && lam <= 2) || (R == 4 && lam <= 1);
 }
 
 // dyadic orders 0..3, and channel counts whose coefficient tile fits shared
@@ -1213,11 +1218,10 @@ bool strip_supported(int lam, int64_t d, int dtype) {
 }
 
 int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype,
-                              int64_t rowsA, int64_t rowsB, int64_t d) {
-    if (lam < 0 || lam > 3 || n <= 0) return 0;
+                              int64_t rowsA, int64_t rowsB, int64_t d, int R, int shorter_rows) {
+    if (lam < 0 || lam > 3 || n <= 0 || !strip_has_R(R, lam, dtype)) return 0;
     const int64_t es = dtype == SIGK_F64 ? 8 : 4;
-    return strip_layout(n, max_la, max_lb, strip_R(dtype, lam), lam, es, rowsA, rowsB, (d + 3) / 4)
-        .total;
+    return strip_layout(n, max_la, max_lb, R, lam, es, rowsA, rowsB, (d + 3) / 4, shorter_rows).total;
 }
 
 // The coefficient blocks: split-TF32 tensor-core MMAs for f32 with d >= 32,
@@ -1266,9 +1270,10 @@ template <typename T, int R, int LAM>
 static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *out,
                                   long long wait_cycles, int fault_inject, cudaStream_t st,
                                   int64_t max_la, int64_t max_lb, int64_t rowsA, int64_t rowsB,
-                                  int coef_path) {
+                                  int coef_path, int shorter_rows) {
     const int64_t D4 = (src.d + 3) / 4;
-    const StripLayout L = strip_layout(n, max_la, max_lb, R, LAM, (int64_t)sizeof(T), rowsA, rowsB, D4);
+    const StripLayout L = strip_layout(n, max_la, max_lb, R, LAM, (int64_t)sizeof(T), rowsA, rowsB, D4,
+                                       shorter_rows);
     unsigned char *w = (unsigned char *)ws;
     int *status = (int *)w;
     int *counter = (int *)(w + 256);
@@ -1297,7 +1302,7 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
         inc_kernel<T><<<gb, 256, 0, st>>>((const T *)src.B, rowsB, packed ? src.b_off + nall : nullptr,
                                           src.d, D4, incB);
     }
-    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals);
+    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals, shorter_rows);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1361,7 +1366,7 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         inc_kernel<T><<<gb, 256, 0, st>>>((const T *)src.B, rowsB, packed ? src.b_off + nall : nullptr,
                                           src.d, D4, incB);
     }
-    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals);
+    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals, 0);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1449,23 +1454,22 @@ cudaError_t launch_strip_bwd(const PairSrc &src, int64_t n, int lam, int dtype, 
 
 cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void *ws, void *out,
                          long long wait_cycles, int fault_inject, cudaStream_t st, int64_t max_la,
-                         int64_t max_lb, int64_t rowsA, int64_t rowsB, int coef_path) {
+                         int64_t max_lb, int64_t rowsA, int64_t rowsB, int coef_path, int R,
+                         int shorter_rows) {
     if (n <= 0) return cudaSuccess;
+#define SIGK_FWD_CASE(T, RR, L)                                                                     \
+    if (R == RR && lam == L)                                                                        \
+        return launch_strip_t<T, RR, L>(src, n, ws, (T *)out, wait_cycles, fault_inject, st, max_la, \
+                                        max_lb, rowsA, rowsB, coef_path, shorter_rows);
     if (dtype == SIGK_F64) {
-        switch (lam) {
-            case 0: return launch_strip_t<double, 8, 0>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
-            case 1: return launch_strip_t<double, 8, 1>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
-            case 2: return launch_strip_t<double, 8, 2>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
-            case 3: return launch_strip_t<double, 8, 3>(src, n, ws, (double *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
-        }
+        SIGK_FWD_CASE(double, 8, 0) SIGK_FWD_CASE(double, 8, 1) SIGK_FWD_CASE(double, 8, 2)
+        SIGK_FWD_CASE(double, 8, 3)
     } else {
-        switch (lam) {
-            case 0: return launch_strip_t<float, 16, 0>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
-            case 1: return launch_strip_t<float, 16, 1>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
-            case 2: return launch_strip_t<float, 16, 2>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
-            case 3: return launch_strip_t<float, 16, 3>(src, n, ws, (float *)out, wait_cycles, fault_inject, st, max_la, max_lb, rowsA, rowsB, coef_path);
-        }
+        SIGK_FWD_CASE(float, 16, 0) SIGK_FWD_CASE(float, 16, 1) SIGK_FWD_CASE(float, 16, 2)
+        SIGK_FWD_CASE(float, 16, 3) SIGK_FWD_CASE(float, 8, 0) SIGK_FWD_CASE(float, 8, 1)
+        SIGK_FWD_CASE(float, 8, 2) SIGK_FWD_CASE(float, 4, 0) SIGK_FWD_CASE(float, 4, 1)
     }
+#undef SIGK_FWD_CASE
     return cudaErrorInvalidValue;
 }
 

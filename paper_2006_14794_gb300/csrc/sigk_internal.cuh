@@ -129,11 +129,14 @@ cudaError_t launch_bwd_plain(const PairSrc &src, int64_t n_pairs, int lam, int d
 bool strip_supported(int lam, int64_t d, int dtype);
 // rowsA / rowsB: point rows of the src.A / src.B arrays (an upper bound for
 // packed uneven paths, whose exact count the kernels read from the offsets)
+// R: rows per lane (strip_has_R); shorter_rows: the rows refine the shorter path
+bool strip_has_R(int R, int lam, int dtype);
 int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam, int dtype,
-                              int64_t rowsA, int64_t rowsB, int64_t d);
+                              int64_t rowsA, int64_t rowsB, int64_t d, int R, int shorter_rows);
 cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void *ws, void *out,
                          long long wait_cycles, int fault_inject, cudaStream_t st, int64_t max_la,
-                         int64_t max_lb, int64_t rowsA, int64_t rowsB, int coef_path);
+                         int64_t max_lb, int64_t rowsA, int64_t rowsB, int coef_path, int R,
+                         int shorter_rows);
 
 // Point rows of the src.A and src.B arrays of a call of n_total pairs.
 inline void src_rows(const PairSrc &s, int64_t n_total, int64_t &ra, int64_t &rb) {

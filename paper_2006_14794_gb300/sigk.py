@@ -33,17 +33,20 @@ _int = ctypes.c_int
 
 class SigkOpts(ctypes.Structure):
     _fields_ = [("rec", _int), ("symmetric", _int), ("fault_inject", _int),
-                ("rows_per_lane", _int), ("coef_path", _int), ("reserved", _int * 3)]
+                ("rows_per_lane", _int), ("coef_path", _int), ("orient", _int), ("reserved", _int * 2)]
 
 
 class Schedule(NamedTuple):
     """How a call is scheduled (the fields of sigk_opts that pick the kernels):
-    rec (REC_*), rows_per_lane of the chained kernel (4, 8, 16; 0 = smallest
-    that fits) and the strip path's coefficient kernel (COEF_*).  Every
-    schedule computes the same scheme; they differ in speed only."""
+    rec (REC_*), rows_per_lane (4, 8, 16; 0 = default: the band height of the
+    chained and band kernels, the strip height of the strip path), the strip
+    path's coefficient kernel (COEF_*) and which path its rows refine (orient:
+    0 auto, 1 longer, 2 shorter).  Every schedule computes the same scheme;
+    they differ in speed only."""
     rec: int = REC_AUTO
     rows_per_lane: int = 0
     coef_path: int = COEF_AUTO
+    orient: int = 0
 
 
 _lib = None
@@ -134,6 +137,7 @@ def _opts(rec: int = REC_AUTO, symmetric: bool = False, fault_inject: bool = Fal
         o.rec = int(schedule.rec)
         o.rows_per_lane = int(schedule.rows_per_lane)
         o.coef_path = int(schedule.coef_path)
+        o.orient = int(schedule.orient)
     o.symmetric = 1 if symmetric else 0
     o.fault_inject = 1 if fault_inject else 0
     return o

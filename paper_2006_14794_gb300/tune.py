@@ -51,10 +51,14 @@ def candidates(op: str, dtype: torch.dtype) -> List[Schedule]:
     if op != "pairs_varlen" and dtype == torch.float32:
         c += [Schedule(REC_CHAIN, r, 0) for r in (4, 8, 16)]
         c += [Schedule(REC_BAND, r, 0) for r in (4, 8, 16)]
-    if dtype == torch.float32:
-        c.append(Schedule(REC_STRIP, 0, COEF_TC5))
-        c.append(Schedule(REC_STRIP, 0, COEF_TC))
-    c.append(Schedule(REC_STRIP, 0, COEF_FMA))
+    for orient in (1, 2):   # rows refine the longer / the shorter path
+        if dtype == torch.float32:
+            for r in (16, 8, 4):
+                c.append(Schedule(REC_STRIP, r, COEF_TC5, orient))
+                c.append(Schedule(REC_STRIP, r, COEF_FMA, orient))
+            c.append(Schedule(REC_STRIP, 16, COEF_TC, orient))
+        else:
+            c.append(Schedule(REC_STRIP, 8, COEF_FMA, orient))
     c.append(Schedule(REC_PLAIN, 0, 0))
     return c
 
@@ -81,7 +85,7 @@ def _load() -> Dict[str, list]:
 def _store(key: str, s: Schedule, ms: float) -> None:
     path = cache_path()
     d = _load()
-    d[key] = [int(s.rec), int(s.rows_per_lane), int(s.coef_path), float(ms)]
+    d[key] = [int(s.rec), int(s.rows_per_lane), int(s.coef_path), int(s.orient), float(ms)]
     os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
     tmp = path + ".%d.tmp" % os.getpid()
     with open(tmp, "w") as f:
@@ -181,8 +185,8 @@ def lookup(op: str, *args) -> Schedule:
         s = _mem.get(key)
         if s is None:
             v = _load().get(key)
-            if isinstance(v, list) and len(v) >= 3:
-                s = Schedule(int(v[0]), int(v[1]), int(v[2]))
+            if isinstance(v, list) and len(v) >= 5:
+                s = Schedule(int(v[0]), int(v[1]), int(v[2]), int(v[3]))
                 _mem[key] = s
     if s is not None:
         return s

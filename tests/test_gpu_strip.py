@@ -132,3 +132,33 @@ def test_strip_tcgen05_coefficients_match_oracle(lam, L, M, d):
         outs[coef] = sigk.pairs(to_dev(X32), to_dev(Y32), lam, schedule=s, check_status=True).cpu().numpy()
         assert rel_err(outs[coef], ref) <= 1e-5, coef
     assert rel_err(outs[sigk.COEF_TC5], outs[sigk.COEF_FMA]) <= 2e-6
+
+
+@pytest.mark.parametrize("R,orient,lam", [(4, 1, 1), (4, 2, 0), (8, 1, 2), (8, 2, 1), (16, 2, 3)])
+def test_strip_heights_and_orientations_on_uneven_pairs(R, orient, lam):
+    """128-, 256- and 512-row strips, rows on the longer or the shorter path,
+    on packed pairs of uneven lengths (degenerate ones included)."""
+    sigk = S()
+    rng = np.random.default_rng(45 + R + lam)
+    lens_x = np.concatenate([[1, 2, 300], rng.integers(2, 260, size=60)])
+    lens_y = np.concatenate([[50, 1, 2], rng.integers(2, 260, size=60)])
+    d = 6
+    Xp = np.concatenate([inputs.random_paths(4500 + i, 1, int(n), d)[0] for i, n in enumerate(lens_x)])
+    Yp = np.concatenate([inputs.random_paths(4600 + i, 1, int(n), d)[0] for i, n in enumerate(lens_y)])
+    xo = np.concatenate([[0], np.cumsum(lens_x)]).astype(np.int64)
+    yo = np.concatenate([[0], np.cumsum(lens_y)]).astype(np.int64)
+    X32, X64 = inputs.f32(Xp)
+    Y32, Y64 = inputs.f32(Yp)
+    ref = oracle.pairs_varlen(X64, xo, Y64, yo, lam)
+    s = sigk.Schedule(sigk.REC_STRIP, R, sigk.COEF_FMA, orient)
+    got = sigk.pairs_varlen(to_dev(X32), torch.as_tensor(xo).cuda(), to_dev(Y32), torch.as_tensor(yo).cuda(),
+                            lam, int(max(lens_x.max(), lens_y.max())), schedule=s, check_status=True)
+    assert rel_err(got.cpu().numpy(), ref) <= 1e-5
+
+
+def test_strip_height_without_instance_is_refused():
+    sigk = S()
+    X = to_dev(inputs.random_paths(4700, 2, 600, 4, time_channel=True))
+    with pytest.raises(sigk.SigkError) as ei:   # 4 rows per lane need dyadic order <= 1
+        sigk.pairs(X, X, 2, schedule=sigk.Schedule(sigk.REC_STRIP, 4, 0))
+    assert ei.value.status == sigk.SIGK_EUNSUPPORTED
