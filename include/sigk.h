@@ -102,8 +102,9 @@ typedef struct {
                          warp-level MMAs for larger d, FMA otherwise), 1 FMA
                          contraction, 2 split-TF32 warp-level MMAs (mma.sync),
                          3 split-TF32 tcgen05 MMAs (d <= 64); 2 and 3 are f32
-                         only (f64 gives SIGK_EUNSUPPORTED); other paths
-                         ignore it                                            */
+                         only (f64 gives SIGK_EUNSUPPORTED).  Band form: 3
+                         takes the tcgen05 contraction, anything else the FMA
+                         one.  Other paths ignore it                          */
     int orient;       /* strip path: which path the rows refine.  0 auto (the
                          shorter path from 1024 pairs per call on, else the
                          longer), 1 the longer (more strips per pair: more

@@ -173,7 +173,7 @@ int run_uniform(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opt
                 PairSrc s3 = s2;
                 s3.kbase = s2.kbase + k0;
                 const int64_t m = n_pairs - k0 < nb ? n_pairs - k0 : nb;
-                cudaError_t e = launch_band_f32(s3, bp, m, (float *)out, ws, st);
+                cudaError_t e = launch_band_f32(s3, bp, m, (float *)out, ws, st, coef_of(opts));
                 if (e != cudaSuccess) return cuda_status(e);
             }
             return SIGK_OK;
@@ -267,7 +267,8 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
         const int64_t nbp = band_bwd_batch(o, bp, n_pairs, STRIP_WS_CAP, bytes);
         if (!ws || (int64_t)ws_bytes < bytes) return SIGK_ENOMEM_WS;
         float *dA = (float *)(sw ? dY : dX), *dB = (float *)(sw ? dX : dY);
-        return cuda_status(launch_band_bwd_f32(o, bp, n_pairs, nbp, (const float *)gout, dA, dB, ws, st));
+        return cuda_status(
+            launch_band_bwd_f32(o, bp, n_pairs, nbp, (const float *)gout, dA, dB, ws, st, coef_of(opts)));
     }
     // the symmetric backward exists in the band form only
     if (rec == SIGK_REC_BAND || src.mode == PM_GRAM_SYM) return SIGK_EUNSUPPORTED;

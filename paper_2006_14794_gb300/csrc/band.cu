@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include "sigk_internal.cuh"
+#include "tc5.cuh"
 
 namespace sigk {
 
@@ -378,6 +379,188 @@ cudaError_t launch_coef(const BandCoefArgs &a, int sms, cudaStream_t st) {
     int64_t grid = (int64_t)sms * per_sm;
     if (grid > a.n_pairs) grid = a.n_pairs;
     kern<<<(int)grid, BC_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// The same band on the fifth-generation tensor cores (tcgen05), for d <= 64.
+// A block takes a contiguous run of pairs; per pair, per 128-row tile of the
+// padded rows: the row increments (scaled by 1/2 4^-lambda) are split into
+// TF32 hi and lo parts and staged once, then the padded columns are walked in
+// chunks of 128 (the next chunk's increments fetched while the MMAs run): one
+// thread issues the split-TF32 MMA chain (D = 128 x 128 fp32 in TMEM), the
+// warps copy D into a shared tile, and each warp then writes four slot
+// positions of one lane block, lane (s, g) reading row l*NG + g of the tile
+// along the slot's window (conflict-free with the tile stride 132) and the
+// lanes of a slot storing one 32-byte window row together.  Entries outside
+// the chunk, and the previous pair's cells of slot 0, are left to the chunk or
+// pair that owns them; the pair's tail goes to slot 0 of the next pair.  Waits
+// are bounded (status word SIGK_ETIMEOUT).
+constexpr int BT5_M = 128, BT5_N = 128, BT5_SS = BT5_N + 4, BT5_T = 256;
+
+inline int bt5_smem_bytes(int64_t d) { return 4 * BT5_M * tc5::tc5_k_of(d) * 4 + BT5_M * BT5_SS * 4; }
+
+template <int NG>
+__global__ void __launch_bounds__(BT5_T, 1) band_coef_tc5_kernel(BandCoefArgs a, int *status, long long max_wait) {
+    constexpr int SLOT = NG * NG;
+    constexpr int NPP = 32 * NG;          // padded rows
+    constexpr int SPW = 32 / NG;          // slot positions per warp task (lane = s * NG + g)
+    extern __shared__ __align__(1024) unsigned char bt5_sm[];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tmem_slot;
+    const int64_t d = a.src.d;
+    const int K = tc5::tc5_k_of(d);
+    const int D4 = (int)((d + 3) / 4);
+    unsigned char *ah = bt5_sm, *al = ah + BT5_M * K * 4;
+    unsigned char *bh = al + BT5_M * K * 4, *bl = bh + BT5_N * K * 4;
+    float *St = reinterpret_cast<float *>(bl + BT5_N * K * 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & (BT5_M - 1), half = tid >> 7;
+    const unsigned idesc = tc5::idesc_tf32(BT5_M, BT5_N);
+    const int TperR = a.TperR, NQ = a.NQ;
+
+    if (warp == 0) tc5::alloc(&tmem_slot, BT5_N);
+    if (tid == 0) tc5::mbar_init(&mbar);
+    tc5::fence_before();
+    __syncthreads();
+    tc5::fence_after();
+    const unsigned tmem = tmem_slot;
+    unsigned phase = 0;
+    bool failed = false;
+
+    const int64_t per = (a.n_pairs + gridDim.x - 1) / gridDim.x;
+    const int64_t kbeg = (int64_t)blockIdx.x * per;
+    const int64_t kend = kbeg + per < a.n_pairs ? kbeg + per : a.n_pairs;
+    for (int64_t k = kbeg; k < kend && !failed; ++k) {
+        const PairRef pr = pair_ref(a.src, k);
+        const float *x = (const float *)a.src.A + pr.a_row0 * d;
+        const float *y = (const float *)a.src.B + pr.b_row0 * d;
+        const int nx = (int)pr.la - 1, ny = (int)pr.lb - 1;
+        // slots no chunk writes: pair 0's slot 0 before its own cells, and the
+        // last pair's tail slot after its tail
+        if (k == 0 || k == a.n_pairs - 1) {
+            for (int v = tid; v < 32 * SLOT; v += BT5_T) {
+                const int l = v / SLOT, e = v - l * SLOT, w = e / NG, gp = e - w * NG;
+                const int g = (gp & 1) ? gp / 2 + NG / 2 : gp / 2;   // inverse of band_gpos
+                if (k == 0 && w < g) a.band[(int64_t)l * SLOT + e] = 0.f;
+                if (k == a.n_pairs - 1 && w >= g) a.band[(((k + 1) * TperR) * 32 + l) * (int64_t)SLOT + e] = 0.f;
+            }
+        }
+        for (int P0 = 0; P0 < NPP && !failed; P0 += BT5_M) {
+            float4 nb[8];
+            __syncthreads();
+            {
+                // the tile's row increments (padded rows P: real row P - vrows), once
+                const int p = P0 + row - a.vrows;
+                float4 av[8];
+                const bool ok = P0 + row < NPP && p >= 0 && p < nx;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int k4 = half * (K / 8) + i;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ok && i < K / 8 && k4 < D4) {
+                        const float *r0 = x + (int64_t)p * d + 4 * k4, *r1 = r0 + d;
+                        const int c = 4 * k4;
+                        v.x = c < d ? r1[0] - r0[0] : 0.f;
+                        v.y = c + 1 < d ? r1[1] - r0[1] : 0.f;
+                        v.z = c + 2 < d ? r1[2] - r0[2] : 0.f;
+                        v.w = c + 3 < d ? r1[3] - r0[3] : 0.f;
+                    }
+                    av[i] = v;
+                }
+                tc5::store_half(ah, al, row, half, K, av, a.scale);
+            }
+            auto fetch_cols = [&](int Q0) {
+                const int q = Q0 + row - a.NQV;
+                const bool ok = Q0 < NQ && Q0 + row < NQ && q >= 0 && q < ny;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int k4 = half * (K / 8) + i;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ok && i < K / 8 && k4 < D4) {
+                        const float *r0 = y + (int64_t)q * d + 4 * k4, *r1 = r0 + d;
+                        const int c = 4 * k4;
+                        v.x = c < d ? r1[0] - r0[0] : 0.f;
+                        v.y = c + 1 < d ? r1[1] - r0[1] : 0.f;
+                        v.z = c + 2 < d ? r1[2] - r0[2] : 0.f;
+                        v.w = c + 3 < d ? r1[3] - r0[3] : 0.f;
+                    }
+                    nb[i] = v;
+                }
+            };
+            fetch_cols(0);
+            for (int Q0 = 0; Q0 < NQ; Q0 += BT5_N) {
+                tc5::store_half(bh, bl, row, half, K, nb, 1.f);
+                tc5::fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    tc5::fence_after();
+                    tc5::gemm_split(tmem, ah, al, bh, bl, K, idesc, false);
+                    tc5::commit(&mbar);
+                }
+                fetch_cols(Q0 + BT5_N);
+                const bool ok = tc5::mbar_wait(&mbar, phase, max_wait);
+                if (__syncthreads_or(!ok)) {
+                    failed = true;
+                    if (tid == 0) atomicExch(status, (int)SIGK_ETIMEOUT);
+                    break;
+                }
+                phase ^= 1;
+                tc5::fence_after();
+                {
+                    const int r = (warp & 3) * 32 + lane, cb = (warp >> 2) * 64;
+#pragma unroll
+                    for (int c0 = 0; c0 < 64; c0 += 32) {
+                        float v[32];
+                        tc5::ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(cb + c0), v);
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            *reinterpret_cast<float4 *>(&St[r * BT5_SS + cb + c0 + j]) =
+                                make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    }
+                }
+                tc5::fence_before();
+                __syncthreads();
+                // slots with entries in this chunk: pos in [ceil((Q0 - NG + 1) / NG), (Q0 + 127 + NG - 1) / NG]
+                const int pos_lo = Q0 / NG, pos_hi = min((Q0 + BT5_N - 1 + NG - 1) / NG, TperR);
+                const int l_lo = P0 / NG, l_hi = min(P0 + BT5_M, NPP) / NG;   // lane blocks of this tile
+                const int npos4 = (pos_hi - pos_lo + SPW) / SPW;
+                const int s = lane / NG, g = lane - s * NG;
+                const int gp = band_gpos<NG>(g);
+                for (int t = warp; t < (l_hi - l_lo) * npos4; t += BT5_T / 32) {
+                    const int l = l_lo + t / npos4;
+                    const int pos = pos_lo + (t - (t / npos4) * npos4) * SPW + s;
+                    if (pos > pos_hi) continue;
+                    const int P = l * NG + g;
+                    const float *srow = St + (P - P0) * BT5_SS;
+                    // destination slot: the pair's own, or (the tail) the next pair's slot 0
+                    const bool tail = pos == TperR;
+                    float *dst = a.band + ((tail ? (k + 1) * TperR : k * TperR + pos) * 32 + l) * (int64_t)SLOT + gp;
+#pragma unroll
+                    for (int w = 0; w < NG; ++w) {
+                        const int Q = pos * NG + w - g;
+                        const bool own = tail ? (w < g) : (Q >= 0);
+                        if (own && Q >= Q0 && Q < Q0 + BT5_N) dst[w * NG] = srow[Q - Q0];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (failed) tc5::mbar_wait(&mbar, phase, max_wait);
+    tc5::fence_before();
+    __syncthreads();
+    if (warp == 0) tc5::dealloc(tmem, BT5_N);
+}
+
+template <int NG>
+cudaError_t launch_coef_tc5(const BandCoefArgs &a, int sms, int *status, cudaStream_t st) {
+    const int smem = bt5_smem_bytes(a.src.d);
+    auto kern = band_coef_tc5_kernel<NG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = sms;
+    if (grid > a.n_pairs) grid = a.n_pairs;
+    kern<<<(int)grid, BT5_T, smem, st>>>(a, status, 1LL << 26);
     return cudaGetLastError();
 }
 
@@ -891,17 +1074,40 @@ bool band_geometry(int64_t La, int64_t Lb, int lam, int rows_per_lane, BandPlan 
     return true;
 }
 
+// workspace: a 256-byte header (the status word of bounded waits), then the band
 int64_t band_bytes(const BandPlan &p, int64_t n_pairs) {
-    return (int64_t)sizeof(float) * (n_pairs * p.TperR + 1) * p.slot_floats;
+    return 256 + (int64_t)sizeof(float) * (n_pairs * p.TperR + 1) * p.slot_floats;
 }
 
+namespace {
+// The band coefficients: the FMA contraction, or on request (coef_path 3,
+// d <= 64) the tcgen05 kernel.  The FMA kernel is the default: it runs two
+// blocks per SM and overlaps staging with arithmetic, where the tensor-core
+// kernel's one block per SM serialises staging, MMAs and the scattered band
+// write-back (measured on the 128 x 128 MMD Gram, d = 32: 1.5 vs 4.8 ms).
+cudaError_t launch_band_coef(const BandCoefArgs &c, int NG, int sms, int *status, cudaStream_t st,
+                             int coef_path) {
+    if (coef_path == 3 && c.src.d <= 64) {
+        if (NG == 8) return launch_coef_tc5<8>(c, sms, status, st);
+        if (NG == 4) return launch_coef_tc5<4>(c, sms, status, st);
+        return launch_coef_tc5<2>(c, sms, status, st);
+    }
+    if (NG == 8) return launch_coef<8>(c, sms, st);
+    if (NG == 4) return launch_coef<4>(c, sms, st);
+    return launch_coef<2>(c, sms, st);
+}
+}  // namespace
+
 cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pairs, float *out,
-                            void *ws, cudaStream_t st) {
+                            void *ws, cudaStream_t st, int coef_path) {
     if (n_pairs <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int *status = (int *)ws;
+    float *band = (float *)((unsigned char *)ws + 256);
+    if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess) return e;
     BandCoefArgs c;
     c.src = src;
     c.n_pairs = n_pairs;
@@ -910,11 +1116,8 @@ cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pai
     c.NQV = p.NQV;
     c.vrows = p.vrows;
     c.scale = 0.5f / (float)(1 << (2 * p.lam));
-    c.band = (float *)ws;
-    if (p.NG == 8) e = launch_coef<8>(c, sms, st);
-    else if (p.NG == 4) e = launch_coef<4>(c, sms, st);
-    else e = launch_coef<2>(c, sms, st);
-    if (e != cudaSuccess) return e;
+    c.band = band;
+    if ((e = launch_band_coef(c, p.NG, sms, status, st, coef_path)) != cudaSuccess) return e;
 
     const int per_sm = band_occupancy_of(p.R, p.lam);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -923,7 +1126,7 @@ cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pai
     memset(&a, 0, sizeof(a));
     a.src = src;
     a.out = out;
-    a.band = (const float *)ws;
+    a.band = band;
     a.n_pairs = n_pairs;
     a.ppw = (n_pairs + warps - 1) / warps;
     a.TperR = p.TperR;
@@ -1014,7 +1217,8 @@ int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t
 }
 
 cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t n, int64_t nbp,
-                                const float *gout, float *dA, float *dB, void *ws, cudaStream_t st) {
+                                const float *gout, float *dA, float *dB, void *ws, cudaStream_t st,
+                                int coef_path) {
     if (n <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1031,8 +1235,10 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
     const float scale = 0.5f / (float)(1 << (2 * p.lam));
     const BwdRegions rg = bwd_regions(src0, p, nbp);
     float *w = (float *)ws;
-    float *band = w;
-    float *gbar = band + rg.band;
+    int *status = (int *)ws;
+    float *band = w + 64;   // after the 256-byte status header
+    float *gbar = w + rg.band;
+    if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess) return e;
     float *ckpt = gbar + rg.gbar;
     float *exitk = ckpt + rg.ckpt;
     float *botq = exitk + rg.exitk;
@@ -1066,10 +1272,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         c.vrows = p.vrows;
         c.scale = scale;
         c.band = band;
-        if (p.NG == 8) e = launch_coef<8>(c, sms, st);
-        else if (p.NG == 4) e = launch_coef<4>(c, sms, st);
-        else e = launch_coef<2>(c, sms, st);
-        if (e != cudaSuccess) return e;
+        if ((e = launch_band_coef(c, p.NG, sms, status, st, coef_path)) != cudaSuccess) return e;
         // 2. the forward sweep, keeping what the adjoint needs
         const int64_t warps = (int64_t)sms * per_sm * BAND_WARPS;
         BandArgs f;

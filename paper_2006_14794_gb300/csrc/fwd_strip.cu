@@ -978,25 +978,6 @@ __device__ __forceinline__ void tc5_fetch(float4 (&v)[8], const float4 *src, int
         v[i] = (src && i < K / 8 && k4 < k4n) ? __ldg(src + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
-// ... split into TF32 hi and lo parts and stored into the K-major tiles.
-__device__ __forceinline__ void tc5_store(unsigned char *hi, unsigned char *lo, int r, int h, int K,
-                                          const float4 (&v)[8], float s) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        if (i >= K / 8) break;
-        const int k4 = h * (K / 8) + i;
-        const float e[4] = {v[i].x * s, v[i].y * s, v[i].z * s, v[i].w * s};
-        uint4 hh, ll;
-        hh.x = tc5::tf32(e[0]); ll.x = tc5::tf32(e[0] - __uint_as_float(hh.x));
-        hh.y = tc5::tf32(e[1]); ll.y = tc5::tf32(e[1] - __uint_as_float(hh.y));
-        hh.z = tc5::tf32(e[2]); ll.z = tc5::tf32(e[2] - __uint_as_float(hh.z));
-        hh.w = tc5::tf32(e[3]); ll.w = tc5::tf32(e[3] - __uint_as_float(hh.w));
-        const int off = tc5::cm_off(r, 4 * k4, K);
-        *reinterpret_cast<uint4 *>(hi + off) = hh;
-        *reinterpret_cast<uint4 *>(lo + off) = ll;
-    }
-}
-
 template <int R, int LAM>
 __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const PairPlan *plan, int64_t n_pairs,
                                                            const int64_t *totals, const float *incA,
@@ -1054,14 +1035,14 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
             float4 av[8];
             tc5_fetch(av, (!rows_empty && p >= 0 && p < pp.nx && P0 + row < CP) ? x + (int64_t)p * D4 : nullptr,
                       half, K, D4);
-            tc5_store(ah, al, row, half, K, av, scale);
+            tc5::store_half(ah, al, row, half, K, av, scale);
             const int q = qfirst + row;
             tc5_fetch(nb, (col_ok(qfirst) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr, half, K, D4);
         }
         for (int q0 = qfirst; q0 <= qlast; q0 += TC5_N) {
             const bool zero = !col_ok(q0);
             if (!zero) {
-                tc5_store(bh, bl, row, half, K, nb, 1.f);
+                tc5::store_half(bh, bl, row, half, K, nb, 1.f);
                 tc5::fence_async_smem();
                 __syncthreads();
                 if (tid == 0) {

@@ -104,8 +104,9 @@ struct BandPlan {
 // Geometry only (no device query); false when the band form has no instance.
 bool band_geometry(int64_t La, int64_t Lb, int lam, int rows_per_lane, BandPlan &p);
 int64_t band_bytes(const BandPlan &p, int64_t n_pairs);
+// coef_path 3: coefficients on tcgen05 (d <= 64); otherwise the FMA contraction
 cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pairs, float *out,
-                            void *ws, cudaStream_t st);
+                            void *ws, cudaStream_t st, int coef_path);
 // The band backward (reversible adjoint): pairs per launch (Gram: whole rows)
 // under cap_bytes, with the workspace that needs; then the launches.  src is
 // oriented (rows refine A); dA / dB (either may be null) are overwritten.
@@ -113,7 +114,8 @@ int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t
                        int64_t &bytes);
 int64_t band_bwd_bytes(const PairSrc &src, const BandPlan &p, int64_t nbp);
 cudaError_t launch_band_bwd_f32(const PairSrc &src, const BandPlan &p, int64_t n, int64_t nbp,
-                                const float *gout, float *dA, float *dB, void *ws, cudaStream_t st);
+                                const float *gout, float *dA, float *dB, void *ws, cudaStream_t st,
+                                int coef_path);
 
 cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype, void *out,
                          cudaStream_t st);

@@ -101,22 +101,27 @@ __device__ __forceinline__ void ld32(unsigned addr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Stage one row of 4*k4n elements (given as float4, scaled by s) as hi and lo
-// TF32 parts into the two K-major tiles.
-__device__ __forceinline__ void stage_row(unsigned char *hi, unsigned char *lo, int r, int K, const float4 *src,
-                                          int k4n, float s) {
-    for (int k4 = 0; k4 < K / 4; ++k4) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (src && k4 < k4n) v = src[k4];
-        const float e[4] = {v.x * s, v.y * s, v.z * s, v.w * s};
-        uint4 h, l;
-        h.x = tf32(e[0]); l.x = tf32(e[0] - __uint_as_float(h.x));
-        h.y = tf32(e[1]); l.y = tf32(e[1] - __uint_as_float(h.y));
-        h.z = tf32(e[2]); l.z = tf32(e[2] - __uint_as_float(h.z));
-        h.w = tf32(e[3]); l.w = tf32(e[3] - __uint_as_float(h.w));
+// K of a d-channel operand: 4-channel groups, rounded up to whole k-steps of 8
+__host__ __device__ inline int tc5_k_of(int64_t d) { return (int)(((d + 3) / 4 * 4 + 7) / 8 * 8); }
+
+// Half of an operand row (K/8 float4 groups from k4 = half * K/8), scaled by
+// s, split into TF32 hi and lo parts and stored into the K-major tiles
+// (two threads per row; K <= 64).
+__device__ __forceinline__ void store_half(unsigned char *hi, unsigned char *lo, int r, int half, int K,
+                                           const float4 (&v)[8], float s) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i >= K / 8) break;
+        const int k4 = half * (K / 8) + i;
+        const float e[4] = {v[i].x * s, v[i].y * s, v[i].z * s, v[i].w * s};
+        uint4 hh, ll;
+        hh.x = tf32(e[0]); ll.x = tf32(e[0] - __uint_as_float(hh.x));
+        hh.y = tf32(e[1]); ll.y = tf32(e[1] - __uint_as_float(hh.y));
+        hh.z = tf32(e[2]); ll.z = tf32(e[2] - __uint_as_float(hh.z));
+        hh.w = tf32(e[3]); ll.w = tf32(e[3] - __uint_as_float(hh.w));
         const int off = cm_off(r, 4 * k4, K);
-        *reinterpret_cast<uint4 *>(hi + off) = h;
-        *reinterpret_cast<uint4 *>(lo + off) = l;
+        *reinterpret_cast<uint4 *>(hi + off) = hh;
+        *reinterpret_cast<uint4 *>(lo + off) = ll;
     }
 }
 

@@ -125,8 +125,9 @@ def test_band_schedule_is_f32_and_equal_length_only(libsigk):
     # neither have uneven lengths
     assert libsigk.sigk_pairs_varlen(P, P, P, P, 3, 32, 40, 1, 0, ctypes.byref(o), P, P, 1 << 30, None) == \
         sigk.SIGK_EUNSUPPORTED
-    # the band workspace: (pairs x macro-steps + 1) slot rows of 32 x NG^2 floats.
+    # the band workspace: a 256-byte header, then (pairs x macro-steps + 1)
+    # slot rows of 32 x NG^2 floats.
     # 256-point paths at dyadic order 1: 510 refined rows -> 16 rows per lane,
     # NG = 8 coarse rows per lane, 512 padded columns -> 32 macro-steps per pair
     n = libsigk.sigk_workspace_bytes(sigk.OP_GRAM, 4, 5, 256, 256, 32, 1, 0, ctypes.byref(o))
-    assert n == 4 * (20 * 32 + 1) * 32 * 64
+    assert n == 256 + 4 * (20 * 32 + 1) * 32 * 64

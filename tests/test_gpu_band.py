@@ -198,3 +198,26 @@ def test_symmetric_backward_argument_checks():
     with pytest.raises(sigk.SigkError) as ei:   # different batches
         sigk.gram_backward(torch.ones(3, 4, device="cuda"), X, Y, 1, symmetric=True)
     assert ei.value.status == sigk.SIGK_EINVAL
+
+
+@pytest.mark.parametrize("R,lam,L,M,d", [
+    (16, 1, 256, 256, 32),   # 8 coarse rows per lane: two 128-row tiles
+    (8, 0, 230, 256, 40),    # 8 per lane, d not a multiple of 8
+    (4, 0, 100, 120, 64),    # 4 per lane: one tile
+    (4, 1, 60, 90, 33),      # 2 per lane: half a tile
+])
+def test_band_tcgen05_coefficients_match_oracle(R, lam, L, M, d):
+    """The band's coefficients from split-TF32 tcgen05 MMAs (coef_path 3),
+    forward and backward, against the oracle."""
+    sigk = S()
+    Bx, By = 5, 6
+    X32, X64 = inputs.f32(inputs.random_paths(4800 + R + lam, Bx, L, d, scale=2.0, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(4900 + R + lam, By, M, d, scale=2.0, time_channel=True))
+    s = sigk.Schedule(sigk.REC_BAND, R, sigk.COEF_TC5)
+    got = sigk.gram(to_dev(X32), to_dev(Y32), lam, schedule=s, check_status=True).cpu().numpy()
+    assert rel_err(got, oracle.gram(X64, Y64, lam)) <= F32_TOL
+    gout = np.random.default_rng(48).normal(size=(Bx, By))
+    rX, rY = oracle.gram_grad(X64, Y64, lam, gout)
+    dX, dY = sigk.gram_backward(to_dev(gout), to_dev(X32), to_dev(Y32), lam, schedule=s)
+    assert grad_err(dX.cpu(), rX) <= GRAD_TOL
+    assert grad_err(dY.cpu(), rY) <= GRAD_TOL
