@@ -13,6 +13,11 @@ estimator named in Sec. 3.1.1, written as the usual U-statistic.
 
 Pins (tests/test_oracle_pins.py) tie it to closed forms, brute-force truncated
 signatures, invariants and finite differences.  Every function is pinned.
+
+Every entry point also takes ``scheme`` ("explicit", or "implicit": the
+four-point quadrature of the remark after the scheme in Sec. 3.1) and
+``static_kernel`` ("linear", or "rbf" with bandwidth ``sigma``: the PDE of the
+paths lifted by a static kernel, Sec. 2.2).
 """
 from __future__ import annotations
 
@@ -46,6 +51,21 @@ def lib():
                                              _dp, _dp, _dp]
         L.oracle_sigk_gram_grad.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _i64, ctypes.c_int,
                                             _dp, _dp, _dp]
+        _dbl, _int = ctypes.c_double, ctypes.c_int
+        L.oracle_sigk_pair_ex.restype = _dbl
+        L.oracle_sigk_pair_ex.argtypes = [_dp, _i64, _dp, _i64, _i64, _int, _int, _int, _dbl]
+        L.oracle_sigk_pairs_ex.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _int, _int, _int, _dbl, _dp]
+        L.oracle_sigk_gram_ex.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _i64, _int, _int, _int,
+                                          _dbl, _dp]
+        L.oracle_sigk_pairs_varlen_ex.argtypes = [_dp, _ip, _dp, _ip, _i64, _i64, _int, _int, _int,
+                                                  _dbl, _dp]
+        L.oracle_sigk_pair_grad_ex.restype = _dbl
+        L.oracle_sigk_pair_grad_ex.argtypes = [_dp, _i64, _dp, _i64, _i64, _int, _int, _int, _dbl,
+                                               _dbl, _dp, _dp]
+        L.oracle_sigk_pairs_grad_ex.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _int, _int, _int,
+                                                _dbl, _dp, _dp, _dp]
+        L.oracle_sigk_gram_grad_ex.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _i64, _int, _int,
+                                               _int, _dbl, _dp, _dp, _dp]
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -56,42 +76,73 @@ def _d(a):
     return a, a.ctypes.data_as(_dp)
 
 
+SCHEMES = {"explicit": 0, "implicit": 1}
+STATIC_KERNELS = {"linear": 0, "rbf": 1}
+
+
+def _variant(scheme, static_kernel, sigma):
+    """(scheme code, kernel code, sigma); None for the paper's main variant
+    (explicit scheme, linear kernel), which runs the original entry points."""
+    sc, kc = SCHEMES[scheme], STATIC_KERNELS[static_kernel]
+    if kc == 1 and not sigma > 0:
+        raise ValueError("the RBF kernel needs sigma > 0")
+    if sc == 0 and kc == 0:
+        return None
+    return sc, kc, float(sigma)
+
+
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
 
 
-def sigkernel(x, y, dyadic_order: int) -> float:
+def sigkernel(x, y, dyadic_order: int, scheme="explicit", static_kernel="linear",
+              sigma=1.0) -> float:
     """k_{x,y} on P_lambda for one pair; x: [L,d], y: [M,d]."""
     x, xp = _d(x)
     y, yp = _d(y)
     assert x.ndim == 2 and y.ndim == 2 and x.shape[1] == y.shape[1]
+    v = _variant(scheme, static_kernel, sigma)
+    if v is not None:
+        return float(lib().oracle_sigk_pair_ex(xp, x.shape[0], yp, y.shape[0], x.shape[1],
+                                               int(dyadic_order), *v))
     return float(lib().oracle_sigk_pair(xp, x.shape[0], yp, y.shape[0], x.shape[1],
                                         int(dyadic_order)))
 
 
-def pairs(X, Y, dyadic_order: int):
+def pairs(X, Y, dyadic_order: int, scheme="explicit", static_kernel="linear", sigma=1.0):
     """out[b] = k(X_b, Y_b); X: [B,L,d], Y: [B,M,d]."""
     X, xp = _d(X)
     Y, yp = _d(Y)
     B, L, d = X.shape
     out = np.empty(B)
+    v = _variant(scheme, static_kernel, sigma)
+    if v is not None:
+        lib().oracle_sigk_pairs_ex(xp, yp, B, L, Y.shape[1], d, int(dyadic_order), *v,
+                                   out.ctypes.data_as(_dp))
+        return out
     lib().oracle_sigk_pairs(xp, yp, B, L, Y.shape[1], d, int(dyadic_order),
                             out.ctypes.data_as(_dp))
     return out
 
 
-def gram(X, Y, dyadic_order: int):
+def gram(X, Y, dyadic_order: int, scheme="explicit", static_kernel="linear", sigma=1.0):
     """out[i,j] = k(X_i, Y_j)."""
     X, xp = _d(X)
     Y, yp = _d(Y)
     Bx, L, d = X.shape
     By, M, _ = Y.shape
     out = np.empty((Bx, By))
+    v = _variant(scheme, static_kernel, sigma)
+    if v is not None:
+        lib().oracle_sigk_gram_ex(xp, yp, Bx, By, L, M, d, int(dyadic_order), *v,
+                                  out.ctypes.data_as(_dp))
+        return out
     lib().oracle_sigk_gram(xp, yp, Bx, By, L, M, d, int(dyadic_order), out.ctypes.data_as(_dp))
     return out
 
 
-def pairs_varlen(Xp, x_off, Yp, y_off, dyadic_order: int):
+def pairs_varlen(Xp, x_off, Yp, y_off, dyadic_order: int, scheme="explicit",
+                 static_kernel="linear", sigma=1.0):
     """Pairs of uneven lengths, packed as [sum L, d] with offsets [B+1]."""
     Xp, xp = _d(Xp)
     Yp, yp = _d(Yp)
@@ -99,36 +150,56 @@ def pairs_varlen(Xp, x_off, Yp, y_off, dyadic_order: int):
     yo = np.ascontiguousarray(y_off, dtype=np.int64)
     B = xo.shape[0] - 1
     out = np.empty(B)
+    v = _variant(scheme, static_kernel, sigma)
+    if v is not None:
+        lib().oracle_sigk_pairs_varlen_ex(xp, xo.ctypes.data_as(_ip), yp, yo.ctypes.data_as(_ip),
+                                          B, Xp.shape[1], int(dyadic_order), *v,
+                                          out.ctypes.data_as(_dp))
+        return out
     lib().oracle_sigk_pairs_varlen(xp, xo.ctypes.data_as(_ip), yp, yo.ctypes.data_as(_ip), B,
                                    Xp.shape[1], int(dyadic_order), out.ctypes.data_as(_dp))
     return out
 
 
-def sigkernel_grad(x, y, dyadic_order: int, gout: float = 1.0):
+def sigkernel_grad(x, y, dyadic_order: int, gout: float = 1.0, scheme="explicit",
+                   static_kernel="linear", sigma=1.0):
     """(k, dk/dx, dk/dy) for one pair (reverse-mode of the discrete scheme)."""
     x, xp = _d(x)
     y, yp = _d(y)
     dx = np.zeros_like(x)
     dy = np.zeros_like(y)
+    v = _variant(scheme, static_kernel, sigma)
+    if v is not None:
+        k = lib().oracle_sigk_pair_grad_ex(xp, x.shape[0], yp, y.shape[0], x.shape[1],
+                                           int(dyadic_order), *v, float(gout),
+                                           dx.ctypes.data_as(_dp), dy.ctypes.data_as(_dp))
+        return float(k), dx, dy
     k = lib().oracle_sigk_pair_grad(xp, x.shape[0], yp, y.shape[0], x.shape[1],
                                     int(dyadic_order), float(gout), dx.ctypes.data_as(_dp),
                                     dy.ctypes.data_as(_dp))
     return float(k), dx, dy
 
 
-def pairs_grad(X, Y, dyadic_order: int, gout):
+def pairs_grad(X, Y, dyadic_order: int, gout, scheme="explicit", static_kernel="linear",
+               sigma=1.0):
     X, xp = _d(X)
     Y, yp = _d(Y)
     g, gp = _d(gout)
     dX = np.zeros_like(X)
     dY = np.zeros_like(Y)
     B, L, d = X.shape
+    v = _variant(scheme, static_kernel, sigma)
+    if v is not None:
+        lib().oracle_sigk_pairs_grad_ex(xp, yp, B, L, Y.shape[1], d, int(dyadic_order), *v, gp,
+                                        dX.ctypes.data_as(_dp), dY.ctypes.data_as(_dp))
+        return dX, dY
     lib().oracle_sigk_pairs_grad(xp, yp, B, L, Y.shape[1], d, int(dyadic_order), gp,
                                  dX.ctypes.data_as(_dp), dY.ctypes.data_as(_dp))
     return dX, dY
 
 
-def gram_grad(X, Y, dyadic_order: int, gout, want_dx: bool = True, want_dy: bool = True):
+def gram_grad(X, Y, dyadic_order: int, gout, want_dx: bool = True, want_dy: bool = True,
+              scheme="explicit", static_kernel="linear", sigma=1.0):
     X, xp = _d(X)
     Y, yp = _d(Y)
     g, gp = _d(gout)
@@ -136,6 +207,12 @@ def gram_grad(X, Y, dyadic_order: int, gout, want_dx: bool = True, want_dy: bool
     By, M, _ = Y.shape
     dX = np.zeros_like(X) if want_dx else None
     dY = np.zeros_like(Y) if want_dy else None
+    v = _variant(scheme, static_kernel, sigma)
+    if v is not None:
+        lib().oracle_sigk_gram_grad_ex(xp, yp, Bx, By, L, M, d, int(dyadic_order), *v, gp,
+                                       dX.ctypes.data_as(_dp) if want_dx else None,
+                                       dY.ctypes.data_as(_dp) if want_dy else None)
+        return dX, dY
     lib().oracle_sigk_gram_grad(xp, yp, Bx, By, L, M, d, int(dyadic_order), gp,
                                 dX.ctypes.data_as(_dp) if want_dx else None,
                                 dY.ctypes.data_as(_dp) if want_dy else None)
