@@ -110,8 +110,34 @@ typedef struct {
                          longer), 1 the longer (more strips per pair: more
                          warps on few pairs), 2 the shorter (fewer virtual
                          rows and fill/drain steps per cell)                   */
+    int scheme;       /* sigk_scheme: 0 the explicit scheme (Sec. 3.1), 1 the
+                         implicit four-point scheme of the remark after it   */
+    int static_kernel;/* sigk_static_kernel: 0 linear (the paths as given),
+                         1 RBF lift with bandwidth `sigma` (Sec. 2.2)         */
+    double sigma;     /* RBF bandwidth, > 0 (ignored for the linear kernel)   */
     int reserved[2];  /* must be 0                                            */
 } sigk_opts;          /* a NULL pointer means all-zero (automatic) options    */
+
+/* Finite-difference scheme (Sec. 3.1).
+ *  EXPLICIT: the scheme above.
+ *  IMPLICIT: the remark after it, whose quadrature of the cell integral uses
+ *    all four corners:
+ *      k(i+1,j+1) = k(i+1,j) + k(i,j+1) - k(i,j)
+ *                   + 1/4 <dx, dy> (k(i,j) + k(i+1,j) + k(i,j+1) + k(i+1,j+1)).
+ *    Solved for k(i+1,j+1) it is the explicit update with 1 + <dx,dy>/2
+ *    replaced by (1 + <dx,dy>/4) / (1 - <dx,dy>/4), so every schedule runs
+ *    it; it is undefined where a refined cell has <dx, dy> = 4 (the inputs
+ *    are then far too coarse for either scheme). */
+typedef enum { SIGK_SCHEME_EXPLICIT = 0, SIGK_SCHEME_IMPLICIT = 1 } sigk_scheme;
+
+/* Static kernel on the ambient space (Sec. 2.2).  The paths are lifted into
+ * the kernel's feature space; the lifted PDE's coefficient on coarse cell
+ * (p, q) is the second difference
+ *   kappa(x_{p+1}, y_{q+1}) - kappa(x_p, y_{q+1}) - kappa(x_{p+1}, y_q) + kappa(x_p, y_q),
+ * split over the cell's 4^lambda refined cells as for the linear kernel.
+ *  LINEAR: kappa(a, b) = <a, b>: the coefficient is <dx_p, dy_q>.
+ *  RBF: kappa(a, b) = exp(-|a - b|^2 / (2 sigma^2)). */
+typedef enum { SIGK_KERNEL_LINEAR = 0, SIGK_KERNEL_RBF = 1 } sigk_static_kernel;
 
 typedef enum {
     SIGK_OP_PAIRS = 0, SIGK_OP_GRAM = 1, SIGK_OP_PAIRS_VARLEN = 2,

@@ -19,12 +19,22 @@ bool opts_ok(const sigk_opts *o) {
         return false;
     if (o->coef_path < 0 || o->coef_path > 3) return false;
     if (o->orient < 0 || o->orient > 2) return false;
+    if (o->scheme != SIGK_SCHEME_EXPLICIT && o->scheme != SIGK_SCHEME_IMPLICIT) return false;
+    if (o->static_kernel != SIGK_KERNEL_LINEAR && o->static_kernel != SIGK_KERNEL_RBF) return false;
+    if (o->static_kernel == SIGK_KERNEL_RBF && !(o->sigma > 0.0 && o->sigma < 1e300)) return false;
     for (int i = 0; i < 2; ++i)
         if (o->reserved[i] != 0) return false;
     return true;
 }
 
 int rec_of(const sigk_opts *o) { return o ? o->rec : SIGK_REC_AUTO; }
+
+// The scheme and static kernel a call solves, carried with its pairs.
+void set_variant(PairSrc &s, const sigk_opts *o) {
+    s.scheme = o ? o->scheme : SIGK_SCHEME_EXPLICIT;
+    s.kernel = o ? o->static_kernel : SIGK_KERNEL_LINEAR;
+    s.sigma = o && o->static_kernel == SIGK_KERNEL_RBF ? o->sigma : 1.0;
+}
 
 int common_checks(int64_t B, int64_t L, int64_t M, int64_t d, int lam, int dtype,
                   const sigk_opts *opts) {
@@ -35,6 +45,8 @@ int common_checks(int64_t B, int64_t L, int64_t M, int64_t d, int lam, int dtype
     if (lam > 8) return SIGK_EUNSUPPORTED;
     if (opts && opts->coef_path >= 2 && dtype != SIGK_F32) return SIGK_EUNSUPPORTED;
     if (opts && opts->coef_path == 3 && d > 64) return SIGK_EUNSUPPORTED;
+    // the RBF lift forms its coefficients with its own kernel (no tensor-core path)
+    if (opts && opts->static_kernel == SIGK_KERNEL_RBF && opts->coef_path >= 2) return SIGK_EUNSUPPORTED;
     return SIGK_OK;
 }
 
@@ -109,7 +121,8 @@ Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, 
         if (band && bpo) *bpo = bp;
         if (rec == SIGK_REC_BAND) return band ? P_BAND : P_FILL;
         ChainPlan p;
-        if (chain_plan(n, la, lb, src.d, lam, p, rows_per_lane)) {
+        // the inline-product chain has no RBF lift: the band form forms its coefficients
+        if (src.kernel == SIGK_KERNEL_LINEAR && chain_plan(n, la, lb, src.d, lam, p, rows_per_lane)) {
             if (cp) *cp = p;
             return P_CHAIN;
         }
@@ -188,8 +201,9 @@ int run_uniform(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opt
 
 // The adjoint's path: the strip backward (f32 auto / chain, f64 chain), else
 // the plain one-block-per-pair backward.
-bool bwd_uses_strip(int lam, int64_t d, int dtype, int rec) {
-    if (!strip_supported(lam, d, dtype)) return false;
+bool bwd_uses_strip(int lam, int64_t d, int dtype, int rec, int kernel) {
+    // the RBF lift's chain rule runs in the plain backward only
+    if (kernel != SIGK_KERNEL_LINEAR || !strip_supported(lam, d, dtype)) return false;
     if (rec == SIGK_REC_STRIP) return true;
     return dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN;
 }
@@ -224,6 +238,7 @@ PairSrc band_orient(const PairSrc &src, int64_t n, bool &swapped) {
 
 bool bwd_uses_band(const PairSrc &src, int lam, int dtype, int rec, int rows, BandPlan &bp) {
     if (dtype != SIGK_F32 || rec == SIGK_REC_PLAIN || rec == SIGK_REC_STRIP) return false;
+    if (src.kernel != SIGK_KERNEL_LINEAR) return false;
     if (src.mode != PM_PAIRS && src.mode != PM_GRAM && src.mode != PM_GRAM_SYM) return false;
     const int64_t la = src.La < src.Lb ? src.La : src.Lb, lb = src.La < src.Lb ? src.Lb : src.La;
     return band_geometry(la, lb, lam, rows, bp);
@@ -240,7 +255,8 @@ int64_t backward_ws_bytes(const PairSrc &src, int64_t n, int lam, int dtype, int
         return bytes;
     }
     if (rec == SIGK_REC_BAND || src.mode == PM_GRAM_SYM) return -1;
-    if (bwd_uses_strip(lam, src.d, dtype, rec)) {
+    if (src.kernel != SIGK_KERNEL_LINEAR && rec == SIGK_REC_STRIP) return -1;
+    if (bwd_uses_strip(lam, src.d, dtype, rec, src.kernel)) {
         int64_t nb, need;
         bwd_strip_batch(src, n, lam, dtype, nb, need);
         return need;
@@ -270,9 +286,11 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
         return cuda_status(
             launch_band_bwd_f32(o, bp, n_pairs, nbp, (const float *)gout, dA, dB, ws, st, coef_of(opts)));
     }
-    // the symmetric backward exists in the band form only
+    // the symmetric backward exists in the band form only, the RBF lift's in
+    // the plain backward only
     if (rec == SIGK_REC_BAND || src.mode == PM_GRAM_SYM) return SIGK_EUNSUPPORTED;
-    if (bwd_uses_strip(lam, src.d, dtype, rec)) {
+    if (src.kernel != SIGK_KERNEL_LINEAR && rec == SIGK_REC_STRIP) return SIGK_EUNSUPPORTED;
+    if (bwd_uses_strip(lam, src.d, dtype, rec, src.kernel)) {
         int64_t nb, need, ra, rb;
         bwd_strip_batch(src, n_pairs, lam, dtype, nb, need);
         src_rows(src, n_pairs, ra, rb);
@@ -327,6 +345,7 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
     if (op == SIGK_OP_PAIRS_BACKWARD || op == SIGK_OP_GRAM_BACKWARD) {
         PairSrc bs;
         memset(&bs, 0, sizeof(bs));
+        set_variant(bs, opts);
         bs.mode = op == SIGK_OP_PAIRS_BACKWARD ? PM_PAIRS : PM_GRAM;
         bs.La = L; bs.Lb = M; bs.d = d;
         bs.nb = By;
@@ -354,6 +373,7 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
     }
     PairSrc src;
     memset(&src, 0, sizeof(src));
+    set_variant(src, opts);
     src.d = d;
     if (op == SIGK_OP_PAIRS) {
         src.mode = PM_PAIRS;
@@ -390,6 +410,7 @@ int sigk_pairs(const void *X, const void *Y, int64_t B, int64_t L, int64_t M, in
     if (!X || !Y || !out) return SIGK_EINVAL;
     PairSrc src;
     memset(&src, 0, sizeof(src));
+    set_variant(src, opts);
     src.mode = PM_PAIRS;
     src.A = X; src.B = Y;
     src.La = L; src.Lb = M; src.d = d;
@@ -408,6 +429,7 @@ int sigk_gram(const void *X, const void *Y, int64_t Bx, int64_t By, int64_t L, i
     if (!X || !Y || !out) return SIGK_EINVAL;
     PairSrc src;
     memset(&src, 0, sizeof(src));
+    set_variant(src, opts);
     src.d = d;
     if (sym) {
         src.mode = PM_GRAM_SYM;
@@ -445,6 +467,7 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, cons
     if (!Xp || !Yp || !x_off || !y_off || !out) return SIGK_EINVAL;
     PairSrc src;
     memset(&src, 0, sizeof(src));
+    set_variant(src, opts);
     src.mode = PM_VARLEN;
     src.A = Xp; src.B = Yp;
     src.a_off = x_off; src.b_off = y_off;
@@ -473,6 +496,7 @@ int sigk_pairs_backward(const void *grad_out, const void *X, const void *Y, int6
     if (!grad_out || !X || !Y) return SIGK_EINVAL;
     PairSrc src;
     memset(&src, 0, sizeof(src));
+    set_variant(src, opts);
     src.mode = PM_PAIRS;
     src.A = X; src.B = Y;
     src.La = L; src.Lb = M; src.d = d;
@@ -498,6 +522,7 @@ int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64
     if (!grad_out || !X || !Y) return SIGK_EINVAL;
     PairSrc src;
     memset(&src, 0, sizeof(src));
+    set_variant(src, opts);
     src.mode = PM_GRAM;
     src.A = X; src.B = Y;
     src.La = L; src.Lb = M; src.d = d;

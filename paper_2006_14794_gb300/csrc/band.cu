@@ -20,6 +20,7 @@
 // (k + 1, 0).  Virtual rows and columns (padding, as in fwd_chain.cu) hold 0.
 #include <string.h>
 
+#include "rbf.cuh"
 #include "sigk_internal.cuh"
 #include "tc5.cuh"
 
@@ -157,6 +158,10 @@ __global__ void __launch_bounds__(BC_THREADS, 2) band_coef_kernel(BandCoefArgs a
                 }
             }
             if (u >= nslots) continue;
+#pragma unroll
+            for (int w = 0; w < NG; ++w)
+#pragma unroll
+                for (int g = 0; g < NG; ++g) acc[w][g] = scheme_coef(acc[w][g] * a.scale, a.src.scheme);
             if (pos < a.TperR && pos > 0) {
                 float4 *dst = reinterpret_cast<float4 *>(a.band + (((k * a.TperR + pos) * 32) + l) * SLOT);
                 if constexpr (NG >= 4) {
@@ -164,12 +169,10 @@ __global__ void __launch_bounds__(BC_THREADS, 2) band_coef_kernel(BandCoefArgs a
                     for (int w = 0; w < NG; ++w)
 #pragma unroll
                         for (int h = 0; h < NG / 4; ++h)
-                            dst[w * (NG / 4) + h] = make_float4(
-                                acc[w][2 * h] * a.scale, acc[w][2 * h + NG / 2] * a.scale,
-                                acc[w][2 * h + 1] * a.scale, acc[w][2 * h + 1 + NG / 2] * a.scale);
+                            dst[w * (NG / 4) + h] = make_float4(acc[w][2 * h], acc[w][2 * h + NG / 2],
+                                                                acc[w][2 * h + 1], acc[w][2 * h + 1 + NG / 2]);
                 } else {
-                    dst[0] = make_float4(acc[0][0] * a.scale, acc[0][1] * a.scale, acc[1][0] * a.scale,
-                                         acc[1][1] * a.scale);
+                    dst[0] = make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]);
                 }
             } else if (pos == 0) {
                 // the pair's own cells (w >= g); the cells w < g belong to the
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(BC_THREADS, 2) band_coef_kernel(BandCoefArgs a
                 for (int w = 0; w < NG; ++w)
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        if (w >= g) dst[w * NG + band_gpos<NG>(g)] = acc[w][g] * a.scale;
+                        if (w >= g) dst[w * NG + band_gpos<NG>(g)] = acc[w][g];
                         else if (k == 0) dst[w * NG + band_gpos<NG>(g)] = 0.f;
                     }
             } else {
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(BC_THREADS, 2) band_coef_kernel(BandCoefArgs a
                 for (int w = 0; w < NG; ++w)
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        if (w < g) dst[w * NG + band_gpos<NG>(g)] = acc[w][g] * a.scale;
+                        if (w < g) dst[w * NG + band_gpos<NG>(g)] = acc[w][g];
                         else if (k == a.n_pairs - 1) dst[w * NG + band_gpos<NG>(g)] = 0.f;
                     }
             }
@@ -515,7 +518,8 @@ __global__ void __launch_bounds__(BT5_T, 1) band_coef_tc5_kernel(BandCoefArgs a,
 #pragma unroll
                         for (int j = 0; j < 32; j += 4)
                             *reinterpret_cast<float4 *>(&St[r * BT5_SS + cb + c0 + j]) =
-                                make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                                make_float4(scheme_coef(v[j], a.src.scheme), scheme_coef(v[j + 1], a.src.scheme),
+                                            scheme_coef(v[j + 2], a.src.scheme), scheme_coef(v[j + 3], a.src.scheme));
                     }
                 }
                 tc5::fence_before();
@@ -884,7 +888,9 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, 6) chain_band_adj_kernel(Band
             const int Q0 = pos * NG + w;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
-                const float v = g < NH ? gN[g].x : gN[g - NH].y;
+                float v = g < NH ? gN[g].x : gN[g - NH].y;
+                if (a.src.scheme != SIGK_SCHEME_EXPLICIT)   // dk/dc' -> dk/dc of the cell's coefficient
+                    v *= scheme_dcoef(g < NH ? CN[g].x : CN[g - NH].y, a.src.scheme);
                 const int Q = Q0 - g;
                 const bool ok = g >= gmin && (Q >= 0 ? (cur_ok && Q >= a.NQV) : prev_ok);
                 float *dst = a.gbar + (Q >= 0 ? row_cur : row_prev) + (int64_t)g * a.g_ld + Q;
@@ -1085,8 +1091,53 @@ namespace {
 // blocks per SM and overlaps staging with arithmetic, where the tensor-core
 // kernel's one block per SM serialises staging, MMAs and the scattered band
 // write-back (measured on the 128 x 128 MMD Gram, d = 32: 1.5 vs 4.8 ms).
+// Band layout of the RBF-lifted coefficients (rbf.cuh): coarse cell (p, q) of
+// pair k is the padded cell (P, Q) = (p + vrows, q + NQV), read by lane P / NG
+// as group g = P % NG at the position pos and window w with pos NG + w = Q + g;
+// pos = TperR is the pair's tail, in slot 0 of pair k + 1.
+struct BandRbfLayout {
+    PairSrc src;
+    float *band;
+    int TperR, NQV, vrows, NG;
+    struct Geo {
+        const float *rows, *cols;
+        int nx, ny;
+        int64_t k;
+    };
+    __device__ Geo geo(int64_t k) const {
+        const PairRef pr = pair_ref(src, k);
+        Geo g;
+        g.rows = (const float *)src.A + pr.a_row0 * src.d;
+        g.cols = (const float *)src.B + pr.b_row0 * src.d;
+        g.nx = (int)pr.la - 1;
+        g.ny = (int)pr.lb - 1;
+        g.k = k;
+        return g;
+    }
+    __device__ void store(const Geo &g, int p, int q, float c) const {
+        const int P = p + vrows, Q = q + NQV;
+        const int l = P / NG, gr = P - l * NG;
+        const int t = Q + gr, pos = t / NG, w = t - pos * NG;
+        const int64_t slot = pos < TperR ? g.k * TperR + pos : (g.k + 1) * TperR;
+        const int gp = gr < NG / 2 ? 2 * gr : 2 * (gr - NG / 2) + 1;   // band_gpos
+        band[(slot * 32 + l) * (int64_t)(NG * NG) + w * NG + gp] = c;
+    }
+};
+
 cudaError_t launch_band_coef(const BandCoefArgs &c, int NG, int sms, int *status, cudaStream_t st,
                              int coef_path) {
+    if (c.src.kernel == SIGK_KERNEL_RBF) {
+        BandRbfLayout lay;
+        lay.src = c.src;
+        lay.band = c.band;
+        lay.TperR = c.TperR;
+        lay.NQV = c.NQV;
+        lay.vrows = c.vrows;
+        lay.NG = NG;
+        const size_t bytes = sizeof(float) * (size_t)(c.n_pairs * c.TperR + 1) * 32 * NG * NG;
+        return launch_rbf_coef<float>(lay, c.n_pairs, c.src.La - 1, c.src.Lb - 1, c.src.d, c.src.sigma,
+                                      (double)c.scale, c.src.scheme, c.band, bytes, sms, st);
+    }
     if (coef_path == 3 && c.src.d <= 64) {
         if (NG == 8) return launch_coef_tc5<8>(c, sms, status, st);
         if (NG == 4) return launch_coef_tc5<4>(c, sms, status, st);

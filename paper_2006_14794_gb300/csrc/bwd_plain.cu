@@ -52,6 +52,8 @@ __global__ void __launch_bounds__(BWD_THREADS) bwd_plain_kernel(BwdArgs a) {
     T *sm = reinterpret_cast<T *>(smraw);
     const T scale = (T)0.5 / (T)(1LL << (2 * a.lam));
     const int lam = a.lam;
+    const bool rbf = a.src.kernel == SIGK_KERNEL_RBF;
+    const T rbf_s = (T)(0.5 / (a.src.sigma * a.src.sigma));
     const int64_t d = a.src.d;
     unsigned char *slot = a.ws + (int64_t)blockIdx.x * a.slot_bytes;
     for (int64_t k = blockIdx.x; k < a.n_pairs; k += gridDim.x) {
@@ -75,12 +77,22 @@ __global__ void __launch_bounds__(BWD_THREADS) bwd_plain_kernel(BwdArgs a) {
         T *Gb = Gm + nx * ny;
         T *Kg = Gb + nx * ny;
 
-        // 1. increment Gram, Gbar = 0
+        // 1. increment Gram (or the RBF lift's second differences), Gbar = 0
         for (int64_t idx = threadIdx.x; idx < nx * ny; idx += blockDim.x) {
             const int64_t p = idx / ny, q = idx - (idx / ny) * ny;
             T g = 0;
-            for (int64_t c = 0; c < d; ++c) g += inc(x, p, d, c) * inc(y, q, d, c);
-            Gm[idx] = g * scale;
+            if (rbf) {
+                T uu = 0, ux = 0, uy = 0, xy = 0, snx = 0, sny = 0;
+                for (int64_t c = 0; c < d; ++c) {
+                    const T u = x[p * d + c] - y[q * d + c], dxv = inc(x, p, d, c), dyv = inc(y, q, d, c);
+                    uu += u * u; ux += u * dxv; uy += u * dyv; xy += dxv * dyv;
+                    snx += dxv * dxv; sny += dyv * dyv;
+                }
+                g = rbf_second_difference(uu, ux, uy, xy, snx, sny, rbf_s);
+            } else {
+                for (int64_t c = 0; c < d; ++c) g += inc(x, p, d, c) * inc(y, q, d, c);
+            }
+            Gm[idx] = scheme_coef(g * scale, a.src.scheme);
             Gb[idx] = 0;
         }
         __syncthreads();
@@ -184,9 +196,61 @@ __global__ void __launch_bounds__(BWD_THREADS) bwd_plain_kernel(BwdArgs a) {
             }
         }
 #undef COEF
+        if (a.src.scheme != SIGK_SCHEME_EXPLICIT) {
+            // the sweeps used c' = scheme_coef(c): Gbar holds dk/dc', turn it into
+            // dk/dc (the adjoint's last diagonal ended with a barrier)
+            for (int64_t idx = threadIdx.x; idx < nx * ny; idx += blockDim.x)
+                Gb[idx] *= scheme_dcoef(Gm[idx], a.src.scheme);
+            __syncthreads();
+        }
+
+        const T f = gk * scale;
+        if (rbf) {
+            // 4'. chain rule through the second difference of kappa: the point
+            // pair (i, j) enters G(p, q) for p in {i-1, i}, q in {j-1, j} with
+            // weight W(i,j) = Gb(i-1,j-1) - Gb(i,j-1) - Gb(i-1,j) + Gb(i,j)
+            // (terms outside the grid 0), and d kappa(a,b)/da = kappa (b - a) /
+            // sigma^2 = -d kappa/db.  Z(i,j) = f W(i,j) kappa(x_i, y_j) / sigma^2
+            // goes where the K grid was (no longer needed); then
+            // dk/dx_i = sum_j Z(i,j) (y_j - x_i), dk/dy_j = sum_i Z(i,j) (x_i - y_j).
+            T *Z = Kg;
+            const int64_t la1 = nx + 1, lb1 = ny + 1;
+            for (int64_t idx = threadIdx.x; idx < la1 * lb1; idx += blockDim.x) {
+                const int64_t i = idx / lb1, j = idx - (idx / lb1) * lb1;
+                T w = 0;
+                if (i >= 1 && j >= 1) w += Gb[(i - 1) * ny + j - 1];
+                if (i < nx && j >= 1) w -= Gb[i * ny + j - 1];
+                if (i >= 1 && j < ny) w -= Gb[(i - 1) * ny + j];
+                if (i < nx && j < ny) w += Gb[i * ny + j];
+                T dd = 0;
+                for (int64_t c = 0; c < d; ++c) {
+                    const T u = x[i * d + c] - y[j * d + c];
+                    dd += u * u;
+                }
+                Z[idx] = f * w * exp(-rbf_s * dd) * (2 * rbf_s);
+            }
+            __syncthreads();
+            if (dx) {
+                for (int64_t idx = threadIdx.x; idx < la1 * d; idx += blockDim.x) {
+                    const int64_t i = idx / d, c = idx - (idx / d) * d;
+                    T sacc = 0;
+                    for (int64_t j = 0; j < lb1; ++j) sacc += Z[i * lb1 + j] * (y[j * d + c] - x[i * d + c]);
+                    atomic_add(&dx[i * d + c], sacc);
+                }
+            }
+            if (dy) {
+                for (int64_t idx = threadIdx.x; idx < lb1 * d; idx += blockDim.x) {
+                    const int64_t j = idx / d, c = idx - (idx / d) * d;
+                    T sacc = 0;
+                    for (int64_t i = 0; i < la1; ++i) sacc += Z[i * lb1 + j] * (x[i * d + c] - y[j * d + c]);
+                    atomic_add(&dy[j * d + c], sacc);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
 
         // 4. chain rule through G(p,q) = <dx_p, dy_q>, into the points
-        const T f = gk * scale;
         if (dx) {
             for (int64_t idx = threadIdx.x; idx < nx * d; idx += blockDim.x) {
                 const int64_t p = idx / d, c = idx - (idx / d) * d;

@@ -116,7 +116,10 @@ __device__ __forceinline__ float dot_inc(const float4 (&dx)[D4], const float4 (&
 // MINB: CTAs per SM the register allocation must allow (6 two-warp CTAs =
 // 12 warps at <= 168 registers measured fastest for the 256x256 Gram; 1 where
 // that cap would spill).
-template <int R, int LAM, int D4, int MINB>
+// IMPL: the implicit scheme's coefficient map (scheme_coef) on every coarse
+// cell, a compile-time choice so that the explicit scheme's loop carries none
+// of it.
+template <int R, int LAM, int D4, int MINB, bool IMPL>
 __global__ void __launch_bounds__(CHAIN_WARPS * 32, MINB) chain_f32_kernel(ChainArgs a) {
     constexpr int S = 1 << LAM;
     constexpr int NG = R / S;        // coarse rows (groups) per lane = windows per macro-step
@@ -207,7 +210,8 @@ __global__ void __launch_bounds__(CHAIN_WARPS * 32, MINB) chain_f32_kernel(Chain
             for (int g = 0; g < NH; ++g) CO[g] = CN[g];
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
-                const float c = dot_inc<D4>(dxr[g], yv[g]);
+                float c = dot_inc<D4>(dxr[g], yv[g]);
+                if constexpr (IMPL) c = scheme_coef(c, SIGK_SCHEME_IMPLICIT);
                 if (g < NH) CN[g].x = c; else CN[g - NH].y = c;
             }
             // ---- the window's S steps
@@ -266,7 +270,8 @@ __global__ void __launch_bounds__(CHAIN_WARPS * 32, MINB) chain_f32_kernel(Chain
 
 template <int R, int LAM, int D4, int MINB>
 cudaError_t launch_one(const ChainArgs &args, const ChainPlan &p, cudaStream_t st) {
-    auto kern = chain_f32_kernel<R, LAM, D4, MINB>;
+    auto kern = args.src.scheme == SIGK_SCHEME_IMPLICIT ? chain_f32_kernel<R, LAM, D4, MINB, true>
+                                                        : chain_f32_kernel<R, LAM, D4, MINB, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          p.smem_bytes);
     if (e != cudaSuccess) return e;
@@ -277,7 +282,7 @@ cudaError_t launch_one(const ChainArgs &args, const ChainPlan &p, cudaStream_t s
 template <int R, int LAM, int D4, int MINB>
 int occupancy(int smem) {
     int nb = 0;
-    auto kern = chain_f32_kernel<R, LAM, D4, MINB>;
+    auto kern = chain_f32_kernel<R, LAM, D4, MINB, false>;   // the implicit instance has the same resources
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, CHAIN_WARPS * 32, smem) != cudaSuccess)

@@ -18,11 +18,21 @@ namespace {
 
 constexpr int PLAIN_THREADS = 512;
 
+// The coarse cell's coefficient: <dx_p, dy_q>, or with the RBF lift (Sec. 2.2)
+// the second difference of kappa over the cell's corners (rbf_s = 1/(2 sigma^2)).
 template <typename T>
 __device__ __forceinline__ T coef(const T *x, const T *y, int64_t d, int64_t p, int64_t q,
-                                  T scale) {
+                                  T scale, int kernel, T rbf_s) {
     const T *x0 = x + p * d, *x1 = x0 + d;
     const T *y0 = y + q * d, *y1 = y0 + d;
+    if (kernel == SIGK_KERNEL_RBF) {
+        T uu = 0, ux = 0, uy = 0, xy = 0, nx = 0, ny = 0;
+        for (int64_t c = 0; c < d; ++c) {
+            const T u = x0[c] - y0[c], dx = x1[c] - x0[c], dy = y1[c] - y0[c];
+            uu += u * u; ux += u * dx; uy += u * dy; xy += dx * dy; nx += dx * dx; ny += dy * dy;
+        }
+        return rbf_second_difference(uu, ux, uy, xy, nx, ny, rbf_s) * scale;
+    }
     T g = 0;
     for (int64_t c = 0; c < d; ++c) g += (x1[c] - x0[c]) * (y1[c] - y0[c]);
     return g * scale;
@@ -36,6 +46,7 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_kernel(PairSrc src, int64
     extern __shared__ unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);
     const T scale = (T)0.5 / (T)(1LL << (2 * lam));
+    const T rbf_s = (T)(0.5 / (src.sigma * src.sigma));
     for (int64_t k = blockIdx.x; k < n_pairs; k += gridDim.x) {
         const PairRef pr = pair_ref(src, k);
         if (pr.la < 2 || pr.lb < 2) {
@@ -83,7 +94,9 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_kernel(PairSrc src, int64
                     // D0 = diag n-1, D1 = diag n-2, D2 = new diag n
                     T v = (T)1;
                     if (a > 0 && b > 0) {
-                        const T c = coef(x, y, src.d, (a - 1) >> lam, (b - 1) >> lam, scale);
+                        const T c = scheme_coef(coef(x, y, src.d, (a - 1) >> lam, (b - 1) >> lam, scale,
+                                                     src.kernel, rbf_s),
+                                                src.scheme);
                         const T kl = D0[a], ku = D0[a - 1], kd = D1[a - 1];
                         v = kl + ku - kd + c * (kl + ku);
                     }
@@ -92,7 +105,9 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_kernel(PairSrc src, int64
                     // D0 = K(n-1), D1 = Q(n-1), D2 = K(n), D3 = Q(n)
                     T kv = (T)1, qv = (T)0;
                     if (a > 0 && b > 0) {
-                        const T c = coef(x, y, src.d, (a - 1) >> lam, (b - 1) >> lam, scale);
+                        const T c = scheme_coef(coef(x, y, src.d, (a - 1) >> lam, (b - 1) >> lam, scale,
+                                                     src.kernel, rbf_s),
+                                                src.scheme);
                         const T kl = D0[a], ku = D0[a - 1], qu = D1[a - 1];
                         qv = qu + c * (kl + ku);
                         kv = kl + qv;

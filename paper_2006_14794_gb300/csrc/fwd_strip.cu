@@ -25,6 +25,7 @@
 // (its result is then meaningless and the call reports the timeout).
 #include <string.h>
 
+#include "rbf.cuh"
 #include "sigk_internal.cuh"
 #include "tc5.cuh"
 
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(256) coef_kernel(PairSrc src, const PairPlan *
                         if (P >= CP) continue;
                         const int p = prow0 + P, q = W - P;
                         const bool ok = p >= 0 && p < pp.nx && q >= 0 && q < pp.ny;
-                        blk[(int64_t)W * CP + P] = ok ? acc[i][j] * scale : (T)0;
+                        blk[(int64_t)W * CP + P] = ok ? scheme_coef(acc[i][j] * scale, src.scheme) : (T)0;
                     }
                 }
             }
@@ -502,6 +503,7 @@ struct AdjArgs {
     int *status;
     T *gbar;         // dense dk/dG (unscaled), [nx][ny] per pair
     long long wait_cycles;
+    int scheme;      // sigk_scheme of the forward (scheme_dcoef)
 };
 
 constexpr int NSR = 8;   // slots of the per-cell sums ring (adjoint)
@@ -683,7 +685,8 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
             for (int g = 0; g < NG; ++g) {
                 const int p = prow0 + NG * lane + g, q = w - NG * lane - g;
                 if (p >= 0 && p < pp.nx && q >= 0 && q < pp.ny)
-                    a.gbar[pp.g_off + (int64_t)p * pp.ny + q] = gN[g];
+                    a.gbar[pp.g_off + (int64_t)p * pp.ny + q] =
+                        a.scheme != SIGK_SCHEME_EXPLICIT ? gN[g] * scheme_dcoef(cn[g], a.scheme) : gN[g];
                 gN[g] = gO[g];
                 gO[g] = 0;
             }
@@ -947,7 +950,8 @@ __global__ void __launch_bounds__(256) coef_tc_kernel(PairSrc src, const PairPla
                     const int Pl = u % 64, Wl = u / 64;
                     const int W = W0 + Wl, P = P0 + Pl;
                     const int col = (64 * hw + Wl - Pl + 63) & 127;   // ring column
-                    if (W < pp.nw && P < CP) blk[(int64_t)W * CP + P] = cs[Pl * TC_CS + col] * scale;
+                    if (W < pp.nw && P < CP)
+                        blk[(int64_t)W * CP + P] = scheme_coef(cs[Pl * TC_CS + col] * scale, src.scheme);
                 }
             }
         }
@@ -1073,7 +1077,7 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
                     float v[32];
                     tc5::ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(cb + c0), v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) St[r * TC5_SS + cb + c0 + j] = v[j];
+                    for (int j = 0; j < 32; ++j) St[r * TC5_SS + cb + c0 + j] = scheme_coef(v[j], src.scheme);
                 }
                 tc5::fence_before();
             }
@@ -1209,11 +1213,54 @@ int64_t strip_workspace_bytes(int64_t n, int64_t max_la, int64_t max_lb, int lam
 // the FMA contraction otherwise (f64, or too few channels: at d = 16 the FMA
 // kernel measured faster, 2.9 vs 3.2 ms on 4096 uneven pairs; at d = 64 the
 // MMAs win, 10.1 vs 13.0 ms on 64 pairs of 4096 points).
+// Strip layout of the RBF-lifted coefficients (rbf.cuh): coarse cell (p, q)
+// is row P of strip s (p + pad / 2^lambda = s CP + P) on diagonal W = P + q.
+template <typename T, int R, int LAM>
+struct StripRbfLayout {
+    PairSrc src;
+    const PairPlan *plan;
+    T *cbuf;
+    struct Geo {
+        const T *rows, *cols;
+        int nx, ny, padc, nw;
+        int64_t c_off;
+    };
+    __device__ Geo geo(int64_t k) const {
+        const PairPlan &pp = plan[k];
+        Geo g;
+        // a_row0 / b_row0 are offsets into the row / column path's own array
+        g.rows = (const T *)(pp.swap ? src.B : src.A) + pp.a_row0 * src.d;
+        g.cols = (const T *)(pp.swap ? src.A : src.B) + pp.b_row0 * src.d;
+        g.nx = pp.nx;
+        g.ny = pp.ny;
+        g.padc = pp.pad >> LAM;
+        g.nw = pp.nw;
+        g.c_off = pp.c_off;
+        return g;
+    }
+    __device__ void store(const Geo &g, int p, int q, T c) const {
+        constexpr int CP = 32 * (R >> LAM);
+        const int Pa = p + g.padc, s = Pa / CP, P = Pa - s * CP;
+        cbuf[g.c_off + ((int64_t)s * g.nw + P + q) * CP + P] = c;
+    }
+};
+
 template <typename T, int R, int LAM>
 static cudaError_t launch_coef(const PairSrc &src, const PairPlan *plan, int64_t n,
                                const int64_t *totals, const T *incA, const T *incB, T *cbuf,
-                               int sms, cudaStream_t st, int coef_path, int *status) {
+                               int sms, cudaStream_t st, int coef_path, int *status, int64_t max_len,
+                               int64_t coef_bytes) {
     cudaError_t e;
+    if (src.kernel == SIGK_KERNEL_RBF) {
+        // the lifted coefficient needs the points, not the increments
+        StripRbfLayout<T, R, LAM> lay;
+        lay.src = src;
+        lay.plan = plan;
+        lay.cbuf = cbuf;
+        return launch_rbf_coef<T>(lay, n, max_len - 1, max_len - 1, src.d, src.sigma,
+                                  0.5 / (double)(1LL << (2 * LAM)), src.scheme, cbuf, (size_t)coef_bytes,
+                                  sms, st);
+    }
     // tcgen05 for f32 with 32 <= d <= 64 (or on request, d <= 64); mma.sync
     // split-TF32 on request (or d > 64); FMA otherwise
     const bool tc5 = sizeof(T) == 4 && src.d <= 64 &&
@@ -1287,8 +1334,8 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, cbuf, sms, st, coef_path, status)) !=
-        cudaSuccess)
+    if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, cbuf, sms, st, coef_path, status,
+                                    max_la > max_lb ? max_la : max_lb, L.bnd - L.coef)) != cudaSuccess)
         return e;
     StripArgs<T> a;
     a.src = src;
@@ -1352,8 +1399,8 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if ((e = launch_coef<T, R, LAM>(src, plan, n, totals, incA, incB, (T *)(w + L.coef), sms, st,
-                                    coef_path, status)) !=
-        cudaSuccess)
+                                    coef_path, status, max_la > max_lb ? max_la : max_lb,
+                                    L.bnd - L.coef)) != cudaSuccess)
         return e;
     {
         StripArgs<T> a;
@@ -1390,6 +1437,7 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         a.status = status;
         a.gbar = (T *)(w + L.gbar);
         a.wait_cycles = wait_cycles;
+        a.scheme = src.scheme;
         auto ak = strip_adj_kernel<T, R, LAM>;
         const int asmem = STRIP_WARPS * adj_warp_elems<T, R, LAM>() * (int)sizeof(T);
         if ((e = cudaFuncSetAttribute(ak, cudaFuncAttributeMaxDynamicSharedMemorySize, asmem)) != cudaSuccess)

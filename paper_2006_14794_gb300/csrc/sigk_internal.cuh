@@ -24,7 +24,53 @@ struct PairSrc {
     int64_t d;
     int64_t out_si, out_sj; // gram: out index = i*out_si + j*out_sj
     int64_t kbase;          // pair k of a launch is pair kbase + k of the call
+    int scheme;             // sigk_scheme: how a cell's coefficient enters (scheme_coef)
+    int kernel;             // sigk_static_kernel
+    double sigma;           // RBF bandwidth
 };
+
+// The implicit scheme (Sec. 3.1, remark after the explicit scheme) solved for
+// its unknown corner is k(a,b) = (k(a,b-1) + k(a-1,b)) (1 + g/4)/(1 - g/4) -
+// k(a-1,b-1): the explicit update with the coefficient c = g/2 of the
+// difference form replaced by c / (1 - c/2).  Every producer of coefficients
+// passes c through this map, so every sweep runs either scheme.
+__device__ __forceinline__ float scheme_coef(float c, int scheme) {
+    return scheme == SIGK_SCHEME_IMPLICIT ? __fdividef(c, 1.f - 0.5f * c) : c;
+}
+__device__ __forceinline__ double scheme_coef(double c, int scheme) {
+    return scheme == SIGK_SCHEME_IMPLICIT ? c / (1.0 - 0.5 * c) : c;
+}
+// The RBF lift (Sec. 2.2): the coarse cell's coefficient is the second
+// difference of kappa(a,b) = exp(-|a-b|^2 / (2 sigma^2)) over its corners.
+// From u = x_p - y_q, dx = x_{p+1} - x_p, dy = y_{q+1} - y_q and the channel
+// sums uu = |u|^2, ux = <u,dx>, uy = <u,dy>, xy = <dx,dy>, nx = |dx|^2,
+// ny = |dy|^2, with s = 1/(2 sigma^2):
+//   kappa(x_p, y_q) = e = exp(-s uu),        kappa(x_p, y_{q+1}) = e exp(A),
+//   kappa(x_{p+1}, y_q) = e exp(B),          kappa(x_{p+1}, y_{q+1}) = e exp(A + B + C),
+// A = s (2 uy - ny), B = -s (2 ux + nx), C = 2 s xy (|u - dy|^2, |u + dx|^2 and
+// |u + dx - dy|^2 expanded), so the second difference is
+//   e (exp(A+B+C) - exp(A) - exp(B) + 1) = e (expm1(A) expm1(B) + exp(A+B) expm1(C)):
+// no O(1) values cancel, and FP32 keeps the relative accuracy of the small
+// coefficient that the plain four-term difference would lose.
+__device__ __forceinline__ float rbf_second_difference(float uu, float ux, float uy, float xy, float nx,
+                                                       float ny, float s) {
+    const float A = s * (2.f * uy - ny), B = -s * (2.f * ux + nx), C = 2.f * s * xy;
+    return expf(-s * uu) * (expm1f(A) * expm1f(B) + expf(A + B) * expm1f(C));
+}
+__device__ __forceinline__ double rbf_second_difference(double uu, double ux, double uy, double xy,
+                                                        double nx, double ny, double s) {
+    const double A = s * (2.0 * uy - ny), B = -s * (2.0 * ux + nx), C = 2.0 * s * xy;
+    return exp(-s * uu) * (expm1(A) * expm1(B) + exp(A + B) * expm1(C));
+}
+
+// dc'/dc of that map, written through c' = c / (1 - c/2): (1 + c'/2)^2.  The
+// adjoint sweeps use c' like the forward and so sum dk/dc'; times this factor
+// per coarse cell it is dk/dc.
+template <typename T>
+__device__ __forceinline__ T scheme_dcoef(T cp, int scheme) {
+    const T t = (T)1 + (T)0.5 * cp;
+    return scheme == SIGK_SCHEME_IMPLICIT ? t * t : (T)1;
+}
 
 struct PairRef {
     int64_t a_row0, la;     // first point row of the A path, and its length

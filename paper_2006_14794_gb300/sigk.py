@@ -31,9 +31,48 @@ _i64 = ctypes.c_int64
 _int = ctypes.c_int
 
 
+SCHEME_EXPLICIT, SCHEME_IMPLICIT = 0, 1
+KERNEL_LINEAR, KERNEL_RBF = 0, 1
+SCHEMES = {"explicit": SCHEME_EXPLICIT, "implicit": SCHEME_IMPLICIT}
+STATIC_KERNELS = {"linear": KERNEL_LINEAR, "rbf": KERNEL_RBF}
+
+
 class SigkOpts(ctypes.Structure):
     _fields_ = [("rec", _int), ("symmetric", _int), ("fault_inject", _int),
-                ("rows_per_lane", _int), ("coef_path", _int), ("orient", _int), ("reserved", _int * 2)]
+                ("rows_per_lane", _int), ("coef_path", _int), ("orient", _int),
+                ("scheme", _int), ("static_kernel", _int), ("sigma", ctypes.c_double),
+                ("reserved", _int * 2)]
+
+
+class Variant(NamedTuple):
+    """What a call solves (the fields of sigk_opts that change the result):
+    the finite-difference scheme ("explicit", or "implicit": the four-point
+    quadrature of the remark after the scheme, Sec. 3.1) and the static kernel
+    that lifts the paths ("linear": the paths as given, or "rbf" with bandwidth
+    sigma, Sec. 2.2)."""
+    scheme: str = "explicit"
+    static_kernel: str = "linear"
+    sigma: float = 1.0
+
+    def key(self) -> str:
+        """'' for the paper's main variant, else a tag for caches."""
+        if self.scheme == "explicit" and self.static_kernel == "linear":
+            return ""
+        return "%s/%s/%r" % (self.scheme, self.static_kernel,
+                             float(self.sigma) if self.static_kernel == "rbf" else 0.0)
+
+
+DEFAULT_VARIANT = Variant()
+
+
+def _variant(variant) -> Variant:
+    if variant is None:
+        return DEFAULT_VARIANT
+    if not isinstance(variant, Variant):
+        raise TypeError("variant must be a sigk.Variant")
+    if variant.scheme not in SCHEMES or variant.static_kernel not in STATIC_KERNELS:
+        raise ValueError("unknown scheme or static kernel: %r" % (variant,))
+    return variant
 
 
 class Schedule(NamedTuple):
@@ -130,9 +169,13 @@ def _stream(dev) -> int:
 
 
 def _opts(rec: int = REC_AUTO, symmetric: bool = False, fault_inject: bool = False,
-          schedule: Optional[Schedule] = None):
+          schedule: Optional[Schedule] = None, variant: Optional[Variant] = None):
     o = SigkOpts()
     o.rec = int(rec)
+    v = _variant(variant)
+    o.scheme = SCHEMES[v.scheme]
+    o.static_kernel = STATIC_KERNELS[v.static_kernel]
+    o.sigma = float(v.sigma) if v.static_kernel == "rbf" else 0.0
     if schedule is not None:
         o.rec = int(schedule.rec)
         o.rows_per_lane = int(schedule.rows_per_lane)
@@ -143,14 +186,14 @@ def _opts(rec: int = REC_AUTO, symmetric: bool = False, fault_inject: bool = Fal
     return o
 
 
-def _resolve(schedule, op, *shape_args):
+def _resolve(schedule, op, *shape_args, variant=None):
     """schedule may be None, a Schedule, or "tuned": look the shape up in the
     tuner's cache (timing the candidates on a miss)."""
     if isinstance(schedule, str):
         if schedule != "tuned":
             raise ValueError("schedule must be a Schedule, None or 'tuned'")
         from . import tune
-        return tune.lookup(op, *shape_args)
+        return tune.lookup(op, *shape_args, variant=_variant(variant))
     return schedule
 
 
@@ -175,11 +218,13 @@ def _workspace(op, b, b2, L, M, d, lam, dt, o, device):
 
 def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO,
           check_status: bool = False, fault_inject: bool = False,
-          schedule: Union[Schedule, str, None] = None) -> torch.Tensor:
+          schedule: Union[Schedule, str, None] = None,
+          variant: Optional[Variant] = None) -> torch.Tensor:
     """out[b] = k(X_b, Y_b).  X: [B, L, d], Y: [B, M, d] (same dtype, same CUDA device).
     check_status: synchronise and raise SigkError if a bounded device wait
     expired (strip path only).  fault_inject: test switch of sigk_opts.
-    schedule: a Schedule (overrides rec) or "tuned" (the tuner's choice)."""
+    schedule: a Schedule (overrides rec) or "tuned" (the tuner's choice).
+    variant: the scheme and static kernel (default: explicit, linear)."""
     X, Y = _dev(X, "X"), _dev(Y, "Y")
     if X.dim() != 3 or Y.dim() != 3 or X.shape[0] != Y.shape[0] or X.shape[2] != Y.shape[2]:
         raise ValueError("pairs wants X [B,L,d] and Y [B,M,d]")
@@ -189,8 +234,8 @@ def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AU
     M = Y.shape[1]
     dt = _dtype_code(X)
     out = torch.empty(B, dtype=X.dtype, device=X.device)
-    schedule = _resolve(schedule, "pairs", X, Y, dyadic_order)
-    o = _opts(rec, fault_inject=fault_inject, schedule=schedule)
+    schedule = _resolve(schedule, "pairs", X, Y, dyadic_order, variant=variant)
+    o = _opts(rec, fault_inject=fault_inject, schedule=schedule, variant=variant)
     ws, nws = _workspace(OP_PAIRS, B, 0, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_pairs(X.data_ptr(), Y.data_ptr(), B, L, M, d, int(dyadic_order), dt,
                             ctypes.byref(o), out.data_ptr(), _ptr(ws), nws, _stream(X.device)),
@@ -202,9 +247,10 @@ def pairs(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AU
 
 def gram(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO,
          symmetric: bool = False, check_status: bool = False,
-         schedule: Union[Schedule, str, None] = None) -> torch.Tensor:
+         schedule: Union[Schedule, str, None] = None,
+         variant: Optional[Variant] = None) -> torch.Tensor:
     """out[i, j] = k(X_i, Y_j).  With symmetric=True, Y must be X and only the
-    upper triangle is solved (then mirrored).  schedule: as for pairs."""
+    upper triangle is solved (then mirrored).  schedule, variant: as for pairs."""
     X, Y = _dev(X, "X"), _dev(Y, "Y")
     if X.dim() != 3 or Y.dim() != 3 or X.shape[2] != Y.shape[2]:
         raise ValueError("gram wants X [Bx,L,d] and Y [By,M,d]")
@@ -214,8 +260,8 @@ def gram(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUT
     By, M = Y.shape[0], Y.shape[1]
     dt = _dtype_code(X)
     out = torch.empty(Bx, By, dtype=X.dtype, device=X.device)
-    schedule = _resolve(schedule, "gram", X, Y, dyadic_order)
-    o = _opts(rec, symmetric, schedule=schedule)
+    schedule = _resolve(schedule, "gram", X, Y, dyadic_order, variant=variant)
+    o = _opts(rec, symmetric, schedule=schedule, variant=variant)
     ws, nws = _workspace(OP_GRAM, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_gram(X.data_ptr(), Y.data_ptr(), Bx, By, L, M, d, int(dyadic_order), dt,
                            ctypes.byref(o), out.data_ptr(), _ptr(ws), nws, _stream(X.device)),
@@ -228,9 +274,10 @@ def gram(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUT
 def pairs_varlen(Xp: torch.Tensor, x_off: torch.Tensor, Yp: torch.Tensor, y_off: torch.Tensor,
                  dyadic_order: int, max_len: int, rec: int = REC_AUTO, check_status: bool = False,
                  fault_inject: bool = False,
-                 schedule: Union[Schedule, str, None] = None) -> torch.Tensor:
+                 schedule: Union[Schedule, str, None] = None,
+                 variant: Optional[Variant] = None) -> torch.Tensor:
     """Pairs of uneven lengths: Xp [sum L, d] with int64 offsets x_off [B+1] (on the GPU).
-    schedule: as for pairs."""
+    schedule, variant: as for pairs."""
     Xp, Yp = _dev(Xp, "Xp"), _dev(Yp, "Yp")
     x_off, y_off = _dev(x_off, "x_off"), _dev(y_off, "y_off")
     if x_off.dtype != torch.int64 or y_off.dtype != torch.int64:
@@ -239,8 +286,9 @@ def pairs_varlen(Xp: torch.Tensor, x_off: torch.Tensor, Yp: torch.Tensor, y_off:
     d = Xp.shape[1]
     dt = _dtype_code(Xp)
     out = torch.empty(B, dtype=Xp.dtype, device=Xp.device)
-    schedule = _resolve(schedule, "pairs_varlen", Xp, x_off, Yp, y_off, dyadic_order, max_len)
-    o = _opts(rec, fault_inject=fault_inject, schedule=schedule)
+    schedule = _resolve(schedule, "pairs_varlen", Xp, x_off, Yp, y_off, dyadic_order, max_len,
+                        variant=variant)
+    o = _opts(rec, fault_inject=fault_inject, schedule=schedule, variant=variant)
     ws, nws = _workspace(OP_PAIRS_VARLEN, B, 0, max_len, max_len, d, dyadic_order, dt, o,
                          Xp.device)
     _check(lib().sigk_pairs_varlen(Xp.data_ptr(), x_off.data_ptr(), Yp.data_ptr(),
@@ -258,7 +306,7 @@ def version() -> str:
 
 def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
                    need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
-                   schedule: Optional[Schedule] = None):
+                   schedule: Optional[Schedule] = None, variant: Optional[Variant] = None):
     """(dX, dY) with dX[b] = grad_out[b] dk(X_b, Y_b)/dX_b (None when not needed)."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     B, L, d = X.shape
@@ -267,7 +315,7 @@ def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dya
     grad_out = grad_out.to(X.dtype)
     dX = torch.empty_like(X) if need_dx else None
     dY = torch.empty_like(Y) if need_dy else None
-    o = _opts(rec, schedule=schedule)
+    o = _opts(rec, schedule=schedule, variant=variant)
     ws, nws = _workspace(OP_PAIRS_BACKWARD, B, 0, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_pairs_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), B, L, M, d,
                                      int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
@@ -277,7 +325,8 @@ def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dya
 
 def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
                   need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
-                  schedule: Optional[Schedule] = None, symmetric: bool = False):
+                  schedule: Optional[Schedule] = None, symmetric: bool = False,
+                  variant: Optional[Variant] = None):
     """(dX, dY): dX[i] = sum_j grad_out[i,j] dk(X_i,Y_j)/dX_i, dY[j] likewise.
     symmetric=True (Y is X): (dX, None) with dX the derivative of
     sum_ij grad_out[i,j] k(X_i, X_j) through both arguments, from the pairs
@@ -291,7 +340,7 @@ def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyad
         need_dx, need_dy = True, False
     dX = torch.empty_like(X) if need_dx else None
     dY = torch.empty_like(Y) if need_dy else None
-    o = _opts(rec, symmetric=symmetric, schedule=schedule)
+    o = _opts(rec, symmetric=symmetric, schedule=schedule, variant=variant)
     ws, nws = _workspace(OP_GRAM_BACKWARD, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_gram_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), Bx, By, L, M,
                                     d, int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
@@ -324,16 +373,18 @@ class SigKernelPairs(torch.autograd.Function):
     """k(X_b, Y_b) with the adjoint sweep as its backward."""
 
     @staticmethod
-    def forward(ctx, X, Y, dyadic_order):
+    def forward(ctx, X, Y, dyadic_order, variant=None):
         ctx.save_for_backward(X, Y)
         ctx.lam = dyadic_order
-        return pairs(X, Y, dyadic_order)
+        ctx.variant = variant
+        return pairs(X, Y, dyadic_order, variant=variant)
 
     @staticmethod
     def backward(ctx, g):
         X, Y = ctx.saved_tensors
-        dX, dY = pairs_backward(g, X, Y, ctx.lam, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
-        return dX, dY, None
+        dX, dY = pairs_backward(g, X, Y, ctx.lam, ctx.needs_input_grad[0], ctx.needs_input_grad[1],
+                                variant=ctx.variant)
+        return dX, dY, None, None
 
 
 class SigKernelGram(torch.autograd.Function):
@@ -342,24 +393,26 @@ class SigKernelGram(torch.autograd.Function):
     forward and (where the band form applies) backward."""
 
     @staticmethod
-    def forward(ctx, X, Y, dyadic_order):
+    def forward(ctx, X, Y, dyadic_order, variant=None):
         ctx.save_for_backward(X, Y)
         ctx.lam = dyadic_order
         ctx.sym = X is Y
-        return gram(X, Y, dyadic_order, symmetric=ctx.sym)
+        ctx.variant = variant
+        return gram(X, Y, dyadic_order, symmetric=ctx.sym, variant=variant)
 
     @staticmethod
     def backward(ctx, g):
         X, Y = ctx.saved_tensors
         if ctx.sym and ctx.needs_input_grad[0] and ctx.needs_input_grad[1]:
             try:
-                dX, _ = gram_backward(g, X, X, ctx.lam, symmetric=True)
-                return dX, None, None
+                dX, _ = gram_backward(g, X, X, ctx.lam, symmetric=True, variant=ctx.variant)
+                return dX, None, None, None
             except SigkError as e:
                 if e.status != SIGK_EUNSUPPORTED:
                     raise
-        dX, dY = gram_backward(g, X, Y, ctx.lam, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
-        return dX, dY, None
+        dX, dY = gram_backward(g, X, Y, ctx.lam, ctx.needs_input_grad[0], ctx.needs_input_grad[1],
+                               variant=ctx.variant)
+        return dX, dY, None, None
 
 
 class _MMD2(torch.autograd.Function):
@@ -374,12 +427,13 @@ class _MMD2(torch.autograd.Function):
         return mmd2_backward(g, m, n, dt, dev)
 
 
-def mmd2_loss(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int) -> torch.Tensor:
+def mmd2_loss(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
+              variant: Optional[Variant] = None) -> torch.Tensor:
     """Differentiable unbiased MMD^2 between two batches of paths, built from
     three signature-kernel Gram matrices."""
-    Kxx = SigKernelGram.apply(X, X, dyadic_order)
-    Kyy = SigKernelGram.apply(Y, Y, dyadic_order)
-    Kxy = SigKernelGram.apply(X, Y, dyadic_order)
+    Kxx = SigKernelGram.apply(X, X, dyadic_order, variant)
+    Kyy = SigKernelGram.apply(Y, Y, dyadic_order, variant)
+    Kxy = SigKernelGram.apply(X, Y, dyadic_order, variant)
     return _MMD2.apply(Kxx, Kyy, Kxy)[0]
 
 

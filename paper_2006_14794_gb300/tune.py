@@ -23,7 +23,8 @@ from typing import Dict, List, Optional, Sequence, Tuple
 import torch
 
 from . import sigk
-from .sigk import COEF_FMA, COEF_TC, COEF_TC5, REC_BAND, REC_CHAIN, REC_PLAIN, REC_STRIP, Schedule
+from .sigk import (COEF_FMA, COEF_TC, COEF_TC5, DEFAULT_VARIANT, REC_BAND, REC_CHAIN, REC_PLAIN,
+                   REC_STRIP, Schedule, Variant)
 
 _lock = threading.Lock()
 _mem: Dict[str, Schedule] = {}
@@ -63,14 +64,18 @@ def candidates(op: str, dtype: torch.dtype) -> List[Schedule]:
     return c
 
 
-def shape_key(op: str, tensors: Sequence, scalars: Sequence, device) -> str:
-    """Cache key: call, tensor shapes and dtype, scalar arguments, GPU, library."""
+def shape_key(op: str, tensors: Sequence, scalars: Sequence, device,
+              variant: Variant = DEFAULT_VARIANT) -> str:
+    """Cache key: call, tensor shapes and dtype, scalar arguments, GPU, library,
+    and the scheme / static kernel when they are not the default."""
     props = torch.cuda.get_device_properties(device)
     shapes = ",".join("x".join(str(int(s)) for s in t.shape) for t in tensors)
     dt = str(tensors[0].dtype).replace("torch.", "")
     sc = ",".join(str(int(v)) for v in scalars)
-    return "%s|%s|%s|%s|%s:%d|%s" % (op, dt, shapes, sc, props.name,
-                                      props.multi_processor_count, sigk.version())
+    key = "%s|%s|%s|%s|%s:%d|%s" % (op, dt, shapes, sc, props.name,
+                                     props.multi_processor_count, sigk.version())
+    vk = variant.key()
+    return key + "|" + vk if vk else key
 
 
 def _load() -> Dict[str, list]:
@@ -117,26 +122,27 @@ def pick(results: Sequence[Tuple[Schedule, Optional[float], Optional[torch.Tenso
     return best
 
 
-def _call(op: str, args, s: Schedule):
+def _call(op: str, args, s: Schedule, variant: Variant = DEFAULT_VARIANT):
     if op == "pairs":
         X, Y, lam = args
-        return sigk.pairs(X, Y, lam, schedule=s)
+        return sigk.pairs(X, Y, lam, schedule=s, variant=variant)
     if op == "gram":
         X, Y, lam = args
-        return sigk.gram(X, Y, lam, schedule=s)
+        return sigk.gram(X, Y, lam, schedule=s, variant=variant)
     if op == "pairs_varlen":
         Xp, xo, Yp, yo, lam, max_len = args
-        return sigk.pairs_varlen(Xp, xo, Yp, yo, lam, max_len, schedule=s)
+        return sigk.pairs_varlen(Xp, xo, Yp, yo, lam, max_len, schedule=s, variant=variant)
     raise ValueError("no tuner for " + op)
 
 
-def _time(op, args, s: Schedule, reps: int, best: Optional[float]):
+def _time(op, args, s: Schedule, reps: int, best: Optional[float],
+          variant: Variant = DEFAULT_VARIANT):
     """(ms per call, output) or (None, None) when the schedule has no instance."""
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     try:
         e0.record(st)
-        out = _call(op, args, s)    # first run: module load, attributes
+        out = _call(op, args, s, variant)    # first run: module load, attributes
         e1.record(st)
         torch.cuda.synchronize()
     except sigk.SigkError as e:
@@ -148,13 +154,14 @@ def _time(op, args, s: Schedule, reps: int, best: Optional[float]):
         return first, out
     e0.record(st)
     for _ in range(reps):
-        out = _call(op, args, s)
+        out = _call(op, args, s, variant)
     e1.record(st)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps, out
 
 
-def tune(op: str, *args, reps: int = 5, store: bool = True) -> Tuple[Schedule, float]:
+def tune(op: str, *args, reps: int = 5, store: bool = True,
+         variant: Variant = DEFAULT_VARIANT) -> Tuple[Schedule, float]:
     """Times every candidate schedule of ``op`` on these arguments and returns
     (fastest schedule, its ms per call); caches it unless store=False."""
     tensors = [a for a in args if isinstance(a, torch.Tensor)]
@@ -163,24 +170,24 @@ def tune(op: str, *args, reps: int = 5, store: bool = True) -> Tuple[Schedule, f
     results = []
     best = None
     for s in candidates(op, tensors[0].dtype):
-        ms, out = _time(op, args, s, reps, best)
+        ms, out = _time(op, args, s, reps, best, variant)
         results.append((s, ms, out))
         if ms is not None and (best is None or ms < best):
             best = ms
     s, ms = pick(results, AGREE_TOL[tensors[0].dtype])
     if store:
-        key = shape_key(op, tensors, scalars, dev)
+        key = shape_key(op, tensors, scalars, dev, variant)
         with _lock:
             _mem[key] = s
             _store(key, s, ms)
     return s, ms
 
 
-def lookup(op: str, *args) -> Schedule:
+def lookup(op: str, *args, variant: Variant = DEFAULT_VARIANT) -> Schedule:
     """The cached schedule for this call shape; tunes (and caches) on a miss."""
     tensors = [a for a in args if isinstance(a, torch.Tensor)]
     scalars = [a for a in args if not isinstance(a, torch.Tensor)]
-    key = shape_key(op, tensors, scalars, tensors[0].device)
+    key = shape_key(op, tensors, scalars, tensors[0].device, variant)
     with _lock:
         s = _mem.get(key)
         if s is None:
@@ -193,7 +200,7 @@ def lookup(op: str, *args) -> Schedule:
     if torch.cuda.is_current_stream_capturing():
         raise sigk.SigkError("schedule for %s not tuned yet: call it once with schedule='tuned' "
                              "before the capture" % op)
-    return tune(op, *args)[0]
+    return tune(op, *args, variant=variant)[0]
 
 
 def clear_memory_cache() -> None:

@@ -101,6 +101,41 @@ def test_schedule_options_are_checked(libsigk):
     assert libsigk.sigk_pairs(P, P, 3, 4, 4, 65, 0, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EUNSUPPORTED
 
 
+def test_variant_options_are_checked(libsigk):
+    from paper_2006_14794_gb300 import sigk
+    P = ctypes.c_void_p(16)
+
+    def call(**kw):
+        o = sigk.SigkOpts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return libsigk.sigk_pairs(P, P, 3, 4, 4, 2, 0, 0, ctypes.byref(o), P, None, 0, None)
+
+    assert call(scheme=2) == sigk.SIGK_EINVAL
+    assert call(scheme=-1) == sigk.SIGK_EINVAL
+    assert call(static_kernel=2) == sigk.SIGK_EINVAL
+    # the RBF bandwidth must be positive and finite
+    assert call(static_kernel=sigk.KERNEL_RBF, sigma=0.0) == sigk.SIGK_EINVAL
+    assert call(static_kernel=sigk.KERNEL_RBF, sigma=-1.0) == sigk.SIGK_EINVAL
+    assert call(static_kernel=sigk.KERNEL_RBF, sigma=float("nan")) == sigk.SIGK_EINVAL
+    assert call(static_kernel=sigk.KERNEL_RBF, sigma=float("inf")) == sigk.SIGK_EINVAL
+    # sigma is ignored for the linear kernel
+    o = sigk.SigkOpts()
+    o.scheme = sigk.SCHEME_IMPLICIT
+    o.sigma = -3.0
+    assert libsigk.sigk_pairs(None, None, 0, 4, 4, 2, 0, 0, ctypes.byref(o), None, None, 0, None) == sigk.SIGK_OK
+
+
+def test_opts_layout_matches_the_header():
+    from paper_2006_14794_gb300 import sigk
+    txt = open(HEADER).read()
+    body = txt[txt.index("typedef struct {"):txt.index("} sigk_opts;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(int|double)\s+([a-z_]+)(\[\d+\])?;", body)
+    assert [f[1] for f in fields] == [f[0] for f in sigk.SigkOpts._fields_]
+    assert ctypes.sizeof(sigk.SigkOpts) == 48
+
+
 def test_forced_strip_schedule_asks_for_workspace(libsigk):
     from paper_2006_14794_gb300 import sigk
     auto, strip = sigk.SigkOpts(), sigk.SigkOpts()
