@@ -461,6 +461,59 @@ def _extra_setup(name, batch=0):
         return ("MMD^2 %d vs %d, L=256, d=32 walks + drift, dyadic order 1, loss + dL/dX, fp32 "
                 "(value counts the forward cells of Kxx, Kyy, Kxy as full Grams)" % (nb, nb), step, cells,
                 3 * cells, oracle_rate, host_step, host, X32.nbytes + Y32.nbytes, X32.nbytes)
+    if name in ("gram256_implicit", "gram256_rbf"):
+        # the benchmark Gram with the implicit scheme (Sec. 3.1 remark) or the
+        # RBF static-kernel lift (Sec. 2.2, sigma = 1)
+        w = inputs.gram_256()
+        lam = w["dyadic_order"]
+        nb = batch if 0 < batch < 256 else 256
+        X32, X64 = inputs.f32(w["X"][:nb])
+        Y32, Y64 = inputs.f32(w["Y"][:nb])
+        nbx, nby, L, d = X32.shape[0], Y32.shape[0], X32.shape[1], X32.shape[2]
+        if name == "gram256_implicit":
+            v = sigk.Variant(scheme="implicit")
+            okw = dict(scheme="implicit")
+            cflop = 2 * d + 2          # <dx, dy>, then c / (1 - c/2)
+            what = "implicit scheme"
+        else:
+            v = sigk.Variant(static_kernel="rbf", sigma=1.0)
+            okw = dict(static_kernel="rbf", sigma=1.0)
+            cflop = 9 * d              # |u|^2, <u,dx>, <u,dy>, <dx,dy> and u = x_p - y_q per channel
+            what = "RBF lift (sigma = 1), explicit scheme"
+        n = (L - 1) << lam
+        cells = nbx * nby * n * n
+        coarse = nbx * nby * (L - 1) * (L - 1)
+        Xd, Yd = torch.from_numpy(X32).cuda(), torch.from_numpy(Y32).cuda()
+
+        def step():
+            return sigk.gram(Xd, Yd, lam, variant=v)
+
+        def host_step(hx, hy, ho):
+            o = sigk.gram(hx.cuda(non_blocking=True), hy.cuda(non_blocking=True), lam, variant=v)
+            ho.copy_(o, non_blocking=True)
+
+        def oracle_rate(budget):
+            t0 = time.perf_counter(); rows = 0
+            while time.perf_counter() - t0 < budget and rows < nbx:
+                oracle.gram(X64[rows:rows + 1], Y64, lam, **okw)
+                rows += 1
+            return rows * nby * n * n / (time.perf_counter() - t0), "%d Gram rows of %d" % (rows, nbx)
+
+        def parity(out):
+            rng = np.random.default_rng(7)
+            idx = rng.choice(nbx * nby, 16, replace=False)
+            o = out.cpu().numpy()
+            errs = []
+            for t in idx:
+                i, j = divmod(int(t), nby)
+                ref = oracle.sigkernel(X64[i], Y64[j], lam, **okw)
+                errs.append(abs(o[i, j] - ref) / max(abs(ref), 1e-3))
+            return float(max(errs)), "16 sampled entries"
+        host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
+                torch.empty(nbx, nby).pin_memory())
+        return ("gram %dx%d, L=M=128, d=8 time-augmented random walks, dyadic order 2, fp32, %s" % (nbx, nby, what),
+                step, cells, 3 * cells + cflop * coarse, oracle_rate, host_step, host,
+                X32.nbytes + Y32.nbytes, nbx * nby * 4, parity)
     raise SystemExit("unknown workload " + name)
 
 
@@ -469,8 +522,9 @@ def run_extra(args):
     torch.cuda.set_device(0)
     from paper_2006_14794_gb300 import sigk
     sigk.lib()
-    desc, step, cells, flop, oracle_rate, host_step, host, h2d, d2h = _extra_setup(args.workload,
-                                                                                   args.batch)
+    setup = _extra_setup(args.workload, args.batch)
+    desc, step, cells, flop, oracle_rate, host_step, host, h2d, d2h = setup[:9]
+    parity = setup[9] if len(setup) > 9 else None
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     for _ in range(max(args.warmup, 3)):
         step()
@@ -488,6 +542,7 @@ def run_extra(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    rel = parity(step()) if parity is not None else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(args.steps):
@@ -514,6 +569,8 @@ def run_extra(args):
         "cpu_baseline": {"value": rate, "unit": "cells/s", "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": sample},
     }
+    if rel is not None:
+        line["rel_err_vs_oracle"] = {"max": rel[0], "sample": rel[1]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -529,9 +586,10 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--batch", type=int, default=0,
-                    help="long64 / mmd128: only the first BATCH pairs / paths per batch (profiling)")
+                    help="long64 / mmd128 / gram256_*: only the first BATCH pairs / paths per batch (profiling)")
     ap.add_argument("--workload", default="gram256",
-                    choices=["gram256", "uneven4096", "long64_l0", "long64_l1", "mmd128"])
+                    choices=["gram256", "uneven4096", "long64_l0", "long64_l1", "mmd128",
+                             "gram256_implicit", "gram256_rbf"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1095,14 +1095,19 @@ namespace {
 // pair k is the padded cell (P, Q) = (p + vrows, q + NQV), read by lane P / NG
 // as group g = P % NG at the position pos and window w with pos NG + w = Q + g;
 // pos = TperR is the pair's tail, in slot 0 of pair k + 1.
+template <int NG>
 struct BandRbfLayout {
     PairSrc src;
     float *band;
-    int TperR, NQV, vrows, NG;
+    int TperR, NQV, vrows;
     struct Geo {
         const float *rows, *cols;
         int nx, ny;
         int64_t k;
+    };
+    struct Row {
+        int64_t lane_off;   // (lane) * NG^2 + band_gpos(g)
+        int gr;             // group of the row within its lane
     };
     __device__ Geo geo(int64_t k) const {
         const PairRef pr = pair_ref(src, k);
@@ -1114,29 +1119,39 @@ struct BandRbfLayout {
         g.k = k;
         return g;
     }
-    __device__ void store(const Geo &g, int p, int q, float c) const {
-        const int P = p + vrows, Q = q + NQV;
-        const int l = P / NG, gr = P - l * NG;
-        const int t = Q + gr, pos = t / NG, w = t - pos * NG;
+    __device__ Row row(const Geo &, int p) const {
+        const int P = p + vrows;
+        Row r;
+        r.gr = P % NG;
+        r.lane_off = (int64_t)(P / NG) * (NG * NG) + band_gpos<NG>(r.gr);
+        return r;
+    }
+    __device__ void store(const Geo &g, const Row &r, int q, float c) const {
+        const int t = q + NQV + r.gr, pos = t / NG, w = t % NG;
         const int64_t slot = pos < TperR ? g.k * TperR + pos : (g.k + 1) * TperR;
-        const int gp = gr < NG / 2 ? 2 * gr : 2 * (gr - NG / 2) + 1;   // band_gpos
-        band[(slot * 32 + l) * (int64_t)(NG * NG) + w * NG + gp] = c;
+        band[slot * (32 * NG * NG) + r.lane_off + w * NG] = c;
     }
 };
+
+template <int NG>
+cudaError_t launch_band_rbf(const BandCoefArgs &c, int sms, cudaStream_t st) {
+    BandRbfLayout<NG> lay;
+    lay.src = c.src;
+    lay.band = c.band;
+    lay.TperR = c.TperR;
+    lay.NQV = c.NQV;
+    lay.vrows = c.vrows;
+    const size_t bytes = sizeof(float) * (size_t)(c.n_pairs * c.TperR + 1) * 32 * NG * NG;
+    return launch_rbf_coef<float>(lay, c.n_pairs, c.src.La - 1, c.src.Lb - 1, c.src.d, c.src.sigma,
+                                  (double)c.scale, c.src.scheme, c.band, bytes, sms, st);
+}
 
 cudaError_t launch_band_coef(const BandCoefArgs &c, int NG, int sms, int *status, cudaStream_t st,
                              int coef_path) {
     if (c.src.kernel == SIGK_KERNEL_RBF) {
-        BandRbfLayout lay;
-        lay.src = c.src;
-        lay.band = c.band;
-        lay.TperR = c.TperR;
-        lay.NQV = c.NQV;
-        lay.vrows = c.vrows;
-        lay.NG = NG;
-        const size_t bytes = sizeof(float) * (size_t)(c.n_pairs * c.TperR + 1) * 32 * NG * NG;
-        return launch_rbf_coef<float>(lay, c.n_pairs, c.src.La - 1, c.src.Lb - 1, c.src.d, c.src.sigma,
-                                      (double)c.scale, c.src.scheme, c.band, bytes, sms, st);
+        if (NG == 8) return launch_band_rbf<8>(c, sms, st);
+        if (NG == 4) return launch_band_rbf<4>(c, sms, st);
+        return launch_band_rbf<2>(c, sms, st);
     }
     if (coef_path == 3 && c.src.d <= 64) {
         if (NG == 8) return launch_coef_tc5<8>(c, sms, status, st);

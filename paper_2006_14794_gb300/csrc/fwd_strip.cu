@@ -1238,10 +1238,19 @@ struct StripRbfLayout {
         g.c_off = pp.c_off;
         return g;
     }
-    __device__ void store(const Geo &g, int p, int q, T c) const {
+    struct Row {
+        int64_t base;   // element of (row P of its strip, diagonal 0)
+    };
+    __device__ Row row(const Geo &g, int p) const {
         constexpr int CP = 32 * (R >> LAM);
         const int Pa = p + g.padc, s = Pa / CP, P = Pa - s * CP;
-        cbuf[g.c_off + ((int64_t)s * g.nw + P + q) * CP + P] = c;
+        Row r;
+        r.base = g.c_off + ((int64_t)s * g.nw + P) * CP + P;
+        return r;
+    }
+    __device__ void store(const Geo &, const Row &r, int q, T c) const {
+        constexpr int CP = 32 * (R >> LAM);
+        cbuf[r.base + (int64_t)q * CP] = c;
     }
 };
 

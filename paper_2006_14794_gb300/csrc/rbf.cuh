@@ -4,20 +4,22 @@
 // corner points (rbf_second_difference), passed through the scheme's map
 // (scheme_coef), and stored where the sweep that follows reads it.
 //
-// The kernel works on 32 x 32 tiles of a pair's coarse grid.  A block stages
-// the tile's 33 row points and 33 column points in shared memory, 32 channels
-// at a time, channel-major; thread t owns row t/8 and columns 4 (t%8) .. +3 of
-// the tile and sums, per channel, the six inner products the second
-// difference needs (|u|^2, <u,dx>, <u,dy>, <dx,dy> per cell, |dx|^2 per row,
-// |dy|^2 per column, u = x_p - y_q): 1 subtraction and 4 FMAs per cell and
-// channel.  Work units are (pair, tile) with the tile count of the largest
-// pair; a unit past its pair's grid does nothing.
+// The kernel works on 32 NR x 32 tiles of a pair's coarse grid (NR = 4 rows
+// per thread in f32, 2 in f64).  A block stages the tile's 32 NR + 1 row points
+// and 33 column points in shared memory, 32 channels at a time,
+// channel-major; thread t owns rows NR (t/8) .. +NR-1 and columns
+// 4 (t%8) .. +3 of the tile and sums, per channel, the six inner
+// products the second difference needs (|u|^2, <u,dx>, <u,dy>, <dx,dy> per
+// cell, |dx|^2 per row, |dy|^2 per column, u = x_p - y_q): 1 subtraction and
+// 4 FMAs per cell and channel.  Work units are (pair, tile) with the tile
+// count of the largest pair; a unit past its pair's grid does nothing.
 //
-// The destination layout is a template parameter with two device calls:
-//   Geo geo(int64_t k)                        pair k's row and column points
-//                                             (rows, cols), coarse sizes (nx,
-//                                             ny) and whatever store() needs
-//   void store(const Geo &, int p, int q, T c) writes coarse cell (p, q)
+// The destination layout is a template parameter with three device calls:
+//   Geo geo(int64_t k)               pair k's row and column points (rows,
+//                                    cols), coarse sizes (nx, ny) and whatever
+//                                    the stores need
+//   Row row(const Geo &, int p)      what the stores of coarse row p share
+//   void store(const Geo &, const Row &, int q, T c)   writes cell (p, q)
 // Entries that are not real cells (padding, virtual rows and columns) are not
 // written: the caller zero-fills the destination first.
 #pragma once
@@ -25,65 +27,100 @@
 
 namespace sigk {
 
-constexpr int RBF_T = 32;     // tile side (coarse cells)
+// rows per thread: 4 in f32, 2 in f64 (register budget); tile rows 32 x that
+template <typename T>
+__host__ __device__ constexpr int rbf_rows() { return sizeof(T) == 4 ? 4 : 2; }
+constexpr int RBF_TC = 32;    // tile columns: 4 per thread
 constexpr int RBF_CH = 32;    // channels staged per pass
 constexpr int RBF_THREADS = 256;
 
 template <typename T, class Layout>
-__global__ void __launch_bounds__(RBF_THREADS) rbf_coef_kernel(Layout lay, int64_t n_pairs, int64_t tiles_r,
-                                                               int64_t tiles_c, int64_t d, T s, T scale,
+__global__ void __launch_bounds__(RBF_THREADS) rbf_coef_kernel(Layout lay, int64_t n_pairs, int tiles_r,
+                                                               int tiles_c, int64_t d, T s, T scale,
                                                                int scheme) {
-    __shared__ T xs[RBF_CH][RBF_T + 1];
-    __shared__ T ys[RBF_CH][RBF_T + 2];
+    constexpr int NR = rbf_rows<T>(), TR = 32 * NR;
+    __shared__ T xs[RBF_CH][TR + 1];
+    __shared__ T ys[RBF_CH][RBF_TC + 2];
     const int tid = threadIdx.x;
-    const int r = tid >> 3, c0 = (tid & 7) * 4;
-    const int64_t per_pair = tiles_r * tiles_c;
+    const int r = (tid >> 3) * NR, c0 = (tid & 7) * 4;
+    const int per_pair = tiles_r * tiles_c;
     const int64_t units = n_pairs * per_pair;
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-        const int64_t k = u / per_pair;
-        const int64_t t = u - k * per_pair;
+        int64_t k;
+        int t;
+        if (units < (1LL << 31)) {   // 32-bit decode (the common case)
+            k = (int)u / per_pair;
+            t = (int)u - (int)k * per_pair;
+        } else {
+            k = u / per_pair;
+            t = (int)(u - k * per_pair);
+        }
         const typename Layout::Geo g = lay.geo(k);
-        const int p0 = (int)(t / tiles_c) * RBF_T, q0 = (int)(t % tiles_c) * RBF_T;
+        const int p0 = (t / tiles_c) * TR, q0 = (t - (t / tiles_c) * tiles_c) * RBF_TC;
         if (p0 >= g.nx || q0 >= g.ny) continue;   // block-uniform
-        T uu[4], ux[4], uy[4], xy[4], ny[4], nx = 0;
+        T uu[NR][4], ux[NR][4], uy[NR][4], xy[NR][4], ny[4], nx[NR];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { uu[j] = 0; ux[j] = 0; uy[j] = 0; xy[j] = 0; ny[j] = 0; }
+        for (int j = 0; j < 4; ++j) {
+            ny[j] = 0;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) { uu[i][j] = 0; ux[i][j] = 0; uy[i][j] = 0; xy[i][j] = 0; }
+        }
+#pragma unroll
+        for (int i = 0; i < NR; ++i) nx[i] = 0;
         for (int64_t cb = 0; cb < d; cb += RBF_CH) {
+            const int nc = d - cb < RBF_CH ? (int)(d - cb) : RBF_CH;
             __syncthreads();
-            // points p0 .. p0+32 and q0 .. q0+32 (0 past the path's last point)
-            for (int v = tid; v < RBF_CH * (RBF_T + 1); v += RBF_THREADS) {
-                const int i = v / RBF_CH, c = v - (v / RBF_CH) * RBF_CH;
-                const bool cin = cb + c < d;
-                xs[c][i] = (cin && p0 + i <= g.nx) ? g.rows[(int64_t)(p0 + i) * d + cb + c] : (T)0;
-                ys[c][i] = (cin && q0 + i <= g.ny) ? g.cols[(int64_t)(q0 + i) * d + cb + c] : (T)0;
+            // points p0 .. p0 + TR and q0 .. q0 + 32 (0 past the path's last
+            // point), channels cb .. cb + nc - 1: consecutive threads read
+            // consecutive channels of a point
+            for (int v = tid; v < nc * (TR + 1); v += RBF_THREADS) {
+                const int i = v / nc, c = v - i * nc;
+                xs[c][i] = p0 + i <= g.nx ? g.rows[(int64_t)(p0 + i) * d + cb + c] : (T)0;
+            }
+            for (int v = tid; v < nc * (RBF_TC + 1); v += RBF_THREADS) {
+                const int i = v / nc, c = v - i * nc;
+                ys[c][i] = q0 + i <= g.ny ? g.cols[(int64_t)(q0 + i) * d + cb + c] : (T)0;
             }
             __syncthreads();
-            const int nc = d - cb < RBF_CH ? (int)(d - cb) : RBF_CH;
+#pragma unroll 2
             for (int c = 0; c < nc; ++c) {
-                const T xa = xs[c][r], dxv = xs[c][r + 1] - xa;
-                nx += dxv * dxv;
+                T xv[NR + 1], dxv[NR];
+#pragma unroll
+                for (int i = 0; i <= NR; ++i) xv[i] = xs[c][r + i];
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    dxv[i] = xv[i + 1] - xv[i];
+                    nx[i] += dxv[i] * dxv[i];
+                }
                 T ya = ys[c][c0];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const T yb = ys[c][c0 + j + 1];
-                    const T dyv = yb - ya, uv = xa - ya;
+                    const T dyv = yb - ya;
                     ny[j] += dyv * dyv;
-                    uu[j] += uv * uv;
-                    ux[j] += uv * dxv;
-                    uy[j] += uv * dyv;
-                    xy[j] += dxv * dyv;
+#pragma unroll
+                    for (int i = 0; i < NR; ++i) {
+                        const T uv = xv[i] - ya;
+                        uu[i][j] += uv * uv;
+                        ux[i][j] += uv * dxv[i];
+                        uy[i][j] += uv * dyv;
+                        xy[i][j] += dxv[i] * dyv;
+                    }
                     ya = yb;
                 }
             }
         }
-        const int p = p0 + r;
-        if (p < g.nx) {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int p = p0 + r + i;
+            if (p >= g.nx) break;
+            const typename Layout::Row row = lay.row(g, p);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int q = q0 + c0 + j;
                 if (q < g.ny) {
-                    const T G = rbf_second_difference(uu[j], ux[j], uy[j], xy[j], nx, ny[j], s);
-                    lay.store(g, p, q, scheme_coef(G * scale, scheme));
+                    const T G = rbf_second_difference(uu[i][j], ux[i][j], uy[i][j], xy[i][j], nx[i], ny[j], s);
+                    lay.store(g, row, q, scheme_coef(G * scale, scheme));
                 }
             }
         }
@@ -99,11 +136,12 @@ cudaError_t launch_rbf_coef(const Layout &lay, int64_t n_pairs, int64_t max_nx, 
     cudaError_t e = cudaMemsetAsync(dst_zero, 0, zero_bytes, st);
     if (e != cudaSuccess) return e;
     if (n_pairs <= 0 || max_nx <= 0 || max_ny <= 0) return cudaSuccess;
-    const int64_t tr = (max_nx + RBF_T - 1) / RBF_T, tc = (max_ny + RBF_T - 1) / RBF_T;
+    constexpr int TR = 32 * rbf_rows<T>();
+    const int64_t tr = (max_nx + TR - 1) / TR, tc = (max_ny + RBF_TC - 1) / RBF_TC;
     int64_t grid = n_pairs * tr * tc;
     if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
     rbf_coef_kernel<T, Layout><<<(int)grid, RBF_THREADS, 0, st>>>(
-        lay, n_pairs, tr, tc, d, (T)(0.5 / (sigma * sigma)), (T)scale, scheme);
+        lay, n_pairs, (int)tr, (int)tc, d, (T)(0.5 / (sigma * sigma)), (T)scale, scheme);
     return cudaGetLastError();
 }
 

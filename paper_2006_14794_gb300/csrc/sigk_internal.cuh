@@ -52,10 +52,29 @@ __device__ __forceinline__ double scheme_coef(double c, int scheme) {
 //   e (exp(A+B+C) - exp(A) - exp(B) + 1) = e (expm1(A) expm1(B) + exp(A+B) expm1(C)):
 // no O(1) values cancel, and FP32 keeps the relative accuracy of the small
 // coefficient that the plain four-term difference would lose.
+// e^x - 1 in FP32 without cancellation: the Taylor series through x^8 / 8! for
+// |x| <= 1/2 (truncation below 2e-8 relative, Horner in FMAs), e^x - 1 beyond,
+// where the subtraction loses less than 4e-7 relative.  The lift's exponents
+// are small differences of squared distances, so the series is the common case.
+__device__ __forceinline__ float expm1_taylor(float x) {
+    if (fabsf(x) > 0.5f) return expf(x) - 1.f;
+    float p = 1.f / 40320.f;
+    p = fmaf(p, x, 1.f / 5040.f);
+    p = fmaf(p, x, 1.f / 720.f);
+    p = fmaf(p, x, 1.f / 120.f);
+    p = fmaf(p, x, 1.f / 24.f);
+    p = fmaf(p, x, 1.f / 6.f);
+    p = fmaf(p, x, 0.5f);
+    p = fmaf(p, x, 1.f);
+    return p * x;
+}
+// The two plain exponentials take the hardware exp2 (__expf): its error is a
+// few 1e-7 relative for the moderate arguments here, and a cell whose points
+// are many bandwidths apart has a negligible coefficient either way.
 __device__ __forceinline__ float rbf_second_difference(float uu, float ux, float uy, float xy, float nx,
                                                        float ny, float s) {
     const float A = s * (2.f * uy - ny), B = -s * (2.f * ux + nx), C = 2.f * s * xy;
-    return expf(-s * uu) * (expm1f(A) * expm1f(B) + expf(A + B) * expm1f(C));
+    return __expf(-s * uu) * (expm1_taylor(A) * expm1_taylor(B) + __expf(A + B) * expm1_taylor(C));
 }
 __device__ __forceinline__ double rbf_second_difference(double uu, double ux, double uy, double xy,
                                                         double nx, double ny, double s) {
