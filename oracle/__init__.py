@@ -66,6 +66,10 @@ def lib():
                                                 _dbl, _dp, _dp, _dp]
         L.oracle_sigk_gram_grad_ex.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _i64, _int, _int,
                                                _int, _dbl, _dp, _dp, _dp]
+        L.oracle_sigk_pair_surface.restype = _dbl
+        L.oracle_sigk_pair_surface.argtypes = [_dp, _i64, _dp, _i64, _i64, _int, _int, _int, _dbl, _dp]
+        L.oracle_sigk_pairs_surface.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _int, _int, _int,
+                                                _dbl, _dp, _dp]
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -107,6 +111,36 @@ def sigkernel(x, y, dyadic_order: int, scheme="explicit", static_kernel="linear"
                                                int(dyadic_order), *v))
     return float(lib().oracle_sigk_pair(xp, x.shape[0], yp, y.shape[0], x.shape[1],
                                         int(dyadic_order)))
+
+
+def surface(x, y, dyadic_order: int, scheme="explicit", static_kernel="linear", sigma=1.0):
+    """The scheme's solution at the sample-grid nodes (P_0 inside P_lambda):
+    [L, M] with surf[i, j] ~ k_{x,y}(s_i, t_j); row and column 0 are 1."""
+    x, xp = _d(x)
+    y, yp = _d(y)
+    sc, kc = SCHEMES[scheme], STATIC_KERNELS[static_kernel]
+    if kc == 1 and not sigma > 0:
+        raise ValueError("the RBF kernel needs sigma > 0")
+    out = np.empty((x.shape[0], y.shape[0]))
+    lib().oracle_sigk_pair_surface(xp, x.shape[0], yp, y.shape[0], x.shape[1], int(dyadic_order), sc,
+                                   kc, float(sigma), out.ctypes.data_as(_dp))
+    return out
+
+
+def pairs_surface(X, Y, dyadic_order: int, scheme="explicit", static_kernel="linear", sigma=1.0):
+    """(k [B], surfaces [B, L, M]) for pairs (X_b, Y_b)."""
+    X, xp = _d(X)
+    Y, yp = _d(Y)
+    B, L, d = X.shape
+    M = Y.shape[1]
+    sc, kc = SCHEMES[scheme], STATIC_KERNELS[static_kernel]
+    if kc == 1 and not sigma > 0:
+        raise ValueError("the RBF kernel needs sigma > 0")
+    out = np.empty(B)
+    surf = np.empty((B, L, M))
+    lib().oracle_sigk_pairs_surface(xp, yp, B, L, M, d, int(dyadic_order), sc, kc, float(sigma),
+                                    out.ctypes.data_as(_dp), surf.ctypes.data_as(_dp))
+    return out, surf
 
 
 def pairs(X, Y, dyadic_order: int, scheme="explicit", static_kernel="linear", sigma=1.0):

@@ -137,6 +137,47 @@ double oracle_sigk_pair_ex(const double *x, int64_t L, const double *y, int64_t 
     return k;
 }
 
+/* The solution surface on the sample grid P_0 (Sec. 3.1: k(s_i, t_j) at the
+ * nodes of the coarse grid, the quantity of Fig. "error"): surf[i * M + j] =
+ * the scheme's value at refined node (2^lambda i, 2^lambda j), i < L, j < M;
+ * row 0 and column 0 are the boundary value 1.  Returns k = surf[L-1][M-1]. */
+double oracle_sigk_pair_surface(const double *x, int64_t L, const double *y, int64_t M, int64_t d,
+                                int lam, int scheme, int kernel, double sigma, double *surf) {
+    for (int64_t j = 0; j < M; ++j) surf[j] = 1.0;
+    for (int64_t i = 0; i < L; ++i) surf[i * M] = 1.0;
+    if (L < 2 || M < 2) return 1.0;
+    const int64_t s = (int64_t)1 << lam;
+    const int64_t Ni = s * (L - 1), Nj = s * (M - 1);
+    const double f = pow4neg(lam);
+    double *prev = (double *)malloc(sizeof(double) * (size_t)(Nj + 1));
+    double *cur = (double *)malloc(sizeof(double) * (size_t)(Nj + 1));
+    double *Grow = (double *)malloc(sizeof(double) * (size_t)(M - 1));
+    for (int64_t b = 0; b <= Nj; ++b) prev[b] = 1.0;
+    int64_t pcur = -1;
+    for (int64_t a = 1; a <= Ni; ++a) {
+        int64_t p = (a - 1) >> lam;
+        if (p != pcur) { coef_row(x, p, y, M, d, kernel, sigma, Grow); pcur = p; }
+        cur[0] = 1.0;
+        for (int64_t b = 1; b <= Nj; ++b)
+            cur[b] = scheme_step(scheme, cur[b - 1], prev[b], prev[b - 1], f * Grow[(b - 1) >> lam]);
+        if (a % s == 0)
+            for (int64_t j = 1; j < M; ++j) surf[(a / s) * M + j] = cur[j * s];
+        double *t = prev; prev = cur; cur = t;
+    }
+    double k = prev[Nj];
+    free(prev); free(cur); free(Grow);
+    return k;
+}
+
+void oracle_sigk_pairs_surface(const double *X, const double *Y, int64_t B, int64_t L, int64_t M,
+                               int64_t d, int lam, int scheme, int kernel, double sigma,
+                               double *out, double *surf) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < B; ++b)
+        out[b] = oracle_sigk_pair_surface(X + b * L * d, L, Y + b * M * d, M, d, lam, scheme, kernel,
+                                          sigma, surf + b * L * M);
+}
+
 void oracle_sigk_pairs_ex(const double *X, const double *Y, int64_t B, int64_t L, int64_t M,
                           int64_t d, int lam, int scheme, int kernel, double sigma, double *out) {
 #pragma omp parallel for schedule(dynamic, 1)

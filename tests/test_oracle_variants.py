@@ -257,3 +257,41 @@ def test_variant_batched_entry_points_agree_with_single_pair():
         np.testing.assert_allclose(pY[1], dy, rtol=1e-14)
     with pytest.raises(ValueError):
         oracle.sigkernel(X[0], Y[0], 0, static_kernel="rbf", sigma=0.0)
+
+
+# ------------------------------------------------------- the solution surface
+
+@pytest.mark.parametrize("lam,kw", [(0, {}), (2, {}), (1, dict(scheme="implicit")),
+                                    (1, dict(static_kernel="rbf", sigma=0.7))])
+def test_surface_is_the_kernel_of_truncated_paths(lam, kw):
+    # The solution at (s_i, t_j) solves the same Goursat problem on the
+    # sub-rectangle [u, s_i] x [v, t_j] (Thm. "PDE" on the restricted paths),
+    # and the scheme restricted to the sub-grid is the same arithmetic: the
+    # surface equals the kernel of the paths cut after their i-th and j-th points.
+    rng = np.random.default_rng(300 + lam)
+    x = np.cumsum(rng.normal(size=(6, 3)) * 0.4, axis=0)
+    y = np.cumsum(rng.normal(size=(5, 3)) * 0.4, axis=0)
+    surf = oracle.surface(x, y, lam, **kw)
+    assert surf.shape == (6, 5)
+    assert np.all(surf[0, :] == 1.0) and np.all(surf[:, 0] == 1.0)
+    for i in range(1, 6):
+        for j in range(1, 5):
+            assert surf[i, j] == oracle.sigkernel(x[:i + 1], y[:j + 1], lam, **kw)
+    k, S = oracle.pairs_surface(x[None], y[None], lam, **kw)
+    np.testing.assert_array_equal(S[0], surf)
+    assert k[0] == surf[-1, -1]
+
+
+def test_surface_converges_to_bessel_at_every_node():
+    # straight lines x = a t, y = b t on [0, 1]: k(s, t) = I_0(2 sqrt(<a,b> s t))
+    # (Appendix A); every node's error falls ~4x per dyadic level.
+    rng = np.random.default_rng(310)
+    a, b = rng.normal(0, np.sqrt(1 / 3), 3), rng.normal(0, np.sqrt(1 / 3), 3)
+    t = np.linspace(0, 1, 5)[:, None]
+    x, y = a * t, b * t
+    ab = float(a @ b)
+    true = np.array([[truth.series_I0(ab * si * tj) for tj in t[:, 0]] for si in t[:, 0]])
+    errs = [np.abs(oracle.surface(x, y, lam) - true)[1:, 1:] for lam in (3, 4, 5)]
+    for e0, e1 in zip(errs, errs[1:]):
+        ratio = e0[e0 > 1e-12] / e1[e0 > 1e-12]
+        assert np.all((ratio > 3.5) & (ratio < 4.5))
