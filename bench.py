@@ -514,6 +514,52 @@ def _extra_setup(name, batch=0):
         return ("gram %dx%d, L=M=128, d=8 time-augmented random walks, dyadic order 2, fp32, %s" % (nbx, nby, what),
                 step, cells, 3 * cells + cflop * coarse, oracle_rate, host_step, host,
                 X32.nbytes + Y32.nbytes, nbx * nby * 4, parity)
+    if name == "surface256":
+        # the solution surface on the sample grid for the benchmark's 65536
+        # pairs (X_i, Y_j) of the 256 x 256 Gram, as a batch of pairs
+        w = inputs.gram_256()
+        lam = w["dyadic_order"]
+        nb = batch if 0 < batch < 256 else 256
+        X32, X64 = inputs.f32(w["X"][:nb])
+        Y32, Y64 = inputs.f32(w["Y"][:nb])
+        L, d = X32.shape[1], X32.shape[2]
+        B = nb * nb
+        Xd = torch.from_numpy(X32).cuda().repeat_interleave(nb, 0).contiguous()
+        Yd = torch.from_numpy(Y32).cuda().repeat(nb, 1, 1).contiguous()
+        n = (L - 1) << lam
+        cells = B * n * n
+        coarse = B * (L - 1) * (L - 1)
+
+        def step():
+            return sigk.pairs_surface(Xd, Yd, lam)[1]
+
+        hx, hy = Xd.cpu().pin_memory(), Yd.cpu().pin_memory()
+        hs = torch.empty(B, L, L).pin_memory()
+
+        def host_step(hx, hy, hs):
+            _, sf = sigk.pairs_surface(hx.cuda(non_blocking=True), hy.cuda(non_blocking=True), lam)
+            hs.copy_(sf, non_blocking=True)
+
+        def oracle_rate(budget):
+            t0 = time.perf_counter(); done = 0
+            while time.perf_counter() - t0 < budget and done < nb:
+                oracle.pairs_surface(np.repeat(X64[done:done + 1], nb, 0), Y64, lam)
+                done += 1
+            return done * nb * n * n / (time.perf_counter() - t0), "%d x %d pairs" % (done, nb)
+
+        def parity(out):
+            rng = np.random.default_rng(8)
+            s = out.cpu().numpy()
+            errs = []
+            for t in rng.choice(B, 6, replace=False):
+                i, j = divmod(int(t), nb)
+                ref = oracle.surface(X64[i], Y64[j], lam)
+                errs.append(float(np.max(np.abs(s[t] - ref) / np.maximum(np.abs(ref), 1e-3))))
+            return max(errs), "6 sampled pairs, every node"
+        return ("%d pairs (X_i, Y_j) of the 256x256 Gram inputs, L=M=128, d=8, dyadic order 2, fp32: "
+                "the solution surface on the sample grid (%d x %d nodes per pair, %.2f GB written)"
+                % (B, L, L, B * L * L * 4 / 1e9), step, cells, 3 * cells + 2 * d * coarse, oracle_rate,
+                host_step, (hx, hy, hs), hx.numel() * 4 + hy.numel() * 4, B * L * L * 4, parity)
     raise SystemExit("unknown workload " + name)
 
 
@@ -589,7 +635,7 @@ def main():
                     help="long64 / mmd128 / gram256_*: only the first BATCH pairs / paths per batch (profiling)")
     ap.add_argument("--workload", default="gram256",
                     choices=["gram256", "uneven4096", "long64_l0", "long64_l1", "mmd128",
-                             "gram256_implicit", "gram256_rbf"])
+                             "gram256_implicit", "gram256_rbf", "surface256"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -141,7 +141,7 @@ typedef enum { SIGK_KERNEL_LINEAR = 0, SIGK_KERNEL_RBF = 1 } sigk_static_kernel;
 
 typedef enum {
     SIGK_OP_PAIRS = 0, SIGK_OP_GRAM = 1, SIGK_OP_PAIRS_VARLEN = 2,
-    SIGK_OP_PAIRS_BACKWARD = 3, SIGK_OP_GRAM_BACKWARD = 4
+    SIGK_OP_PAIRS_BACKWARD = 3, SIGK_OP_GRAM_BACKWARD = 4, SIGK_OP_PAIRS_SURFACE = 5
 } sigk_op;
 
 /* Bytes of device workspace the call `op` needs for these sizes (B_or_Bx is
@@ -171,6 +171,23 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp,
                       const int64_t *y_off, int64_t B, int64_t d, int64_t max_len,
                       int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *ws,
                       size_t ws_bytes, void *stream);
+
+/* The solution surface on the sample grid: surf[b][i][j] = the scheme's value
+ * at the node (s_i, t_j) of the sample grid P_0 inside P_lambda, i.e. at
+ * refined node (2^lambda i, 2^lambda j): the solution k_{x,y}(s_i, t_j) of the
+ * Goursat problem on [u, s_i] x [v, t_j] (Sec. 3.1, the grids of Def. P_lambda
+ * and Fig. "error"), for i < L over X_b's points and j < M over Y_b's.  Row 0
+ * and column 0 are the boundary value 1; surf[b][L-1][M-1] = out[b] = k.
+ * X: [B, L, d], Y: [B, M, d]; out: [B]; surf: [B, L, M] (both overwritten).
+ * opts as for sigk_pairs (scheme and static kernel included).  f32 pairs
+ * whose shorter path fits a warp (2^lambda (L-1) <= 512) run the band sweep
+ * with its workspace (size it with SIGK_OP_PAIRS_SURFACE); others the plain
+ * sweep without one.  SIGK_REC_STRIP gives SIGK_EUNSUPPORTED (the strip path
+ * keeps no surface); SIGK_REC_BAND where the band form does not apply too.
+ * Writes B L M elements: HBM-bound once the grid is small. */
+int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64_t M, int64_t d,
+                       int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *surf,
+                       void *ws, size_t ws_bytes, void *stream);
 
 /* Reverse-mode derivative of sigk_pairs: dX[b] = grad_out[b] dk_b/dX_b and
  * dY[b] = grad_out[b] dk_b/dY_b (either output may be NULL to skip it).

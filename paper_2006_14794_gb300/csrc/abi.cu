@@ -313,6 +313,14 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
                                         smem, st));
 }
 
+// The surface's path: the band sweep's surface instance for f32 pairs whose
+// shorter path fits a warp (rec AUTO, CHAIN or BAND), else the plain sweep.
+bool surface_uses_band(const PairSrc &src, int lam, int dtype, int rec, int rows, BandPlan &bp) {
+    if (dtype != SIGK_F32 || rec == SIGK_REC_PLAIN || rec == SIGK_REC_STRIP) return false;
+    const int64_t la = src.La < src.Lb ? src.La : src.Lb, lb = src.La < src.Lb ? src.Lb : src.La;
+    return band_geometry(la, lb, lam, rows, bp);
+}
+
 }  // namespace
 
 extern "C" {
@@ -335,13 +343,26 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
                             int dyadic_order, int dtype, const sigk_opts *opts) {
     if (common_checks(B_or_Bx, L, M, d, dyadic_order, dtype, opts) != SIGK_OK) return 0;
     int64_t n_pairs;
-    if (op == SIGK_OP_PAIRS || op == SIGK_OP_PAIRS_VARLEN || op == SIGK_OP_PAIRS_BACKWARD)
+    if (op == SIGK_OP_PAIRS || op == SIGK_OP_PAIRS_VARLEN || op == SIGK_OP_PAIRS_BACKWARD ||
+        op == SIGK_OP_PAIRS_SURFACE)
         n_pairs = B_or_Bx;
     else if (op == SIGK_OP_GRAM || op == SIGK_OP_GRAM_BACKWARD)
         n_pairs = (By < 0) ? 0 : (opts && opts->symmetric ? B_or_Bx * (B_or_Bx + 1) / 2 : B_or_Bx * By);
     else
         return 0;
     if (n_pairs == 0 || L < 2 || M < 2) return 0;
+    if (op == SIGK_OP_PAIRS_SURFACE) {
+        PairSrc ss;
+        memset(&ss, 0, sizeof(ss));
+        set_variant(ss, opts);
+        ss.mode = PM_PAIRS;
+        ss.La = L; ss.Lb = M; ss.d = d;
+        BandPlan bp;
+        if (!surface_uses_band(ss, dyadic_order, dtype, rec_of(opts), rows_of(opts), bp)) return 0;
+        int64_t nb, need;
+        band_batch(bp, n_pairs, nb, need);
+        return (size_t)need;
+    }
     if (op == SIGK_OP_PAIRS_BACKWARD || op == SIGK_OP_GRAM_BACKWARD) {
         PairSrc bs;
         memset(&bs, 0, sizeof(bs));
@@ -485,6 +506,57 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, cons
     return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, (cudaStream_t)stream));
 }
 
+
+int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64_t M, int64_t d,
+                       int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *surf,
+                       void *ws, size_t ws_bytes, void *stream) {
+    int s = common_checks(B, L, M, d, dyadic_order, dtype, opts);
+    if (s) return s;
+    if (opts && opts->symmetric) return SIGK_EINVAL;
+    if (B == 0) return SIGK_OK;
+    if (!X || !Y || !out || !surf) return SIGK_EINVAL;
+    const int rec = rec_of(opts);
+    if (rec == SIGK_REC_STRIP) return SIGK_EUNSUPPORTED;   // the strip path has no surface
+    cudaStream_t st = (cudaStream_t)stream;
+    PairSrc src;
+    memset(&src, 0, sizeof(src));
+    set_variant(src, opts);
+    src.mode = PM_PAIRS;
+    src.A = X; src.B = Y;
+    src.La = L; src.Lb = M; src.d = d;
+    BandPlan bp;
+    const bool band = surface_uses_band(src, dyadic_order, dtype, rec, rows_of(opts), bp);
+    if (rec == SIGK_REC_BAND && !band) return SIGK_EUNSUPPORTED;
+    if (band) {
+        int64_t nb, need;
+        band_batch(bp, B, nb, need);
+        if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
+    }
+    // boundary nodes (row and column 0) are 1; the sweeps write the others
+    cudaError_t e = launch_fill_one(surf, B * L * M, dtype, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (L < 2 || M < 2) return cuda_status(launch_fill_one(out, B, dtype, st));
+    if (!band) return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, st, surf));
+    // rows refine the shorter path: node (i, j) of the sweep is surface (i, j),
+    // or (j, i) when X and Y swap places
+    PairSrc s2 = src;
+    int64_t sa = M, sb = 1;
+    if (L > M) {
+        s2.A = Y; s2.B = X;
+        s2.La = M; s2.Lb = L;
+        sa = 1; sb = M;
+    }
+    int64_t nb, need;
+    band_batch(bp, B, nb, need);
+    for (int64_t k0 = 0; k0 < B; k0 += nb) {
+        PairSrc s3 = s2;
+        s3.kbase = k0;
+        const int64_t m = B - k0 < nb ? B - k0 : nb;
+        e = launch_band_f32(s3, bp, m, (float *)out, ws, st, coef_of(opts), (float *)surf, L * M, sa, sb);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return SIGK_OK;
+}
 
 int sigk_pairs_backward(const void *grad_out, const void *X, const void *Y, int64_t B, int64_t L,
                         int64_t M, int64_t d, int dyadic_order, int dtype, const sigk_opts *opts,

@@ -213,6 +213,11 @@ struct BandArgs {
     float *botq;     // [warp][steps + 1]: Q of the warp's last row before each step
     int nck;         // checkpoint slots per warp
     int64_t bq_stride;
+    // the solution surface on the sample grid (SURF instances): node (i, j) of
+    // the launch's pair k at surf[(kbase + k) s_pair + i s_a + j s_b]
+    float *surf;
+    int64_t s_pair, s_a, s_b;
+    int vtop, vpad;  // virtual refined rows above / columns left of each pair
 };
 
 constexpr int BAND_CK = 8;   // macro-steps between checkpoints of the forward state
@@ -236,7 +241,16 @@ __device__ __forceinline__ void load_window(float (&v)[NG], const float *p) {
 // The sweep: fwd_chain.cu's chain_f32_kernel with its staging and dot
 // products replaced by one coefficient vector per window, prefetched one
 // macro-step ahead into the registers the window has just consumed.
-template <int R, int LAM, int MINB, bool SAVE>
+//
+// SURF: also store the solution at the sample-grid nodes (the surface).  Row
+// r of lane l, padded row R l + r, is refined node row a = R l + r + 1 - vtop;
+// at step j of position pos it computes padded column pos R + j - r (the
+// previous pair's when negative), node column b = that + 1 - vpad.  vtop and
+// vpad are multiples of 2^lambda, so the node is on the sample grid exactly
+// when a and b are: r % 2^lambda = 2^lambda - 1 (the last row of each coarse
+// group), and then b = j - r + 1 = j + 2 (mod 2^lambda), i.e. at step
+// j % 2^lambda = 2^lambda - 2 of each window (0 for dyadic orders 0 and 1).
+template <int R, int LAM, int MINB, bool SAVE, bool SURF = false>
 __global__ void __launch_bounds__(BAND_WARPS * 32, MINB) chain_band_kernel(BandArgs a) {
     constexpr int S = 1 << LAM;
     constexpr int NG = R / S;
@@ -336,6 +350,21 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, MINB) chain_band_kernel(BandA
                     const float2 qn = __ffma2_rn(c, sum, qu);
                     KP[i] = __fadd2_rn(KP[i], qn);
                     QP[i] = qn;
+                    if constexpr (SURF) {
+                        constexpr int JS = S >= 2 ? S - 2 : 0;
+                        if (jj == JS && s1 == S - 1) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int r = i + h * H;
+                                int bp = pos * R + w * S + JS - r, kk = kl;
+                                if (bp < 0) { bp += TperR * R; --kk; }
+                                const int an = R * lane + r + 1 - a.vtop, bn = bp + 1 - a.vpad;
+                                if (kk >= 0 && kk < np && an > 0 && bn > 0)
+                                    a.surf[(a.src.kbase + k0 + kk) * a.s_pair + (int64_t)(an >> LAM) * a.s_a +
+                                           (int64_t)(bn >> LAM) * a.s_b] = h ? KP[i].y : KP[i].x;
+                            }
+                        }
+                    }
                     if (i == H - 1) {
                         shK = __shfl_up_sync(FULL, KP[i].y, 1);
                         shQ = __shfl_up_sync(FULL, QP[i].y, 1);
@@ -1165,7 +1194,8 @@ cudaError_t launch_band_coef(const BandCoefArgs &c, int NG, int sms, int *status
 }  // namespace
 
 cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pairs, float *out,
-                            void *ws, cudaStream_t st, int coef_path) {
+                            void *ws, cudaStream_t st, int coef_path, float *surf, int64_t s_pair,
+                            int64_t s_a, int64_t s_b) {
     if (n_pairs <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1196,12 +1226,21 @@ cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pai
     a.n_pairs = n_pairs;
     a.ppw = (n_pairs + warps - 1) / warps;
     a.TperR = p.TperR;
+    a.surf = surf;
+    a.s_pair = s_pair;
+    a.s_a = s_a;
+    a.s_b = s_b;
+    a.vtop = p.vrows << p.lam;
+    a.vpad = p.NQV << p.lam;
     const int64_t nwarps = (n_pairs + a.ppw - 1) / a.ppw;
     const int grid = (int)((nwarps + BAND_WARPS - 1) / BAND_WARPS);
-#define X(r, l, mb)                                                          \
-    if (p.R == r && p.lam == l) {                                            \
-        chain_band_kernel<r, l, mb, false><<<grid, BAND_WARPS * 32, 0, st>>>(a); \
-        return cudaGetLastError();                                           \
+#define X(r, l, mb)                                                                  \
+    if (p.R == r && p.lam == l) {                                                    \
+        if (surf)                                                                    \
+            chain_band_kernel<r, l, mb, false, true><<<grid, BAND_WARPS * 32, 0, st>>>(a); \
+        else                                                                         \
+            chain_band_kernel<r, l, mb, false><<<grid, BAND_WARPS * 32, 0, st>>>(a);       \
+        return cudaGetLastError();                                                   \
     }
     SIGK_BAND_CASES(X)
 #undef X

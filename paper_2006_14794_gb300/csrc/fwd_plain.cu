@@ -40,9 +40,12 @@ __device__ __forceinline__ T coef(const T *x, const T *y, int64_t d, int64_t p, 
 
 // Q_FORM = false: the printed scheme (three diagonals of K).
 // Q_FORM = true:  the difference form (K and Q on two diagonals each).
+// surf (optional, pairs of uniform lengths only): the solution at the
+// sample-grid nodes, node (i, j) of pair k at surf[k La Lb + i Lb + j] (i over
+// the A path); the refined node (a, b) is one when both are multiples of 2^lambda.
 template <typename T, bool Q_FORM>
 __global__ void __launch_bounds__(PLAIN_THREADS) plain_kernel(PairSrc src, int64_t n_pairs,
-                                                               int lam, int64_t wcap, T *out) {
+                                                               int lam, int64_t wcap, T *out, T *surf) {
     extern __shared__ unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);
     const T scale = (T)0.5 / (T)(1LL << (2 * lam));
@@ -60,10 +63,15 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_kernel(PairSrc src, int64
         const T *x = (const T *)src.A + pr.a_row0 * src.d;
         const T *y = (const T *)src.B + pr.b_row0 * src.d;
         int64_t la = pr.la, lb = pr.lb;
-        if (la > lb) {
+        const bool swapped = la > lb;
+        if (swapped) {
             const T *t = x; x = y; y = t;
             int64_t tl = la; la = lb; lb = tl;
         }
+        // surface strides of the sweep's rows and columns (rows index the A path unless swapped)
+        T *sf = surf ? surf + pr.out0 * pr.la * pr.lb : nullptr;
+        const int64_t sr = swapped ? 1 : pr.lb, sc = swapped ? pr.lb : 1;
+        const int64_t smask = (1LL << lam) - 1;
         const int64_t Ni = (la - 1) << lam, Nj = (lb - 1) << lam;
         const int64_t W = Ni + 1;
         if (W > wcap) {
@@ -99,6 +107,7 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_kernel(PairSrc src, int64
                                                 src.scheme);
                         const T kl = D0[a], ku = D0[a - 1], kd = D1[a - 1];
                         v = kl + ku - kd + c * (kl + ku);
+                        if (sf && (a & smask) == 0 && (b & smask) == 0) sf[(a >> lam) * sr + (b >> lam) * sc] = v;
                     }
                     D2[a] = v;
                 } else {
@@ -111,6 +120,7 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_kernel(PairSrc src, int64
                         const T kl = D0[a], ku = D0[a - 1], qu = D1[a - 1];
                         qv = qu + c * (kl + ku);
                         kv = kl + qv;
+                        if (sf && (a & smask) == 0 && (b & smask) == 0) sf[(a >> lam) * sr + (b >> lam) * sc] = kv;
                     }
                     D2[a] = kv;
                     D3[a] = qv;
@@ -141,7 +151,7 @@ __global__ void fill_one_kernel(T *out, int64_t n) {
 
 template <typename T, bool QF>
 cudaError_t launch_plain_t(const PairSrc &src, int64_t n_pairs, int lam, T *out, cudaStream_t st,
-                           int64_t min_len) {
+                           int64_t min_len, T *surf) {
     const int64_t W = ((min_len > 1 ? min_len - 1 : 0) << lam) + 1;
     const int64_t smem = (QF ? 4 : 3) * W * (int64_t)sizeof(T);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
@@ -155,7 +165,7 @@ cudaError_t launch_plain_t(const PairSrc &src, int64_t n_pairs, int lam, T *out,
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)sms * per_sm;
     if (grid > n_pairs) grid = n_pairs;
-    kern<<<(int)grid, PLAIN_THREADS, (int)smem, st>>>(src, n_pairs, lam, W, out);
+    kern<<<(int)grid, PLAIN_THREADS, (int)smem, st>>>(src, n_pairs, lam, W, out, surf);
     return cudaGetLastError();
 }
 
@@ -165,12 +175,12 @@ cudaError_t launch_plain_t(const PairSrc &src, int64_t n_pairs, int lam, T *out,
 // uneven lengths the caller passes in src.La the longest length any pair's
 // shorter path can have.
 cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype, void *out,
-                         cudaStream_t st) {
+                         cudaStream_t st, void *surf) {
     if (n_pairs <= 0) return cudaSuccess;
     const int64_t min_len = src.mode == PM_VARLEN ? src.La : (src.La < src.Lb ? src.La : src.Lb);
     if (dtype == SIGK_F64)
-        return launch_plain_t<double, false>(src, n_pairs, lam, (double *)out, st, min_len);
-    return launch_plain_t<float, true>(src, n_pairs, lam, (float *)out, st, min_len);
+        return launch_plain_t<double, false>(src, n_pairs, lam, (double *)out, st, min_len, (double *)surf);
+    return launch_plain_t<float, true>(src, n_pairs, lam, (float *)out, st, min_len, (float *)surf);
 }
 
 cudaError_t launch_fill_one(void *out, int64_t n, int dtype, cudaStream_t st) {

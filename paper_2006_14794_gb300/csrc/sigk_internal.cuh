@@ -170,8 +170,11 @@ struct BandPlan {
 bool band_geometry(int64_t La, int64_t Lb, int lam, int rows_per_lane, BandPlan &p);
 int64_t band_bytes(const BandPlan &p, int64_t n_pairs);
 // coef_path 3: coefficients on tcgen05 (d <= 64); otherwise the FMA contraction
+// surf (optional): the solution surface, node (i, j) of pair k (of the call)
+// at surf[k s_pair + i s_a + j s_b]; nodes on row or column 0 are not written
 cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pairs, float *out,
-                            void *ws, cudaStream_t st, int coef_path);
+                            void *ws, cudaStream_t st, int coef_path, float *surf = nullptr,
+                            int64_t s_pair = 0, int64_t s_a = 0, int64_t s_b = 0);
 // The band backward (reversible adjoint): pairs per launch (Gram: whole rows)
 // under cap_bytes, with the workspace that needs; then the launches.  src is
 // oriented (rows refine A); dA / dB (either may be null) are overwritten.
@@ -183,7 +186,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src, const BandPlan &p, int64_t n
                                 int coef_path);
 
 cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype, void *out,
-                         cudaStream_t st);
+                         cudaStream_t st, void *surf = nullptr);
 
 cudaError_t launch_fill_one(void *out, int64_t n, int dtype, cudaStream_t st);
 

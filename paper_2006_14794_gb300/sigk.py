@@ -7,7 +7,7 @@ not need a GPU; calling it needs the built ``libsigk.so`` and fails loudly when
 it is missing (there is no CPU fallback).
 
 Names follow the C ABI: ``pairs``, ``gram``, ``pairs_varlen``,
-``pairs_backward``, ``gram_backward``, ``mmd2``; the autograd wrappers are
+``pairs_surface``, ``pairs_backward``, ``gram_backward``, ``mmd2``; the autograd wrappers are
 ``SigKernelPairs``, ``SigKernelGram`` and ``mmd2_loss``.
 """
 from __future__ import annotations
@@ -24,7 +24,7 @@ SIGK_OK, SIGK_EINVAL, SIGK_ENOMEM_WS, SIGK_ECUDA, SIGK_ETIMEOUT, SIGK_EUNSUPPORT
 SIGK_F32, SIGK_F64 = 0, 1
 REC_AUTO, REC_CHAIN, REC_PLAIN, REC_STRIP, REC_BAND = 0, 1, 2, 3, 4
 COEF_AUTO, COEF_FMA, COEF_TC, COEF_TC5 = 0, 1, 2, 3
-OP_PAIRS, OP_GRAM, OP_PAIRS_VARLEN, OP_PAIRS_BACKWARD, OP_GRAM_BACKWARD = range(5)
+OP_PAIRS, OP_GRAM, OP_PAIRS_VARLEN, OP_PAIRS_BACKWARD, OP_GRAM_BACKWARD, OP_PAIRS_SURFACE = range(6)
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -100,6 +100,8 @@ SIGNATURES = [
                          ctypes.c_size_t, _vp]),
     ("sigk_pairs_varlen", _int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _int, _int, _vp, _vp,
                                  _vp, ctypes.c_size_t, _vp]),
+    ("sigk_pairs_surface", _int, [_vp, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp, _vp, _vp, _vp,
+                                  ctypes.c_size_t, _vp]),
     ("sigk_pairs_backward", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp, _vp,
                                    _vp, _vp, ctypes.c_size_t, _vp]),
     ("sigk_gram_backward", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _int, _int, _vp,
@@ -298,6 +300,29 @@ def pairs_varlen(Xp: torch.Tensor, x_off: torch.Tensor, Yp: torch.Tensor, y_off:
     if check_status:
         _status(ws, Xp.device)
     return out
+
+
+def pairs_surface(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int, rec: int = REC_AUTO,
+                  schedule: Optional[Schedule] = None, variant: Optional[Variant] = None):
+    """(k [B], surf [B, L, M]): the solution at the sample-grid nodes,
+    surf[b, i, j] ~ k_{X_b, Y_b}(s_i, t_j) (row and column 0 are 1,
+    surf[:, -1, -1] = k)."""
+    X, Y = _dev(X, "X"), _dev(Y, "Y")
+    if X.dim() != 3 or Y.dim() != 3 or X.shape[0] != Y.shape[0] or X.shape[2] != Y.shape[2]:
+        raise ValueError("pairs_surface wants X [B,L,d] and Y [B,M,d]")
+    if X.dtype != Y.dtype:
+        raise TypeError("X and Y must share a dtype")
+    B, L, d = X.shape
+    M = Y.shape[1]
+    dt = _dtype_code(X)
+    out = torch.empty(B, dtype=X.dtype, device=X.device)
+    surf = torch.empty(B, L, M, dtype=X.dtype, device=X.device)
+    o = _opts(rec, schedule=schedule, variant=variant)
+    ws, nws = _workspace(OP_PAIRS_SURFACE, B, 0, L, M, d, dyadic_order, dt, o, X.device)
+    _check(lib().sigk_pairs_surface(X.data_ptr(), Y.data_ptr(), B, L, M, d, int(dyadic_order), dt,
+                                    ctypes.byref(o), out.data_ptr(), surf.data_ptr(), _ptr(ws), nws,
+                                    _stream(X.device)), "sigk_pairs_surface")
+    return out, surf
 
 
 def version() -> str:
