@@ -18,6 +18,9 @@ Every entry point also takes ``scheme`` ("explicit", or "implicit": the
 four-point quadrature of the remark after the scheme in Sec. 3.1) and
 ``static_kernel`` ("linear", or "rbf" with bandwidth ``sigma``: the PDE of the
 paths lifted by a static kernel, Sec. 2.2).
+
+``support_reduction`` is the proximal gradient iteration of Sec. 5.3 on a
+given Gram matrix (numpy float64, one matrix-vector product per step).
 """
 from __future__ import annotations
 
@@ -275,3 +278,34 @@ def mmd2_grad_x(X, Y, dyadic_order: int):
     gxy = np.full((m, n), -2.0 / (m * n))
     dXc, _ = gram_grad(X, Y, dyadic_order, gxy, want_dy=False)
     return dXa + dXb + dXc
+
+
+def soft_threshold(v, tau):
+    """The soft-thresholding operator of Sec. 5.3, A_tau(v)_i = v_i - tau if
+    v_i > tau, 0 if |v_i| <= tau, v_i + tau if v_i < -tau."""
+    v = np.asarray(v, dtype=np.float64)
+    out = np.zeros_like(v)
+    out[v > tau] = v[v > tau] - tau
+    out[v < -tau] = v[v < -tau] + tau
+    return out
+
+
+def support_reduction(K, alpha, beta0, gamma: float, lam: float, iters: int):
+    """Proximal gradient descent for min_beta L(beta) + lam |beta|_1 with
+    L(beta) = sum_ij (alpha_i - beta_i)(alpha_j - beta_j) K_ij (Sec. 5.3):
+      beta <- A_{gamma lam}(beta - gamma grad L(beta)),  grad L = -2 K (alpha - beta)
+    (the soft threshold at gamma lam is the proximal map of gamma lam |.|_1).
+    Returns (beta after `iters` steps, loss history [iters + 1] of
+    L(beta^t) + lam |beta^t|_1)."""
+    K = np.asarray(K, dtype=np.float64)
+    a = np.asarray(alpha, dtype=np.float64)
+    b = np.array(beta0, dtype=np.float64)
+    hist = []
+    for _ in range(iters):
+        r = a - b
+        g = K @ r
+        hist.append(float(r @ g) + lam * float(np.abs(b).sum()))
+        b = soft_threshold(b + 2.0 * gamma * g, gamma * lam)
+    r = a - b
+    hist.append(float(r @ (K @ r)) + lam * float(np.abs(b).sum()))
+    return b, np.array(hist)

@@ -106,6 +106,27 @@ def long_pairs(seed: int = SEEDS[5], B: int = 64, L: int = 4096, d: int = 64):
     return dict(X=X, Y=Y, dyadic_orders=(0, 1))
 
 
+def fbm_paths(seed: int = 2006_0006, B: int = 30, L: int = 64, hursts=(0.2, 0.5, 0.8)):
+    """The support-reduction example of Sec. 5.3: B sample paths of fractional
+    Brownian motion on [0, 1], each with a Hurst exponent drawn uniformly from
+    `hursts`, time-augmented (d = 2: t, B^H_t), L points.  Drawn exactly on
+    the grid t_i = i / (L - 1) from the covariance
+    1/2 (s^2H + t^2H - |s - t|^2H) by its Cholesky factor.  Returns (paths
+    [B, L, 2], the Hurst exponent of each path)."""
+    r = _rngs(seed, 2)
+    H = r[0].choice(np.asarray(hursts, dtype=np.float64), size=B)
+    t = np.linspace(0.0, 1.0, L)
+    s, u = np.meshgrid(t[1:], t[1:], indexing="ij")
+    X = np.zeros((B, L, 2))
+    X[:, :, 0] = t
+    for b in range(B):
+        h2 = 2.0 * H[b]
+        C = 0.5 * (s ** h2 + u ** h2 - np.abs(s - u) ** h2)
+        Lc = np.linalg.cholesky(C + 1e-12 * np.eye(L - 1))
+        X[b, 1:, 1] = Lc @ r[1].standard_normal(L - 1)
+    return X, H
+
+
 def random_paths(seed: int, B: int, L: int, d: int, scale: float = 1.0, time_channel: bool = False):
     """Generic seeded paths for tests: walks with xi ~ N(0, scale^2/(L d))."""
     r = _rngs(seed, 1)[0]
