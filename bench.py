@@ -560,6 +560,47 @@ def _extra_setup(name, batch=0):
                 "the solution surface on the sample grid (%d x %d nodes per pair, %.2f GB written)"
                 % (B, L, L, B * L * L * 4 / 1e9), step, cells, 3 * cells + 2 * d * coarse, oracle_rate,
                 host_step, (hx, hy, hs), hx.numel() * 4 + hy.numel() * 4, B * L * L * 4, parity)
+    if name == "support_fbm30":
+        # the support-reduction example of Sec. 5.3: 30 fBM paths (Hurst
+        # exponents from {0.2, 0.5, 0.8}), their signature-kernel Gram, then
+        # proximal gradient descent on the weights; one step = the Gram + 2000
+        # iterations
+        X, H = inputs.fbm_paths()
+        X[:, :, 1] *= 0.5 / np.abs(X[:, :, 1]).max()
+        X32, X64 = inputs.f32(X)
+        lam_d, iters, pen = 3, 2000, 0.5
+        n, L = X32.shape[0], X32.shape[1]
+        Xd = torch.from_numpy(X32).cuda()
+        K0 = sigk.gram(Xd, Xd, lam_d)
+        gamma = float(0.5 / np.abs(np.linalg.eigvalsh(K0.double().cpu().numpy())).max())
+        a = torch.full((n,), 1.0 / n, device="cuda")
+        b0 = torch.zeros(n, device="cuda")
+        cells = n * n * ((L - 1) << lam_d) ** 2
+
+        def step():
+            K = sigk.gram(Xd, Xd, lam_d)
+            return sigk.support_reduction(K, a, b0, gamma, pen, iters)[0]
+
+        def host_step(hx, hb):
+            xd = hx.cuda(non_blocking=True)
+            K = sigk.gram(xd, xd, lam_d)
+            hb.copy_(sigk.support_reduction(K, a, b0, gamma, pen, iters)[0], non_blocking=True)
+
+        def oracle_rate(budget):
+            t0 = time.perf_counter()
+            K = oracle.gram(X64, X64, lam_d)
+            oracle.support_reduction(K, np.full(n, 1.0 / n), np.zeros(n), gamma, pen, iters)
+            return cells / (time.perf_counter() - t0), "the whole step (Gram + %d iterations)" % iters
+
+        def parity(out):
+            K = oracle.gram(X64, X64, lam_d)
+            rb, _ = oracle.support_reduction(K, np.full(n, 1.0 / n), np.zeros(n), gamma, pen, iters)
+            o = out.double().cpu().numpy()
+            return float(np.max(np.abs(o - rb)) / np.max(np.abs(rb))), "beta after %d iterations" % iters
+        return ("support reduction (Sec. 5.3): 30 fBM paths, L=%d, d=2, Gram at dyadic order %d, then %d "
+                "proximal gradient steps (lam = %g), fp32" % (L, lam_d, iters, pen), step, cells,
+                3 * cells, oracle_rate, host_step,
+                (torch.from_numpy(X32).pin_memory(), torch.empty(n).pin_memory()), X32.nbytes, n * 4, parity)
     raise SystemExit("unknown workload " + name)
 
 
@@ -635,7 +676,7 @@ def main():
                     help="long64 / mmd128 / gram256_*: only the first BATCH pairs / paths per batch (profiling)")
     ap.add_argument("--workload", default="gram256",
                     choices=["gram256", "uneven4096", "long64_l0", "long64_l1", "mmd128",
-                             "gram256_implicit", "gram256_rbf", "surface256"])
+                             "gram256_implicit", "gram256_rbf", "surface256", "support_fbm30"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -245,6 +245,23 @@ int sigk_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int6
 int sigk_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *gKxx,
                        void *gKyy, void *gKxy, void *stream);
 
+/* Moments-matching reduction of the support of a discrete measure on paths
+ * (Sec. 5.3).  With K the signature-kernel Gram of the support's N paths
+ * (e.g. sigk_gram of X with itself) and weights alpha, proximal gradient
+ * descent on L(beta) + lam |beta|_1, L(beta) = (alpha - beta)^T K (alpha - beta):
+ *   beta <- A_{gamma lam}(beta + 2 gamma K (alpha - beta)),
+ * A_tau the paper's soft-thresholding operator (the proximal map of
+ * tau |.|_1; the paper writes A_gamma with the penalty folded in).
+ * K: [N, N] (symmetric), alpha: [N]; beta: [N], in: beta^0, out: beta after
+ * `iters` steps; loss: [iters + 1] or NULL, L(beta^t) + lam |beta^t|_1 for
+ * t = 0..iters.  gamma > 0 (convergence needs gamma <= 1 / (2 |K|)),
+ * lam >= 0, iters >= 0.  One thread block runs every step in one launch,
+ * with alpha and beta (and K, for N up to about 220 in f32) in shared memory;
+ * N above 17066 (f32) or 8533 (f64) gives SIGK_EUNSUPPORTED.  No workspace.
+ * The loss is summed with atomic adds: its last bits may vary run to run. */
+int sigk_support_reduction(const void *K, const void *alpha, void *beta, int64_t N, double gamma,
+                           double lam, int iters, int dtype, void *loss, void *stream);
+
 /* Status word of the last strip-path call that used workspace `ws` on
  * `stream`: synchronises the stream, then returns SIGK_OK or SIGK_ETIMEOUT
  * (a bounded device wait expired; that call's results are meaningless).

@@ -627,6 +627,22 @@ int sigk_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *
     return cuda_status(launch_mmd2_backward(grad, m, n, dtype, gKxx, gKyy, gKxy, (cudaStream_t)stream));
 }
 
+int sigk_support_reduction(const void *K, const void *alpha, void *beta, int64_t N, double gamma,
+                           double lam, int iters, int dtype, void *loss, void *stream) {
+    if (N < 0 || iters < 0) return SIGK_EINVAL;
+    if (dtype != SIGK_F32 && dtype != SIGK_F64) return SIGK_EINVAL;
+    if (!(gamma > 0.0 && gamma < 1e300) || !(lam >= 0.0 && lam < 1e300)) return SIGK_EINVAL;
+    const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+    if (N == 0) {
+        if (loss && cudaMemsetAsync(loss, 0, (size_t)(iters + 1) * es, (cudaStream_t)stream) != cudaSuccess)
+            return SIGK_ECUDA;
+        return SIGK_OK;
+    }
+    if (!K || !alpha || !beta) return SIGK_EINVAL;
+    if (N > support_max_n(dtype)) return SIGK_EUNSUPPORTED;
+    return cuda_status(launch_support(K, alpha, beta, N, gamma, lam, iters, dtype, loss, (cudaStream_t)stream));
+}
+
 int sigk_stream_status(void *stream, void *ws) {
     if (!ws) return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? SIGK_OK : SIGK_ECUDA;
     int st = 0;

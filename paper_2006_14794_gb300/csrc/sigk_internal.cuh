@@ -223,6 +223,11 @@ cudaError_t launch_strip_bwd(const PairSrc &src, int64_t n, int lam, int dtype, 
                              cudaStream_t st, int64_t max_la, int64_t max_lb, int64_t rowsA,
                              int64_t rowsB, int coef_path);
 
+// Support reduction (support.cu): largest N one block holds, and the launch.
+int64_t support_max_n(int dtype);
+cudaError_t launch_support(const void *K, const void *alpha, void *beta, int64_t N, double gamma,
+                           double lam, int iters, int dtype, void *loss, cudaStream_t st);
+
 cudaError_t launch_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n,
                         int dtype, void *out, cudaStream_t st);
 cudaError_t launch_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *gKxx,

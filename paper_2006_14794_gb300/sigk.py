@@ -109,6 +109,8 @@ SIGNATURES = [
     ("sigk_pairs_backward_noalloc", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _int, _int,
                                            _vp, _vp, _vp]),
     ("sigk_mmd2", _int, [_vp, _vp, _vp, _i64, _i64, _int, _vp, _vp]),
+    ("sigk_support_reduction", _int, [_vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double, _int,
+                                      _int, _vp, _vp]),
     ("sigk_mmd2_backward", _int, [_vp, _i64, _i64, _int, _vp, _vp, _vp, _vp]),
     ("sigk_stream_status", _int, [_vp, _vp]),
     ("sigk_strerror", ctypes.c_char_p, [_int]),
@@ -392,6 +394,25 @@ def mmd2_backward(grad: torch.Tensor, m: int, n: int, dtype, device):
                                     gyy.data_ptr(), gxy.data_ptr(), _stream(device)),
            "sigk_mmd2_backward")
     return gxx, gyy, gxy
+
+
+def support_reduction(K: torch.Tensor, alpha: torch.Tensor, beta0: torch.Tensor, gamma: float,
+                      lam: float, iters: int):
+    """Moments-matching support reduction (Sec. 5.3): proximal gradient
+    descent on (alpha - beta)^T K (alpha - beta) + lam |beta|_1 from beta0.
+    Returns (beta after `iters` steps, loss history [iters + 1])."""
+    K, alpha = _dev(K, "K"), _dev(alpha, "alpha")
+    N = K.shape[0]
+    if K.shape != (N, N) or alpha.shape != (N,) or tuple(beta0.shape) != (N,):
+        raise ValueError("support_reduction wants K [N,N], alpha [N], beta0 [N]")
+    dt = _dtype_code(K)
+    alpha = alpha.to(K.dtype).contiguous()
+    beta = _dev(beta0, "beta0").to(K.dtype).clone().contiguous()
+    loss = torch.empty(iters + 1, dtype=K.dtype, device=K.device)
+    _check(lib().sigk_support_reduction(K.data_ptr(), alpha.data_ptr(), beta.data_ptr(), N, float(gamma),
+                                        float(lam), int(iters), dt, loss.data_ptr(), _stream(K.device)),
+           "sigk_support_reduction")
+    return beta, loss
 
 
 class SigKernelPairs(torch.autograd.Function):
