@@ -968,7 +968,9 @@ __global__ void __launch_bounds__(256) coef_tc_kernel(PairSrc src, const PairPla
 // and store it along its anti-diagonals (each diagonal W a contiguous run of
 // P).  Cells outside the grid are zero (zero increments).  Waits on the MMA
 // barrier are bounded: on expiry the block records SIGK_ETIMEOUT and stops.
-constexpr int TC5_M = 128, TC5_N = 128, TC5_SS = TC5_N + 2;   // shared tile stride: conflict-free diagonals
+// shared tile stride 132: rows start on 16-byte boundaries (vector stores of
+// the read-back) and a diagonal's reads, row stride 131 apart, hit distinct banks
+constexpr int TC5_M = 128, TC5_N = 128, TC5_SS = TC5_N + 4;
 constexpr int TC5_T = 256;                                     // threads: two per operand row
 
 __host__ __device__ inline int tc5_k(int64_t d) { return (int)(((d + 3) / 4 * 4 + 7) / 8 * 8); }
@@ -1004,7 +1006,7 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
     const float scale = 0.5f / (float)(1 << (2 * LAM));
     const unsigned idesc = tc5::idesc_tf32(TC5_M, TC5_N);
 
-    if (warp == 0) tc5::alloc(&tmem_slot, TC5_N);
+    if (warp == 0) tc5::alloc(&tmem_slot, 2 * TC5_N);   // two 128-column accumulators
     if (tid == 0) tc5::mbar_init(&mbar);
     tc5::fence_before();
     __syncthreads();
@@ -1043,24 +1045,30 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
             const int q = qfirst + row;
             tc5_fetch(nb, (col_ok(qfirst) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr, half, K, D4);
         }
-        for (int q0 = qfirst; q0 <= qlast; q0 += TC5_N) {
+        // chunk c covers columns q0 = qfirst + c TC5_N ..; its accumulator is
+        // TMEM columns (c & 1) TC5_N .., so chunk c + 1's MMAs run while chunk c
+        // is read back and written out
+        const int nch = (qlast - qfirst) / TC5_N + 1;
+        auto issue = [&](int c) {   // stage chunk c's column increments (in nb), start its MMAs
+            tc5::store_half(bh, bl, row, half, K, nb, 1.f);
+            tc5::fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc5::fence_after();
+                tc5::gemm_split(tmem + (unsigned)((c & 1) * TC5_N), ah, al, bh, bl, K, idesc, false);
+                tc5::commit(&mbar);
+            }
+        };
+        auto fetch_chunk = [&](int c) {
+            const int qn = qfirst + c * TC5_N, q = qn + row;
+            tc5_fetch(nb, (c < nch && col_ok(qn) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr, half,
+                      K, D4);
+        };
+        if (col_ok(qfirst)) issue(0);
+        fetch_chunk(1);
+        for (int c = 0; c < nch; ++c) {
+            const int q0 = qfirst + c * TC5_N;
             const bool zero = !col_ok(q0);
-            if (!zero) {
-                tc5::store_half(bh, bl, row, half, K, nb, 1.f);
-                tc5::fence_async_smem();
-                __syncthreads();
-                if (tid == 0) {
-                    tc5::fence_after();
-                    tc5::gemm_split(tmem, ah, al, bh, bl, K, idesc, false);
-                    tc5::commit(&mbar);
-                }
-            }
-            // fetch the next chunk's column increments while the MMAs run
-            {
-                const int qn = q0 + TC5_N, q = qn + row;
-                tc5_fetch(nb, (qn <= qlast && col_ok(qn) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr,
-                          half, K, D4);
-            }
             if (!zero) {
                 const bool ok = tc5::mbar_wait(&mbar, phase, max_wait);
                 if (__syncthreads_or(!ok)) {   // block-uniform
@@ -1070,28 +1078,41 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
                 }
                 phase ^= 1;
                 tc5::fence_after();
+            }
+            // the MMAs of chunk c are done with the column operand: chunk c + 1's can start
+            if (c + 1 < nch) {
+                if (col_ok(q0 + TC5_N)) issue(c + 1);
+                fetch_chunk(c + 2);
+            }
+            if (!zero) {
                 // D into the shared tile: warp w reads TMEM lanes 32 (w % 4) .., columns 64 (w / 4) ..
                 const int r = (warp & 3) * 32 + lane, cb = (warp >> 2) * 64;
+                const unsigned dc = tmem + (unsigned)((c & 1) * TC5_N);
 #pragma unroll
                 for (int c0 = 0; c0 < 64; c0 += 32) {
                     float v[32];
-                    tc5::ld32(tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(cb + c0), v);
+                    tc5::ld32(dc + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(cb + c0), v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) St[r * TC5_SS + cb + c0 + j] = scheme_coef(v[j], src.scheme);
+                    for (int j = 0; j < 32; j += 4)
+                        *reinterpret_cast<float4 *>(&St[r * TC5_SS + cb + c0 + j]) =
+                            make_float4(scheme_coef(v[j], src.scheme), scheme_coef(v[j + 1], src.scheme),
+                                        scheme_coef(v[j + 2], src.scheme), scheme_coef(v[j + 3], src.scheme));
                 }
                 tc5::fence_before();
             }
             __syncthreads();
-            // diagonals W = q + P of this chunk: P in [W - q0 - 127, W - q0] within the slice
-            const int wlo = q0 + P0 > 0 ? q0 + P0 : 0;
-            const int whi = q0 + P0 + TC5_N + TC5_M - 2 < pp.nw - 1 ? q0 + P0 + TC5_N + TC5_M - 2 : pp.nw - 1;
-            for (int W = wlo + warp; W <= whi; W += NW) {
-                int plo = W - q0 - (TC5_N - 1), phi = W - q0;
-                if (plo < P0) plo = P0;
-                if (phi > P0 + TC5_M - 1) phi = P0 + TC5_M - 1;
-                if (phi > CP - 1) phi = CP - 1;
-                for (int P = plo + lane; P <= phi; P += 32)
-                    blk[(int64_t)W * CP + P] = zero ? 0.f : St[(P - P0) * TC5_SS + (W - P - q0)];
+            // write-out along the diagonals W = q + P: warps 2b, 2b + 1 own slice
+            // rows Pl = 32 b + lane and take every other diagonal offset
+            // dd = Pl + (q - q0) of that row block, one coalesced store each
+            {
+                const int Pl = (warp & 3) * 32 + lane, P = P0 + Pl;
+                const int dlo = (warp & 3) * 32, dhi = dlo + 31 + TC5_N - 1;
+#pragma unroll 4
+                for (int dd = dlo + (warp >> 2); dd <= dhi; dd += 2) {
+                    const int ci = dd - Pl, W = q0 + P0 + dd;
+                    if (ci >= 0 && ci < TC5_N && W >= 0 && W < pp.nw && P < CP)
+                        blk[(int64_t)W * CP + P] = zero ? 0.f : St[Pl * TC5_SS + ci];
+                }
             }
             __syncthreads();
         }
@@ -1101,7 +1122,7 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
     if (failed) tc5::mbar_wait(&mbar, phase, max_wait);
     tc5::fence_before();
     __syncthreads();
-    if (warp == 0) tc5::dealloc(tmem, TC5_N);
+    if (warp == 0) tc5::dealloc(tmem, 2 * TC5_N);
 }
 
 template <typename T>
