@@ -647,13 +647,10 @@ struct BandAdjArgs {
     int nck;
     int64_t bq_stride;
     const float *gout;      // incoming gradient, indexed like the forward's outputs
-    float *gbar;            // dk/dc (unscaled), dense
-    int64_t g_ld;           // floats per gbar row
-    int64_t a_first;        // first A path of this launch (rows of gbar count from it)
-    int gram;               // 1: gbar columns hold every B path (Gram), 0: one block per pair
+    float *gband;           // dk/dc (unscaled) in the band layout, TperR + 1 slots per pair
+                            // (slot TperR: the pair's tail), unpacked by band_gbar_kernel
     int64_t n_pairs, ppw;
     int TperR, NQ, NQV, vrows, nx, ny;
-    float *junk;            // 32 floats per warp: the target of stores that fall outside the grid
 };
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -670,6 +667,75 @@ __device__ __forceinline__ void cp_async(void *dst, const void *src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// A window row of NG values (NH float2: groups g, g + NH) to 16-byte aligned
+// band memory.
+template <int NG>
+__device__ __forceinline__ void store_window(float *dst, const float2 (&v)[NG / 2]) {
+    if constexpr (NG == 8) {
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        reinterpret_cast<float4 *>(dst)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    } else if constexpr (NG == 4) {
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    } else {
+        reinterpret_cast<float2 *>(dst)[0] = v[0];
+    }
+}
+
+// dk/dc from the adjoint's band layout into the dense Gbar the chain-rule
+// contractions read: [row path * nx][column path * ny] (Gram: every column
+// path of the call; pairs: one nx x ny block per pair).  Pair k's cell (P, Q)
+// = (l NG + g, Q) is in slot (k, pos) window w with pos NG + w = Q + g (slot
+// TperR: the tail).  A block takes GB_POS positions of one pair: it stages
+// those slots and the next one in shared memory (coalesced), then writes the
+// real cells of columns Q in [pos0 NG, (pos0 + GB_POS) NG) row by row, each
+// row a contiguous run.
+constexpr int GB_POS = 4;
+constexpr int GB_THREADS = 256;
+
+struct BandGbarArgs {
+    PairSrc src;
+    const float *gband;
+    float *gbar;
+    int64_t g_ld;           // floats per gbar row
+    int64_t a_first;        // first A path of this launch (rows of gbar count from it)
+    int gram;               // 1: gbar columns hold every B path of the call
+    int64_t n_pairs;
+    int TperR, NQV, vrows, nx, ny;
+};
+
+template <int NG>
+__global__ void __launch_bounds__(GB_THREADS) band_gbar_kernel(BandGbarArgs a) {
+    constexpr int SLOT = NG * NG;
+    constexpr int NP = 32 * NG;                 // padded rows
+    constexpr int SPAN = GB_POS * NG;           // columns per block task
+    __shared__ __align__(16) float sl[(GB_POS + 1) * 32 * SLOT];
+    const int ngroups = (a.TperR + GB_POS - 1) / GB_POS;
+    const int64_t tasks = a.n_pairs * ngroups;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const int64_t k = t / ngroups;
+        const int pos0 = (int)(t - k * ngroups) * GB_POS;
+        const int npos = min(GB_POS + 1, a.TperR + 1 - pos0);   // slots pos0 .. pos0 + npos - 1
+        __syncthreads();
+        const float4 *src = reinterpret_cast<const float4 *>(a.gband + ((k * (a.TperR + 1) + pos0) * 32) * (int64_t)SLOT);
+        for (int v = threadIdx.x; v < npos * 32 * SLOT / 4; v += GB_THREADS)
+            reinterpret_cast<float4 *>(sl)[v] = src[v];
+        __syncthreads();
+        const PairRef pr = pair_ref(a.src, k);
+        const int64_t ia = pr.a_row0 / a.src.La - a.a_first;
+        const int64_t jb = a.gram ? pr.b_row0 / a.src.Lb : 0;
+        float *base = a.gbar + ia * a.nx * a.g_ld + jb * a.ny;
+        const int Qlo = pos0 * NG;
+        for (int v = threadIdx.x; v < NP * SPAN; v += GB_THREADS) {
+            const int P = v / SPAN, Q = Qlo + (v - (v / SPAN) * SPAN);
+            const int p = P - a.vrows, q = Q - a.NQV;
+            if (p < 0 || p >= a.nx || q < 0 || q >= a.ny) continue;
+            const int l = P / NG, g = P - (P / NG) * NG;
+            const int tq = Q + g, pos = tq / NG, w = tq - (tq / NG) * NG;   // pos - pos0 in [0, npos)
+            base[(int64_t)p * a.g_ld + q] = sl[((pos - pos0) * 32 + l) * SLOT + w * NG + band_gpos<NG>(g)];
+        }
+    }
+}
 
 template <int R, int LAM>
 __host__ __device__ constexpr int adj_warp_floats() {
@@ -699,7 +765,6 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, 6) chain_band_adj_kernel(Band
     float *ring = adj_sm + (size_t)warp * adj_warp_floats<R, LAM>();
     float *bqs = ring + 2 * 32 * SLOT;
     const float *bq = a.botq + gw * a.bq_stride;
-    float *junk = a.junk + gw * 32 + lane;
     auto chunk = [&](int c) { return NCH >= 8 ? (c ^ (lane & 7)) : (NCH >= 2 ? (c ^ (lane & (NCH - 1))) : c); };
     auto lane_slot = [&](int buf) { return ring + ((size_t)buf * 32 + lane) * SLOT; };
 
@@ -757,13 +822,6 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, 6) chain_band_adj_kernel(Band
 #pragma unroll
         for (int g = 0; g < NH; ++g) c[g] = make_float2(v[2 * g], v[2 * g + 1]);   // groups g, g + NH
     };
-    // start of pair kk's dk/dc block in gbar
-    auto gbase = [&](int kk) -> int64_t {
-        const PairRef pr = pair_ref(a.src, k0 + kk);
-        const int64_t ia = pr.a_row0 / a.src.La - a.a_first;
-        const int64_t jb = a.gram ? pr.b_row0 / a.src.Lb : 0;
-        return ia * a.nx * a.g_ld + jb * a.ny;
-    };
 
     // forward state as (K, -Q): undoing a step then needs no negation
     float2 KP[H], QN[H], A[H], V[H];
@@ -791,9 +849,6 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, 6) chain_band_adj_kernel(Band
             cp_commit();
         }
     }
-    int cached_kl = -1000000;
-    int64_t row_cur = 0, row_prev = 0;     // gbar address of (row lane*NG - vrows, column -NQV) of pairs kl, kl-1
-    const int gmin = a.vrows - lane * NG;  // groups g >= gmin are real rows
 
     for (int64_t m = mlast; m >= 0; --m) {
         if (m != mlast && --pos < 0) {
@@ -815,12 +870,12 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, 6) chain_band_adj_kernel(Band
             }
         }
         const bool cur_ok = kl >= 0 && kl < np, prev_ok = kl >= 1 && kl <= np;
-        if (kl != cached_kl) {
-            cached_kl = kl;
-            const int64_t off = (int64_t)(lane * NG - a.vrows) * a.g_ld - a.NQV;
-            if (cur_ok) row_cur = gbase(kl) + off;
-            if (prev_ok) row_prev = gbase(kl - 1) + off + a.NQ;
-        }
+        // the lane's slot rows in the dk/dc band: this pair's position, and at
+        // position 0 also the previous pair's tail slot (its cells with w < g)
+        float *gs_cur = cur_ok ? a.gband + (((k0 + kl) * (TperR + 1) + pos) * 32 + lane) * (int64_t)SLOT : nullptr;
+        float *gs_prev = (trans && prev_ok)
+                             ? a.gband + (((k0 + kl - 1) * (TperR + 1) + TperR) * 32 + lane) * (int64_t)SLOT
+                             : nullptr;
         // rows turning over in this macro-step leave pair kl - 1 in reverse;
         // lane 31 seeds that pair's incoming gradient at its corner
         float gseed = 0.f;
@@ -913,18 +968,18 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, 6) chain_band_adj_kernel(Band
                 if (lane == 31) qd = -qbot;
                 QN[H - 1] = make_float2(t0.y, qd);
             }
-            // window w's cells are complete: (P, Q) = (lane*NG + g, pos*NG + w - g)
-            const int Q0 = pos * NG + w;
+            // window w's cells are complete: (P, Q) = (lane*NG + g, pos*NG + w - g),
+            // in the order of the band's groups (g, g + NH side by side): one
+            // vector store of the window row per slot
+            if (a.src.scheme != SIGK_SCHEME_EXPLICIT) {   // dk/dc' -> dk/dc of the cell's coefficient
 #pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                float v = g < NH ? gN[g].x : gN[g - NH].y;
-                if (a.src.scheme != SIGK_SCHEME_EXPLICIT)   // dk/dc' -> dk/dc of the cell's coefficient
-                    v *= scheme_dcoef(g < NH ? CN[g].x : CN[g - NH].y, a.src.scheme);
-                const int Q = Q0 - g;
-                const bool ok = g >= gmin && (Q >= 0 ? (cur_ok && Q >= a.NQV) : prev_ok);
-                float *dst = a.gbar + (Q >= 0 ? row_cur : row_prev) + (int64_t)g * a.g_ld + Q;
-                *(ok ? dst : junk) = v;   // no branch: cells outside the grid go to the warp's junk slot
+                for (int g = 0; g < NH; ++g) {
+                    gN[g].x *= scheme_dcoef(CN[g].x, a.src.scheme);
+                    gN[g].y *= scheme_dcoef(CN[g].y, a.src.scheme);
+                }
             }
+            if (gs_cur) store_window<NG>(gs_cur + w * NG, gN);
+            if (gs_prev) store_window<NG>(gs_prev + w * NG, gN);
 #pragma unroll
             for (int g = 0; g < NH; ++g) { gN[g] = gO[g]; gO[g] = make_float2(0.f, 0.f); CNP[g] = CN[g]; }
         }
@@ -1273,8 +1328,8 @@ int64_t up4(int64_t v) { return (v + 3) / 4 * 4; }
 // for any pairs-per-warp split (they are checked against the actual split at
 // launch).
 struct BwdRegions {
-    int64_t band, gbar, ckpt, exitk, botq, incA, incB, dincA, dincB, part, junk;
-    int64_t total() const { return band + gbar + ckpt + exitk + botq + incA + incB + dincA + dincB + part + junk; }
+    int64_t band, gbar, ckpt, exitk, botq, incA, incB, dincA, dincB, part, gband;
+    int64_t total() const { return band + gbar + ckpt + exitk + botq + incA + incB + dincA + dincB + part + gband; }
 };
 
 BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
@@ -1296,7 +1351,8 @@ BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
     r.dincB = r.incB;
     // split-K partial tiles of the Gram's contractions
     r.part = gram ? up4((int64_t)GEMM_MAX_SPLIT * (nA * nx > nB * ny ? nA * nx : nB * ny) * d) : 0;
-    r.junk = (nbp + 1) * 32;
+    // the adjoint's dk/dc in the band layout: TperR + 1 slots per pair
+    r.gband = up4(nbp * ((int64_t)p.TperR + 1) * 32 * p.NG * p.NG);
     return r;
 }
 
@@ -1352,7 +1408,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
     float *dincA = incB + rg.incB;
     float *dincB = dincA + rg.dincA;
     float *part = dincB + rg.dincB;
-    float *junk = part + rg.part;
+    float *gband = part + rg.part;
     const int64_t nBall = gram ? src0.nb : 0;
     if (gram) {
         // every column path is used by every launch: increments once, gradients summed
@@ -1417,10 +1473,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         ad.nck = f.nck;
         ad.bq_stride = f.bq_stride;
         ad.gout = gout;
-        ad.gbar = gbar;
-        ad.g_ld = gram ? nBall * ny : ny;
-        ad.a_first = a0;
-        ad.gram = gram ? 1 : 0;
+        ad.gband = gband;
         ad.n_pairs = m;
         ad.ppw = f.ppw;
         ad.TperR = p.TperR;
@@ -1429,7 +1482,6 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         ad.vrows = p.vrows;
         ad.nx = (int)nx;
         ad.ny = (int)ny;
-        ad.junk = junk;
         launched = false;
 #define X(r, l, mb)                                                  \
         if (p.R == r && p.lam == l) {                                \
@@ -1439,6 +1491,28 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         SIGK_BAND_CASES(X)
 #undef X
         if (!launched) return cudaErrorInvalidValue;
+        // 3b. dk/dc from the band layout into the dense Gbar
+        {
+            BandGbarArgs gb;
+            gb.src = src;
+            gb.gband = gband;
+            gb.gbar = gbar;
+            gb.g_ld = gram ? nBall * ny : ny;
+            gb.a_first = a0;
+            gb.gram = gram ? 1 : 0;
+            gb.n_pairs = m;
+            gb.TperR = p.TperR;
+            gb.NQV = p.NQV;
+            gb.vrows = p.vrows;
+            gb.nx = (int)nx;
+            gb.ny = (int)ny;
+            const int64_t tasks = m * ((p.TperR + GB_POS - 1) / GB_POS);
+            const int ggrid = (int)(tasks < (int64_t)sms * 8 ? tasks : (int64_t)sms * 8);
+            if (p.NG == 8) band_gbar_kernel<8><<<ggrid, GB_THREADS, 0, st>>>(gb);
+            else if (p.NG == 4) band_gbar_kernel<4><<<ggrid, GB_THREADS, 0, st>>>(gb);
+            else band_gbar_kernel<2><<<ggrid, GB_THREADS, 0, st>>>(gb);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         // 4. increments of this launch's paths
         band_inc_kernel<<<sms * 4, 256, 0, st>>>((const float *)src.A + a0 * src.La * d, nA, src.La, d, incA);
         if (!gram)
