@@ -102,6 +102,15 @@ void band_batch(const BandPlan &bp, int64_t n, int64_t &nb, int64_t &bytes) {
         bytes = band_bytes(bp, nb);
     }
 }
+// The same with the solution surface's band-layout values after the band.
+void band_surface_batch(const BandPlan &bp, int64_t n, int64_t &nb, int64_t &bytes) {
+    nb = n;
+    bytes = band_surface_bytes(bp, nb);
+    while (nb > 1 && bytes > STRIP_WS_CAP) {
+        nb = (nb + 1) / 2;
+        bytes = band_surface_bytes(bp, nb);
+    }
+}
 
 Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, ChainPlan *cp,
                     int rows_per_lane = 0, BandPlan *bpo = nullptr) {
@@ -360,7 +369,7 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         BandPlan bp;
         if (!surface_uses_band(ss, dyadic_order, dtype, rec_of(opts), rows_of(opts), bp)) return 0;
         int64_t nb, need;
-        band_batch(bp, n_pairs, nb, need);
+        band_surface_batch(bp, n_pairs, nb, need);
         return (size_t)need;
     }
     if (op == SIGK_OP_PAIRS_BACKWARD || op == SIGK_OP_GRAM_BACKWARD) {
@@ -529,13 +538,17 @@ int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64
     if (rec == SIGK_REC_BAND && !band) return SIGK_EUNSUPPORTED;
     if (band) {
         int64_t nb, need;
-        band_batch(bp, B, nb, need);
+        band_surface_batch(bp, B, nb, need);
         if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
     }
     // boundary nodes (row and column 0) are 1; the sweeps write the others
-    cudaError_t e = launch_fill_one(surf, B * L * M, dtype, st);
+    if (L < 2 || M < 2) {
+        cudaError_t e = launch_fill_one(surf, B * L * M, dtype, st);
+        if (e != cudaSuccess) return cuda_status(e);
+        return cuda_status(launch_fill_one(out, B, dtype, st));
+    }
+    cudaError_t e = launch_surface_border(surf, B, L, M, dtype, st);
     if (e != cudaSuccess) return cuda_status(e);
-    if (L < 2 || M < 2) return cuda_status(launch_fill_one(out, B, dtype, st));
     if (!band) return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, st, surf));
     // rows refine the shorter path: node (i, j) of the sweep is surface (i, j),
     // or (j, i) when X and Y swap places
@@ -547,7 +560,7 @@ int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64
         sa = 1; sb = M;
     }
     int64_t nb, need;
-    band_batch(bp, B, nb, need);
+    band_surface_batch(bp, B, nb, need);
     for (int64_t k0 = 0; k0 < B; k0 += nb) {
         PairSrc s3 = s2;
         s3.kbase = k0;

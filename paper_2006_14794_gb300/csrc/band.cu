@@ -213,11 +213,11 @@ struct BandArgs {
     float *botq;     // [warp][steps + 1]: Q of the warp's last row before each step
     int nck;         // checkpoint slots per warp
     int64_t bq_stride;
-    // the solution surface on the sample grid (SURF instances): node (i, j) of
-    // the launch's pair k at surf[(kbase + k) s_pair + i s_a + j s_b]
-    float *surf;
-    int64_t s_pair, s_a, s_b;
-    int vtop, vpad;  // virtual refined rows above / columns left of each pair
+    // the solution surface on the sample grid (SURF instances): each lane's
+    // values at the sample-grid nodes, a window row per window, in the band
+    // layout with TperR + 1 slots per pair (slot TperR: the tail); unpacked by
+    // band_gbar_kernel in surface mode
+    float *sband;
 };
 
 constexpr int BAND_CK = 8;   // macro-steps between checkpoints of the forward state
@@ -238,11 +238,25 @@ __device__ __forceinline__ void load_window(float (&v)[NG], const float *p) {
     }
 }
 
+// A window row of NG values (NH float2: groups g, g + NH) to 16-byte aligned
+// band memory.
+template <int NG>
+__device__ __forceinline__ void store_window(float *dst, const float2 (&v)[NG / 2]) {
+    if constexpr (NG == 8) {
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        reinterpret_cast<float4 *>(dst)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    } else if constexpr (NG == 4) {
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    } else {
+        reinterpret_cast<float2 *>(dst)[0] = v[0];
+    }
+}
+
 // The sweep: fwd_chain.cu's chain_f32_kernel with its staging and dot
 // products replaced by one coefficient vector per window, prefetched one
 // macro-step ahead into the registers the window has just consumed.
 //
-// SURF: also store the solution at the sample-grid nodes (the surface).  Row
+// SURF: also keep the solution at the sample-grid nodes (the surface).  Row
 // r of lane l, padded row R l + r, is refined node row a = R l + r + 1 - vtop;
 // at step j of position pos it computes padded column pos R + j - r (the
 // previous pair's when negative), node column b = that + 1 - vpad.  vtop and
@@ -250,6 +264,10 @@ __device__ __forceinline__ void load_window(float (&v)[NG], const float *p) {
 // when a and b are: r % 2^lambda = 2^lambda - 1 (the last row of each coarse
 // group), and then b = j - r + 1 = j + 2 (mod 2^lambda), i.e. at step
 // j % 2^lambda = 2^lambda - 2 of each window (0 for dyadic orders 0 and 1).
+// There, group g of window w holds node (p + 1, q) (dyadic order 0: (p + 1,
+// q + 1)) of the coarse cell (p, q) = (P - vrows, Q - NQV), (P, Q) = (lane NG
+// + g, pos NG + w - g): the band layout's cell, so the lane stores its NG
+// values as one window row.
 template <int R, int LAM, int MINB, bool SAVE, bool SURF = false>
 __global__ void __launch_bounds__(BAND_WARPS * 32, MINB) chain_band_kernel(BandArgs a) {
     constexpr int S = 1 << LAM;
@@ -350,21 +368,6 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, MINB) chain_band_kernel(BandA
                     const float2 qn = __ffma2_rn(c, sum, qu);
                     KP[i] = __fadd2_rn(KP[i], qn);
                     QP[i] = qn;
-                    if constexpr (SURF) {
-                        constexpr int JS = S >= 2 ? S - 2 : 0;
-                        if (jj == JS && s1 == S - 1) {
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const int r = i + h * H;
-                                int bp = pos * R + w * S + JS - r, kk = kl;
-                                if (bp < 0) { bp += TperR * R; --kk; }
-                                const int an = R * lane + r + 1 - a.vtop, bn = bp + 1 - a.vpad;
-                                if (kk >= 0 && kk < np && an > 0 && bn > 0)
-                                    a.surf[(a.src.kbase + k0 + kk) * a.s_pair + (int64_t)(an >> LAM) * a.s_a +
-                                           (int64_t)(bn >> LAM) * a.s_b] = h ? KP[i].y : KP[i].x;
-                            }
-                        }
-                    }
                     if (i == H - 1) {
                         shK = __shfl_up_sync(FULL, KP[i].y, 1);
                         shQ = __shfl_up_sync(FULL, QP[i].y, 1);
@@ -376,6 +379,21 @@ __global__ void __launch_bounds__(BAND_WARPS * 32, MINB) chain_band_kernel(BandA
                                 if (pr.out1 >= 0) a.out[pr.out1] = KP[i].y;
                             }
                         }
+                    }
+                }
+                if constexpr (SURF) {
+                    constexpr int JS = S >= 2 ? S - 2 : 0;
+                    if (jj == JS) {
+                        // rows g S + S - 1 (packed with g + NH) are at their group's node
+                        float2 sv[NH];
+#pragma unroll
+                        for (int g = 0; g < NH; ++g) sv[g] = KP[g * S + S - 1];
+                        if (kl >= 0 && kl < np)
+                            store_window<NG>(a.sband + (((k0 + kl) * (TperR + 1) + pos) * 32 + lane) * (int64_t)SLOT +
+                                                 w * NG, sv);
+                        if (trans && kl >= 1 && kl <= np)   // the previous pair's tail
+                            store_window<NG>(a.sband + (((k0 + kl - 1) * (TperR + 1) + TperR) * 32 + lane) *
+                                                           (int64_t)SLOT + w * NG, sv);
                     }
                 }
                 if (SAVE && lane == 31) bq[m * R + j + 1] = QP[H - 1].y;
@@ -668,20 +686,6 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// A window row of NG values (NH float2: groups g, g + NH) to 16-byte aligned
-// band memory.
-template <int NG>
-__device__ __forceinline__ void store_window(float *dst, const float2 (&v)[NG / 2]) {
-    if constexpr (NG == 8) {
-        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-        reinterpret_cast<float4 *>(dst)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-    } else if constexpr (NG == 4) {
-        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    } else {
-        reinterpret_cast<float2 *>(dst)[0] = v[0];
-    }
-}
-
 // dk/dc from the adjoint's band layout into the dense Gbar the chain-rule
 // contractions read: [row path * nx][column path * ny] (Gram: every column
 // path of the call; pairs: one nx x ny block per pair).  Pair k's cell (P, Q)
@@ -692,6 +696,11 @@ __device__ __forceinline__ void store_window(float *dst, const float2 (&v)[NG / 
 // row a contiguous run.
 constexpr int GB_POS = 4;
 constexpr int GB_THREADS = 256;
+// position groups per pair: the columns Q < NQ = TperR NG, and for the
+// surface also Q = NQ (its last node column, in the tail slot)
+__host__ __device__ inline int gb_groups(int TperR, bool surf) {
+    return (TperR + (surf ? 1 : 0) + GB_POS - 1) / GB_POS;
+}
 
 struct BandGbarArgs {
     PairSrc src;
@@ -702,6 +711,13 @@ struct BandGbarArgs {
     int gram;               // 1: gbar columns hold every B path of the call
     int64_t n_pairs;
     int TperR, NQV, vrows, nx, ny;
+    // surface mode (s_pair > 0): the band holds the sweep's values at the
+    // sample-grid nodes, node (p + 1, q + q_off) of cell (p, q) (q_off = 1 at
+    // dyadic order 0, where the stored node is the cell's lower-right corner;
+    // 0 above, the lower-left one, the last column coming from the tail slot);
+    // they go to gbar[(kbase + k) s_pair + (p + 1) s_a + (q + q_off) s_b]
+    int64_t s_pair, s_a, s_b;
+    int q_off;
 };
 
 template <int NG>
@@ -710,7 +726,7 @@ __global__ void __launch_bounds__(GB_THREADS) band_gbar_kernel(BandGbarArgs a) {
     constexpr int NP = 32 * NG;                 // padded rows
     constexpr int SPAN = GB_POS * NG;           // columns per block task
     __shared__ __align__(16) float sl[(GB_POS + 1) * 32 * SLOT];
-    const int ngroups = (a.TperR + GB_POS - 1) / GB_POS;
+    const int ngroups = gb_groups(a.TperR, a.s_pair > 0);
     const int64_t tasks = a.n_pairs * ngroups;
     for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
         const int64_t k = t / ngroups;
@@ -721,18 +737,29 @@ __global__ void __launch_bounds__(GB_THREADS) band_gbar_kernel(BandGbarArgs a) {
         for (int v = threadIdx.x; v < npos * 32 * SLOT / 4; v += GB_THREADS)
             reinterpret_cast<float4 *>(sl)[v] = src[v];
         __syncthreads();
-        const PairRef pr = pair_ref(a.src, k);
-        const int64_t ia = pr.a_row0 / a.src.La - a.a_first;
-        const int64_t jb = a.gram ? pr.b_row0 / a.src.Lb : 0;
-        float *base = a.gbar + ia * a.nx * a.g_ld + jb * a.ny;
+        const bool surf = a.s_pair > 0;
+        float *base;
+        int64_t sr = a.g_ld, sc = 1;
+        if (surf) {
+            base = a.gbar + (a.src.kbase + k) * a.s_pair + a.s_a;   // node row p + 1
+            sr = a.s_a;
+            sc = a.s_b;
+        } else {
+            const PairRef pr = pair_ref(a.src, k);
+            const int64_t ia = pr.a_row0 / a.src.La - a.a_first;
+            const int64_t jb = a.gram ? pr.b_row0 / a.src.Lb : 0;
+            base = a.gbar + ia * a.nx * a.g_ld + jb * a.ny;
+        }
+        const int qlo = surf ? 1 - a.q_off : 0, qhi = surf ? a.ny - a.q_off : a.ny - 1;
+        if (surf) base += (int64_t)a.q_off * sc;
         const int Qlo = pos0 * NG;
         for (int v = threadIdx.x; v < NP * SPAN; v += GB_THREADS) {
             const int P = v / SPAN, Q = Qlo + (v - (v / SPAN) * SPAN);
             const int p = P - a.vrows, q = Q - a.NQV;
-            if (p < 0 || p >= a.nx || q < 0 || q >= a.ny) continue;
+            if (p < 0 || p >= a.nx || q < qlo || q > qhi) continue;
             const int l = P / NG, g = P - (P / NG) * NG;
             const int tq = Q + g, pos = tq / NG, w = tq - (tq / NG) * NG;   // pos - pos0 in [0, npos)
-            base[(int64_t)p * a.g_ld + q] = sl[((pos - pos0) * 32 + l) * SLOT + w * NG + band_gpos<NG>(g)];
+            base[(int64_t)p * sr + (int64_t)q * sc] = sl[((pos - pos0) * 32 + l) * SLOT + w * NG + band_gpos<NG>(g)];
         }
     }
 }
@@ -1169,6 +1196,16 @@ int64_t band_bytes(const BandPlan &p, int64_t n_pairs) {
     return 256 + (int64_t)sizeof(float) * (n_pairs * p.TperR + 1) * p.slot_floats;
 }
 
+// The surface's band-layout values (TperR + 1 slots per pair) after the band:
+// their float offset from the band's start, and the whole workspace.
+int64_t band_surface_offset(const BandPlan &p, int64_t n_pairs) {
+    return ((n_pairs * p.TperR + 1) * p.slot_floats + 63) / 64 * 64;
+}
+int64_t band_surface_bytes(const BandPlan &p, int64_t n_pairs) {
+    return 256 + (int64_t)sizeof(float) *
+                     (band_surface_offset(p, n_pairs) + n_pairs * (p.TperR + 1) * p.slot_floats);
+}
+
 namespace {
 // The band coefficients: the FMA contraction, or on request (coef_path 3,
 // d <= 64) the tcgen05 kernel.  The FMA kernel is the default: it runs two
@@ -1281,25 +1318,45 @@ cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pai
     a.n_pairs = n_pairs;
     a.ppw = (n_pairs + warps - 1) / warps;
     a.TperR = p.TperR;
-    a.surf = surf;
-    a.s_pair = s_pair;
-    a.s_a = s_a;
-    a.s_b = s_b;
-    a.vtop = p.vrows << p.lam;
-    a.vpad = p.NQV << p.lam;
+    // the surface's band-layout values follow the coefficient band in the workspace
+    a.sband = surf ? band + band_surface_offset(p, n_pairs) : nullptr;
     const int64_t nwarps = (n_pairs + a.ppw - 1) / a.ppw;
     const int grid = (int)((nwarps + BAND_WARPS - 1) / BAND_WARPS);
+    bool launched = false;
 #define X(r, l, mb)                                                                  \
     if (p.R == r && p.lam == l) {                                                    \
         if (surf)                                                                    \
             chain_band_kernel<r, l, mb, false, true><<<grid, BAND_WARPS * 32, 0, st>>>(a); \
         else                                                                         \
             chain_band_kernel<r, l, mb, false><<<grid, BAND_WARPS * 32, 0, st>>>(a);       \
-        return cudaGetLastError();                                                   \
+        launched = true;                                                             \
     }
     SIGK_BAND_CASES(X)
 #undef X
-    return cudaErrorInvalidValue;
+    if (!launched) return cudaErrorInvalidValue;
+    if ((e = cudaGetLastError()) != cudaSuccess || !surf) return e;
+    // the surface from the band layout into [pair][L][M]
+    BandGbarArgs gb;
+    memset(&gb, 0, sizeof(gb));
+    gb.src = src;
+    gb.gband = a.sband;
+    gb.gbar = surf;
+    gb.n_pairs = n_pairs;
+    gb.TperR = p.TperR;
+    gb.NQV = p.NQV;
+    gb.vrows = p.vrows;
+    gb.nx = (int)(src.La - 1);
+    gb.ny = (int)(src.Lb - 1);
+    gb.s_pair = s_pair;
+    gb.s_a = s_a;
+    gb.s_b = s_b;
+    gb.q_off = p.lam == 0 ? 1 : 0;
+    const int64_t tasks = n_pairs * gb_groups(p.TperR, true);
+    const int ggrid = (int)(tasks < (int64_t)sms * 8 ? tasks : (int64_t)sms * 8);
+    if (p.NG == 8) band_gbar_kernel<8><<<ggrid, GB_THREADS, 0, st>>>(gb);
+    else if (p.NG == 4) band_gbar_kernel<4><<<ggrid, GB_THREADS, 0, st>>>(gb);
+    else band_gbar_kernel<2><<<ggrid, GB_THREADS, 0, st>>>(gb);
+    return cudaGetLastError();
 }
 
 }  // namespace sigk
@@ -1494,6 +1551,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         // 3b. dk/dc from the band layout into the dense Gbar
         {
             BandGbarArgs gb;
+            memset(&gb, 0, sizeof(gb));   // s_pair = 0: the dense Gbar, not the surface
             gb.src = src;
             gb.gband = gband;
             gb.gbar = gbar;
@@ -1506,7 +1564,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
             gb.vrows = p.vrows;
             gb.nx = (int)nx;
             gb.ny = (int)ny;
-            const int64_t tasks = m * ((p.TperR + GB_POS - 1) / GB_POS);
+            const int64_t tasks = m * gb_groups(p.TperR, false);
             const int ggrid = (int)(tasks < (int64_t)sms * 8 ? tasks : (int64_t)sms * 8);
             if (p.NG == 8) band_gbar_kernel<8><<<ggrid, GB_THREADS, 0, st>>>(gb);
             else if (p.NG == 4) band_gbar_kernel<4><<<ggrid, GB_THREADS, 0, st>>>(gb);

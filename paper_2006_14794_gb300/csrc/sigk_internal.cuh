@@ -169,9 +169,13 @@ struct BandPlan {
 // Geometry only (no device query); false when the band form has no instance.
 bool band_geometry(int64_t La, int64_t Lb, int lam, int rows_per_lane, BandPlan &p);
 int64_t band_bytes(const BandPlan &p, int64_t n_pairs);
+// with the solution surface: the band, then the surface values in the band layout
+int64_t band_surface_offset(const BandPlan &p, int64_t n_pairs);
+int64_t band_surface_bytes(const BandPlan &p, int64_t n_pairs);
 // coef_path 3: coefficients on tcgen05 (d <= 64); otherwise the FMA contraction
 // surf (optional): the solution surface, node (i, j) of pair k (of the call)
-// at surf[k s_pair + i s_a + j s_b]; nodes on row or column 0 are not written
+// at surf[k s_pair + i s_a + j s_b]; nodes on row or column 0 are not written.
+// It needs band_surface_bytes of workspace instead of band_bytes.
 cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pairs, float *out,
                             void *ws, cudaStream_t st, int coef_path, float *surf = nullptr,
                             int64_t s_pair = 0, int64_t s_a = 0, int64_t s_b = 0);
@@ -189,6 +193,8 @@ cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype
                          cudaStream_t st, void *surf = nullptr);
 
 cudaError_t launch_fill_one(void *out, int64_t n, int dtype, cudaStream_t st);
+// row 0 and column 0 of B solution surfaces [L][M] set to 1
+cudaError_t launch_surface_border(void *surf, int64_t B, int64_t L, int64_t M, int dtype, cudaStream_t st);
 
 bool bwd_plain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, int dtype,
                     int64_t &grid, int64_t &slot_bytes, int64_t &smem);
