@@ -693,7 +693,7 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // TperR: the tail).  A block takes GB_POS positions of one pair: it stages
 // those slots and the next one in shared memory (coalesced), then writes the
 // real cells of columns Q in [pos0 NG, (pos0 + GB_POS) NG) row by row, each
-// row a contiguous run.
+// row a contiguous run (window rows staged NG + 1 floats apart).
 constexpr int GB_POS = 4;
 constexpr int GB_THREADS = 256;
 // position groups per pair: the columns Q < NQ = TperR NG, and for the
@@ -725,7 +725,10 @@ __global__ void __launch_bounds__(GB_THREADS) band_gbar_kernel(BandGbarArgs a) {
     constexpr int SLOT = NG * NG;
     constexpr int NP = 32 * NG;                 // padded rows
     constexpr int SPAN = GB_POS * NG;           // columns per block task
-    __shared__ __align__(16) float sl[(GB_POS + 1) * 32 * SLOT];
+    constexpr int WS = NG + 1;                  // staged window row stride: consecutive
+                                                // columns of a row hit distinct banks
+    constexpr int SS = NG * WS;                 // staged slot stride
+    __shared__ float sl[(GB_POS + 1) * 32 * SS];
     const int ngroups = gb_groups(a.TperR, a.s_pair > 0);
     const int64_t tasks = a.n_pairs * ngroups;
     for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
@@ -734,8 +737,15 @@ __global__ void __launch_bounds__(GB_THREADS) band_gbar_kernel(BandGbarArgs a) {
         const int npos = min(GB_POS + 1, a.TperR + 1 - pos0);   // slots pos0 .. pos0 + npos - 1
         __syncthreads();
         const float4 *src = reinterpret_cast<const float4 *>(a.gband + ((k * (a.TperR + 1) + pos0) * 32) * (int64_t)SLOT);
-        for (int v = threadIdx.x; v < npos * 32 * SLOT / 4; v += GB_THREADS)
-            reinterpret_cast<float4 *>(sl)[v] = src[v];
+        for (int v = threadIdx.x; v < npos * 32 * SLOT / 4; v += GB_THREADS) {
+            const float4 x = src[v];
+            const int slot = v / (SLOT / 4), e = (v - slot * (SLOT / 4)) * 4;
+            float *d = sl + slot * SS;
+            d[(e / NG) * WS + e % NG] = x.x;
+            d[((e + 1) / NG) * WS + (e + 1) % NG] = x.y;
+            d[((e + 2) / NG) * WS + (e + 2) % NG] = x.z;
+            d[((e + 3) / NG) * WS + (e + 3) % NG] = x.w;
+        }
         __syncthreads();
         const bool surf = a.s_pair > 0;
         float *base;
@@ -759,7 +769,7 @@ __global__ void __launch_bounds__(GB_THREADS) band_gbar_kernel(BandGbarArgs a) {
             if (p < 0 || p >= a.nx || q < qlo || q > qhi) continue;
             const int l = P / NG, g = P - (P / NG) * NG;
             const int tq = Q + g, pos = tq / NG, w = tq - (tq / NG) * NG;   // pos - pos0 in [0, npos)
-            base[(int64_t)p * sr + (int64_t)q * sc] = sl[((pos - pos0) * 32 + l) * SLOT + w * NG + band_gpos<NG>(g)];
+            base[(int64_t)p * sr + (int64_t)q * sc] = sl[((pos - pos0) * 32 + l) * SS + w * WS + band_gpos<NG>(g)];
         }
     }
 }
