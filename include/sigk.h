@@ -93,8 +93,9 @@ typedef struct {
     int rows_per_lane;/* schedule: refined rows per lane (4, 8 or 16; 0 =
                          default).  Chained and band kernels: the band height
                          32 x rows_per_lane (default the smallest that fits).
-                         Strip path (f32: 16 by default, 8 for dyadic order
-                         <= 2, 4 for <= 1; f64: 8): the strip height.  A value
+                         Strip path (f32: 16 by default, 8 at dyadic order 0;
+                         8 for dyadic order <= 2, 4 for <= 1 on request; f64:
+                         8): the strip height.  A value
                          without an instance gives SIGK_EUNSUPPORTED; the
                          plain path ignores it                                */
     int coef_path;    /* strip path coefficients: 0 auto (split-TF32 on the

@@ -64,10 +64,14 @@ constexpr int64_t STRIP_WS_CAP = 8LL << 30;
 int fault_of(const sigk_opts *o) { return o ? o->fault_inject : 0; }
 int rows_of(const sigk_opts *o) { return o ? o->rows_per_lane : 0; }
 int coef_of(const sigk_opts *o) { return o ? o->coef_path : 0; }
-// the strip path's rows per lane (its default, or the requested one)
-int strip_R_of(const sigk_opts *o, int dtype) {
+// the strip path's rows per lane (its default, or the requested one).  f32
+// defaults to 512-row strips, 256-row ones at dyadic order 0: there every
+// refined cell reads its own coefficient, and twice the strips (warps) hide
+// that better (64 pairs of 4096 points: 5.3 against 6.2 ms; at order 1 the
+// 512-row strips stay faster, 7.4 against 7.7 ms)
+int strip_R_of(const sigk_opts *o, int dtype, int lam) {
     const int r = rows_of(o);
-    return r != 0 ? r : (dtype == SIGK_F64 ? 8 : 16);
+    return r != 0 ? r : (dtype == SIGK_F64 ? 8 : (lam == 0 ? 8 : 16));
 }
 // rows refine the shorter path: on request, or by default with many pairs
 // in flight (parallelism then comes from the pairs, and fewer virtual rows
@@ -82,7 +86,7 @@ void strip_batch(const PairSrc &src, int64_t n, int64_t la, int64_t lb, int lam,
                  const sigk_opts *opts, int64_t &nb, int64_t &bytes) {
     int64_t ra, rb;
     src_rows(src, n, ra, rb);
-    const int R = strip_R_of(opts, dtype), sh = shorter_of(opts, n);
+    const int R = strip_R_of(opts, dtype, lam), sh = shorter_of(opts, n);
     nb = n;
     bytes = strip_workspace_bytes(nb, la, lb, lam, dtype, ra, rb, src.d, R, sh);
     while (nb > 1 && bytes > STRIP_WS_CAP) {
@@ -118,7 +122,8 @@ Path choose_uniform(const PairSrc &src, int64_t n, int lam, int dtype, int rec, 
     if (rec == SIGK_REC_PLAIN) return P_PLAIN;
     if (rec == SIGK_REC_STRIP)
         return strip_supported(lam, src.d, dtype) &&
-                       strip_has_R(rows_per_lane ? rows_per_lane : (dtype == SIGK_F64 ? 8 : 16), lam, dtype)
+                       strip_has_R(rows_per_lane ? rows_per_lane : (dtype == SIGK_F64 ? 8 : (lam == 0 ? 8 : 16)),
+                                   lam, dtype)
                    ? P_STRIP : P_FILL;
     if (rec == SIGK_REC_BAND && dtype != SIGK_F32) return P_FILL;
     if (dtype == SIGK_F64 && rec != SIGK_REC_CHAIN) return P_PLAIN;
@@ -147,7 +152,7 @@ int run_strip(PairSrc src, int64_t n, int lam, int dtype, int64_t la, int64_t lb
     int64_t nb, need, ra, rb;
     strip_batch(src, n, la, lb, lam, dtype, opts, nb, need);
     src_rows(src, n, ra, rb);
-    if (!strip_has_R(strip_R_of(opts, dtype), lam, dtype)) return SIGK_EUNSUPPORTED;
+    if (!strip_has_R(strip_R_of(opts, dtype, lam), lam, dtype)) return SIGK_EUNSUPPORTED;
     if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         PairSrc s = src;
@@ -155,7 +160,7 @@ int run_strip(PairSrc src, int64_t n, int lam, int dtype, int64_t la, int64_t lb
         const int64_t m = n - k0 < nb ? n - k0 : nb;
         cudaError_t e = launch_strip(s, m, lam, dtype, ws, out, WAIT_CYCLES,
                                      k0 == 0 ? fault_of(opts) : 0, st, la, lb, ra, rb, coef_of(opts),
-                                     strip_R_of(opts, dtype), shorter_of(opts, n));
+                                     strip_R_of(opts, dtype, lam), shorter_of(opts, n));
         if (e != cudaSuccess) return cuda_status(e);
     }
     return SIGK_OK;
