@@ -400,7 +400,8 @@ def _extra_setup(name, batch=0):
                 torch.as_tensor(xo).pin_memory(), torch.as_tensor(yo).pin_memory(),
                 torch.empty(4096).pin_memory())
         return ("4096 pairs, L,M ~ U{16..512}, d=16 walks, dyadic order 1, fp32; tuned schedule "
-                "rec=%d coef_path=%d, one CUDA graph per call" % (sched.rec, sched.coef_path), step, cells,
+                "rec=%d rows_per_lane=%d coef_path=%d orient=%d, one CUDA graph per call"
+                % (sched.rec, sched.rows_per_lane, sched.coef_path, sched.orient), step, cells,
                 3 * cells + 2 * 16 * coarse, oracle_rate, host_step, host,
                 X32.nbytes + Y32.nbytes + xo.nbytes + yo.nbytes, 4096 * 4)
     if name.startswith("long64"):
