@@ -194,7 +194,11 @@ int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64
  * dY[b] = grad_out[b] dk_b/dY_b (either output may be NULL to skip it).
  * The paper states no gradient; this is the exact derivative of the discrete
  * scheme (adjoint sweep from the terminal corner, then the chain rule through
- * <dx_p, dy_q>).  grad_out: [B]; dX: [B, L, d]; dY: [B, M, d] (overwritten). */
+ * <dx_p, dy_q>).  grad_out: [B]; dX: [B, L, d]; dY: [B, M, d] (overwritten).
+ * opts->scheme selects the scheme differentiated.  With the RBF lift
+ * (opts->static_kernel) the chain rule goes through the second difference of
+ * kappa and runs in the one-block-per-pair backward; SIGK_REC_STRIP,
+ * SIGK_REC_BAND and the symmetric Gram backward then give SIGK_EUNSUPPORTED. */
 int sigk_pairs_backward(const void *grad_out, const void *X, const void *Y, int64_t B,
                         int64_t L, int64_t M, int64_t d, int dyadic_order, int dtype,
                         const sigk_opts *opts, void *dX, void *dY, void *ws, size_t ws_bytes,
