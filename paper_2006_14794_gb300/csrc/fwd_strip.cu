@@ -2,8 +2,13 @@
 // horizontal strips of 32*R refined rows; a persistent kernel hands strips to
 // warps in pair order from an atomic counter, and the strips of one pair form
 // a wavefront across warps (Sec. 3.1.1's anti-diagonal parallelism carried
-// from one warp to the next): each strip publishes its bottom row in chunks of
-// CW columns behind release flags, and the strip below consumes them.
+// from one warp to the next): each strip writes its bottom row column by
+// column into a buffer that the strip below reads in chunks of CW columns.
+// The buffer is filled with an all-ones bit pattern before the sweep, a NaN
+// that no arithmetic result has, so a value carries its own readiness: the
+// writer uses relaxed stores with no flag and no fence, and the reader loads a
+// chunk with relaxed loads half a chunk before it needs it and polls again
+// only where some lane still sees the pattern.
 //
 // Inside a strip the work is laid out as in the chained kernel: lane l holds
 // rows R*l .. R*l+R-1, row r of lane l works on column t - R*l - r + 1 at step
@@ -20,7 +25,7 @@
 // (above a pair's first row, padding the first strip) and columns outside the
 // grid have c = 0, which keeps K = 1 and Q = 0 exactly there.
 //
-// Waits are bounded: a consumer that does not see its chunk within
+// Waits are bounded: a reader that does not see its chunk within
 // `wait_cycles` records SIGK_ETIMEOUT in the status word and carries on
 // (its result is then meaningless and the call reports the timeout).
 #include <string.h>
@@ -42,7 +47,7 @@ struct PairPlan {
     int64_t a_row0, b_row0;  // first point row of the row path and column path
     int64_t c_off;           // start of this pair's coefficient blocks (elements)
     int64_t bnd_off;         // start of its bottom-row buffers (elements)
-    int64_t flag_off;        // start of its chunk flags
+    int64_t flag_off;        // start of its chunk flags (the adjoint's)
     int64_t strip_base;      // global index of its first strip
     int64_t out0, out1;
     int ni, nj;              // refined rows / columns
@@ -272,6 +277,31 @@ __global__ void __launch_bounds__(256) coef_kernel(PairSrc src, const PairPlan *
 
 // ---- the persistent strip sweep --------------------------------------------
 
+// The strip boundary rows: relaxed accesses at GPU scope, each value read or
+// written whole; the all-ones pattern marks a value not yet written.
+__device__ __forceinline__ float ld_relaxed(const float *p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_relaxed(const double *p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ bool unwritten(float v) { return __float_as_uint(v) == 0xffffffffu; }
+__device__ __forceinline__ bool unwritten(double v) { return __double_as_longlong(v) == -1LL; }
+// a value that happens to have the pattern (only a NaN can) is stored as
+// another NaN
+__device__ __forceinline__ void st_boundary(float *p, float v) {
+    if (unwritten(v)) v = __uint_as_float(0x7fffffffu);
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+}
+__device__ __forceinline__ void st_boundary(double *p, double v) {
+    if (unwritten(v)) v = __longlong_as_double(0x7fffffffffffffffLL);
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+}
+
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -289,8 +319,7 @@ struct StripArgs {
     const int64_t *totals;
     int64_t n_pairs;
     const T *cbuf;
-    T *bnd;
-    int *flags;
+    T *bnd;          // boundary rows, filled with the all-ones pattern first
     int *counter;
     int *status;
     T *out;
@@ -323,6 +352,20 @@ __device__ __forceinline__ void ring_commit() { asm volatile("cp.async.commit_gr
 template <int N>
 __device__ __forceinline__ void ring_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// FP32 rows i and i + R/2 of a lane are carried as one float2 (FADD2/FFMA2:
+// one issue slot for two rows, bit for bit the scalar arithmetic); FP64 rows
+// are scalar.
+template <typename T>
+struct RowPair {
+    static constexpr bool PACK = false;
+    using V = T;
+};
+template <>
+struct RowPair<float> {
+    static constexpr bool PACK = true;
+    using V = float2;
+};
+
 template <typename T, int R, int LAM>
 __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a) {
     constexpr int S = 1 << LAM;
@@ -353,40 +396,65 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
         const T *blk = a.cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
         const T *top = s > 0 ? a.bnd + pp.bnd_off + (int64_t)(s - 1) * nj * 2 : nullptr;
         T *bot = s < pp.ns - 1 ? a.bnd + pp.bnd_off + (int64_t)s * nj * 2 : nullptr;
-        const int *ftop = s > 0 ? a.flags + pp.flag_off + (s - 1) : nullptr;
-        int *fbot = s < pp.ns - 1 ? a.flags + pp.flag_off + s : nullptr;
         const bool mute = a.fault_inject && lo == 0 && s == 0;
         const int tend = nj + TH - 1;   // steps until the last row leaves column nj
 
+        // scalar rows (FP64), or rows (i, i + H) and groups (g, g + NH) in
+        // float2s (FP32, NG even for every FP32 instance)
+        constexpr bool PACK = RowPair<T>::PACK;
+        constexpr int H = R / 2, NH = NG / 2;
+        static_assert(!PACK || NG % 2 == 0, "an even number of coarse rows per lane");
         T K[R], Q[R], cn[NG], co[NG];
+        float2 KP[H], QP[H], CN[NH > 0 ? NH : 1], CO[NH > 0 ? NH : 1];
+        if constexpr (PACK) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) { K[r] = 1; Q[r] = 0; }
+            for (int i = 0; i < H; ++i) { KP[i] = make_float2(1.f, 1.f); QP[i] = make_float2(0.f, 0.f); }
 #pragma unroll
-        for (int g = 0; g < NG; ++g) { cn[g] = 0; co[g] = 0; }
+            for (int g = 0; g < NH; ++g) { CN[g] = make_float2(0.f, 0.f); CO[g] = CN[g]; }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) { K[r] = 1; Q[r] = 0; }
+#pragma unroll
+            for (int g = 0; g < NG; ++g) { cn[g] = 0; co[g] = 0; }
+        }
         T pK = 1, pQ = 0;
         bool timed_out = false;
-        // the top row's next chunk, two values per lane, loaded a chunk ahead
+        // the top row's chunk c, columns c CW .. c CW + CW - 1, two values a
+        // lane: loaded half a chunk before it is published to the warp, and
+        // loaded again, within the wait bound, while some lane still sees the
+        // unwritten pattern
         T tn0 = 0, tn1 = 0;
-        auto fetch_top = [&](int c) {
-            if (!top || c * CW >= nj) return;
-            const int need = (c + 1) * CW < nj ? c + 1 : (nj + CW - 1) / CW;
-            if (!timed_out) {
-                const long long t0 = clock64();
-                while (ld_acquire(ftop) < need) {
-                    if (clock64() - t0 > a.wait_cycles) {
-                        timed_out = true;
-                        if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
-                        break;
-                    }
-                    __nanosleep(200);
-                }
-            }
-            __syncwarp();
-            const int col = c * CW + lane;   // zero-based column of this lane's (K, Q)
-            tn0 = col < nj ? top[(int64_t)col * 2] : (T)0;
-            tn1 = col < nj ? top[(int64_t)col * 2 + 1] : (T)0;
+        auto load_top = [&](int c) {
+            const int col = c * CW + lane;
+            tn0 = col < nj ? ld_relaxed(top + (int64_t)col * 2) : (T)0;
+            tn1 = col < nj ? ld_relaxed(top + (int64_t)col * 2 + 1) : (T)0;
         };
-        fetch_top(0);
+        auto wait_top = [&](int c) {
+            const long long t0 = clock64();
+            while (!timed_out && __any_sync(FULL, unwritten(tn0) || unwritten(tn1))) {
+                if (__any_sync(FULL, clock64() - t0 > a.wait_cycles)) {
+                    timed_out = true;
+                    if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(100);
+                load_top(c);
+            }
+        };
+        if (top) {
+            // start once chunks 0 and 1 are written: from then on a chunk
+            // loaded half a chunk early is there already (both strips step
+            // at the same pace)
+            load_top(0);
+            wait_top(0);
+            tb[2 * lane] = tn0;
+            tb[2 * lane + 1] = tn1;
+            __syncwarp();
+            if (CW < nj) {
+                load_top(1);
+                wait_top(1);
+            }
+        }
         // fill the ring with diagonals 0 .. NRING-2 (one commit group each)
 #pragma unroll
         for (int k = 0; k < NRING - 1; ++k) {
@@ -405,59 +473,98 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                 ring_wait<NRING - 1>();
             }
             const T *cw = &ring[warp][w % NRING][lane * NG];
+            if constexpr (PACK) {
 #pragma unroll
-            for (int g = 0; g < NG; ++g) { co[g] = cn[g]; cn[g] = cw[g]; }
+                for (int g = 0; g < NH; ++g) { CO[g] = CN[g]; CN[g] = make_float2(cw[g], cw[g + NH]); }
+            } else {
+#pragma unroll
+                for (int g = 0; g < NG; ++g) { co[g] = cn[g]; cn[g] = cw[g]; }
+            }
 #pragma unroll
             for (int jj = 0; jj < S; ++jj) {
                 const int t = w * S + jj;
                 if (t >= tend) break;
-                if (top && (t % CW) == 0 && t < nj) {
-                    // chunk t/CW (columns t+1 .. t+CW) was loaded one chunk ago:
-                    // publish it to the warp, then fetch the next one
-                    tb[2 * lane] = tn0;
-                    tb[2 * lane + 1] = tn1;
-                    __syncwarp();
-                    fetch_top(t / CW + 1);
+                if (top && t < nj && t >= CW) {
+                    // chunk t/CW (columns t+1 .. t+CW) was loaded half a chunk
+                    // ago: publish it to the warp; load the next one half a
+                    // chunk on (chunks 0 and 1 were loaded at the start)
+                    if ((t % CW) == 0) {
+                        wait_top(t / CW);
+                        __syncwarp();
+                        tb[2 * lane] = tn0;
+                        tb[2 * lane + 1] = tn1;
+                        __syncwarp();
+                    } else if ((t % CW) == CW / 2 && (t / CW + 1) * CW < nj) {
+                        load_top(t / CW + 1);
+                    }
                 }
                 // lane 0's row 0 is at column t + 1 now
                 if (lane == 0 && top) {
                     if (t < nj) { pK = tb[(t % CW) * 2]; pQ = tb[(t % CW) * 2 + 1]; }
                 }
                 T shK = 0, shQ = 0;
-                T sum[R];
+                const int bcol = t - (TH - 1);   // zero-based column of the lane's last row
+                const bool bstore = lane == 31 && bot && !mute && bcol >= 0 && bcol < nj;
+                if constexpr (PACK) {
+                    const float kH1 = KP[H - 1].x, qH1 = QP[H - 1].x;   // row H-1 before this step
+                    float2 sum[H];
 #pragma unroll
-                for (int r = R - 1; r >= 0; --r) {
-                    const int g = r / S, sr = r % S;
-                    const T c = (jj >= sr) ? cn[g] : co[g];
-                    const T kl = K[r];
-                    const T ku = r > 0 ? K[r > 0 ? r - 1 : 0] : pK;
-                    const T qu = r > 0 ? Q[r > 0 ? r - 1 : 0] : pQ;
-                    sum[r] = kl + ku;
-                    const T qn = qu + c * sum[r];
-                    K[r] = kl + qn;
-                    Q[r] = qn;
-                    if (r == R - 1) {
-                        shK = __shfl_up_sync(FULL, K[r], 1);
-                        shQ = __shfl_up_sync(FULL, Q[r], 1);
-                        if (lane == 31 && bot && !mute) {
-                            const int col = t - (TH - 1);   // zero-based column of the last row
-                            if (col >= 0 && col < nj) {
-                                bot[(int64_t)col * 2] = K[r];
-                                bot[(int64_t)col * 2 + 1] = Q[r];
-                                if ((col + 1) % CW == 0 || col + 1 == nj) {
-                                    // measured: a fence before the release store publishes
-                                    // faster than the release store alone
-                                    __threadfence();
-                                    st_release(fbot, (col + CW) / CW);
-                                }
+                    for (int i = H - 1; i >= 0; --i) {
+                        const int g1 = i / S, s1 = i % S;   // row i; row i+H: group g1+NH, same s1
+                        const float2 c = (jj >= s1) ? CN[g1] : CO[g1];
+                        float2 ku, qu;
+                        if (i > 0) {
+                            ku = KP[i > 0 ? i - 1 : 0];
+                            qu = QP[i > 0 ? i - 1 : 0];
+                        } else {
+                            ku = make_float2(pK, kH1);
+                            qu = make_float2(pQ, qH1);
+                        }
+                        sum[i] = __fadd2_rn(KP[i], ku);
+                        const float2 qn = __ffma2_rn(c, sum[i], qu);
+                        KP[i] = __fadd2_rn(KP[i], qn);
+                        QP[i] = qn;
+                        if (i == H - 1) {
+                            shK = __shfl_up_sync(FULL, KP[i].y, 1);
+                            shQ = __shfl_up_sync(FULL, QP[i].y, 1);
+                            if (bstore) {
+                                st_boundary(bot + (int64_t)bcol * 2, KP[i].y);
+                                st_boundary(bot + (int64_t)bcol * 2 + 1, QP[i].y);
                             }
                         }
                     }
-                }
-                if (a.sums) {
-                    T *dst = a.sums + pp.s_off + ((int64_t)s * tend + t) * TH + lane * R;
+                    if (a.sums) {
+                        T *dst = a.sums + pp.s_off + ((int64_t)s * tend + t) * TH + lane * R;
 #pragma unroll
-                    for (int r = 0; r < R; ++r) dst[r] = sum[r];
+                        for (int i = 0; i < H; ++i) { dst[i] = sum[i].x; dst[i + H] = sum[i].y; }
+                    }
+                } else {
+                    T sum[R];
+#pragma unroll
+                    for (int r = R - 1; r >= 0; --r) {
+                        const int g = r / S, sr = r % S;
+                        const T c = (jj >= sr) ? cn[g] : co[g];
+                        const T kl = K[r];
+                        const T ku = r > 0 ? K[r > 0 ? r - 1 : 0] : pK;
+                        const T qu = r > 0 ? Q[r > 0 ? r - 1 : 0] : pQ;
+                        sum[r] = kl + ku;
+                        const T qn = qu + c * sum[r];
+                        K[r] = kl + qn;
+                        Q[r] = qn;
+                        if (r == R - 1) {
+                            shK = __shfl_up_sync(FULL, K[r], 1);
+                            shQ = __shfl_up_sync(FULL, Q[r], 1);
+                            if (bstore) {
+                                st_boundary(bot + (int64_t)bcol * 2, K[r]);
+                                st_boundary(bot + (int64_t)bcol * 2 + 1, Q[r]);
+                            }
+                        }
+                    }
+                    if (a.sums) {
+                        T *dst = a.sums + pp.s_off + ((int64_t)s * tend + t) * TH + lane * R;
+#pragma unroll
+                        for (int r = 0; r < R; ++r) dst[r] = sum[r];
+                    }
                 }
                 if (lane == 0) {
                     if (!top) { pK = 1; pQ = 0; }
@@ -469,8 +576,10 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
         }
         ring_wait<0>();
         if (a.out && s == pp.ns - 1 && lane == 31) {
-            a.out[pp.out0] = K[R - 1];
-            if (pp.out1 >= 0) a.out[pp.out1] = K[R - 1];
+            T kc;
+            if constexpr (PACK) kc = KP[H - 1].y; else kc = K[R - 1];
+            a.out[pp.out0] = kc;
+            if (pp.out1 >= 0) a.out[pp.out1] = kc;
         }
     }
 }
@@ -1142,10 +1251,10 @@ __global__ void strip_trivial_kernel(PairSrc src, int64_t n, T *out) {
 // ---- host side --------------------------------------------------------------
 
 // Workspace layout (bytes, each part 256-aligned):
-//   status (int) | counter (u64) | totals (4 x i64) | plan [n] | flags [nflags]
+//   status (int) | counter (u64) | totals (4 x i64) | plan [n]
 //   | coefficients [ncoef] | bottom rows [nbnd]
 struct StripLayout {
-    int64_t plan, flags, coef, bnd, incA, incB, total;
+    int64_t plan, coef, bnd, incA, incB, total;
     // backward only
     int64_t vflags, vbuf, sums, gbar;
 };
@@ -1165,8 +1274,6 @@ static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R
     int64_t off = 256 + 256 + 256;
     L.plan = off;
     off += al256(n * (int64_t)sizeof(PairPlan));
-    L.flags = off;
-    off += al256(n * (ns > 1 ? ns - 1 : 0) * 4 + 4);
     L.coef = off;
     off += al256(n * ns * nw * CP * es);
     L.bnd = off;
@@ -1337,14 +1444,14 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     int *counter = (int *)(w + 256);
     int64_t *totals = (int64_t *)(w + 512);
     PairPlan *plan = (PairPlan *)(w + L.plan);
-    int *flags = (int *)(w + L.flags);
     T *cbuf = (T *)(w + L.coef);
     T *bnd = (T *)(w + L.bnd);
     T *incA = (T *)(w + L.incA);
     T *incB = (T *)(w + L.incB);
     cudaError_t e;
     if ((e = cudaMemsetAsync(w, 0, 768, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(flags, 0, (size_t)(L.coef - L.flags), st)) != cudaSuccess) return e;
+    // every byte of the bottom rows to 0xff: the unwritten pattern
+    if ((e = cudaMemsetAsync(bnd, 0xff, (size_t)(L.incA - L.bnd), st)) != cudaSuccess) return e;
     strip_trivial_kernel<T><<<64, 256, 0, st>>>(src, n, out);
     {
         const bool packed = src.mode == PM_VARLEN;
@@ -1374,7 +1481,6 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     a.n_pairs = n;
     a.cbuf = cbuf;
     a.bnd = bnd;
-    a.flags = flags;
     a.counter = counter;
     a.status = status;
     a.out = out;
@@ -1409,7 +1515,7 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
     T *incB = (T *)(w + L.incB);
     cudaError_t e;
     if ((e = cudaMemsetAsync(w, 0, 768, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w + L.flags, 0, (size_t)(L.coef - L.flags), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w + L.bnd, 0xff, (size_t)(L.incA - L.bnd), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w + L.vflags, 0, (size_t)(L.vbuf - L.vflags), st)) != cudaSuccess) return e;
     {
         const bool packed = src.mode == PM_VARLEN;
@@ -1440,7 +1546,6 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         a.n_pairs = n;
         a.cbuf = (const T *)(w + L.coef);
         a.bnd = (T *)(w + L.bnd);
-        a.flags = (int *)(w + L.flags);
         a.counter = counter;
         a.status = status;
         a.out = nullptr;
