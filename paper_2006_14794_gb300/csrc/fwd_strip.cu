@@ -1069,21 +1069,28 @@ __global__ void __launch_bounds__(256) coef_tc_kernel(PairSrc src, const PairPla
 
 // ---- coefficients on the fifth-generation tensor cores (tcgen05, f32, d <= 64) ----
 // The same blocks as coef_kernel: d(W, P) = c(prow0 + P, W - P) for W < nw,
-// P < CP.  A block of 128 threads takes a 128-row slice of a strip's coarse
+// P < CP.  A block of 256 threads takes a 128-row slice of a strip's coarse
 // rows (the row increments, pre-scaled by 1/2 4^-lambda, split into TF32 hi
-// and lo parts once) and walks the columns in chunks of 128: the chunk's
-// column increments are split and staged, one thread issues the split-TF32
-// MMAs (D in TMEM, 128 x 128 fp32), the warps read D back into a shared tile
-// and store it along its anti-diagonals (each diagonal W a contiguous run of
-// P).  Cells outside the grid are zero (zero increments).  Waits on the MMA
-// barrier are bounded: on expiry the block records SIGK_ETIMEOUT and stops.
-// shared tile stride 132: rows start on 16-byte boundaries (vector stores of
-// the read-back) and a diagonal's reads, row stride 131 apart, hit distinct banks
-constexpr int TC5_M = 128, TC5_N = 128, TC5_SS = TC5_N + 4;
+// and lo parts once) and walks the columns in chunks of 128, chunk c covering
+// q = qfirst + 128 c .. + 127 with qfirst = -(P0 + 127): the chunk's column
+// increments are split and staged and one thread issues the split-TF32 MMAs
+// into one of three 128-column TMEM accumulators.  Diagonal block m
+// (W = 128 m .. 128 m + 127 of all 128 slice rows) is then exactly the part of
+// chunk m on or right of each row's diagonal (row Pl: its last Pl + 1
+// columns) and the rest of chunk m + 1 (its first 127 - Pl columns).  Once
+// chunk m + 1's MMAs are done, chunk m + 2's are issued, the warps read the two
+// parts back into a diagonal-major shared tile St[W - 128 m][Pl] (each thread
+// its own row: scalar stores, conflict-free with a row stride of 128 floats)
+// and every diagonal leaves as one contiguous run of 128 floats, float4 a
+// lane.  Cells outside the grid are zero (zero increments; chunks outside the
+// grid skip their MMAs and read back as zero).  Waits on the MMA barrier are
+// bounded: on expiry the block records SIGK_ETIMEOUT and stops.
+constexpr int TC5_M = 128, TC5_N = 128, TC5_SS = 128;
 constexpr int TC5_T = 256;                                     // threads: two per operand row
+constexpr int TC5_NACC = 3;                                    // accumulators in flight
 
 __host__ __device__ inline int tc5_k(int64_t d) { return (int)(((d + 3) / 4 * 4 + 7) / 8 * 8); }
-inline int tc5_smem_bytes(int64_t d) { return 4 * TC5_M * tc5_k(d) * 4 + TC5_M * TC5_SS * 4; }
+inline int tc5_smem_bytes(int64_t d) { return 4 * TC5_M * tc5_k(d) * 4 + TC5_N * TC5_SS * 4; }
 
 // Half of a row (K/8 float4s from k4 = h * K/8) of increments into registers.
 __device__ __forceinline__ void tc5_fetch(float4 (&v)[8], const float4 *src, int h, int K, int k4n) {
@@ -1101,7 +1108,7 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
     constexpr int S = 1 << LAM;
     constexpr int CP = 32 * (R / S);
     constexpr int RB = CP >= TC5_M ? CP / TC5_M : 1;   // 128-row slices per strip
-    constexpr int NW = TC5_T / 32;
+    static_assert(CP % 4 == 0, "float4 rows of a diagonal");
     extern __shared__ __align__(1024) unsigned char tc5_sm[];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ unsigned tmem_slot;
@@ -1109,13 +1116,15 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
     const int D4 = (int)((src.d + 3) / 4);
     unsigned char *ah = tc5_sm, *al = ah + TC5_M * K * 4;
     unsigned char *bh = al + TC5_M * K * 4, *bl = bh + TC5_N * K * 4;
-    float *St = reinterpret_cast<float *>(bl + TC5_N * K * 4);
+    float *St = reinterpret_cast<float *>(bl + TC5_N * K * 4);   // [diagonal][slice row]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = tid & (TC5_M - 1), half = tid >> 7;   // operand row and half of K this thread stages
+    const int qw = warp & 3, hsel = warp >> 2;            // TMEM lane quarter, which of its two warps
+    const int Pl = qw * 32 + lane;                        // the slice row this thread reads back
     const float scale = 0.5f / (float)(1 << (2 * LAM));
     const unsigned idesc = tc5::idesc_tf32(TC5_M, TC5_N);
 
-    if (warp == 0) tc5::alloc(&tmem_slot, 2 * TC5_N);   // two 128-column accumulators
+    if (warp == 0) tc5::alloc(&tmem_slot, 512);   // three 128-column accumulators (a power of two)
     if (tid == 0) tc5::mbar_init(&mbar);
     tc5::fence_before();
     __syncthreads();
@@ -1141,8 +1150,14 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
         const int P0 = rb * TC5_M;
         const int prow0 = s * CP - (pp.pad >> LAM) + P0;   // coarse row of slice row 0
         const bool rows_empty = prow0 + TC5_M - 1 < 0 || prow0 >= pp.nx;
-        const int qfirst = -(P0 + TC5_M - 1), qlast = pp.nw - 1 - P0;   // column range of the slice's diagonals
-        auto col_ok = [&](int q0) { return !rows_empty && q0 + TC5_N - 1 >= 0 && q0 < pp.ny; };
+        const int qfirst = -(P0 + TC5_M - 1);
+        const int nblk = (pp.nw + TC5_N - 1) / TC5_N;      // diagonal blocks
+        const int nch = nblk + 1;                           // chunks
+        // chunk c has an accumulator (its columns meet the grid)
+        auto live = [&](int c) {
+            const int q0 = qfirst + c * TC5_N;
+            return c < nch && !rows_empty && q0 + TC5_N - 1 >= 0 && q0 < pp.ny;
+        };
         float4 nb[8];   // the next chunk's column increments, fetched ahead
         __syncthreads();
         {
@@ -1152,86 +1167,89 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
                       half, K, D4);
             tc5::store_half(ah, al, row, half, K, av, scale);
             const int q = qfirst + row;
-            tc5_fetch(nb, (col_ok(qfirst) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr, half, K, D4);
+            tc5_fetch(nb, (live(0) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr, half, K, D4);
         }
-        // chunk c covers columns q0 = qfirst + c TC5_N ..; its accumulator is
-        // TMEM columns (c & 1) TC5_N .., so chunk c + 1's MMAs run while chunk c
-        // is read back and written out
-        const int nch = (qlast - qfirst) / TC5_N + 1;
         auto issue = [&](int c) {   // stage chunk c's column increments (in nb), start its MMAs
             tc5::store_half(bh, bl, row, half, K, nb, 1.f);
             tc5::fence_async_smem();
             __syncthreads();
             if (tid == 0) {
                 tc5::fence_after();
-                tc5::gemm_split(tmem + (unsigned)((c & 1) * TC5_N), ah, al, bh, bl, K, idesc, false);
+                tc5::gemm_split(tmem + (unsigned)((c % TC5_NACC) * TC5_N), ah, al, bh, bl, K, idesc, false);
                 tc5::commit(&mbar);
             }
         };
         auto fetch_chunk = [&](int c) {
             const int qn = qfirst + c * TC5_N, q = qn + row;
-            tc5_fetch(nb, (c < nch && col_ok(qn) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr, half,
-                      K, D4);
+            tc5_fetch(nb, (live(c) && q >= 0 && q < pp.ny) ? y + (int64_t)q * D4 : nullptr, half, K, D4);
         };
-        if (col_ok(qfirst)) issue(0);
+        // chunk c's MMAs done (block-uniform result; false after a timeout)
+        auto wait_chunk = [&](int c) {
+            if (!live(c)) return true;
+            const bool ok = tc5::mbar_wait(&mbar, phase, max_wait);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicExch(status, (int)SIGK_ETIMEOUT);
+                return false;
+            }
+            phase ^= 1;
+            tc5::fence_after();
+            return true;
+        };
+        if (live(0)) issue(0);
         fetch_chunk(1);
-        for (int c = 0; c < nch; ++c) {
-            const int q0 = qfirst + c * TC5_N;
-            const bool zero = !col_ok(q0);
-            if (!zero) {
-                const bool ok = tc5::mbar_wait(&mbar, phase, max_wait);
-                if (__syncthreads_or(!ok)) {   // block-uniform
-                    failed = true;
-                    if (tid == 0) atomicExch(status, (int)SIGK_ETIMEOUT);
-                    break;
-                }
-                phase ^= 1;
-                tc5::fence_after();
+        if (!wait_chunk(0)) { failed = true; break; }
+        if (live(1)) issue(1);
+        fetch_chunk(2);
+        for (int m = 0; m < nblk; ++m) {
+            if (!wait_chunk(m + 1)) { failed = true; break; }
+            // chunk m + 2 into the accumulator chunk m - 1 used (read back last block)
+            if (m + 2 < nch) {
+                if (live(m + 2)) issue(m + 2);
+                fetch_chunk(m + 3);
             }
-            // the MMAs of chunk c are done with the column operand: chunk c + 1's can start
-            if (c + 1 < nch) {
-                if (col_ok(q0 + TC5_N)) issue(c + 1);
-                fetch_chunk(c + 2);
-            }
-            if (!zero) {
-                // D into the shared tile: warp w reads TMEM lanes 32 (w % 4) .., columns 64 (w / 4) ..
-                const int r = (warp & 3) * 32 + lane, cb = (warp >> 2) * 64;
-                const unsigned dc = tmem + (unsigned)((c & 1) * TC5_N);
+            // read-back: of the quarter's five 32-column pieces (chunk m's
+            // columns 96 - 32 qw .. 127, chunk m + 1's 0 .. 127 - 32 qw), this
+            // warp takes every other one
+            for (int pc = hsel; pc < 5; pc += 2) {
+                const bool first = pc <= qw;                  // a piece of chunk m
+                const int c = first ? m : m + 1;
+                const int cb = first ? 3 - qw + pc : pc - qw - 1;
+                float v[32];
+                if (live(c)) {
+                    tc5::ld32(tmem + ((unsigned)(qw * 32) << 16) + (unsigned)((c % TC5_NACC) * TC5_N + cb * 32), v);
+                } else {
 #pragma unroll
-                for (int c0 = 0; c0 < 64; c0 += 32) {
-                    float v[32];
-                    tc5::ld32(dc + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(cb + c0), v);
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4)
-                        *reinterpret_cast<float4 *>(&St[r * TC5_SS + cb + c0 + j]) =
-                            make_float4(scheme_coef(v[j], src.scheme), scheme_coef(v[j + 1], src.scheme),
-                                        scheme_coef(v[j + 2], src.scheme), scheme_coef(v[j + 3], src.scheme));
+                    for (int k = 0; k < 32; ++k) v[k] = 0.f;
                 }
-                tc5::fence_before();
+                // column lc = 32 cb + k lies on diagonal j = lc + Pl - 127 (chunk
+                // m) or lc + Pl + 1 (chunk m + 1) of the block
+                const int j0 = 32 * cb + Pl + (first ? -(TC5_N - 1) : 1);
+                float *dst = St + j0 * TC5_SS + Pl;
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if ((unsigned)(j0 + k) < (unsigned)TC5_N) dst[k * TC5_SS] = scheme_coef(v[k], src.scheme);
             }
+            tc5::fence_before();
             __syncthreads();
-            // write-out along the diagonals W = q + P: warps 2b, 2b + 1 own slice
-            // rows Pl = 32 b + lane and take every other diagonal offset
-            // dd = Pl + (q - q0) of that row block, one coalesced store each
-            {
-                const int Pl = (warp & 3) * 32 + lane, P = P0 + Pl;
-                const int dlo = (warp & 3) * 32, dhi = dlo + 31 + TC5_N - 1;
+            // write-out: warp w stores diagonals j = w, w + 8, .., 128 floats each
+            if (P0 + 4 * lane < CP) {
 #pragma unroll 4
-                for (int dd = dlo + (warp >> 2); dd <= dhi; dd += 2) {
-                    const int ci = dd - Pl, W = q0 + P0 + dd;
-                    if (ci >= 0 && ci < TC5_N && W >= 0 && W < pp.nw && P < CP)
-                        blk[(int64_t)W * CP + P] = zero ? 0.f : St[Pl * TC5_SS + ci];
+                for (int j = warp; j < TC5_N; j += TC5_T / 32) {
+                    const int W = m * TC5_N + j;
+                    if (W < pp.nw)
+                        *reinterpret_cast<float4 *>(blk + (int64_t)W * CP + P0 + 4 * lane) =
+                            *reinterpret_cast<const float4 *>(St + j * TC5_SS + 4 * lane);
                 }
             }
             __syncthreads();
         }
     }
     // after a timeout, give the outstanding MMAs another bounded wait before
-    // the accumulator is released
+    // the accumulators are released
     if (failed) tc5::mbar_wait(&mbar, phase, max_wait);
     tc5::fence_before();
     __syncthreads();
-    if (warp == 0) tc5::dealloc(tmem, 2 * TC5_N);
+    if (warp == 0) tc5::dealloc(tmem, 512);
 }
 
 template <typename T>

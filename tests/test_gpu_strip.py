@@ -134,6 +134,33 @@ def test_strip_tcgen05_coefficients_match_oracle(lam, L, M, d):
     assert rel_err(outs[sigk.COEF_TC5], outs[sigk.COEF_FMA]) <= 2e-6
 
 
+@pytest.mark.parametrize("R,orient,lam", [(4, 1, 1), (8, 2, 0), (8, 1, 2), (16, 2, 1)])
+def test_strip_tcgen05_coefficients_on_uneven_pairs(R, orient, lam):
+    """The tcgen05 coefficient blocks on packed pairs of uneven lengths: slices
+    past a pair's last row, chunks outside its columns (no MMAs, read back as
+    zero), 64- to 512-row strips and the last partial diagonal block."""
+    sigk = S()
+    rng = np.random.default_rng(4700 + R + lam)
+    lens_x = np.concatenate([[1, 2, 390, 129], rng.integers(2, 300, size=20)])
+    lens_y = np.concatenate([[70, 1, 2, 258], rng.integers(2, 300, size=20)])
+    d = 48
+    Xp = np.concatenate([inputs.random_paths(4800 + i, 1, int(n), d)[0] for i, n in enumerate(lens_x)])
+    Yp = np.concatenate([inputs.random_paths(4900 + i, 1, int(n), d)[0] for i, n in enumerate(lens_y)])
+    xo = np.concatenate([[0], np.cumsum(lens_x)]).astype(np.int64)
+    yo = np.concatenate([[0], np.cumsum(lens_y)]).astype(np.int64)
+    X32, X64 = inputs.f32(Xp)
+    Y32, Y64 = inputs.f32(Yp)
+    ref = oracle.pairs_varlen(X64, xo, Y64, yo, lam)
+    outs = {}
+    for coef in (sigk.COEF_TC5, sigk.COEF_FMA):
+        s = sigk.Schedule(sigk.REC_STRIP, R, coef, orient)
+        outs[coef] = sigk.pairs_varlen(to_dev(X32), torch.as_tensor(xo).cuda(), to_dev(Y32),
+                                       torch.as_tensor(yo).cuda(), lam, int(max(lens_x.max(), lens_y.max())),
+                                       schedule=s, check_status=True).cpu().numpy()
+        assert rel_err(outs[coef], ref) <= 1e-5, coef
+    assert rel_err(outs[sigk.COEF_TC5], outs[sigk.COEF_FMA]) <= 2e-6
+
+
 @pytest.mark.parametrize("R,orient,lam", [(4, 1, 1), (4, 2, 0), (8, 1, 2), (8, 2, 1), (16, 2, 3)])
 def test_strip_heights_and_orientations_on_uneven_pairs(R, orient, lam):
     """128-, 256- and 512-row strips, rows on the longer or the shorter path,
