@@ -47,7 +47,6 @@ struct PairPlan {
     int64_t a_row0, b_row0;  // first point row of the row path and column path
     int64_t c_off;           // start of this pair's coefficient blocks (elements)
     int64_t bnd_off;         // start of its bottom-row buffers (elements)
-    int64_t flag_off;        // start of its chunk flags (the adjoint's)
     int64_t strip_base;      // global index of its first strip
     int64_t out0, out1;
     int ni, nj;              // refined rows / columns
@@ -59,12 +58,16 @@ struct PairPlan {
     int64_t g_off;           // backward: start of its dense dk/dG [nx][ny]
 };
 
+// totals[]: the sums of the coefficient, boundary-row, strip, sums and dk/dG
+// sizes over all pairs
+constexpr int TOT_STRIPS = 2;
+
 template <int R, int LAM>
 __global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *totals, int shorter_rows) {
     constexpr int S = 1 << LAM;
     constexpr int TH = 32 * R;
     constexpr int CP = 32 * (R / S);
-    __shared__ int64_t part[6][512];
+    __shared__ int64_t part[5][512];
     // pass 1: per-pair shape
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
         const PairRef pr = pair_ref(src, k);
@@ -88,49 +91,46 @@ __global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *tot
         p.nw = ((p.nj + TH - 2) >> LAM) + 2;
         p.c_off = (int64_t)p.ns * p.nw * CP;        // sizes for now, offsets after the scan
         p.bnd_off = p.ns > 0 ? (int64_t)(p.ns - 1) * p.nj * 2 : 0;
-        p.flag_off = p.ns > 0 ? p.ns - 1 : 0;
         p.strip_base = p.ns;
         p.s_off = (int64_t)p.ns * (p.nj + TH - 1) * TH;
         p.g_off = (int64_t)p.nx * p.ny;
         plan[k] = p;
     }
     __syncthreads();
-    // pass 2: exclusive scans of the four sizes, in chunks of blockDim
-    int64_t run[6] = {0, 0, 0, 0, 0, 0};
+    // pass 2: exclusive scans of the five sizes, in chunks of blockDim
+    int64_t run[5] = {0, 0, 0, 0, 0};
     for (int64_t base = 0; base < n; base += blockDim.x) {
         const int64_t k = base + threadIdx.x;
-        int64_t v[6] = {0, 0, 0, 0, 0, 0};
+        int64_t v[5] = {0, 0, 0, 0, 0};
         if (k < n) {
             v[0] = plan[k].c_off;
             v[1] = plan[k].bnd_off;
-            v[2] = plan[k].flag_off;
-            v[3] = plan[k].strip_base;
-            v[4] = plan[k].s_off;
-            v[5] = plan[k].g_off;
+            v[2] = plan[k].strip_base;
+            v[3] = plan[k].s_off;
+            v[4] = plan[k].g_off;
         }
-        for (int j = 0; j < 6; ++j) part[j][threadIdx.x] = v[j];
+        for (int j = 0; j < 5; ++j) part[j][threadIdx.x] = v[j];
         __syncthreads();
         for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-            int64_t t[6];
-            for (int j = 0; j < 6; ++j)
+            int64_t t[5];
+            for (int j = 0; j < 5; ++j)
                 t[j] = (int)threadIdx.x >= off ? part[j][threadIdx.x - off] : 0;
             __syncthreads();
-            for (int j = 0; j < 6; ++j) part[j][threadIdx.x] += t[j];
+            for (int j = 0; j < 5; ++j) part[j][threadIdx.x] += t[j];
             __syncthreads();
         }
         if (k < n) {
             plan[k].c_off = run[0] + part[0][threadIdx.x] - v[0];
             plan[k].bnd_off = run[1] + part[1][threadIdx.x] - v[1];
-            plan[k].flag_off = run[2] + part[2][threadIdx.x] - v[2];
-            plan[k].strip_base = run[3] + part[3][threadIdx.x] - v[3];
-            plan[k].s_off = run[4] + part[4][threadIdx.x] - v[4];
-            plan[k].g_off = run[5] + part[5][threadIdx.x] - v[5];
+            plan[k].strip_base = run[2] + part[2][threadIdx.x] - v[2];
+            plan[k].s_off = run[3] + part[3][threadIdx.x] - v[3];
+            plan[k].g_off = run[4] + part[4][threadIdx.x] - v[4];
         }
-        for (int j = 0; j < 6; ++j) run[j] += part[j][blockDim.x - 1];
+        for (int j = 0; j < 5; ++j) run[j] += part[j][blockDim.x - 1];
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        for (int j = 0; j < 6; ++j) totals[j] = run[j];
+        for (int j = 0; j < 5; ++j) totals[j] = run[j];
 }
 
 // ---- increments: dx_r = x_{r+1} - x_r for every point row r of a path array,
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256) coef_kernel(PairSrc src, const PairPlan *
     V4 *sx = reinterpret_cast<V4 *>(smraw);          // GT rows of dx
     V4 *sy = sx + GT * RS;                            // 2*GT-1 rows of dy
     const T scale = (T)0.5 / (T)(1LL << (2 * LAM));
-    const int64_t total_strips = totals[3];
+    const int64_t total_strips = totals[TOT_STRIPS];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     for (int64_t gs = blockIdx.x; gs < total_strips; gs += gridDim.x) {
         // the pair of this strip: last plan with strip_base <= gs
@@ -302,16 +302,6 @@ __device__ __forceinline__ void st_boundary(double *p, double v) {
     asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
 }
 
-__device__ __forceinline__ int ld_acquire(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(int *p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 template <typename T>
 struct StripArgs {
     PairSrc src;
@@ -378,7 +368,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     T *tb = topbuf[warp];
-    const int64_t total_strips = a.totals[3];
+    const int64_t total_strips = a.totals[TOT_STRIPS];
 
     for (;;) {
         int64_t gs = 0;
@@ -606,8 +596,8 @@ struct AdjArgs {
     int64_t n_pairs;
     const T *cbuf;
     const T *sums;
-    T *vbuf;         // per pair, per strip boundary: V of the lower strip's first row [nj]
-    int *vflags;     // chunks of vbuf published, counted from the right
+    T *vbuf;         // per pair, per strip boundary: V of the lower strip's first row [nj],
+                     // filled with the all-ones pattern first
     int *counter;
     int *status;
     T *gbar;         // dense dk/dG (unscaled), [nx][ny] per pair
@@ -645,7 +635,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
     T *ringc = reinterpret_cast<T *>(adj_smem) + (size_t)warp * adj_warp_elems<T, R, LAM>();
     T *rings = ringc + NRING * CP;
     T *bb = rings + NSR * 32 * R;
-    const int64_t total_strips = a.totals[3];
+    const int64_t total_strips = a.totals[TOT_STRIPS];
 
     for (;;) {
         int64_t gs = 0;
@@ -665,9 +655,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
         const T *blk = a.cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
         const T *sst = a.sums + pp.s_off + (int64_t)s * tend * TH;
         const T *below = s < pp.ns - 1 ? a.vbuf + pp.bnd_off / 2 + (int64_t)s * nj : nullptr;
-        const int *fbelow = s < pp.ns - 1 ? a.vflags + pp.flag_off + s : nullptr;
         T *above = s > 0 ? a.vbuf + pp.bnd_off / 2 + (int64_t)(s - 1) * nj : nullptr;
-        int *fabove = s > 0 ? a.vflags + pp.flag_off + (s - 1) : nullptr;
         const int prow0 = s * CP - (pp.pad >> LAM);
 
         T A[R], V[R], cp[R], cn[NG], co[NG], gN[NG], gO[NG];
@@ -677,29 +665,38 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
         for (int g = 0; g < NG; ++g) { gN[g] = 0; gO[g] = 0; }
         bool timed_out = false;
 
-        // the row below's V, chunks counted from the right; one value per lane,
-        // fetched a chunk ahead (c: chunk index from the right)
+        // the row below's V in chunks counted from the right, chunk c holding
+        // columns nj - 1 - c CW - lane: loaded half a chunk before it is
+        // published to the warp, and again, within the wait bound, while some
+        // lane still sees the unwritten pattern (as in the forward)
         T vn = 0;
-        auto fetch_below = [&](int c) {
-            const int hi_col = nj - 1 - c * CW;   // rightmost column of chunk c
-            if (!below || hi_col < 0) return;
-            const int need = c + 1;
-            if (!timed_out) {
-                const long long t0 = clock64();
-                while (ld_acquire(fbelow) < need) {
-                    if (clock64() - t0 > a.wait_cycles) {
-                        timed_out = true;
-                        if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
-                        break;
-                    }
-                    __nanosleep(200);
-                }
-            }
-            __syncwarp();
-            const int col = hi_col - lane;
-            vn = col >= 0 ? below[col] : (T)0;
+        auto load_below = [&](int c) {
+            const int col = nj - 1 - c * CW - lane;
+            vn = col >= 0 ? ld_relaxed(below + col) : (T)0;
         };
-        fetch_below(0);
+        auto wait_below = [&](int c) {
+            const long long t0 = clock64();
+            while (!timed_out && __any_sync(FULL, unwritten(vn))) {
+                if (__any_sync(FULL, clock64() - t0 > a.wait_cycles)) {
+                    timed_out = true;
+                    if (lane == 0) atomicExch(a.status, (int)SIGK_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(100);
+                load_below(c);
+            }
+        };
+        if (below) {
+            // start once chunks 0 and 1 are written
+            load_below(0);
+            wait_below(0);
+            bb[lane] = vn;
+            __syncwarp();
+            if (CW < nj) {
+                load_below(1);
+                wait_below(1);
+            }
+        }
 
         // one initial group: coefficient diagonals nwin-1 .. nwin-NRING+1 and
         // the sums of steps tend-1 .. tend-PD; then one group per step
@@ -749,11 +746,18 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
                 ring_commit();
                 ring_wait<PD>();   // the sums of step t (fetched PD steps ago) have landed
                 const int col31 = t - (TH - 1);   // zero-based column of the strip's last row
-                if (below && col31 >= 0 && col31 < nj && ((nj - 1 - col31) % CW) == 0) {
-                    // chunk (nj-1-col31)/CW was fetched a chunk ago: publish, fetch the next
-                    bb[lane] = vn;
-                    __syncwarp();
-                    fetch_below((nj - 1 - col31) / CW + 1);
+                if (below && col31 >= 0 && col31 < nj - CW) {
+                    // chunk c = (nj-1-col31)/CW (c >= 1) was loaded half a chunk
+                    // ago: publish it; load chunk c + 1 half a chunk on
+                    const int off = nj - 1 - col31, c = off / CW;
+                    if (off % CW == 0) {
+                        wait_below(c);
+                        __syncwarp();
+                        bb[lane] = vn;
+                        __syncwarp();
+                    } else if (off % CW == CW / 2 && (c + 1) * CW < nj) {
+                        load_below(c + 1);
+                    }
                 }
                 T vbel;
                 if (below)
@@ -778,16 +782,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
                     if (jj >= sr) gN[g] += An * sm[r]; else gO[g] += An * sm[r];
                 }
                 // lane 0's first row is at column t: its V goes to the strip above
-                if (above && lane == 0 && t < nj) {
-                    above[t] = V[0];
-                    const int done = nj - t;
-                    if (done % CW == 0 || t == 0) {
-                        // measured: a fence before the release store publishes faster
-                        // than the release store alone
-                        __threadfence();
-                        st_release(fabove, (done + CW - 1) / CW);
-                    }
-                }
+                if (above && lane == 0 && t < nj) st_boundary(above + t, V[0]);
             }
             // diagonal w is complete for every group of the lane
 #pragma unroll
@@ -945,7 +940,7 @@ __global__ void __launch_bounds__(256) coef_tc_kernel(PairSrc src, const PairPla
     unsigned *yl = yh + 64 * XS;
     float *cs = reinterpret_cast<float *>(yl + 64 * XS);   // rectangle ring: 64 x 128 columns
     const float scale = 0.5f / (float)(1 << (2 * LAM));
-    const int64_t total_strips = totals[3];
+    const int64_t total_strips = totals[TOT_STRIPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
     const int pw = 32 * (warp >> 2), qw = 16 * (warp & 3);
@@ -1082,7 +1077,7 @@ __global__ void __launch_bounds__(256) coef_tc_kernel(PairSrc src, const PairPla
 // parts back into a diagonal-major shared tile St[W - 128 m][Pl] (each thread
 // its own row: scalar stores, conflict-free with a row stride of 128 floats)
 // and every diagonal leaves as one contiguous run of 128 floats, float4 a
-// lane.  Cells outside the grid are zero (zero increments; chunks outside the
+// lane, through the scheme's map.  Cells outside the grid are zero (zero increments; chunks outside the
 // grid skip their MMAs and read back as zero).  Waits on the MMA barrier are
 // bounded: on expiry the block records SIGK_ETIMEOUT and stops.
 constexpr int TC5_M = 128, TC5_N = 128, TC5_SS = 128;
@@ -1133,7 +1128,7 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
     unsigned phase = 0;
     bool failed = false;
 
-    const int64_t items = totals[3] * RB;
+    const int64_t items = totals[TOT_STRIPS] * RB;
     for (int64_t it = blockIdx.x; it < items && !failed; it += gridDim.x) {
         const int64_t gs = it / RB;
         const int rb = (int)(it - gs * RB);
@@ -1207,27 +1202,44 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
                 if (live(m + 2)) issue(m + 2);
                 fetch_chunk(m + 3);
             }
-            // read-back: of the quarter's five 32-column pieces (chunk m's
-            // columns 96 - 32 qw .. 127, chunk m + 1's 0 .. 127 - 32 qw), this
-            // warp takes every other one
-            for (int pc = hsel; pc < 5; pc += 2) {
-                const bool first = pc <= qw;                  // a piece of chunk m
-                const int c = first ? m : m + 1;
-                const int cb = first ? 3 - qw + pc : pc - qw - 1;
-                float v[32];
+            // read-back.  Row Pl = 32 qw + lane takes, from its quarter's 32-column
+            // TMEM blocks, chunk m's columns 127 - Pl .. 127 and chunk m + 1's
+            // 0 .. 126 - Pl.  Pieces 1 .. 3 (chunk m's blocks 4 - qw .. 3, then
+            // chunk m + 1's blocks 0 .. 2 - qw) lie wholly on diagonals
+            // 32 (pc - 1) + lane + 1 + k of the block; block 3 - qw of both
+            // chunks splits at k = 31 - lane and both halves land on diagonal
+            // (97 + lane + k) mod 128 (piece 0).  Warp hsel = 0 takes pieces 0
+            // and 2, hsel = 1 pieces 1 and 3: 64 stores a thread, none masked.
+            auto piece = [&](int c, int cb, float (&v)[32]) {
                 if (live(c)) {
                     tc5::ld32(tmem + ((unsigned)(qw * 32) << 16) + (unsigned)((c % TC5_NACC) * TC5_N + cb * 32), v);
                 } else {
 #pragma unroll
                     for (int k = 0; k < 32; ++k) v[k] = 0.f;
                 }
-                // column lc = 32 cb + k lies on diagonal j = lc + Pl - 127 (chunk
-                // m) or lc + Pl + 1 (chunk m + 1) of the block
-                const int j0 = 32 * cb + Pl + (first ? -(TC5_N - 1) : 1);
-                float *dst = St + j0 * TC5_SS + Pl;
+            };
 #pragma unroll
-                for (int k = 0; k < 32; ++k)
-                    if ((unsigned)(j0 + k) < (unsigned)TC5_N) dst[k * TC5_SS] = scheme_coef(v[k], src.scheme);
+            for (int e = 0; e < 2; ++e) {
+                const int pc = 2 * e + hsel;
+                float v[32];
+                if (pc == 0) {
+                    float w[32];
+                    piece(m, 3 - qw, v);
+                    piece(m + 1, 3 - qw, w);
+                    float *lo = St + (lane - 31) * TC5_SS + Pl;   // k >= 31 - lane: diagonal k + lane - 31
+                    float *hi = St + (lane + 97) * TC5_SS + Pl;   // k < 31 - lane: diagonal k + lane + 97
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        if (k >= 31 - lane) lo[k * TC5_SS] = v[k];
+                        else hi[k * TC5_SS] = w[k];
+                    }
+                } else {
+                    const bool first = pc <= qw;                  // a block of chunk m
+                    piece(first ? m : m + 1, first ? 3 - qw + pc : pc - qw - 1, v);
+                    float *dst = St + (32 * (pc - 1) + lane + 1) * TC5_SS + Pl;
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) dst[k * TC5_SS] = v[k];
+                }
             }
             tc5::fence_before();
             __syncthreads();
@@ -1236,9 +1248,16 @@ __global__ void __launch_bounds__(TC5_T, 1) coef_tc5_kernel(PairSrc src, const P
 #pragma unroll 4
                 for (int j = warp; j < TC5_N; j += TC5_T / 32) {
                     const int W = m * TC5_N + j;
-                    if (W < pp.nw)
-                        *reinterpret_cast<float4 *>(blk + (int64_t)W * CP + P0 + 4 * lane) =
-                            *reinterpret_cast<const float4 *>(St + j * TC5_SS + 4 * lane);
+                    if (W < pp.nw) {
+                        float4 v = *reinterpret_cast<const float4 *>(St + j * TC5_SS + 4 * lane);
+                        if (src.scheme != SIGK_SCHEME_EXPLICIT) {
+                            v.x = scheme_coef(v.x, src.scheme);
+                            v.y = scheme_coef(v.y, src.scheme);
+                            v.z = scheme_coef(v.z, src.scheme);
+                            v.w = scheme_coef(v.w, src.scheme);
+                        }
+                        *reinterpret_cast<float4 *>(blk + (int64_t)W * CP + P0 + 4 * lane) = v;
+                    }
                 }
             }
             __syncthreads();
@@ -1269,12 +1288,12 @@ __global__ void strip_trivial_kernel(PairSrc src, int64_t n, T *out) {
 // ---- host side --------------------------------------------------------------
 
 // Workspace layout (bytes, each part 256-aligned):
-//   status (int) | counter (u64) | totals (4 x i64) | plan [n]
+//   status (int) | counters (u64) | totals (5 x i64) | plan [n]
 //   | coefficients [ncoef] | bottom rows [nbnd]
 struct StripLayout {
     int64_t plan, coef, bnd, incA, incB, total;
     // backward only
-    int64_t vflags, vbuf, sums, gbar;
+    int64_t vbuf, sums, gbar;
 };
 
 static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
@@ -1301,7 +1320,7 @@ static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R
     L.incB = off;
     off += al256(rowsB * D4 * 4 * es);
     L.total = off;
-    L.vflags = L.vbuf = L.sums = L.gbar = 0;
+    L.vbuf = L.sums = L.gbar = 0;
     return L;
 }
 
@@ -1313,8 +1332,6 @@ static StripLayout strip_layout_bwd(int64_t n, int64_t max_la, int64_t max_lb, i
     const int64_t nx = lx - 1, ny = ly - 1, ni = nx * S, nj = ny * S;
     const int64_t ns = (ni + TH - 1) / TH;
     int64_t off = L.total;
-    L.vflags = off;
-    off += al256(n * (ns > 1 ? ns - 1 : 0) * 4 + 4);
     L.vbuf = off;
     off += al256(n * (ns > 1 ? ns - 1 : 0) * nj * es + es);
     L.sums = off;
@@ -1534,7 +1551,7 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
     cudaError_t e;
     if ((e = cudaMemsetAsync(w, 0, 768, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w + L.bnd, 0xff, (size_t)(L.incA - L.bnd), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w + L.vflags, 0, (size_t)(L.vbuf - L.vflags), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w + L.vbuf, 0xff, (size_t)(L.sums - L.vbuf), st)) != cudaSuccess) return e;
     {
         const bool packed = src.mode == PM_VARLEN;
         const int64_t na = rowsA * D4 * 4, nbv = rowsB * D4 * 4;
@@ -1585,7 +1602,6 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         a.cbuf = (const T *)(w + L.coef);
         a.sums = (const T *)(w + L.sums);
         a.vbuf = (T *)(w + L.vbuf);
-        a.vflags = (int *)(w + L.vflags);
         a.counter = counter2;
         a.status = status;
         a.gbar = (T *)(w + L.gbar);
