@@ -356,14 +356,15 @@ struct RowPair<float> {
     using V = float2;
 };
 
-template <typename T, int R, int LAM>
+// SAVE: also store each cell's K(a,b-1) + K(a-1,b) for the adjoint (a.sums)
+template <typename T, int R, int LAM, bool SAVE>
 __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a) {
     constexpr int S = 1 << LAM;
     constexpr int NG = R / S;
     constexpr int CP = 32 * NG;
     constexpr int TH = 32 * R;
     static_assert(R % S == 0, "whole coarse rows per lane");
-    __shared__ T topbuf[STRIP_WARPS][CW * 2];
+    __shared__ __align__(16) T topbuf[STRIP_WARPS][CW * 2];
     __shared__ __align__(16) T ring[STRIP_WARPS][NRING][CP];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -452,7 +453,16 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
             ring_commit();
         }
 
-        for (int w = 0; w * S < tend; ++w) {
+        // lane 0 of a strip with a top row takes its row-0 neighbour from the
+        // published chunk (columns past nj keep the last); lane 0 of a first
+        // strip keeps the boundary K = 1, Q = 0; the other lanes take lane - 1's
+        // last row
+        const bool top0 = top != nullptr && lane == 0;
+        const bool bst = bot != nullptr && !mute && lane == 31;
+        constexpr int WPC = CW / S;   // windows per chunk of the top row
+        static_assert(WPC >= 2 && CW % (2 * S) == 0, "a chunk spans whole windows, half a chunk too");
+        const int nwin = (tend + S - 1) / S;
+        for (int w = 0; w < nwin; ++w) {
             // diagonal w + NRING - 1 into the slot diagonal w - 1 used; then
             // diagonal w has landed (at most NRING - 1 newer groups in flight)
             {
@@ -470,31 +480,36 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
 #pragma unroll
                 for (int g = 0; g < NG; ++g) { co[g] = cn[g]; cn[g] = cw[g]; }
             }
-#pragma unroll
-            for (int jj = 0; jj < S; ++jj) {
-                const int t = w * S + jj;
-                if (t >= tend) break;
-                if (top && t < nj && t >= CW) {
-                    // chunk t/CW (columns t+1 .. t+CW) was loaded half a chunk
-                    // ago: publish it to the warp; load the next one half a
-                    // chunk on (chunks 0 and 1 were loaded at the start)
-                    if ((t % CW) == 0) {
-                        wait_top(t / CW);
+            // the top row at the window's first step t = w S: chunk c = t / CW
+            // (columns t+1 .. t+CW) was loaded half a chunk ago, publish it;
+            // load chunk c + 1 half a chunk on (chunks 0 and 1 were loaded at
+            // the start)
+            if (top) {
+                const int c = w / WPC, wc = w % WPC;
+                if (c >= 1 && c * CW < nj) {
+                    if (wc == 0) {
+                        wait_top(c);
                         __syncwarp();
                         tb[2 * lane] = tn0;
                         tb[2 * lane + 1] = tn1;
                         __syncwarp();
-                    } else if ((t % CW) == CW / 2 && (t / CW + 1) * CW < nj) {
-                        load_top(t / CW + 1);
+                    } else if (wc == WPC / 2 && (c + 1) * CW < nj) {
+                        load_top(c + 1);
                     }
                 }
+            }
+#pragma unroll
+            for (int jj = 0; jj < S; ++jj) {
+                const int t = w * S + jj;
+                if (S > 1 && t >= tend) break;   // only the last window can be partial
                 // lane 0's row 0 is at column t + 1 now
-                if (lane == 0 && top) {
-                    if (t < nj) { pK = tb[(t % CW) * 2]; pQ = tb[(t % CW) * 2 + 1]; }
+                if (top0 && t < nj) {
+                    pK = tb[(t % CW) * 2];
+                    pQ = tb[(t % CW) * 2 + 1];
                 }
                 T shK = 0, shQ = 0;
+                const bool bstore = bst && (unsigned)(t - (TH - 1)) < (unsigned)nj;
                 const int bcol = t - (TH - 1);   // zero-based column of the lane's last row
-                const bool bstore = lane == 31 && bot && !mute && bcol >= 0 && bcol < nj;
                 if constexpr (PACK) {
                     const float kH1 = KP[H - 1].x, qH1 = QP[H - 1].x;   // row H-1 before this step
                     float2 sum[H];
@@ -523,7 +538,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                             }
                         }
                     }
-                    if (a.sums) {
+                    if constexpr (SAVE) {
                         T *dst = a.sums + pp.s_off + ((int64_t)s * tend + t) * TH + lane * R;
 #pragma unroll
                         for (int i = 0; i < H; ++i) { dst[i] = sum[i].x; dst[i + H] = sum[i].y; }
@@ -550,15 +565,13 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                             }
                         }
                     }
-                    if (a.sums) {
+                    if constexpr (SAVE) {
                         T *dst = a.sums + pp.s_off + ((int64_t)s * tend + t) * TH + lane * R;
 #pragma unroll
                         for (int r = 0; r < R; ++r) dst[r] = sum[r];
                     }
                 }
-                if (lane == 0) {
-                    if (!top) { pK = 1; pQ = 0; }
-                } else {
+                if (lane != 0) {
                     pK = shK;
                     pQ = shQ;
                 }
@@ -1292,6 +1305,7 @@ __global__ void strip_trivial_kernel(PairSrc src, int64_t n, T *out) {
 //   | coefficients [ncoef] | bottom rows [nbnd]
 struct StripLayout {
     int64_t plan, coef, bnd, incA, incB, total;
+    int64_t strips;   // at most this many strips (n x the longest pair's)
     // backward only
     int64_t vbuf, sums, gbar;
 };
@@ -1321,6 +1335,7 @@ static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R
     off += al256(rowsB * D4 * 4 * es);
     L.total = off;
     L.vbuf = L.sums = L.gbar = 0;
+    L.strips = n * ns;
     return L;
 }
 
@@ -1466,6 +1481,16 @@ static cudaError_t launch_coef(const PairSrc &src, const PairPlan *plan, int64_t
     return cudaGetLastError();
 }
 
+// Persistent sweep grid: every CTA resident at once (a strip only ever waits
+// on an earlier strip, which some resident warp holds), and no more warps than
+// there can be strips, so that the block scheduler spreads the working warps
+// over the SMs.
+static int strip_grid(const StripLayout &L, int sms, int per_sm) {
+    const int64_t need = (L.strips + STRIP_WARPS - 1) / STRIP_WARPS;
+    const int64_t full = (int64_t)sms * per_sm;
+    return (int)(need < 1 ? 1 : need < full ? need : full);
+}
+
 template <typename T, int R, int LAM>
 static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *out,
                                   long long wait_cycles, int fault_inject, cudaStream_t st,
@@ -1522,15 +1547,13 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
     a.wait_cycles = wait_cycles;
     a.fault_inject = fault_inject;
     a.sums = nullptr;
-    auto sk = strip_kernel<T, R, LAM>;
+    auto sk = strip_kernel<T, R, LAM, false>;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk, STRIP_WARPS * 32, 0)) !=
         cudaSuccess)
         return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    // every CTA resident at once: a strip only ever waits on an earlier strip,
-    // which some resident warp holds
-    sk<<<sms * per_sm, STRIP_WARPS * 32, 0, st>>>(a);
+    sk<<<strip_grid(L, sms, per_sm), STRIP_WARPS * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1587,12 +1610,12 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         a.wait_cycles = wait_cycles;
         a.fault_inject = 0;
         a.sums = (T *)(w + L.sums);
-        auto sk = strip_kernel<T, R, LAM>;
+        auto sk = strip_kernel<T, R, LAM, true>;
         int per_sm = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk, STRIP_WARPS * 32, 0)) != cudaSuccess)
             return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        sk<<<sms * per_sm, STRIP_WARPS * 32, 0, st>>>(a);
+        sk<<<strip_grid(L, sms, per_sm), STRIP_WARPS * 32, 0, st>>>(a);
     }
     {
         AdjArgs<T> a;
