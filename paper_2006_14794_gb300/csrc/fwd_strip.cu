@@ -292,14 +292,15 @@ __device__ __forceinline__ double ld_relaxed(const double *p) {
 __device__ __forceinline__ bool unwritten(float v) { return __float_as_uint(v) == 0xffffffffu; }
 __device__ __forceinline__ bool unwritten(double v) { return __double_as_longlong(v) == -1LL; }
 // a value that happens to have the pattern (only a NaN can) is stored as
-// another NaN
+// another NaN: the unsigned minimum with all-ones-but-one leaves every other
+// bit pattern as it is
 __device__ __forceinline__ void st_boundary(float *p, float v) {
-    if (unwritten(v)) v = __uint_as_float(0x7fffffffu);
-    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+    const unsigned b = umin(__float_as_uint(v), 0xfffffffeu);
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(b));
 }
 __device__ __forceinline__ void st_boundary(double *p, double v) {
-    if (unwritten(v)) v = __longlong_as_double(0x7fffffffffffffffLL);
-    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+    const unsigned long long b = ullmin((unsigned long long)__double_as_longlong(v), 0xfffffffffffffffeULL);
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b));
 }
 
 template <typename T>
@@ -498,14 +499,22 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                     }
                 }
             }
+            // the window's S top-row values (K, Q), read by every lane (one
+            // broadcast address) and taken by lane 0 of a strip with a top row
+            T topv[2 * S];
+            {
+                const T *src = tb + ((w * S) % CW) * 2;
+#pragma unroll
+                for (int e = 0; e < 2 * S; ++e) topv[e] = src[e];
+            }
 #pragma unroll
             for (int jj = 0; jj < S; ++jj) {
                 const int t = w * S + jj;
                 if (S > 1 && t >= tend) break;   // only the last window can be partial
                 // lane 0's row 0 is at column t + 1 now
                 if (top0 && t < nj) {
-                    pK = tb[(t % CW) * 2];
-                    pQ = tb[(t % CW) * 2 + 1];
+                    pK = topv[2 * jj];
+                    pQ = topv[2 * jj + 1];
                 }
                 T shK = 0, shQ = 0;
                 const bool bstore = bst && (unsigned)(t - (TH - 1)) < (unsigned)nj;
@@ -1638,7 +1647,7 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ak, STRIP_WARPS * 32, asmem)) != cudaSuccess)
             return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        ak<<<sms * per_sm, STRIP_WARPS * 32, asmem, st>>>(a);
+        ak<<<strip_grid(L, sms, per_sm), STRIP_WARPS * 32, asmem, st>>>(a);
     }
     const T scale = (T)0.5 / (T)(1LL << (2 * LAM));
     grad_chain_kernel<T><<<sms * 4, 256, 0, st>>>(src, plan, n, (const T *)(w + L.gbar), incA, incB,
