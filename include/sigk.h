@@ -216,6 +216,25 @@ int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64
                        int dtype, const sigk_opts *opts, void *dX, void *dY, void *ws,
                        size_t ws_bytes, void *stream);
 
+/* sigk_gram and sigk_gram_backward in one pass, for a caller whose grad_out
+ * does not depend on the Gram's values (a loss linear in the Gram, such as
+ * the unbiased MMD^2 of Sec. 4, whose derivative with respect to each Gram is
+ * a constant matrix).  out [Bx, By] receives the Gram's values, written by
+ * the backward's own forward sweep (the band form, which also keeps the
+ * checkpoints the adjoint needs; within rounding of sigk_gram's values where
+ * sigk_gram picks another sweep), dX and dY what sigk_gram_backward computes
+ * for grad_out; arguments, opts (symmetric included) and layouts as there.
+ * The workspace is the backward's (size it with SIGK_OP_GRAM_BACKWARD).
+ * Saves the separate forward call: its coefficient contraction and sweep.
+ * Only where the backward runs in the band form (f32, the shorter path
+ * fitting a warp, both lengths >= 2, the linear static kernel):
+ * SIGK_EUNSUPPORTED otherwise, before any launch, and the caller then makes
+ * the two calls. */
+int sigk_gram_value_and_grad(const void *grad_out, const void *X, const void *Y, int64_t Bx,
+                             int64_t By, int64_t L, int64_t M, int64_t d, int dyadic_order,
+                             int dtype, const sigk_opts *opts, void *out, void *dX, void *dY,
+                             void *ws, size_t ws_bytes, void *stream);
+
 /* sigk_pairs_backward without a workspace argument: the paper has no
  * counterpart; this entry point exists for callers that cannot allocate
  * device memory at call time (a process that hands all device memory to its

@@ -280,9 +280,11 @@ int64_t backward_ws_bytes(const PairSrc &src, int64_t n, int lam, int dtype, int
     return grid * slot;
 }
 
+// out: when non-null, the band backward's forward sweep also writes the
+// values (the caller has checked that the band form applies)
 int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_opts *opts,
                  const void *gout, void *dX, void *dY, int64_t nX, int64_t nY, void *ws,
-                 size_t ws_bytes, cudaStream_t st) {
+                 size_t ws_bytes, cudaStream_t st, void *out = nullptr) {
     const int64_t es = dtype == SIGK_F64 ? 8 : 4;
     if (dX && cudaMemsetAsync(dX, 0, (size_t)(nX * es), st) != cudaSuccess) return SIGK_ECUDA;
     if (dY && cudaMemsetAsync(dY, 0, (size_t)(nY * es), st) != cudaSuccess) return SIGK_ECUDA;
@@ -298,7 +300,8 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
         if (!ws || (int64_t)ws_bytes < bytes) return SIGK_ENOMEM_WS;
         float *dA = (float *)(sw ? dY : dX), *dB = (float *)(sw ? dX : dY);
         return cuda_status(
-            launch_band_bwd_f32(o, bp, n_pairs, nbp, (const float *)gout, dA, dB, ws, st, coef_of(opts)));
+            launch_band_bwd_f32(o, bp, n_pairs, nbp, (const float *)gout, dA, dB, ws, st, coef_of(opts),
+                                (float *)out));
     }
     // the symmetric backward exists in the band form only, the RBF lift's in
     // the plain backward only
@@ -627,6 +630,33 @@ int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64
     }
     return run_backward(src, Bx * By, dyadic_order, dtype, opts, grad_out, dX, dY, Bx * L * d,
                         By * M * d, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int sigk_gram_value_and_grad(const void *grad_out, const void *X, const void *Y, int64_t Bx, int64_t By,
+                             int64_t L, int64_t M, int64_t d, int dyadic_order, int dtype,
+                             const sigk_opts *opts, void *out, void *dX, void *dY, void *ws, size_t ws_bytes,
+                             void *stream) {
+    int s = common_checks(Bx, L, M, d, dyadic_order, dtype, opts);
+    if (s) return s;
+    if (By < 0) return SIGK_EINVAL;
+    const bool sym = opts && opts->symmetric;
+    if (sym && (Bx != By || L != M || dY)) return SIGK_EINVAL;
+    if (Bx == 0 || By == 0) return SIGK_OK;
+    if (!grad_out || !X || !Y || !out) return SIGK_EINVAL;
+    PairSrc src;
+    memset(&src, 0, sizeof(src));
+    set_variant(src, opts);
+    src.mode = sym ? PM_GRAM_SYM : PM_GRAM;
+    src.A = X; src.B = sym ? X : Y;
+    src.La = L; src.Lb = M; src.d = d;
+    src.nb = By;
+    src.out_si = By; src.out_sj = 1;
+    const int64_t n = sym ? Bx * (Bx + 1) / 2 : Bx * By;
+    BandPlan bp;
+    if (L < 2 || M < 2 || !bwd_uses_band(src, dyadic_order, dtype, rec_of(opts), rows_of(opts), bp))
+        return SIGK_EUNSUPPORTED;
+    return run_backward(src, n, dyadic_order, dtype, opts, grad_out, dX, sym ? nullptr : dY, Bx * L * d,
+                        sym ? 0 : By * M * d, ws, ws_bytes, (cudaStream_t)stream, out);
 }
 
 int sigk_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n, int dtype,

@@ -1446,7 +1446,7 @@ int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t
 
 cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t n, int64_t nbp,
                                 const float *gout, float *dA, float *dB, void *ws, cudaStream_t st,
-                                int coef_path) {
+                                int coef_path, float *out) {
     if (n <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1519,6 +1519,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         f.ckpt = ckpt;
         f.exitk = exitk;
         f.botq = botq;
+        f.out = out;   // the values too, when the caller asks (sigk_gram_value_and_grad)
         const int fgrid = (int)((nwarps + BAND_WARPS - 1) / BAND_WARPS);
         bool launched = false;
 #define X(r, l, mb)                                                              \

@@ -185,9 +185,10 @@ cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pai
 int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t cap_bytes,
                        int64_t &bytes);
 int64_t band_bwd_bytes(const PairSrc &src, const BandPlan &p, int64_t nbp);
+// out: null, or where the forward sweep also writes the values
 cudaError_t launch_band_bwd_f32(const PairSrc &src, const BandPlan &p, int64_t n, int64_t nbp,
                                 const float *gout, float *dA, float *dB, void *ws, cudaStream_t st,
-                                int coef_path);
+                                int coef_path, float *out = nullptr);
 
 cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype, void *out,
                          cudaStream_t st, void *surf = nullptr);

@@ -106,6 +106,8 @@ SIGNATURES = [
                                    _vp, _vp, ctypes.c_size_t, _vp]),
     ("sigk_gram_backward", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _int, _int, _vp,
                                   _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    ("sigk_gram_value_and_grad", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _int, _int, _vp,
+                                        _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     ("sigk_pairs_backward_noalloc", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _int, _int,
                                            _vp, _vp, _vp]),
     ("sigk_mmd2", _int, [_vp, _vp, _vp, _i64, _i64, _int, _vp, _vp]),
@@ -375,6 +377,34 @@ def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyad
     return dX, dY
 
 
+def gram_value_and_grad(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
+                        need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
+                        schedule: Optional[Schedule] = None, symmetric: bool = False,
+                        variant: Optional[Variant] = None):
+    """(K, dX, dY) in one pass: K as gram computes it and (dX, dY) as
+    gram_backward computes them for grad_out, for a grad_out known before K (a
+    loss linear in the Gram).  The band backward's forward sweep writes K.
+    SigkError with SIGK_EUNSUPPORTED where the backward is not the band form;
+    the caller then calls gram and gram_backward."""
+    X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
+    Bx, L, d = X.shape
+    By, M = Y.shape[0], Y.shape[1]
+    dt = _dtype_code(X)
+    grad_out = grad_out.to(X.dtype).contiguous()
+    if symmetric:
+        need_dx, need_dy = True, False
+    out = torch.empty(Bx, By, dtype=X.dtype, device=X.device)
+    dX = torch.empty_like(X) if need_dx else None
+    dY = torch.empty_like(Y) if need_dy else None
+    o = _opts(rec, symmetric=symmetric, schedule=schedule, variant=variant)
+    ws, nws = _workspace(OP_GRAM_BACKWARD, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
+    _check(lib().sigk_gram_value_and_grad(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), Bx, By, L, M,
+                                          d, int(dyadic_order), dt, ctypes.byref(o), out.data_ptr(),
+                                          _ptr(dX), _ptr(dY), _ptr(ws), nws, _stream(X.device)),
+           "sigk_gram_value_and_grad")
+    return out, dX, dY
+
+
 def mmd2(Kxx: torch.Tensor, Kyy: torch.Tensor, Kxy: torch.Tensor) -> torch.Tensor:
     """Unbiased MMD^2 from the three Gram matrices (one element tensor)."""
     Kxx, Kyy, Kxy = _dev(Kxx, "Kxx"), _dev(Kyy, "Kyy"), _dev(Kxy, "Kxy")
@@ -473,10 +503,50 @@ class _MMD2(torch.autograd.Function):
         return mmd2_backward(g, m, n, dt, dev)
 
 
+class _MMD2Fused(torch.autograd.Function):
+    """MMD^2 and its gradient in one forward: the loss is linear in the three
+    Grams, so dL/dK is a constant matrix (sigk_mmd2_backward of 1) before any
+    Gram is known, and each Gram's values and input gradient come from one
+    sigk_gram_value_and_grad call.  The backward scales the stored gradients."""
+
+    @staticmethod
+    def forward(ctx, X, Y, dyadic_order, variant):
+        m, n = X.shape[0], Y.shape[0]
+        need_x, need_y = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        one = torch.ones(1, dtype=X.dtype, device=X.device)
+        gxx, gyy, gxy = mmd2_backward(one, m, n, X.dtype, X.device)
+        # a Gram whose paths need no gradient is only evaluated
+        if need_x:
+            Kxx, dX, _ = gram_value_and_grad(gxx, X, X, dyadic_order, symmetric=True, variant=variant)
+        else:
+            Kxx, dX = gram(X, X, dyadic_order, symmetric=True, variant=variant), None
+        if need_y:
+            Kyy, dY, _ = gram_value_and_grad(gyy, Y, Y, dyadic_order, symmetric=True, variant=variant)
+        else:
+            Kyy, dY = gram(Y, Y, dyadic_order, symmetric=True, variant=variant), None
+        Kxy, dXb, dYb = gram_value_and_grad(gxy, X, Y, dyadic_order, need_x, need_y, variant=variant)
+        ctx.save_for_backward(dX + dXb if need_x else None, dY + dYb if need_y else None)
+        return mmd2(Kxx, Kyy, Kxy)
+
+    @staticmethod
+    def backward(ctx, g):
+        dX, dY = ctx.saved_tensors
+        return (dX * g.reshape(1).to(dX.dtype) if dX is not None else None,
+                dY * g.reshape(1).to(dY.dtype) if dY is not None else None, None, None)
+
+
 def mmd2_loss(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
               variant: Optional[Variant] = None) -> torch.Tensor:
     """Differentiable unbiased MMD^2 between two batches of paths, built from
-    three signature-kernel Gram matrices."""
+    three signature-kernel Gram matrices.  When a gradient is wanted and the
+    backward runs in the band form, each Gram's values and gradient come from
+    one fused call (_MMD2Fused); otherwise the Grams' own autograd functions."""
+    if torch.is_grad_enabled() and (X.requires_grad or Y.requires_grad):
+        try:
+            return _MMD2Fused.apply(X, Y, dyadic_order, variant)[0]
+        except SigkError as e:
+            if e.status != SIGK_EUNSUPPORTED:
+                raise
     Kxx = SigKernelGram.apply(X, X, dyadic_order, variant)
     Kyy = SigKernelGram.apply(Y, Y, dyadic_order, variant)
     Kxy = SigKernelGram.apply(X, Y, dyadic_order, variant)

@@ -78,6 +78,31 @@ def test_argument_checks_need_no_gpu(libsigk):
     assert libsigk.sigk_gram(None, None, 0, 5, 4, 4, 2, 0, 0, None, None, None, 0, None) == sigk.SIGK_OK
 
 
+def test_value_and_grad_checks_need_no_gpu(libsigk):
+    """sigk_gram_value_and_grad refuses, before any CUDA work, what only the
+    two separate calls can do."""
+    from paper_2006_14794_gb300 import sigk
+    P = ctypes.c_void_p(16)   # never dereferenced: the checks fail first
+    f = libsigk.sigk_gram_value_and_grad
+
+    def call(Bx=2, By=2, L=4, M=4, d=2, lam=0, dtype=0, out=P, dY=P, **kw):
+        o = sigk.SigkOpts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return f(P, P, P, Bx, By, L, M, d, lam, dtype, ctypes.byref(o), out, P, dY, None, 0, None)
+
+    assert call(out=None) == sigk.SIGK_EINVAL
+    assert call(symmetric=1) == sigk.SIGK_EINVAL              # symmetric: dY must be NULL
+    assert call(symmetric=1, By=3, dY=None) == sigk.SIGK_EINVAL
+    assert call(Bx=0) == sigk.SIGK_OK
+    # outside the band form: the caller makes the two calls
+    assert call(L=1) == sigk.SIGK_EUNSUPPORTED
+    assert call(dtype=1) == sigk.SIGK_EUNSUPPORTED
+    assert call(rec=sigk.REC_STRIP) == sigk.SIGK_EUNSUPPORTED
+    assert call(static_kernel=sigk.KERNEL_RBF, sigma=1.0) == sigk.SIGK_EUNSUPPORTED
+    assert call(L=600, M=600) == sigk.SIGK_EUNSUPPORTED        # 599 rows: no band
+
+
 def test_schedule_options_are_checked(libsigk):
     from paper_2006_14794_gb300 import sigk
     P = ctypes.c_void_p(16)

@@ -191,6 +191,66 @@ def test_band_symmetric_backward_matches_oracle(lam, L, d):
     assert grad_err(X.grad.cpu(), rX + rY) <= GRAD_TOL
 
 
+@pytest.mark.parametrize("R,lam,L,M,d,sym", [
+    (16, 1, 256, 256, 32, False),   # the MMD workload's shape
+    (16, 1, 256, 256, 32, True),
+    (8, 1, 100, 90, 17, False),     # rows refine the second path
+    (8, 2, 40, 40, 9, True),
+    (4, 0, 60, 70, 6, False),       # d <= 16: sigk_gram's default is the chain kernel
+])
+def test_gram_value_and_grad_equals_the_two_calls(R, lam, L, M, d, sym):
+    """sigk_gram_value_and_grad: the backward's forward sweep writes the
+    values; gradients identical to sigk_gram_backward's, values identical to
+    sigk_gram's on the same schedule and within the FP32 bar of the oracle
+    (sigk_gram's default for d <= 16, the chain kernel, rounds differently)."""
+    sigk = S()
+    Bx, By = 7, (7 if sym else 6)
+    X32, X64 = inputs.f32(inputs.random_paths(5100 + R + lam, Bx, L, d, scale=2.0, time_channel=True))
+    Y32, Y64 = (X32, X64) if sym else inputs.f32(
+        inputs.random_paths(5200 + R + lam, By, M, d, scale=2.0, time_channel=True))
+    gout = to_dev(np.random.default_rng(51).normal(size=(Bx, By)))
+    X, Y = to_dev(X32), to_dev(Y32)
+    s = sigk.Schedule(sigk.REC_BAND, R, 0)
+    K, dX, dY = sigk.gram_value_and_grad(gout, X, Y, lam, schedule=s, symmetric=sym)
+    rX, rY = sigk.gram_backward(gout, X, Y, lam, schedule=s, symmetric=sym)
+    assert torch.equal(dX, rX)
+    assert (dY is None and rY is None) if sym else torch.equal(dY, rY)
+    assert torch.equal(K, sigk.gram(X, Y, lam, symmetric=sym, schedule=s))
+    assert rel_err(K.cpu().numpy(), oracle.gram(X64, Y64, lam)) <= F32_TOL
+
+
+def test_mmd2_loss_fused_equals_composed():
+    """mmd2_loss with a gradient wanted takes the fused path; the composition
+    of the Grams' autograd functions gives the same loss and gradients."""
+    sigk = S()
+    w = inputs.mmd_batches(B=12, L=64)
+    lam = w["dyadic_order"]
+    X = to_dev(inputs.f32(w["X"])[0]).requires_grad_(True)
+    Y = to_dev(inputs.f32(w["Y"])[0]).requires_grad_(True)
+    v = sigk.mmd2_loss(X, Y, lam)
+    def fn_name(t):   # the node under the [0] select
+        return type(t.grad_fn.next_functions[0][0]).__name__
+
+    assert "MMD2Fused" in fn_name(v)
+    (3.0 * v).backward()
+    X2 = X.detach().clone().requires_grad_(True)
+    Y2 = Y.detach().clone().requires_grad_(True)
+    Kxx = sigk.SigKernelGram.apply(X2, X2, lam, None)
+    Kyy = sigk.SigKernelGram.apply(Y2, Y2, lam, None)
+    Kxy = sigk.SigKernelGram.apply(X2, Y2, lam, None)
+    v2 = sigk._MMD2.apply(Kxx, Kyy, Kxy)[0]
+    (3.0 * v2).backward()
+    assert abs(v.item() - v2.item()) <= 1e-6 * max(1.0, abs(v2.item()))
+    assert grad_err(X.grad.cpu(), X2.grad.cpu()) <= 1e-6
+    assert grad_err(Y.grad.cpu(), Y2.grad.cpu()) <= 1e-6
+    # outside the band form (FP64) the composition runs
+    X64 = X.detach().double().requires_grad_(True)
+    v64 = sigk.mmd2_loss(X64, Y.detach().double(), lam)
+    assert "MMD2Fused" not in fn_name(v64)
+    (3.0 * v64).backward()
+    assert grad_err(X64.grad.cpu(), X2.grad.cpu()) <= 1e-4
+
+
 def test_symmetric_backward_argument_checks():
     sigk = S()
     X = to_dev(inputs.random_paths(4200, 3, 20, 3))
