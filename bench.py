@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -92,7 +93,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+        # the raw samples: SIGK_CLOCKS_DIR if set, else the temporary directory
+        out_dir = os.environ.get("SIGK_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, "sigk_clocks_rank%d.csv" % gpu_index)
 
     def start(self):
         try:
