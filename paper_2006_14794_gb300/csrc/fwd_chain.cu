@@ -40,9 +40,10 @@
 // Arithmetic: rows i and i + R/2 of a lane are carried as one float2, so each
 // pair of rows costs one packed add, one packed fma and one packed add
 // (FADD2/FFMA2: half the issue slots of scalar FP32 at the same FP32 lane
-// throughput).  The macro-step of R steps is a runtime loop over its
-// R / 2^lambda coarse-column windows with the 2^lambda steps of a window
-// unrolled, which keeps the loop body small enough for the instruction cache.
+// throughput).  A macro-step's R / 2^lambda coarse-column windows and each
+// window's 2^lambda steps are unrolled (R steps of straight-line code), so the
+// column increments' shift from group to group is register renaming; the
+// macro-steps themselves are a runtime loop.
 #include <algorithm>
 
 #include "sigk_internal.cuh"
