@@ -40,10 +40,9 @@
 // Arithmetic: rows i and i + R/2 of a lane are carried as one float2, so each
 // pair of rows costs one packed add, one packed fma and one packed add
 // (FADD2/FFMA2: half the issue slots of scalar FP32 at the same FP32 lane
-// throughput).  A macro-step's R / 2^lambda coarse-column windows and each
-// window's 2^lambda steps are unrolled (R steps of straight-line code), so the
-// column increments' shift from group to group is register renaming; the
-// macro-steps themselves are a runtime loop.
+// throughput).  A macro-step's R / 2^lambda windows and their 2^lambda steps
+// are unrolled (R steps of straight-line code), so the column increments'
+// shift from group to group is register renaming; macro-steps are a loop.
 #include <algorithm>
 
 #include "sigk_internal.cuh"
