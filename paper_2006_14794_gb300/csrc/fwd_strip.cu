@@ -343,20 +343,6 @@ __device__ __forceinline__ void ring_commit() { asm volatile("cp.async.commit_gr
 template <int N>
 __device__ __forceinline__ void ring_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// FP32 rows i and i + R/2 of a lane are carried as one float2 (FADD2/FFMA2:
-// one issue slot for two rows, bit for bit the scalar arithmetic); FP64 rows
-// are scalar.
-template <typename T>
-struct RowPair {
-    static constexpr bool PACK = false;
-    using V = T;
-};
-template <>
-struct RowPair<float> {
-    static constexpr bool PACK = true;
-    using V = float2;
-};
-
 // SAVE: also store each cell's K(a,b-1) + K(a-1,b) for the adjoint (a.sums)
 template <typename T, int R, int LAM, bool SAVE>
 __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a) {
@@ -391,9 +377,10 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
         const bool mute = a.fault_inject && lo == 0 && s == 0;
         const int tend = nj + TH - 1;   // steps until the last row leaves column nj
 
-        // scalar rows (FP64), or rows (i, i + H) and groups (g, g + NH) in
-        // float2s (FP32, NG even for every FP32 instance)
-        constexpr bool PACK = RowPair<T>::PACK;
+        // FP32: rows (i, i + H) and groups (g, g + NH) of a lane in float2s
+        // (FADD2/FFMA2: one issue slot for two rows, bit for bit the scalar
+        // arithmetic; NG is even for every FP32 instance).  FP64: scalar rows.
+        constexpr bool PACK = sizeof(T) == 4;
         constexpr int H = R / 2, NH = NG / 2;
         static_assert(!PACK || NG % 2 == 0, "an even number of coarse rows per lane");
         T K[R], Q[R], cn[NG], co[NG];
