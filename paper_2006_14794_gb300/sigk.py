@@ -335,8 +335,11 @@ def version() -> str:
 
 def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
                    need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
-                   schedule: Optional[Schedule] = None, variant: Optional[Variant] = None):
-    """(dX, dY) with dX[b] = grad_out[b] dk(X_b, Y_b)/dX_b (None when not needed)."""
+                   schedule: Optional[Schedule] = None, variant: Optional[Variant] = None,
+                   check_status: bool = False):
+    """(dX, dY) with dX[b] = grad_out[b] dk(X_b, Y_b)/dX_b (None when not needed).
+    check_status: as for pairs (waits for the stream, raises on a device-side
+    timeout)."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     B, L, d = X.shape
     M = Y.shape[1]
@@ -349,6 +352,8 @@ def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dya
     _check(lib().sigk_pairs_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), B, L, M, d,
                                      int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
                                      _ptr(ws), nws, _stream(X.device)), "sigk_pairs_backward")
+    if check_status:
+        _status(ws, X.device)
     return dX, dY
 
 

@@ -89,6 +89,29 @@ def test_injected_fault_is_reported_as_timeout():
     assert rel_err(got, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_nan_inputs_pass_through_the_boundary_rows(dtype):
+    """A NaN in one pair's path reaches that pair's result and no other, and
+    the boundary rows (whose unwritten entries hold an all-ones NaN pattern)
+    still hand it on: no wait times out, forward or backward."""
+    sigk = S()
+    B, L, d = 3, 1100, 3   # 1099 rows: several strips per pair
+    X64 = inputs.random_paths(1650, B, L, d)
+    Y64 = inputs.random_paths(1651, B, L, d)
+    bad = X64.copy()
+    bad[1, 300, 1] = np.nan
+    X = to_dev(bad, dtype)
+    Y = to_dev(Y64, dtype)
+    got = sigk.pairs(X, Y, 0, rec=sigk.REC_STRIP, check_status=True).cpu().numpy()
+    assert np.isnan(got[1]) and np.all(np.isfinite(got[[0, 2]]))
+    keep = np.array([0, 2])
+    assert rel_err(got[keep], oracle.pairs(X64[keep], Y64[keep], 0)) <= (1e-5 if dtype == torch.float32 else 1e-11)
+    if dtype == torch.float32:
+        dX, _ = sigk.pairs_backward(torch.ones(B, device="cuda"), X, Y, 0, rec=sigk.REC_STRIP,
+                                    check_status=True)
+        assert torch.isnan(dX[1]).any() and torch.isfinite(dX[[0, 2]]).all()
+
+
 def test_graph_captured_calls_replay_correctly():
     # the uneven-length strip path (memsets, planning, coefficients, sweep) and
     # the chained Gram, each captured once and replayed on new inputs
