@@ -60,6 +60,9 @@ int cuda_status(cudaError_t e) {
 constexpr long long WAIT_CYCLES = 2000000000LL;
 // Largest workspace the strip path asks for; bigger batches run in pieces.
 constexpr int64_t STRIP_WS_CAP = 8LL << 30;
+// the band backward's batches: a 128 x 128 Gram of 256-point paths (band,
+// dense dk/dG and its band layout, about 13 GB) in one launch
+constexpr int64_t BAND_BWD_WS_CAP = 16LL << 30;
 
 int fault_of(const sigk_opts *o) { return o ? o->fault_inject : 0; }
 int rows_of(const sigk_opts *o) { return o ? o->rows_per_lane : 0; }
@@ -265,7 +268,7 @@ int64_t backward_ws_bytes(const PairSrc &src, int64_t n, int lam, int dtype, int
         bool sw;
         const PairSrc o = band_orient(src, n, sw);
         int64_t bytes;
-        band_bwd_batch(o, bp, n, STRIP_WS_CAP, bytes);
+        band_bwd_batch(o, bp, n, BAND_BWD_WS_CAP, bytes);
         return bytes;
     }
     if (rec == SIGK_REC_BAND || src.mode == PM_GRAM_SYM) return -1;
@@ -296,7 +299,7 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
         bool sw;
         const PairSrc o = band_orient(src, n_pairs, sw);
         int64_t bytes;
-        const int64_t nbp = band_bwd_batch(o, bp, n_pairs, STRIP_WS_CAP, bytes);
+        const int64_t nbp = band_bwd_batch(o, bp, n_pairs, BAND_BWD_WS_CAP, bytes);
         if (!ws || (int64_t)ws_bytes < bytes) return SIGK_ENOMEM_WS;
         float *dA = (float *)(sw ? dY : dX), *dB = (float *)(sw ? dX : dY);
         return cuda_status(
