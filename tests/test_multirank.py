@@ -31,7 +31,7 @@ def _rank(rank, world, port, out):
 
 def test_max_over_ranks_two_gloo_ranks():
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_rank, args=(2, port, out), nprocs=2, start_method="spawn")
         assert out[0] == 15.0 and out[1] == 15.0
