@@ -462,9 +462,18 @@ def _extra_setup(name, batch=0):
             return 4 * nb * 510 * 510 / (time.perf_counter() - t0), "4 x %d pairs of Kxy (forward only)" % nb
         host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
                 torch.empty(X32.shape).pin_memory())
+        # algorithmic flop per step, full Grams: the coefficients of the three
+        # Grams (2d per coarse cell) and their forward sweeps (3 per refined
+        # cell); the adjoint sweeps of Kxx and Kxy, the Grams with X in them (7
+        # per refined cell: two multiply-adds, an add and the dk/dc
+        # multiply-add); the chain-rule contractions into dX (2 (255 nb)^2 d
+        # each: one for Kxy, two for Kxx, X in both arguments)
+        gram_cells, gram_coarse, nch = nb * nb * 510 * 510, nb * nb * 255 * 255, 32
+        flop = (3 * gram_coarse * 2 * nch + 3 * gram_cells * 3 + 2 * gram_cells * 7
+                + 3 * 2 * (255 * nb) ** 2 * nch)
         return ("MMD^2 %d vs %d, L=256, d=32 walks + drift, dyadic order 1, loss + dL/dX, fp32 "
                 "(value counts the forward cells of Kxx, Kyy, Kxy as full Grams)" % (nb, nb), step, cells,
-                3 * cells, oracle_rate, host_step, host, X32.nbytes + Y32.nbytes, X32.nbytes)
+                flop, oracle_rate, host_step, host, X32.nbytes + Y32.nbytes, X32.nbytes)
     if name in ("gram256_implicit", "gram256_rbf"):
         # the benchmark Gram with the implicit scheme (Sec. 3.1 remark) or the
         # RBF static-kernel lift (Sec. 2.2, sigma = 1)
