@@ -349,6 +349,11 @@ def run_gpu(args):
             "fp64_plain_gpu": f64,
             "cpu_baseline": cpu,
         }
+        if ws == 1 and not args.skip_workloads:
+            # the other configurations, measured in the same run (one GPU)
+            del flush
+            torch.cuda.empty_cache()
+            line["workloads"] = run_workloads(args)
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -357,16 +362,102 @@ def run_gpu(args):
     return 0
 
 
-# ---- other workloads (parity cases of the test suite, measured here on request) ----
+# ---- the other workloads ----------------------------------------------------
+#
+# Each is a parity case of the test suite at full size, measured the same way
+# as the headline: W >= 3 untimed calls, then >= 5 timed calls bracketed by
+# CUDA events on the launching stream with a 256 MB L2 flush before each, the
+# result checked against the oracle on sampled outputs, and the oracle timed
+# on this host's cores on a bounded sample of the same workload.  The default
+# run reports all of them under the headline line's "workloads" key;
+# `--workload NAME` prints one of them as a line of its own (with e2e).
 
-def _extra_setup(name, batch=0):
-    """(description, step(), cells per step, flop per step, oracle-sample fn, h2d/d2h info).
-    batch > 0 keeps the first `batch` pairs of the long-pair workload (a small
-    case for profilers)."""
+# Dense FP64 of the GB300, nominal (MEASURED_PEAKS.json has no FP64 figure).
+FP64_PEAK_NOMINAL_TF = 1.25
+
+
+def _pick(rng_seed, n, k, must=()):
+    rng = np.random.default_rng(rng_seed)
+    idx = list(must) + [int(v) for v in rng.choice(n, size=min(k, n), replace=False)]
+    return sorted(set(idx))
+
+
+def _timed_oracle(fn):
+    t0 = time.perf_counter()
+    r = fn()
+    return r, time.perf_counter() - t0
+
+
+def _workload(name, batch=0, cache=None):
+    """The workload `name` as a dict:
+    desc, dtype ("f32" | "f64"), step() (one timed call; returns what parity
+    reads), cells and pairs per step, flop per step (the algorithmic work),
+    kernels (the launches of one step, dominant first), oracle_rate(budget)
+    -> (cells/s, sample, threads), parity(out) -> (rel err, sample),
+    host_step(*host) with host buffers and its h2d / d2h bytes.
+    batch > 0 keeps the first `batch` pairs / paths (a small case for
+    profilers); cache: dict shared between workloads (oracle results)."""
     import torch
     from paper_2006_14794_gb300 import inputs, sigk, tune
     import oracle
+    cache = {} if cache is None else cache
+
+    if name in ("gram_small_f64", "gram_small_f32"):
+        # config 1: Gram 8 x 8, L=32, d=3 (time + 2 walks), dyadic order 1,
+        # plus the 8 straight-line pairs of the closed-form check
+        w = inputs.gram_small()
+        lam = w["dyadic_order"]
+        f64 = name.endswith("f64")
+        tdt = torch.float64 if f64 else torch.float32
+        X32, X64 = inputs.f32(w["X"])
+        Y32, Y64 = inputs.f32(w["Y"])
+        lx32, lx64 = inputs.f32(w["lines_x"])
+        ly32, ly64 = inputs.f32(w["lines_y"])
+        src = (X64, Y64, lx64, ly64) if f64 else (X32, Y32, lx32, ly32)
+        Xd, Yd, LXd, LYd = [torch.as_tensor(a, dtype=tdt).cuda() for a in src]
+        n = (32 - 1) << lam
+        cells = (64 + 8) * n * n
+        coarse = (64 + 8) * 31 * 31
+
+        def step():
+            return sigk.gram(Xd, Yd, lam), sigk.pairs(LXd, LYd, lam)
+
+        def refs():
+            if "gram_small" not in cache:
+                cache["gram_small"] = _timed_oracle(
+                    lambda: (oracle.gram(X64, Y64, lam), oracle.pairs(lx64, ly64, lam)))
+            return cache["gram_small"]
+
+        def oracle_rate(budget):
+            _, dt = refs()
+            return cells / dt, "the whole step (64 Gram entries + 8 straight-line pairs)", oracle.num_threads()
+
+        def parity(out):
+            (K, Ln), _ = refs()
+            g = np.concatenate([out[0].double().cpu().numpy().ravel(), out[1].double().cpu().numpy()])
+            r = np.concatenate([K.ravel(), Ln])
+            return float(np.max(np.abs(g - r) / np.maximum(np.abs(r), 1e-3))), "all 72 outputs"
+
+        host = tuple(torch.as_tensor(a, dtype=tdt).pin_memory() for a in src) + (
+            torch.empty(8, 8, dtype=tdt).pin_memory(), torch.empty(8, dtype=tdt).pin_memory())
+
+        def host_step(hx, hy, hlx, hly, hk, hl):
+            k = sigk.gram(hx.cuda(non_blocking=True), hy.cuda(non_blocking=True), lam)
+            l = sigk.pairs(hlx.cuda(non_blocking=True), hly.cuda(non_blocking=True), lam)
+            hk.copy_(k, non_blocking=True)
+            hl.copy_(l, non_blocking=True)
+        es = 8 if f64 else 4
+        return dict(
+            desc="Gram 8x8, L=M=32, d=3 (time + 2 walks), dyadic order 1, plus 8 straight-line pairs, %s"
+                 % ("fp64 (plain per-pair sweep, the printed scheme)" if f64 else "fp32 (chained register sweep)"),
+            dtype="f64" if f64 else "f32", step=step, cells=cells, pairs=72,
+            flop=3 * cells + 2 * 3 * coarse,
+            kernels="plain_kernel<double>" if f64 else "chain_f32_kernel",
+            oracle_rate=oracle_rate, parity=parity, host_step=host_step, host=host,
+            h2d=sum(a.nbytes for a in src), d2h=72 * es)
+
     if name == "uneven4096":
+        # config 3: 4096 pairs, L, M ~ U{16..512}, d=16 walks, dyadic order 1
         w = inputs.uneven_pairs()
         lam = w["dyadic_order"]
         X32, X64 = inputs.f32(w["Xp"])
@@ -377,8 +468,8 @@ def _extra_setup(name, batch=0):
         coarse = int(np.sum((lx - 1) * (ly - 1)))
         Xd, Yd = torch.from_numpy(X32).cuda(), torch.from_numpy(Y32).cuda()
         xod, yod = torch.as_tensor(xo).cuda(), torch.as_tensor(yo).cuda()
-        # schedule chosen by timing the candidates on these inputs (before the
-        # timed region), then the whole call captured as one CUDA graph
+        # the schedule chosen by timing the candidates on these inputs (before
+        # the timed region), then the whole call captured as one CUDA graph
         sched, _ = tune.tune("pairs_varlen", Xd, xod, Yd, yod, lam, 512, store=False)
         g = sigk.graphed(sigk.pairs_varlen, Xd, xod, Yd, yod, lam, max_len=512, schedule=sched)
 
@@ -398,51 +489,115 @@ def _extra_setup(name, batch=0):
                 sxo = np.concatenate([[0], np.cumsum(lx[b])]); syo = np.concatenate([[0], np.cumsum(ly[b])])
                 oracle.pairs_varlen(sub_x, sxo, sub_y, syo, lam)
                 cc += int(np.sum(((lx[b] - 1) << lam) * ((ly[b] - 1) << lam))); done = b[-1] + 1
-            return cc / (time.perf_counter() - t0), "%d of 4096 pairs" % done
+            return cc / (time.perf_counter() - t0), "pairs 0..%d of 4096" % (done - 1), oracle.num_threads()
+
+        def parity(out):
+            o = out.cpu().numpy()
+            cl = (lx - 1) * (ly - 1)
+            idx = _pick(8, 4096, 60, must=(0, 4095, int(np.argmax(cl)), int(np.argmin(cl))))
+            ref = np.array([oracle.sigkernel(X64[xo[b]:xo[b + 1]], Y64[yo[b]:yo[b + 1]], lam) for b in idx])
+            return float(np.max(np.abs(o[idx] - ref) / np.maximum(np.abs(ref), 1e-3))), \
+                "%d pairs (60 random, the first, the last, the most and the fewest cells)" % len(idx)
         host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
                 torch.as_tensor(xo).pin_memory(), torch.as_tensor(yo).pin_memory(),
                 torch.empty(4096).pin_memory())
-        return ("4096 pairs, L,M ~ U{16..512}, d=16 walks, dyadic order 1, fp32; tuned schedule "
-                "rec=%d rows_per_lane=%d coef_path=%d orient=%d, one CUDA graph per call"
-                % (sched.rec, sched.rows_per_lane, sched.coef_path, sched.orient), step, cells,
-                3 * cells + 2 * 16 * coarse, oracle_rate, host_step, host,
-                X32.nbytes + Y32.nbytes + xo.nbytes + yo.nbytes, 4096 * 4)
+        return dict(
+            desc="4096 pairs, L,M ~ U{16..512}, d=16 walks, dyadic order 1, fp32; tuned schedule "
+                 "rec=%d rows_per_lane=%d coef_path=%d orient=%d, one CUDA graph per call"
+                 % (sched.rec, sched.rows_per_lane, sched.coef_path, sched.orient),
+            dtype="f32", step=step, cells=cells, pairs=4096, flop=3 * cells + 2 * 16 * coarse,
+            kernels=_uneven_kernels(sched), oracle_rate=oracle_rate, parity=parity,
+            host_step=host_step, host=host, h2d=X32.nbytes + Y32.nbytes + xo.nbytes + yo.nbytes,
+            d2h=4096 * 4)
+
     if name.startswith("long64"):
-        lam = int(name[-1])
+        # config 5: 64 pairs, L=M=4096, d=64 (time + 63 walks), dyadic order 0 / 1
+        lam = int(name[len("long64_l")])
+        f64 = name.endswith("_f64")
         w = inputs.long_pairs()
         nb = batch if 0 < batch < 64 else 64
         X32, X64 = inputs.f32(w["X"][:nb])
         Y32, Y64 = inputs.f32(w["Y"][:nb])
         n = (4095 << lam)
         cells = nb * n * n
-        Xd, Yd = torch.from_numpy(X32).cuda(), torch.from_numpy(Y32).cuda()
+        tdt = torch.float64 if f64 else torch.float32
+        Xd = torch.as_tensor(X64 if f64 else X32, dtype=tdt).cuda()
+        Yd = torch.as_tensor(Y64 if f64 else Y32, dtype=tdt).cuda()
+        # FP64 takes the strip path (the recurrence precision form); FP32 the
+        # library's default (strip path, tensor-core coefficients)
+        rec = sigk.REC_CHAIN if f64 else sigk.REC_AUTO
 
         def step():
-            return sigk.pairs(Xd, Yd, lam)
+            return sigk.pairs(Xd, Yd, lam, rec=rec)
 
         def host_step(hx, hy, ho):
-            o = sigk.pairs(hx.cuda(non_blocking=True), hy.cuda(non_blocking=True), lam)
+            o = sigk.pairs(hx.cuda(non_blocking=True), hy.cuda(non_blocking=True), lam, rec=rec)
             ho.copy_(o, non_blocking=True)
 
+        # the oracle on 8 of the pairs (spread over the batch), timed, and
+        # their values as the parity reference; the rate extrapolates to 64
+        sample = sorted(set(int(v) for v in np.linspace(0, nb - 1, min(8, nb)).round()))
+
+        def refs():
+            key = ("long64", lam, nb)
+            if key not in cache:
+                cache[key] = _timed_oracle(lambda: oracle.pairs(X64[sample], Y64[sample], lam))
+            return cache[key]
+
         def oracle_rate(budget):
-            t0 = time.perf_counter()
-            oracle.pairs(X64[:1], Y64[:1], lam)
-            return n * n / (time.perf_counter() - t0), "1 of 64 pairs (single thread: one pair)"
-        host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
-                torch.empty(nb).pin_memory())
-        return ("%d pairs, L=M=4096, d=64 time-augmented walks, dyadic order %d, fp32" % (nb, lam), step,
-                cells, 3 * cells + 2 * 64 * nb * 4095 * 4095, oracle_rate, host_step, host,
-                X32.nbytes + Y32.nbytes, nb * 4)
+            _, dt = refs()
+            return len(sample) * n * n / dt, "%d of %d pairs (indices %s), one OpenMP thread per pair; " \
+                "the rate extrapolates to the whole batch" % (len(sample), nb, sample), \
+                min(len(sample), oracle.num_threads())
+
+        def parity(out):
+            ref, _ = refs()
+            o = out.double().cpu().numpy()[sample]
+            return float(np.max(np.abs(o - ref) / np.maximum(np.abs(ref), 1e-3))), \
+                "%d pairs %s" % (len(sample), sample)
+        host = (torch.as_tensor(X64 if f64 else X32, dtype=tdt).pin_memory(),
+                torch.as_tensor(Y64 if f64 else Y32, dtype=tdt).pin_memory(),
+                torch.empty(nb, dtype=tdt).pin_memory())
+        es = 8 if f64 else 4
+        kern = ("coef_kernel<double> (FMA contraction) + strip_kernel<double, 8, lambda> (256-row strips)"
+                if f64 else "coef_tc5_kernel (split-TF32 tcgen05 contraction) + strip_kernel<float> "
+                            "(%d-row strips)" % (256 if lam == 0 else 512))
+        return dict(
+            desc="%d pairs, L=M=4096, d=64 time-augmented walks, dyadic order %d, %s"
+                 % (nb, lam, "fp64 recurrence and contraction (strip path)" if f64 else "fp32 recurrence, "
+                    "split-TF32 increment Gram"),
+            dtype="f64" if f64 else "f32", step=step, cells=cells, pairs=nb,
+            flop=3 * cells + 2 * 64 * nb * 4095 * 4095, kernels=kern, oracle_rate=oracle_rate,
+            parity=parity, host_step=host_step, host=host, h2d=2 * nb * 4096 * 64 * es, d2h=nb * es)
+
     if name == "mmd128":
+        # config 4: MMD^2 between 128 and 128 paths, L=256, d=32, dyadic order 1;
+        # one step = the loss and dL/dX
         w = inputs.mmd_batches()
         lam = w["dyadic_order"]
         nb = batch if 1 < batch < 128 else 128
         X32, X64 = inputs.f32(w["X"][:nb])
         Y32, Y64 = inputs.f32(w["Y"][:nb])
-        npairs = nb * nb * 3
-        cells = npairs * (510 * 510)
         Yd = torch.from_numpy(Y32).cuda()
         Xd = torch.from_numpy(X32).cuda()
+        nc, nn = 510 * 510, 255 * 255
+        # the pairs the U-statistic uses: i < j of Kxx and Kyy, all of Kxy
+        u_pairs = nb * (nb - 1) + nb * nb
+        cells = u_pairs * nc
+        # algorithmic flop of the step as it runs: Kxx and Kyy are symmetric
+        # Grams (pairs i <= j, n(n+1)/2 of them), Kxy is full.  Coefficients
+        # (2d per coarse cell) and forward sweeps (3 per refined cell) of all
+        # three; adjoint sweeps of Kxx and Kxy, the Grams with X in them (7 per
+        # refined cell: two multiply-adds, an add and the dk/dc multiply-add);
+        # chain-rule contractions into dX, 2 (255 nb)^2 d each: one for Kxy,
+        # and for Kxx the row-role and column-role contractions over i <= j,
+        # together one full contraction
+        sym = nb * (nb + 1) // 2
+        fwd_pairs = 2 * sym + nb * nb
+        adj_pairs = sym + nb * nb
+        nch = 32
+        flop = (fwd_pairs * nn * 2 * nch + fwd_pairs * nc * 3 + adj_pairs * nc * 7
+                + 2 * 2 * (255 * nb) ** 2 * nch)
 
         def step():
             X = Xd.clone().requires_grad_(True)
@@ -456,24 +611,50 @@ def _extra_setup(name, batch=0):
             v.backward()
             hg.copy_(X.grad, non_blocking=True)
 
+        rows = [0, min(77, nb - 1)]
+
+        def refs():
+            key = ("mmd128", nb)
+            if key not in cache:
+                m = n = nb
+
+                def run():
+                    gxx = np.full((1, m), 1.0 / (m * (m - 1)))
+                    gxy = np.full((1, n), -2.0 / (m * n))
+                    out = []
+                    for i in rows:
+                        gi = gxx.copy()
+                        gi[0, i] = 0.0
+                        a, _ = oracle.gram_grad(X64[i:i + 1], X64, lam, gi, want_dy=False)
+                        b, _ = oracle.gram_grad(X64[i:i + 1], Y64, lam, gxy, want_dy=False)
+                        out.append(2.0 * a[0] + b[0])
+                    return out
+                cache[key] = _timed_oracle(run)
+            return cache[key]
+
         def oracle_rate(budget):
-            t0 = time.perf_counter()
-            oracle.gram(X64[:4], Y64, lam)
-            return 4 * nb * 510 * 510 / (time.perf_counter() - t0), "4 x %d pairs of Kxy (forward only)" % nb
+            _, dt = refs()
+            pairs_done = len(rows) * 2 * nb
+            return pairs_done * nc / dt, "values and gradients of the %d pairs of rows %s of Kxx and Kxy " \
+                "(dL/dX_i for those rows); forward cells of those pairs per second" % (pairs_done, rows), \
+                oracle.num_threads()
+
+        def parity(out):
+            want, _ = refs()
+            g = out.double().cpu().numpy()
+            err = max(float(np.max(np.abs(g[i] - wv)) / np.max(np.abs(wv))) for i, wv in zip(rows, want))
+            return err, "dL/dX rows %s (max |g - g_ref| / max |g_ref| per row)" % rows
         host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
                 torch.empty(X32.shape).pin_memory())
-        # algorithmic flop per step, full Grams: the coefficients of the three
-        # Grams (2d per coarse cell) and their forward sweeps (3 per refined
-        # cell); the adjoint sweeps of Kxx and Kxy, the Grams with X in them (7
-        # per refined cell: two multiply-adds, an add and the dk/dc
-        # multiply-add); the chain-rule contractions into dX (2 (255 nb)^2 d
-        # each: one for Kxy, two for Kxx, X in both arguments)
-        gram_cells, gram_coarse, nch = nb * nb * 510 * 510, nb * nb * 255 * 255, 32
-        flop = (3 * gram_coarse * 2 * nch + 3 * gram_cells * 3 + 2 * gram_cells * 7
-                + 3 * 2 * (255 * nb) ** 2 * nch)
-        return ("MMD^2 %d vs %d, L=256, d=32 walks + drift, dyadic order 1, loss + dL/dX, fp32 "
-                "(value counts the forward cells of Kxx, Kyy, Kxy as full Grams)" % (nb, nb), step, cells,
-                flop, oracle_rate, host_step, host, X32.nbytes + Y32.nbytes, X32.nbytes)
+        return dict(
+            desc="MMD^2 %d vs %d, L=256, d=32 walks + drift, dyadic order 1, loss + dL/dX, fp32 "
+                 "(cells: the forward cells of the U-statistic's %d distinct pairs)" % (nb, nb, u_pairs),
+            dtype="f32", step=step, cells=cells, pairs=u_pairs, flop=flop,
+            kernels="chain_band_adj_kernel + band_gemm_kernel + band_coef_kernel + band_gbar_kernel + "
+                    "chain_band_kernel (band form; fused value-and-gradient calls for Kxx and Kxy)",
+            oracle_rate=oracle_rate, parity=parity, host_step=host_step, host=host,
+            h2d=X32.nbytes + Y32.nbytes, d2h=X32.nbytes)
+
     if name in ("gram256_implicit", "gram256_rbf"):
         # the benchmark Gram with the implicit scheme (Sec. 3.1 remark) or the
         # RBF static-kernel lift (Sec. 2.2, sigma = 1)
@@ -488,11 +669,13 @@ def _extra_setup(name, batch=0):
             okw = dict(scheme="implicit")
             cflop = 2 * d + 2          # <dx, dy>, then c / (1 - c/2)
             what = "implicit scheme"
+            kern = "chain_f32_kernel (implicit instance)"
         else:
             v = sigk.Variant(static_kernel="rbf", sigma=1.0)
             okw = dict(static_kernel="rbf", sigma=1.0)
             cflop = 9 * d              # |u|^2, <u,dx>, <u,dy>, <dx,dy> and u = x_p - y_q per channel
             what = "RBF lift (sigma = 1), explicit scheme"
+            kern = "rbf_coef_kernel + chain_band_kernel"
         n = (L - 1) << lam
         cells = nbx * nby * n * n
         coarse = nbx * nby * (L - 1) * (L - 1)
@@ -510,7 +693,8 @@ def _extra_setup(name, batch=0):
             while time.perf_counter() - t0 < budget and rows < nbx:
                 oracle.gram(X64[rows:rows + 1], Y64, lam, **okw)
                 rows += 1
-            return rows * nby * n * n / (time.perf_counter() - t0), "%d Gram rows of %d" % (rows, nbx)
+            return rows * nby * n * n / (time.perf_counter() - t0), "%d Gram rows of %d" % (rows, nbx), \
+                oracle.num_threads()
 
         def parity(out):
             rng = np.random.default_rng(7)
@@ -524,9 +708,13 @@ def _extra_setup(name, batch=0):
             return float(max(errs)), "16 sampled entries"
         host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
                 torch.empty(nbx, nby).pin_memory())
-        return ("gram %dx%d, L=M=128, d=8 time-augmented random walks, dyadic order 2, fp32, %s" % (nbx, nby, what),
-                step, cells, 3 * cells + cflop * coarse, oracle_rate, host_step, host,
-                X32.nbytes + Y32.nbytes, nbx * nby * 4, parity)
+        return dict(
+            desc="gram %dx%d, L=M=128, d=8 time-augmented random walks, dyadic order 2, fp32, %s"
+                 % (nbx, nby, what),
+            dtype="f32", step=step, cells=cells, pairs=nbx * nby, flop=3 * cells + cflop * coarse,
+            kernels=kern, oracle_rate=oracle_rate, parity=parity, host_step=host_step, host=host,
+            h2d=X32.nbytes + Y32.nbytes, d2h=nbx * nby * 4)
+
     if name == "surface256":
         # the solution surface on the sample grid for the benchmark's 65536
         # pairs (X_i, Y_j) of the 256 x 256 Gram, as a batch of pairs
@@ -558,7 +746,8 @@ def _extra_setup(name, batch=0):
             while time.perf_counter() - t0 < budget and done < nb:
                 oracle.pairs_surface(np.repeat(X64[done:done + 1], nb, 0), Y64, lam)
                 done += 1
-            return done * nb * n * n / (time.perf_counter() - t0), "%d x %d pairs" % (done, nb)
+            return done * nb * n * n / (time.perf_counter() - t0), "%d x %d pairs" % (done, nb), \
+                oracle.num_threads()
 
         def parity(out):
             rng = np.random.default_rng(8)
@@ -569,10 +758,15 @@ def _extra_setup(name, batch=0):
                 ref = oracle.surface(X64[i], Y64[j], lam)
                 errs.append(float(np.max(np.abs(s[t] - ref) / np.maximum(np.abs(ref), 1e-3))))
             return max(errs), "6 sampled pairs, every node"
-        return ("%d pairs (X_i, Y_j) of the 256x256 Gram inputs, L=M=128, d=8, dyadic order 2, fp32: "
-                "the solution surface on the sample grid (%d x %d nodes per pair, %.2f GB written)"
-                % (B, L, L, B * L * L * 4 / 1e9), step, cells, 3 * cells + 2 * d * coarse, oracle_rate,
-                host_step, (hx, hy, hs), hx.numel() * 4 + hy.numel() * 4, B * L * L * 4, parity)
+        return dict(
+            desc="%d pairs (X_i, Y_j) of the 256x256 Gram inputs, L=M=128, d=8, dyadic order 2, fp32: "
+                 "the solution surface on the sample grid (%d x %d nodes per pair, %.2f GB written)"
+                 % (B, L, L, B * L * L * 4 / 1e9),
+            dtype="f32", step=step, cells=cells, pairs=B, flop=3 * cells + 2 * d * coarse,
+            kernels="chain_band_kernel (surface instance) + band_gbar_kernel (surface unpack)",
+            oracle_rate=oracle_rate, parity=parity, host_step=host_step, host=(hx, hy, hs),
+            h2d=hx.numel() * 4 + hy.numel() * 4, d2h=B * L * L * 4)
+
     if name == "support_fbm30":
         # the support-reduction example of Sec. 5.3: 30 fBM paths (Hurst
         # exponents from {0.2, 0.5, 0.8}), their signature-kernel Gram, then
@@ -603,18 +797,112 @@ def _extra_setup(name, batch=0):
             t0 = time.perf_counter()
             K = oracle.gram(X64, X64, lam_d)
             oracle.support_reduction(K, np.full(n, 1.0 / n), np.zeros(n), gamma, pen, iters)
-            return cells / (time.perf_counter() - t0), "the whole step (Gram + %d iterations)" % iters
+            return cells / (time.perf_counter() - t0), "the whole step (Gram + %d iterations)" % iters, \
+                oracle.num_threads()
 
         def parity(out):
             K = oracle.gram(X64, X64, lam_d)
             rb, _ = oracle.support_reduction(K, np.full(n, 1.0 / n), np.zeros(n), gamma, pen, iters)
             o = out.double().cpu().numpy()
             return float(np.max(np.abs(o - rb)) / np.max(np.abs(rb))), "beta after %d iterations" % iters
-        return ("support reduction (Sec. 5.3): 30 fBM paths, L=%d, d=2, Gram at dyadic order %d, then %d "
-                "proximal gradient steps (lam = %g), fp32" % (L, lam_d, iters, pen), step, cells,
-                3 * cells, oracle_rate, host_step,
-                (torch.from_numpy(X32).pin_memory(), torch.empty(n).pin_memory()), X32.nbytes, n * 4, parity)
+        return dict(
+            desc="support reduction (Sec. 5.3): 30 fBM paths, L=%d, d=2, Gram at dyadic order %d, then %d "
+                 "proximal gradient steps (lam = %g), fp32" % (L, lam_d, iters, pen),
+            dtype="f32", step=step, cells=cells, pairs=n * n, flop=3 * cells,
+            kernels="chain_f32_kernel + support_kernel", oracle_rate=oracle_rate, parity=parity,
+            host_step=host_step, host=(torch.from_numpy(X32).pin_memory(), torch.empty(n).pin_memory()),
+            h2d=X32.nbytes, d2h=n * 4)
     raise SystemExit("unknown workload " + name)
+
+
+def _uneven_kernels(sched):
+    return ("plan_kernel + inc_kernel + coef_kernel (FMA contraction) + strip_kernel<float> "
+            "(strip path, %s-row strips)" % (32 * sched.rows_per_lane if sched.rows_per_lane else "default"))
+
+
+def _peak(dtype, sms):
+    if dtype == "f64":
+        return FP64_PEAK_NOMINAL_TF, "nominal dense FP64 of the GB300 (no measured FP64 figure)"
+    tf, mhz, src = fp32_peak_tflops(sms)
+    return tf, "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s max SM clock)" % (sms, mhz, src)
+
+
+def measure_workload(name, args, cache=None, with_e2e=False, with_clocks=True):
+    """Times one workload as described above; returns its result dict."""
+    import torch
+    wl = _workload(name, args.batch, cache)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        wl["step"]()
+    torch.cuda.synchronize()
+    steps = max(args.wl_steps, 5)
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    clocks = ClockSampler(0) if with_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    out = None
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(st)
+        out = wl["step"]()
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    rel, rel_sample = wl["parity"](out)
+    props = torch.cuda.get_device_properties(0)
+    peak_tf, peak_src = _peak(wl["dtype"], props.multi_processor_count)
+    ach = wl["flop"] / (ms * 1e-3) / 1e12
+    if args.skip_cpu:
+        cpu = {"value": None, "unit": "cells/s", "cores": 0, "kind": "oracle", "sample": "skipped (--skip-cpu)"}
+    else:
+        rate, sample, cores = wl["oracle_rate"](args.wl_cpu_seconds)
+        cpu = {"value": rate, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample}
+    res = {
+        "config": wl["desc"], "dtype": wl["dtype"], "steps": steps, "ms_per_step": ms,
+        "cells_per_s": wl["cells"] / (ms * 1e-3), "pairs_per_s": wl["pairs"] / (ms * 1e-3),
+        "cells_per_step": wl["cells"], "pairs_per_step": wl["pairs"],
+        "rel_err_vs_oracle": {"max": rel, "sample": rel_sample},
+        "roofline": {"bound": "alu", "work_flop_per_step": wl["flop"], "achieved": ach, "peak": peak_tf,
+                     "unit": "TFLOP/s", "frac": ach / peak_tf, "peak_source": peak_src,
+                     "kernels": wl["kernels"],
+                     "note": "whole call (all of its kernels) over CUDA events"},
+        "clocks": clk, "cpu_baseline": cpu,
+    }
+    if with_e2e:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            wl["host_step"](*wl["host"])
+        e1.record(st)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / steps
+        res["e2e"] = {"value": wl["cells"] / (e2e_ms * 1e-3), "unit": "cells/s",
+                      "h2d_bytes_per_step": int(wl["h2d"]), "d2h_bytes_per_step": int(wl["d2h"]),
+                      "ms_per_step": e2e_ms}
+    del flush
+    torch.cuda.empty_cache()
+    return res
+
+
+# the configurations of the workload statement besides the headline Gram
+# (configs 1, 3, 4, 5; config 5 in FP32 and FP64 at both dyadic orders)
+DEFAULT_WORKLOADS = ["gram_small_f64", "gram_small_f32", "uneven4096", "mmd128", "long64_l0", "long64_l1",
+                     "long64_l0_f64", "long64_l1_f64"]
+
+
+def run_workloads(args):
+    cache = {}
+    res = {}
+    for name in DEFAULT_WORKLOADS:
+        try:
+            res[name] = measure_workload(name, args, cache)
+        except Exception as e:   # one broken workload must not hide the others
+            res[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+    return res
 
 
 def run_extra(args):
@@ -622,58 +910,20 @@ def run_extra(args):
     torch.cuda.set_device(0)
     from paper_2006_14794_gb300 import sigk
     sigk.lib()
-    setup = _extra_setup(args.workload, args.batch)
-    desc, step, cells, flop, oracle_rate, host_step, host, h2d, d2h = setup[:9]
-    parity = setup[9] if len(setup) > 9 else None
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    st = torch.cuda.current_stream()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(0)
-    clocks.start()
-    time.sleep(0.3)
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev[i][0].record(st)
-        step()
-        ev[i][1].record(st)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    rel = parity(step()) if parity is not None else None
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.steps):
-        host_step(*host)
-    e1.record(st)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    props = torch.cuda.get_device_properties(0)
-    peak_tf, mhz, src = fp32_peak_tflops(props.multi_processor_count)
-    ach = flop / (ms * 1e-3) / 1e12
-    rate, sample = (None, "skipped (--skip-cpu)") if args.skip_cpu else oracle_rate(args.cpu_seconds)
-    import oracle
+    r = measure_workload(args.workload, args, with_e2e=True)
+    import oracle  # noqa: F401
     line = {
-        "metric": METRIC, "value": cells / (ms * 1e-3), "unit": "cells/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "l2": "flushed (256 MB write) before each step"},
-        "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": ach / peak_tf, "traffic": None,
-                     "note": "whole call (all of its kernels) over CUDA events"},
-        "clocks": clk,
-        "e2e": {"value": cells / (e2e_ms * 1e-3), "unit": "cells/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
-        "cpu_baseline": {"value": rate, "unit": "cells/s", "cores": oracle.num_threads(),
-                         "kind": "oracle", "sample": sample},
+        "metric": METRIC, "value": r["cells_per_s"], "unit": "cells/s", "n_gpus": 1,
+        "steps": r["steps"], "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"],
+        "data": "synthetic",
+        "config": {"workload": r["config"], "l2": "flushed (256 MB write) before each step"},
+        "pairs_per_s": r["pairs_per_s"],
+        "roofline": r["roofline"], "clocks": r["clocks"], "e2e": r["e2e"],
+        "cpu_baseline": r["cpu_baseline"], "rel_err_vs_oracle": r["rel_err_vs_oracle"],
     }
-    if rel is not None:
-        line["rel_err_vs_oracle"] = {"max": rel[0], "sample": rel[1]}
     print(json.dumps(line), flush=True)
     return 0
-
 
 
 def main():
@@ -684,12 +934,17 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-workloads", action="store_true",
+                    help="the headline line only (no 'workloads' key)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--wl-steps", type=int, default=5, help="timed steps per workload (>= 5)")
+    ap.add_argument("--wl-cpu-seconds", type=float, default=3.0,
+                    help="oracle time budget per workload where the sample is time-bounded")
     ap.add_argument("--batch", type=int, default=0,
                     help="long64 / mmd128 / gram256_*: only the first BATCH pairs / paths per batch (profiling)")
     ap.add_argument("--workload", default="gram256",
-                    choices=["gram256", "uneven4096", "long64_l0", "long64_l1", "mmd128",
-                             "gram256_implicit", "gram256_rbf", "surface256", "support_fbm30"])
+                    choices=["gram256"] + DEFAULT_WORKLOADS + ["gram256_implicit", "gram256_rbf",
+                                                               "surface256", "support_fbm30"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
