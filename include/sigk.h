@@ -116,7 +116,11 @@ typedef struct {
     int static_kernel;/* sigk_static_kernel: 0 linear (the paths as given),
                          1 RBF lift with bandwidth `sigma` (Sec. 2.2)         */
     double sigma;     /* RBF bandwidth, > 0 (ignored for the linear kernel)   */
-    int reserved[2];  /* must be 0                                            */
+    int accumulate;   /* backward calls (sigk_pairs_backward, sigk_gram_backward,
+                         sigk_gram_value_and_grad): 0 overwrites dX / dY, 1
+                         adds the gradients to what dX / dY hold (a loss that
+                         sums several Grams of the same paths)                */
+    int reserved[1];  /* must be 0                                            */
 } sigk_opts;          /* a NULL pointer means all-zero (automatic) options    */
 
 /* Finite-difference scheme (Sec. 3.1).
@@ -247,8 +251,10 @@ int sigk_gram_value_and_grad(const void *grad_out, const void *X, const void *Y,
  * Returns SIGK_EUNSUPPORTED when one pair's scratch,
  * (2 (L-1)(M-1) + (2^lambda (L-1) + 1)(2^lambda (M-1) + 1)) elements,
  * exceeds the array.  The first call on each device looks the array's device
- * address up once (cudaGetSymbolAddress, with that device current); make
- * that first call before any stream capture.  All calls share the array:
+ * address up (cudaGetSymbolAddress, with that device current) and keeps it
+ * for that device's context; the first call after the context was reset
+ * (cudaDeviceReset) looks it up again.  Make that first call before any
+ * stream capture.  All calls share the array:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller.  No state carries over between calls. */
 int sigk_pairs_backward_noalloc(const void *grad_out, const void *X, const void *Y, int64_t B,
@@ -268,6 +274,15 @@ int sigk_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int6
  * gKxy [m,n] (any may be NULL). */
 int sigk_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *gKxx,
                        void *gKyy, void *gKxy, void *stream);
+
+/* The chain rule through a scalar loss whose input gradients were formed
+ * before its upstream derivative was known (sigk_gram_value_and_grad with a
+ * constant dL/dK, as for the unbiased MMD^2, which is linear in the Grams):
+ *   g_out[i] = grad[0] * g_in[i],  i < n.
+ * grad: device, one element; g_in, g_out: device, n elements (may alias).
+ * n >= 0.  Asynchronous on `stream`; no workspace. */
+int sigk_scale_grad(const void *grad, const void *g_in, void *g_out, int64_t n, int dtype,
+                    void *stream);
 
 /* Moments-matching reduction of the support of a discrete measure on paths
  * (Sec. 5.3).  With K the signature-kernel Gram of the support's N paths

@@ -348,6 +348,7 @@ cudaError_t launch_bwd_plain(const PairSrc &src, int64_t n_pairs, int lam, int d
 // (the kernel clears its dk/dG accumulator itself), so no state carries over
 // from one call to the next.
 // ---------------------------------------------------------------------------
+#include <cuda.h>   // CUcontext / CUresult types; the two driver calls are fetched at run time
 #include <mutex>
 
 #define SIGK_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -357,22 +358,66 @@ static __device__ __align__(256) unsigned char sigk_noalloc_scratch[SIGK_NOALLOC
 
 namespace {
 
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[SIGK_NOALLOC_MAX_DEVICES];
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name is only a stand-in for it).
+std::mutex g_noalloc_mu;
+struct NoallocSlot {
+    void *ptr;                  // the array's device address in that context
+    unsigned long long ctx_id;  // the context it was looked up in (0: unknown)
+};
+NoallocSlot g_noalloc[SIGK_NOALLOC_MAX_DEVICES];
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// Process-unique id of the calling thread's current context, 0 when there is
+// none yet or the driver cannot say.  A device reset ends the context, and the
+// library image (with the array) is loaded again in the next one, possibly at
+// another address: the id tells a cached address from a stale one.
+unsigned long long current_ctx_id() {
+    if (!g_ctx_fns_tried) {
+        g_ctx_fns_tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_id = (CtxGetIdFn)f;
+    }
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (g_ctx_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device: the host-side
+// name is only a stand-in for it.  Set-up, once per device and context: the
+// first call on a device, and the first after that device's context was
+// reset, look the address up with cudaGetSymbolAddress; later calls in the
+// same context reuse it.
 int noalloc_scratch(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SIGK_ECUDA;
     if (dev < 0 || dev >= SIGK_NOALLOC_MAX_DEVICES) return SIGK_EUNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, sigk_noalloc_scratch) != cudaSuccess || !p) return SIGK_ECUDA;
-        g_noalloc_ptr[dev] = p;
+    NoallocSlot &sl = g_noalloc[dev];
+    const unsigned long long id = current_ctx_id();
+    if (sl.ptr && id != 0 && sl.ctx_id == id) {
+        *out = sl.ptr;
+        return SIGK_OK;
     }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, sigk_noalloc_scratch) != cudaSuccess || !p) return SIGK_ECUDA;
+    // the look-up makes the device's context current if it was not yet
+    sl.ptr = p;
+    sl.ctx_id = id != 0 ? id : current_ctx_id();
+    *out = p;
     return SIGK_OK;
 }
 
