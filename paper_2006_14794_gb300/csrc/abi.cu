@@ -22,8 +22,8 @@ bool opts_ok(const sigk_opts *o) {
     if (o->scheme != SIGK_SCHEME_EXPLICIT && o->scheme != SIGK_SCHEME_IMPLICIT) return false;
     if (o->static_kernel != SIGK_KERNEL_LINEAR && o->static_kernel != SIGK_KERNEL_RBF) return false;
     if (o->static_kernel == SIGK_KERNEL_RBF && !(o->sigma > 0.0 && o->sigma < 1e300)) return false;
-    for (int i = 0; i < 2; ++i)
-        if (o->reserved[i] != 0) return false;
+    if (o->accumulate != 0 && o->accumulate != 1) return false;
+    if (o->reserved[0] != 0) return false;
     return true;
 }
 
@@ -65,6 +65,8 @@ constexpr int64_t STRIP_WS_CAP = 8LL << 30;
 constexpr int64_t BAND_BWD_WS_CAP = 16LL << 30;
 
 int fault_of(const sigk_opts *o) { return o ? o->fault_inject : 0; }
+// backward calls: add into dX / dY instead of overwriting them
+bool accumulate_of(const sigk_opts *o) { return o && o->accumulate; }
 int rows_of(const sigk_opts *o) { return o ? o->rows_per_lane : 0; }
 int coef_of(const sigk_opts *o) { return o ? o->coef_path : 0; }
 // the strip path's rows per lane (its default, or the requested one).  f32
@@ -289,8 +291,11 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
                  const void *gout, void *dX, void *dY, int64_t nX, int64_t nY, void *ws,
                  size_t ws_bytes, cudaStream_t st, void *out = nullptr) {
     const int64_t es = dtype == SIGK_F64 ? 8 : 4;
-    if (dX && cudaMemsetAsync(dX, 0, (size_t)(nX * es), st) != cudaSuccess) return SIGK_ECUDA;
-    if (dY && cudaMemsetAsync(dY, 0, (size_t)(nY * es), st) != cudaSuccess) return SIGK_ECUDA;
+    // every path below adds into zeroed outputs (atomics), except the band
+    // form, whose last kernel writes each output once (and adds on request)
+    const bool acc = accumulate_of(opts);
+    if (!acc && dX && cudaMemsetAsync(dX, 0, (size_t)(nX * es), st) != cudaSuccess) return SIGK_ECUDA;
+    if (!acc && dY && cudaMemsetAsync(dY, 0, (size_t)(nY * es), st) != cudaSuccess) return SIGK_ECUDA;
     if (n_pairs == 0 || src.La < 2 || src.Lb < 2 || (!dX && !dY)) return SIGK_OK;
     const int rec = rec_of(opts);
     if (rec == SIGK_REC_STRIP && !strip_supported(lam, src.d, dtype)) return SIGK_EUNSUPPORTED;
@@ -304,7 +309,7 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
         float *dA = (float *)(sw ? dY : dX), *dB = (float *)(sw ? dX : dY);
         return cuda_status(
             launch_band_bwd_f32(o, bp, n_pairs, nbp, (const float *)gout, dA, dB, ws, st, coef_of(opts),
-                                (float *)out));
+                                (float *)out, acc));
     }
     // the symmetric backward exists in the band form only, the RBF lift's in
     // the plain backward only
@@ -611,6 +616,7 @@ int sigk_gram_backward(const void *grad_out, const void *X, const void *Y, int64
     if (sym && (Bx != By || L != M || dY)) return SIGK_EINVAL;
     if (Bx == 0 || By == 0) {
         const int64_t es = dtype == SIGK_F64 ? 8 : 4;
+        if (accumulate_of(opts)) return SIGK_OK;
         if (dX && Bx && cudaMemsetAsync(dX, 0, (size_t)(Bx * L * d * es), (cudaStream_t)stream)) return SIGK_ECUDA;
         if (dY && By && cudaMemsetAsync(dY, 0, (size_t)(By * M * d * es), (cudaStream_t)stream)) return SIGK_ECUDA;
         return SIGK_OK;
@@ -676,6 +682,14 @@ int sigk_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *
     if (dtype != SIGK_F32 && dtype != SIGK_F64) return SIGK_EINVAL;
     if (!grad) return SIGK_EINVAL;
     return cuda_status(launch_mmd2_backward(grad, m, n, dtype, gKxx, gKyy, gKxy, (cudaStream_t)stream));
+}
+
+int sigk_scale_grad(const void *grad, const void *g_in, void *g_out, int64_t n, int dtype, void *stream) {
+    if (n < 0) return SIGK_EINVAL;
+    if (dtype != SIGK_F32 && dtype != SIGK_F64) return SIGK_EINVAL;
+    if (n == 0) return SIGK_OK;
+    if (!grad || !g_in || !g_out) return SIGK_EINVAL;
+    return cuda_status(launch_scale_grad(grad, g_in, g_out, n, dtype, (cudaStream_t)stream));
 }
 
 int sigk_support_reduction(const void *K, const void *alpha, void *beta, int64_t N, double gamma,

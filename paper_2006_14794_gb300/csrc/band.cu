@@ -1159,9 +1159,9 @@ __global__ void band_split_sum_kernel(const float *partial, int ksplit, int64_t 
 
 // Point gradients from increment gradients: x_p enters dx_{p-1} (+) and dx_p
 // (-), so dX[path][p] = scale (dinc[p-1] - dinc[p]) (terms outside 0..L-2
-// absent).  Overwrites dpts.
+// absent).  Overwrites dpts, or adds to it (add).
 __global__ void band_points_kernel(const float *dinc, int64_t npaths, int64_t L, int64_t d, float scale,
-                                   float *dpts) {
+                                   int add, float *dpts) {
     const int64_t total = npaths * L * d;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -1170,7 +1170,8 @@ __global__ void band_points_kernel(const float *dinc, int64_t npaths, int64_t L,
         const float *di = dinc + path * (L - 1) * d + c;
         const float lo = p >= 1 ? di[(p - 1) * d] : 0.f;
         const float hi = p < L - 1 ? di[p * d] : 0.f;
-        dpts[v] = scale * (lo - hi);
+        const float g = scale * (lo - hi);
+        dpts[v] = add ? dpts[v] + g : g;
     }
 }
 
@@ -1446,7 +1447,7 @@ int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t
 
 cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t n, int64_t nbp,
                                 const float *gout, float *dA, float *dB, void *ws, cudaStream_t st,
-                                int coef_path, float *out) {
+                                int coef_path, float *out, bool add) {
     if (n <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1655,13 +1656,14 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 6. point gradients
         if (dA)
-            band_points_kernel<<<sms * 4, 256, 0, st>>>(dincA, nA, src.La, d, scale, dA + a0 * src.La * d);
+            band_points_kernel<<<sms * 4, 256, 0, st>>>(dincA, nA, src.La, d, scale, add, dA + a0 * src.La * d);
         if (dB && !gram)
-            band_points_kernel<<<sms * 4, 256, 0, st>>>(dincB, m, src.Lb, d, scale, dB + src.kbase * src.Lb * d);
+            band_points_kernel<<<sms * 4, 256, 0, st>>>(dincB, m, src.Lb, d, scale, add,
+                                                      dB + src.kbase * src.Lb * d);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (dB && gram) {
-        band_points_kernel<<<sms * 4, 256, 0, st>>>(dincB, nBall, src0.Lb, d, scale, dB);
+        band_points_kernel<<<sms * 4, 256, 0, st>>>(dincB, nBall, src0.Lb, d, scale, add, dB);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -54,7 +54,28 @@ __global__ void mmd2_backward_kernel(const T *grad, int64_t m, int64_t n, T *gKx
         for (int64_t i = t0; i < m * n; i += stride) gKxy[i] = axy;
 }
 
+// g_out = grad[0] g_in: the chain rule through the scalar loss for input
+// gradients formed with a unit upstream derivative.
+template <typename T>
+__global__ void scale_grad_kernel(const T *grad, const T *g_in, T *g_out, int64_t n) {
+    const T g = grad[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        g_out[i] = g * g_in[i];
+}
+
 }  // namespace
+
+cudaError_t launch_scale_grad(const void *grad, const void *g_in, void *g_out, int64_t n, int dtype,
+                              cudaStream_t st) {
+    const int grid = (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048);
+    if (dtype == SIGK_F64)
+        scale_grad_kernel<double><<<grid, 256, 0, st>>>((const double *)grad, (const double *)g_in,
+                                                         (double *)g_out, n);
+    else
+        scale_grad_kernel<float><<<grid, 256, 0, st>>>((const float *)grad, (const float *)g_in,
+                                                        (float *)g_out, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n,
                         int dtype, void *out, cudaStream_t st) {

@@ -185,10 +185,11 @@ cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pai
 int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t cap_bytes,
                        int64_t &bytes);
 int64_t band_bwd_bytes(const PairSrc &src, const BandPlan &p, int64_t nbp);
-// out: null, or where the forward sweep also writes the values
+// out: null, or where the forward sweep also writes the values; add: the
+// gradients are added to what dA / dB hold instead of overwriting them
 cudaError_t launch_band_bwd_f32(const PairSrc &src, const BandPlan &p, int64_t n, int64_t nbp,
                                 const float *gout, float *dA, float *dB, void *ws, cudaStream_t st,
-                                int coef_path, float *out = nullptr);
+                                int coef_path, float *out = nullptr, bool add = false);
 
 cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype, void *out,
                          cudaStream_t st, void *surf = nullptr);
@@ -237,6 +238,8 @@ cudaError_t launch_support(const void *K, const void *alpha, void *beta, int64_t
 
 cudaError_t launch_mmd2(const void *Kxx, const void *Kyy, const void *Kxy, int64_t m, int64_t n,
                         int dtype, void *out, cudaStream_t st);
+cudaError_t launch_scale_grad(const void *grad, const void *g_in, void *g_out, int64_t n, int dtype,
+                              cudaStream_t st);
 cudaError_t launch_mmd2_backward(const void *grad, int64_t m, int64_t n, int dtype, void *gKxx,
                                  void *gKyy, void *gKxy, cudaStream_t st);
 

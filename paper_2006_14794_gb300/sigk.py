@@ -7,7 +7,8 @@ not need a GPU; calling it needs the built ``libsigk.so`` and fails loudly when
 it is missing (there is no CPU fallback).
 
 Names follow the C ABI: ``pairs``, ``gram``, ``pairs_varlen``,
-``pairs_surface``, ``pairs_backward``, ``gram_backward``, ``mmd2``; the autograd wrappers are
+``pairs_surface``, ``pairs_backward``, ``gram_backward``, ``gram_value_and_grad``, ``mmd2``,
+``scale_grad``; the autograd wrappers are
 ``SigKernelPairs``, ``SigKernelGram`` and ``mmd2_loss``.
 """
 from __future__ import annotations
@@ -41,7 +42,7 @@ class SigkOpts(ctypes.Structure):
     _fields_ = [("rec", _int), ("symmetric", _int), ("fault_inject", _int),
                 ("rows_per_lane", _int), ("coef_path", _int), ("orient", _int),
                 ("scheme", _int), ("static_kernel", _int), ("sigma", ctypes.c_double),
-                ("reserved", _int * 2)]
+                ("accumulate", _int), ("reserved", _int * 1)]
 
 
 class Variant(NamedTuple):
@@ -111,6 +112,7 @@ SIGNATURES = [
     ("sigk_pairs_backward_noalloc", _int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _int, _int,
                                            _vp, _vp, _vp]),
     ("sigk_mmd2", _int, [_vp, _vp, _vp, _i64, _i64, _int, _vp, _vp]),
+    ("sigk_scale_grad", _int, [_vp, _vp, _vp, _i64, _int, _vp]),
     ("sigk_support_reduction", _int, [_vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double, _int,
                                       _int, _vp, _vp]),
     ("sigk_mmd2_backward", _int, [_vp, _i64, _i64, _int, _vp, _vp, _vp, _vp]),
@@ -175,7 +177,8 @@ def _stream(dev) -> int:
 
 
 def _opts(rec: int = REC_AUTO, symmetric: bool = False, fault_inject: bool = False,
-          schedule: Optional[Schedule] = None, variant: Optional[Variant] = None):
+          schedule: Optional[Schedule] = None, variant: Optional[Variant] = None,
+          accumulate: bool = False):
     o = SigkOpts()
     o.rec = int(rec)
     v = _variant(variant)
@@ -189,6 +192,7 @@ def _opts(rec: int = REC_AUTO, symmetric: bool = False, fault_inject: bool = Fal
         o.orient = int(schedule.orient)
     o.symmetric = 1 if symmetric else 0
     o.fault_inject = 1 if fault_inject else 0
+    o.accumulate = 1 if accumulate else 0
     return o
 
 
@@ -336,18 +340,19 @@ def version() -> str:
 def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
                    need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
                    schedule: Optional[Schedule] = None, variant: Optional[Variant] = None,
-                   check_status: bool = False):
+                   check_status: bool = False, dX: Optional[torch.Tensor] = None,
+                   dY: Optional[torch.Tensor] = None, accumulate: bool = False):
     """(dX, dY) with dX[b] = grad_out[b] dk(X_b, Y_b)/dX_b (None when not needed).
     check_status: as for pairs (waits for the stream, raises on a device-side
-    timeout)."""
+    timeout).  dX / dY: output buffers to use (else new ones); accumulate:
+    add the gradients to what they hold."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     B, L, d = X.shape
     M = Y.shape[1]
     dt = _dtype_code(X)
     grad_out = grad_out.to(X.dtype)
-    dX = torch.empty_like(X) if need_dx else None
-    dY = torch.empty_like(Y) if need_dy else None
-    o = _opts(rec, schedule=schedule, variant=variant)
+    dX, dY = _grad_buffers(X, Y, need_dx, need_dy, dX, dY, accumulate)
+    o = _opts(rec, schedule=schedule, variant=variant, accumulate=accumulate)
     ws, nws = _workspace(OP_PAIRS_BACKWARD, B, 0, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_pairs_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), B, L, M, d,
                                      int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
@@ -360,11 +365,13 @@ def pairs_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dya
 def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
                   need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
                   schedule: Optional[Schedule] = None, symmetric: bool = False,
-                  variant: Optional[Variant] = None):
+                  variant: Optional[Variant] = None, dX: Optional[torch.Tensor] = None,
+                  dY: Optional[torch.Tensor] = None, accumulate: bool = False):
     """(dX, dY): dX[i] = sum_j grad_out[i,j] dk(X_i,Y_j)/dX_i, dY[j] likewise.
     symmetric=True (Y is X): (dX, None) with dX the derivative of
     sum_ij grad_out[i,j] k(X_i, X_j) through both arguments, from the pairs
-    i <= j only (f32, band form; SigkError with SIGK_EUNSUPPORTED otherwise)."""
+    i <= j only (f32, band form; SigkError with SIGK_EUNSUPPORTED otherwise).
+    dX / dY, accumulate: as for pairs_backward."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     Bx, L, d = X.shape
     By, M = Y.shape[0], Y.shape[1]
@@ -372,9 +379,8 @@ def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyad
     grad_out = grad_out.to(X.dtype).contiguous()
     if symmetric:
         need_dx, need_dy = True, False
-    dX = torch.empty_like(X) if need_dx else None
-    dY = torch.empty_like(Y) if need_dy else None
-    o = _opts(rec, symmetric=symmetric, schedule=schedule, variant=variant)
+    dX, dY = _grad_buffers(X, Y, need_dx, need_dy, dX, dY, accumulate)
+    o = _opts(rec, symmetric=symmetric, schedule=schedule, variant=variant, accumulate=accumulate)
     ws, nws = _workspace(OP_GRAM_BACKWARD, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_gram_backward(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), Bx, By, L, M,
                                     d, int(dyadic_order), dt, ctypes.byref(o), _ptr(dX), _ptr(dY),
@@ -385,12 +391,15 @@ def gram_backward(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyad
 def gram_value_and_grad(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,
                         need_dx: bool = True, need_dy: bool = True, rec: int = REC_AUTO,
                         schedule: Optional[Schedule] = None, symmetric: bool = False,
-                        variant: Optional[Variant] = None):
+                        variant: Optional[Variant] = None, dX: Optional[torch.Tensor] = None,
+                        dY: Optional[torch.Tensor] = None, accumulate: bool = False):
     """(K, dX, dY) in one pass: K as gram computes it and (dX, dY) as
     gram_backward computes them for grad_out, for a grad_out known before K (a
     loss linear in the Gram).  The band backward's forward sweep writes K.
-    SigkError with SIGK_EUNSUPPORTED where the backward is not the band form;
-    the caller then calls gram and gram_backward."""
+    dX / dY: output buffers to use (else new ones); accumulate: add the
+    gradients to what they hold.  SigkError with SIGK_EUNSUPPORTED where the
+    backward is not the band form; the caller then calls gram and
+    gram_backward."""
     X, Y, grad_out = _dev(X, "X"), _dev(Y, "Y"), _dev(grad_out, "grad_out")
     Bx, L, d = X.shape
     By, M = Y.shape[0], Y.shape[1]
@@ -399,15 +408,41 @@ def gram_value_and_grad(grad_out: torch.Tensor, X: torch.Tensor, Y: torch.Tensor
     if symmetric:
         need_dx, need_dy = True, False
     out = torch.empty(Bx, By, dtype=X.dtype, device=X.device)
-    dX = torch.empty_like(X) if need_dx else None
-    dY = torch.empty_like(Y) if need_dy else None
-    o = _opts(rec, symmetric=symmetric, schedule=schedule, variant=variant)
+    dX, dY = _grad_buffers(X, Y, need_dx, need_dy, dX, dY, accumulate)
+    o = _opts(rec, symmetric=symmetric, schedule=schedule, variant=variant, accumulate=accumulate)
     ws, nws = _workspace(OP_GRAM_BACKWARD, Bx, By, L, M, d, dyadic_order, dt, o, X.device)
     _check(lib().sigk_gram_value_and_grad(grad_out.data_ptr(), X.data_ptr(), Y.data_ptr(), Bx, By, L, M,
                                           d, int(dyadic_order), dt, ctypes.byref(o), out.data_ptr(),
                                           _ptr(dX), _ptr(dY), _ptr(ws), nws, _stream(X.device)),
            "sigk_gram_value_and_grad")
     return out, dX, dY
+
+
+def _out_buffer(t: torch.Tensor, like: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.shape != like.shape or t.dtype != like.dtype or \
+            t.device != like.device or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous tensor shaped like its input" % name)
+    return t
+
+
+def _grad_buffers(X, Y, need_dx, need_dy, dX, dY, accumulate):
+    """The backward's output buffers: the caller's (checked), else new ones."""
+    if accumulate and ((need_dx and dX is None) or (need_dy and dY is None)):
+        raise ValueError("accumulate wants the dX / dY buffers to add into")
+    dX = (_out_buffer(dX, X, "dX") if dX is not None else torch.empty_like(X)) if need_dx else None
+    dY = (_out_buffer(dY, Y, "dY") if dY is not None else torch.empty_like(Y)) if need_dy else None
+    return dX, dY
+
+
+def scale_grad(grad: torch.Tensor, g: torch.Tensor) -> torch.Tensor:
+    """grad[0] * g, for input gradients g formed with a unit upstream
+    derivative (sigk_scale_grad)."""
+    g = _dev(g, "g")
+    grad = _dev(grad.reshape(1).to(g.dtype), "grad")
+    out = torch.empty_like(g)
+    _check(lib().sigk_scale_grad(grad.data_ptr(), g.data_ptr(), out.data_ptr(), g.numel(), _dtype_code(g),
+                                 _stream(g.device)), "sigk_scale_grad")
+    return out
 
 
 def mmd2(Kxx: torch.Tensor, Kyy: torch.Tensor, Kxy: torch.Tensor) -> torch.Tensor:
@@ -512,7 +547,9 @@ class _MMD2Fused(torch.autograd.Function):
     """MMD^2 and its gradient in one forward: the loss is linear in the three
     Grams, so dL/dK is a constant matrix (sigk_mmd2_backward of 1) before any
     Gram is known, and each Gram's values and input gradient come from one
-    sigk_gram_value_and_grad call.  The backward scales the stored gradients."""
+    sigk_gram_value_and_grad call; the Kxy call adds its gradients into those
+    of Kxx and Kyy.  The backward scales the stored gradients by the upstream
+    derivative (sigk_scale_grad)."""
 
     @staticmethod
     def forward(ctx, X, Y, dyadic_order, variant):
@@ -529,15 +566,16 @@ class _MMD2Fused(torch.autograd.Function):
             Kyy, dY, _ = gram_value_and_grad(gyy, Y, Y, dyadic_order, symmetric=True, variant=variant)
         else:
             Kyy, dY = gram(Y, Y, dyadic_order, symmetric=True, variant=variant), None
-        Kxy, dXb, dYb = gram_value_and_grad(gxy, X, Y, dyadic_order, need_x, need_y, variant=variant)
-        ctx.save_for_backward(dX + dXb if need_x else None, dY + dYb if need_y else None)
+        Kxy, dX, dY = gram_value_and_grad(gxy, X, Y, dyadic_order, need_x, need_y, variant=variant,
+                                          dX=dX, dY=dY, accumulate=True)
+        ctx.save_for_backward(dX, dY)
         return mmd2(Kxx, Kyy, Kxy)
 
     @staticmethod
     def backward(ctx, g):
         dX, dY = ctx.saved_tensors
-        return (dX * g.reshape(1).to(dX.dtype) if dX is not None else None,
-                dY * g.reshape(1).to(dY.dtype) if dY is not None else None, None, None)
+        return (scale_grad(g, dX) if dX is not None else None,
+                scale_grad(g, dY) if dY is not None else None, None, None)
 
 
 def mmd2_loss(X: torch.Tensor, Y: torch.Tensor, dyadic_order: int,

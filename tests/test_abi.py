@@ -69,8 +69,17 @@ def test_argument_checks_need_no_gpu(libsigk):
     assert libsigk.sigk_pairs(P, P, 3, 4, 4, 2, 9, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EUNSUPPORTED
     assert libsigk.sigk_pairs(P, P, 3, 4, 4, 2, -1, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EINVAL
     assert libsigk.sigk_pairs(None, P, 3, 4, 4, 2, 1, 0, None, P, None, 0, None) == sigk.SIGK_EINVAL
-    o.reserved[1] = 1
+    o.reserved[0] = 1
     assert libsigk.sigk_gram(P, P, 2, 2, 4, 4, 2, 0, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EINVAL
+    o.reserved[0] = 0
+    o.accumulate = 2
+    assert libsigk.sigk_gram(P, P, 2, 2, 4, 4, 2, 0, 0, ctypes.byref(o), P, None, 0, None) == sigk.SIGK_EINVAL
+    o.accumulate = 0
+    # the scalar chain rule: sizes and dtype checked before any launch
+    assert libsigk.sigk_scale_grad(P, P, P, -1, 0, None) == sigk.SIGK_EINVAL
+    assert libsigk.sigk_scale_grad(P, P, P, 4, 5, None) == sigk.SIGK_EINVAL
+    assert libsigk.sigk_scale_grad(None, P, P, 4, 0, None) == sigk.SIGK_EINVAL
+    assert libsigk.sigk_scale_grad(None, None, None, 0, 0, None) == sigk.SIGK_OK
     o2 = sigk.SigkOpts(); o2.symmetric = 1
     assert libsigk.sigk_gram(P, P, 2, 3, 4, 4, 2, 0, 0, ctypes.byref(o2), P, None, 0, None) == sigk.SIGK_EINVAL
     # empty batches are valid and launch nothing
