@@ -816,6 +816,10 @@ def _workload(name, batch=0, cache=None):
 
 
 def _uneven_kernels(sched):
+    from paper_2006_14794_gb300 import sigk
+    if sched.rec == sigk.REC_BAND:
+        return ("vband_sweep_kernel (one launch per band class) + vb_coef_kernel (FMA contraction into "
+                "the band) + vb_pairs_kernel + vb_plan_kernel (device planning)")
     return ("plan_kernel + inc_kernel + coef_kernel (FMA contraction) + strip_kernel<float> "
             "(strip path, %s-row strips)" % (32 * sched.rows_per_lane if sched.rows_per_lane else "default"))
 

@@ -105,7 +105,11 @@ typedef struct {
                          3 split-TF32 tcgen05 MMAs (d <= 64); 2 and 3 are f32
                          only (f64 gives SIGK_EUNSUPPORTED).  Band form: 3
                          takes the tcgen05 contraction, anything else the FMA
-                         one.  Other paths ignore it                          */
+                         one; in a Gram's backward 3 also takes the chain
+                         rule (the contractions of dk/dc with the increments)
+                         to the tcgen05 tensor cores.  Uneven lengths in the
+                         band form always use the FMA contraction.  Other
+                         paths ignore it                                      */
     int orient;       /* strip path: which path the rows refine.  0 auto (the
                          shorter path from 1024 pairs per call on, else the
                          longer), 1 the longer (more strips per pair: more
@@ -171,7 +175,15 @@ int sigk_gram(const void *X, const void *Y, int64_t Bx, int64_t By, int64_t L, i
 /* Pairs of uneven lengths.  Path b of X is rows x_off[b] .. x_off[b+1]-1 of
  * Xp [sum L, d]; likewise Y.  x_off, y_off: device int64 [B+1], nondecreasing,
  * x_off[0] = 0.  max_len: an upper bound on every path length (host value).
- * out: [B].  Same scheme as sigk_pairs, per pair. */
+ * out: [B].  Same scheme as sigk_pairs, per pair.
+ * f32 with rec AUTO or BAND (default rows_per_lane, linear static kernel):
+ * the band form with every pair's geometry planned on the device (no host
+ * round trip; CUDA-graph capturable), when 2^lambda (max_len - 1) refined
+ * rows fit its largest band (dyadic order 0: 512, orders 1 and 2: 1024;
+ * orders above 2 have none), else the strip path (rec BAND: then
+ * SIGK_EUNSUPPORTED).  Its classes run on library-owned streams forked from
+ * and joined to `stream` by events, created on the first such call on a
+ * device. */
 int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp,
                       const int64_t *y_off, int64_t B, int64_t d, int64_t max_len,
                       int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *ws,

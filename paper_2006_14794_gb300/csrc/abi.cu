@@ -102,6 +102,25 @@ void strip_batch(const PairSrc &src, int64_t n, int64_t la, int64_t lb, int lam,
 
 enum Path { P_FILL, P_CHAIN, P_BAND, P_STRIP, P_PLAIN };
 
+// Pairs of uneven lengths in the band form: f32, the linear static kernel,
+// rec AUTO or BAND with the default band heights, and every path short enough
+// for the largest band class.
+bool varlen_uses_band(int64_t d, int64_t max_len, int lam, int dtype, const sigk_opts *o) {
+    const int rec = rec_of(o);
+    if (rec != SIGK_REC_AUTO && rec != SIGK_REC_BAND) return false;
+    if (rows_of(o) != 0) return false;
+    return vband_supported(lam, d, max_len, dtype, o ? o->static_kernel : SIGK_KERNEL_LINEAR);
+}
+// Pairs per varlen band launch and the workspace that needs.
+void vband_batch(int64_t n, int64_t max_len, int lam, int64_t &nb, int64_t &bytes) {
+    nb = n;
+    bytes = vband_workspace_bytes(nb, max_len, lam);
+    while (nb > 1 && bytes > STRIP_WS_CAP) {
+        nb = (nb + 1) / 2;
+        bytes = vband_workspace_bytes(nb, max_len, lam);
+    }
+}
+
 // Band-form pairs per launch and the workspace (the coefficient band) that needs.
 void band_batch(const BandPlan &bp, int64_t n, int64_t &nb, int64_t &bytes) {
     nb = n;
@@ -405,7 +424,12 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
     }
     int64_t nb, need;
     if (op == SIGK_OP_PAIRS_VARLEN) {
+        if (varlen_uses_band(d, L, dyadic_order, dtype, opts)) {
+            vband_batch(n_pairs, L, dyadic_order, nb, need);
+            return (size_t)need;
+        }
         const int rec = rec_of(opts);
+        if (rec == SIGK_REC_BAND) return 0;   // the call refuses it
         const bool strip = strip_supported(dyadic_order, d, dtype) &&
                            (rec == SIGK_REC_STRIP ||
                             (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN));
@@ -520,7 +544,20 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, cons
     src.La = max_len; src.Lb = max_len;
     src.d = d;
     const int rec = rec_of(opts);
-    if (rec == SIGK_REC_BAND) return SIGK_EUNSUPPORTED;   // the band form needs equal lengths
+    if (varlen_uses_band(d, max_len, dyadic_order, dtype, opts)) {
+        int64_t nb, need;
+        vband_batch(B, max_len, dyadic_order, nb, need);
+        if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
+        for (int64_t k0 = 0; k0 < B; k0 += nb) {
+            PairSrc s2 = src;
+            s2.kbase = k0;
+            const int64_t m = B - k0 < nb ? B - k0 : nb;
+            cudaError_t e = launch_vband(s2, m, dyadic_order, max_len, (float *)out, ws, (cudaStream_t)stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        return SIGK_OK;
+    }
+    if (rec == SIGK_REC_BAND) return SIGK_EUNSUPPORTED;   // no band class holds the longest path
     const bool strip = strip_supported(dyadic_order, d, dtype) &&
                        (rec == SIGK_REC_STRIP ||
                         (dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN));

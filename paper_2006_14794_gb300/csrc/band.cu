@@ -1643,15 +1643,42 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
                        (unsigned)(batches * g1.ksplit));
         const dim3 gd2((unsigned)((g2.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N),
                        (unsigned)(batches * g2.ksplit));
+        // a Gram's contractions on the tensor cores (split-TF32) with the
+        // tcgen05 path (coef_path 3), else on the FP32 pipe
+        const bool tc = gram && coef_path == 3 && chain_gemm_tc5_ok(g1.M, g1.K, (int)d);
+        auto as_chain = [&](const GemmArgs &ga, int add) {
+            ChainGemm cg;
+            cg.G = ga.G;
+            cg.g_ld = ga.g_ld;
+            cg.trans = ga.trans;
+            cg.Bm = ga.Bm;
+            cg.C = ga.C;
+            cg.M = ga.M;
+            cg.K = ga.K;
+            cg.N = ga.N;
+            cg.add = add;
+            cg.tri_rb = ga.tri_rb;
+            cg.tri_cb = ga.tri_cb;
+            return cg;
+        };
         if (dA) {
-            band_gemm_kernel<<<gd1, 256, 0, st>>>(g1);
-            if (g1.ksplit > 1)
-                band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g1.ksplit, g1.M * d, 0, dincA);
+            if (tc) {
+                if ((e = launch_chain_gemm_tc5(as_chain(g1, 0), status, st)) != cudaSuccess) return e;
+            } else {
+                band_gemm_kernel<<<gd1, 256, 0, st>>>(g1);
+                if (g1.ksplit > 1)
+                    band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g1.ksplit, g1.M * d, 0, dincA);
+            }
         }
         if (dB || sym) {
-            band_gemm_kernel<<<gd2, 256, 0, st>>>(g2);
-            if (g2.ksplit > 1)
-                band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g2.ksplit, g2.M * d, add_b ? 1 : 0, g2.C);
+            if (tc) {
+                if ((e = launch_chain_gemm_tc5(as_chain(g2, add_b ? 1 : 0), status, st)) != cudaSuccess) return e;
+            } else {
+                band_gemm_kernel<<<gd2, 256, 0, st>>>(g2);
+                if (g2.ksplit > 1)
+                    band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g2.ksplit, g2.M * d, add_b ? 1 : 0,
+                                                                   g2.C);
+            }
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 6. point gradients

@@ -216,6 +216,32 @@ cudaError_t launch_strip(const PairSrc &src, int64_t n, int lam, int dtype, void
                          int64_t max_lb, int64_t rowsA, int64_t rowsB, int coef_path, int R,
                          int shorter_rows);
 
+// The band form for pairs of uneven lengths (vband.cu): pairs planned on the
+// device into band-height classes and chains, f32, the linear static kernel.
+// Supported when every path of at most max_len points fits the largest class.
+bool vband_supported(int lam, int64_t d, int64_t max_len, int dtype, int kernel);
+int64_t vband_workspace_bytes(int64_t n, int64_t max_len, int lam);
+cudaError_t launch_vband(const PairSrc &src, int64_t n, int lam, int64_t max_len, float *out, void *ws,
+                         cudaStream_t st);
+
+// The band backward's chain rule on the tcgen05 tensor cores (chain_tc5.cu):
+// C = G B (trans = 0) or G^T B (trans = 1), G [M][K] (trans: [K][M]) with row
+// stride g_ld, B [K][N], C [M][N]; add: C += instead of C =; tri_rb > 0: a
+// symmetric Gram's blocks (tri_rb x tri_cb) below the diagonal are zero and
+// skipped.  Split-TF32 products (FP32 accuracy), N <= 64.
+struct ChainGemm {
+    const float *G;
+    int64_t g_ld;
+    int trans;
+    const float *Bm;
+    float *C;
+    int64_t M, K;
+    int N, add;
+    int64_t tri_rb, tri_cb;
+};
+bool chain_gemm_tc5_ok(int64_t M, int64_t K, int N);
+cudaError_t launch_chain_gemm_tc5(const ChainGemm &g, int *status, cudaStream_t st);
+
 // Point rows of the src.A and src.B arrays of a call of n_total pairs.
 inline void src_rows(const PairSrc &s, int64_t n_total, int64_t &ra, int64_t &rb) {
     if (s.mode == PM_PAIRS) { ra = n_total * s.La; rb = n_total * s.Lb; }

@@ -183,16 +183,22 @@ def test_forced_strip_schedule_asks_for_workspace(libsigk):
     assert libsigk.sigk_workspace_bytes(sigk.OP_PAIRS, 64, 0, 33, 33, 4, 4, 1, ctypes.byref(strip)) == 0
 
 
-def test_band_schedule_is_f32_and_equal_length_only(libsigk):
+def test_band_schedule_is_f32_only(libsigk):
     from paper_2006_14794_gb300 import sigk
     o = sigk.SigkOpts()
     o.rec = sigk.REC_BAND
     P = ctypes.c_void_p(16)
-    # f64 has no band form
+    # f64 has no band form, for equal or uneven lengths
     assert libsigk.sigk_pairs(P, P, 3, 40, 40, 32, 1, 1, ctypes.byref(o), P, P, 1 << 30, None) == \
         sigk.SIGK_EUNSUPPORTED
-    # neither have uneven lengths
-    assert libsigk.sigk_pairs_varlen(P, P, P, P, 3, 32, 40, 1, 0, ctypes.byref(o), P, P, 1 << 30, None) == \
+    assert libsigk.sigk_pairs_varlen(P, P, P, P, 3, 32, 40, 1, 1, ctypes.byref(o), P, P, 1 << 30, None) == \
+        sigk.SIGK_EUNSUPPORTED
+    # uneven f32 lengths take the band form when the longest path fits its
+    # largest band (1024 refined rows at dyadic order 1): a workspace, and the
+    # refusal beyond
+    assert libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_VARLEN, 3, 0, 513, 513, 16, 1, 0, ctypes.byref(o)) > 0
+    assert libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_VARLEN, 3, 0, 514, 514, 16, 1, 0, ctypes.byref(o)) == 0
+    assert libsigk.sigk_pairs_varlen(P, P, P, P, 3, 16, 514, 1, 0, ctypes.byref(o), P, P, 1 << 30, None) == \
         sigk.SIGK_EUNSUPPORTED
     # the band workspace: a 256-byte header, then (pairs x macro-steps + 1)
     # slot rows of 32 x NG^2 floats.
