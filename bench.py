@@ -510,7 +510,7 @@ def _workload(name, batch=0, cache=None):
             host_step=host_step, host=host, h2d=X32.nbytes + Y32.nbytes + xo.nbytes + yo.nbytes,
             d2h=4096 * 4)
 
-    if name.startswith("long64"):
+    if name.startswith("long64") and not name.endswith("_grad"):
         # config 5: 64 pairs, L=M=4096, d=64 (time + 63 walks), dyadic order 0 / 1
         lam = int(name[len("long64_l")])
         f64 = name.endswith("_f64")
@@ -569,6 +569,64 @@ def _workload(name, batch=0, cache=None):
             dtype="f64" if f64 else "f32", step=step, cells=cells, pairs=nb,
             flop=3 * cells + 2 * 64 * nb * 4095 * 4095, kernels=kern, oracle_rate=oracle_rate,
             parity=parity, host_step=host_step, host=host, h2d=2 * nb * 4096 * 64 * es, d2h=nb * es)
+
+    if name == "long64_l1_grad":
+        # config 5's backward: the gradient of sum_b g_b k(X_b, Y_b) for the
+        # 64 long pairs at dyadic order 1 (strip path: the forward with
+        # checkpoints, the adjoint undoing it in place, the chain rule)
+        lam = 1
+        w = inputs.long_pairs()
+        nb = batch if 0 < batch < 64 else 64
+        X32, X64 = inputs.f32(w["X"][:nb])
+        Y32, Y64 = inputs.f32(w["Y"][:nb])
+        n = 4095 << lam
+        cells = nb * n * n
+        coarse = nb * 4095 * 4095
+        Xd, Yd = torch.from_numpy(X32).cuda(), torch.from_numpy(Y32).cuda()
+        gv = np.random.default_rng(55).normal(size=nb)
+        gd = torch.as_tensor(gv, dtype=torch.float32).cuda()
+
+        def step():
+            return sigk.pairs_backward(gd, Xd, Yd, lam)
+
+        sample = [0, nb - 1] if nb > 1 else [0]
+
+        def refs():
+            key = ("long64_grad", nb)
+            if key not in cache:
+                cache[key] = _timed_oracle(lambda: oracle.pairs_grad(X64[sample], Y64[sample], lam, gv[sample]))
+            return cache[key]
+
+        def oracle_rate(budget):
+            _, dt = refs()
+            return len(sample) * n * n / dt, "values and gradients of pairs %s; forward cells of those pairs " \
+                "per second" % sample, min(len(sample), oracle.num_threads())
+
+        def parity(out):
+            (rX, rY), _ = refs()
+            dX, dY = out
+            e = 0.0
+            for got, ref in ((dX.double().cpu().numpy()[sample], rX), (dY.double().cpu().numpy()[sample], rY)):
+                e = max(e, float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+            return e, "dX, dY of pairs %s (max |g - g_ref| / max |g_ref|)" % sample
+
+        host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
+                torch.empty(X32.shape).pin_memory())
+
+        def host_step(hx, hy, hg):
+            dX, _ = sigk.pairs_backward(gd, hx.cuda(non_blocking=True), hy.cuda(non_blocking=True), lam)
+            hg.copy_(dX, non_blocking=True)
+        # flop: the coefficients (2d a coarse cell), the forward sweep (3 a
+        # refined cell), the adjoint (7: two multiply-adds, an add, the dk/dc
+        # multiply-add) and the undone forward step (3), the chain rule
+        # (2 x 2d a coarse cell)
+        return dict(
+            desc="gradient of sum_b g_b k(X_b, Y_b), %d pairs, L=M=4096, d=64 time-augmented walks, dyadic "
+                 "order 1, fp32 (strip adjoint with checkpoints every 64 steps)" % nb,
+            dtype="f32", step=step, cells=cells, pairs=nb, flop=2 * 64 * coarse + 13 * cells + 4 * 64 * coarse,
+            kernels="strip_adj_kernel + strip_kernel (checkpointing forward) + coef_tc5_kernel + grad_chain_kernel",
+            oracle_rate=oracle_rate, parity=parity, host_step=host_step, host=host,
+            h2d=X32.nbytes + Y32.nbytes, d2h=X32.nbytes)
 
     if name == "mmd128":
         # config 4: MMD^2 between 128 and 128 paths, L=256, d=32, dyadic order 1;
@@ -893,9 +951,10 @@ def measure_workload(name, args, cache=None, with_e2e=False, with_clocks=True):
 
 
 # the configurations of the workload statement besides the headline Gram
-# (configs 1, 3, 4, 5; config 5 in FP32 and FP64 at both dyadic orders)
+# (configs 1, 3, 4, 5; config 5 in FP32 and FP64 at both dyadic orders, and
+# its backward at dyadic order 1)
 DEFAULT_WORKLOADS = ["gram_small_f64", "gram_small_f32", "uneven4096", "mmd128", "long64_l0", "long64_l1",
-                     "long64_l0_f64", "long64_l1_f64"]
+                     "long64_l0_f64", "long64_l1_f64", "long64_l1_grad"]
 
 
 def run_workloads(args):

@@ -41,6 +41,12 @@ namespace {
 constexpr int STRIP_WARPS = 2;   // warps per CTA
 constexpr int CW = 32;           // columns per published chunk of a bottom row
 
+// Steps between the backward's checkpoints of the forward state: the adjoint
+// undoes the steps in between in place, and each undo rounds once more.
+template <typename T>
+__host__ __device__ constexpr int strip_ck() { return sizeof(T) == 4 ? 64 : 128; }
+inline int strip_ck_of(int64_t es) { return es == 4 ? 64 : 128; }
+
 // ---- planning: per-pair sizes and offsets, computed on the device ----------
 
 struct PairPlan {
@@ -54,7 +60,7 @@ struct PairPlan {
     int ns, pad;             // strips, virtual refined rows above the first
     int nw;                  // windows (coefficient diagonals) per strip
     int swap;                // 1: the rows refine the B path (src.B), columns the A path
-    int64_t s_off;           // backward: start of its per-cell sums K(a,b-1) + K(a-1,b)
+    int64_t s_off;           // backward: start of its checkpoints of the forward state
     int64_t g_off;           // backward: start of its dense dk/dG [nx][ny]
 };
 
@@ -62,8 +68,11 @@ struct PairPlan {
 // sizes over all pairs
 constexpr int TOT_STRIPS = 2;
 
+// ck: steps between the backward's checkpoints (0: forward only); with it
+// every strip, the last too, keeps its bottom row
 template <int R, int LAM>
-__global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *totals, int shorter_rows) {
+__global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *totals, int shorter_rows,
+                            int ck) {
     constexpr int S = 1 << LAM;
     constexpr int TH = 32 * R;
     constexpr int CP = 32 * (R / S);
@@ -90,9 +99,9 @@ __global__ void plan_kernel(PairSrc src, int64_t n, PairPlan *plan, int64_t *tot
         p.pad = p.ns * TH - p.ni;
         p.nw = ((p.nj + TH - 2) >> LAM) + 2;
         p.c_off = (int64_t)p.ns * p.nw * CP;        // sizes for now, offsets after the scan
-        p.bnd_off = p.ns > 0 ? (int64_t)(p.ns - 1) * p.nj * 2 : 0;
+        p.bnd_off = p.ns > 0 ? (int64_t)(ck ? p.ns : p.ns - 1) * p.nj * 2 : 0;
         p.strip_base = p.ns;
-        p.s_off = (int64_t)p.ns * (p.nj + TH - 1) * TH;
+        p.s_off = ck ? (int64_t)p.ns * ((p.nj + TH - 1 + ck - 1) / ck) * TH * 2 : 0;
         p.g_off = (int64_t)p.nx * p.ny;
         plan[k] = p;
     }
@@ -316,7 +325,7 @@ struct StripArgs {
     T *out;
     long long wait_cycles;
     int fault_inject;   // 1: the first strip of the first pair never publishes
-    T *sums;            // backward: per-cell K(a,b-1) + K(a-1,b), [strip][step][lane][R]; or null
+    T *sums;            // backward: checkpoints of the state, [strip][step / ck][lane][K 0..R-1, Q 0..R-1]
 };
 
 constexpr int NRING = 8;   // coefficient diagonals in flight per warp
@@ -343,7 +352,9 @@ __device__ __forceinline__ void ring_commit() { asm volatile("cp.async.commit_gr
 template <int N>
 __device__ __forceinline__ void ring_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// SAVE: also store each cell's K(a,b-1) + K(a-1,b) for the adjoint (a.sums)
+// SAVE: also keep what the adjoint needs to run the sweep backwards: every
+// strip's bottom row (the last strip's too) and, after every ck-th step (and
+// the last), the (K, Q) of all the strip's rows (a.sums)
 template <typename T, int R, int LAM, bool SAVE>
 __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a) {
     constexpr int S = 1 << LAM;
@@ -373,7 +384,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
         const int nj = pp.nj;
         const T *blk = a.cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
         const T *top = s > 0 ? a.bnd + pp.bnd_off + (int64_t)(s - 1) * nj * 2 : nullptr;
-        T *bot = s < pp.ns - 1 ? a.bnd + pp.bnd_off + (int64_t)s * nj * 2 : nullptr;
+        T *bot = (s < pp.ns - 1 || SAVE) ? a.bnd + pp.bnd_off + (int64_t)s * nj * 2 : nullptr;
         const bool mute = a.fault_inject && lo == 0 && s == 0;
         const int tend = nj + TH - 1;   // steps until the last row leaves column nj
 
@@ -535,9 +546,16 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                         }
                     }
                     if constexpr (SAVE) {
-                        T *dst = a.sums + pp.s_off + ((int64_t)s * tend + t) * TH + lane * R;
+                        constexpr int CK = strip_ck<T>();
+                        if ((t + 1) % CK == 0 || t == tend - 1) {
+                            const int nck = (tend + CK - 1) / CK;
+                            T *dst = a.sums + pp.s_off + (((int64_t)s * nck + t / CK) * 32 + lane) * (2 * R);
 #pragma unroll
-                        for (int i = 0; i < H; ++i) { dst[i] = sum[i].x; dst[i + H] = sum[i].y; }
+                            for (int i = 0; i < H; ++i) {
+                                dst[i] = KP[i].x; dst[i + H] = KP[i].y;
+                                dst[R + i] = QP[i].x; dst[R + i + H] = QP[i].y;
+                            }
+                        }
                     }
                 } else {
                     T sum[R];
@@ -562,9 +580,13 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                         }
                     }
                     if constexpr (SAVE) {
-                        T *dst = a.sums + pp.s_off + ((int64_t)s * tend + t) * TH + lane * R;
+                        constexpr int CK = strip_ck<T>();
+                        if ((t + 1) % CK == 0 || t == tend - 1) {
+                            const int nck = (tend + CK - 1) / CK;
+                            T *dst = a.sums + pp.s_off + (((int64_t)s * nck + t / CK) * 32 + lane) * (2 * R);
 #pragma unroll
-                        for (int r = 0; r < R; ++r) dst[r] = sum[r];
+                            for (int r = 0; r < R; ++r) { dst[r] = K[r]; dst[R + r] = Q[r]; }
+                        }
                     }
                 }
                 if (lane != 0) {
@@ -594,9 +616,22 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
 // backwards (rows ascending within a step, V passed up the lanes and, between
 // strips, through chunked buffers behind bounded waits, strips of a pair in
 // reverse order) has every input ready.  Each cell adds A(a,b) (K(a,b-1) +
-// K(a-1,b)), read back from the forward's store, to dk/dG of its coarse cell;
-// a group's coarse cell is complete at the end of the window whose diagonal
-// it sits on.
+// K(a-1,b)) to dk/dG of its coarse cell; a group's coarse cell is complete at
+// the end of the window whose diagonal it sits on.
+//
+// The sums K(a,b-1) + K(a-1,b) are not stored: the forward state is run
+// backwards with it.  After forward step t row a holds (K(a,b), Q(a,b)) at its
+// column b, and the step is undone in place (exact algebra; each undo rounds
+// once more in floating point):
+//   K(a,b-1) = K(a,b) - Q(a,b),
+//   sum      = K(a,b-1) + K(a-1,b)       (the row above's undone K),
+//   Q(a,b-1) = Q(a+1,b-1) - c(a+1,b-1) sum(a+1,b-1)   (from the row below).
+// The strip's first row takes K(a-1,b) from the strip above's bottom row, its
+// last row takes its (K, Q) from its own bottom row (both kept by the
+// forward), and the state is reloaded from the forward's checkpoints every ck
+// steps, which bounds the drift.  The backward's memory is the strips'
+// bottom rows and checkpoints, O(Ni Nj / ck) per pair instead of a value per
+// cell.
 
 template <typename T>
 struct AdjArgs {
@@ -604,7 +639,8 @@ struct AdjArgs {
     const int64_t *totals;
     int64_t n_pairs;
     const T *cbuf;
-    const T *sums;
+    const T *ckpt;   // the forward's checkpoints: [strip][step / ck][lane][K 0..R-1, Q 0..R-1]
+    const T *bnd;    // the forward's bottom rows (K, Q) per column, every strip
     T *vbuf;         // per pair, per strip boundary: V of the lower strip's first row [nj],
                      // filled with the all-ones pattern first
     int *counter;
@@ -614,22 +650,9 @@ struct AdjArgs {
     int scheme;      // sigk_scheme of the forward (scheme_dcoef)
 };
 
-constexpr int NSR = 8;   // slots of the per-cell sums ring (adjoint)
-constexpr int PD = 4;    // steps the sums are fetched ahead (< (NRING - 1) steps)
-
 template <typename T, int R, int LAM>
 __host__ __device__ constexpr int adj_warp_elems() {
-    return NRING * 32 * (R >> LAM) + NSR * 32 * R + CW;
-}
-
-// The lane's R sums of one step, NSR-slot ring, 16-byte cp.async chunks.
-template <typename T, int R>
-__device__ __forceinline__ void sums_fetch(T *slot, const T *src) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(slot);
-#pragma unroll
-    for (int o = 0; o < R * (int)sizeof(T); o += 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + o),
-                     "l"((const char *)src + o) : "memory");
+    return NRING * 32 * (R >> LAM) + CW;
 }
 
 template <typename T, int R, int LAM>
@@ -638,12 +661,12 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
     constexpr int NG = R / S;
     constexpr int CP = 32 * NG;
     constexpr int TH = 32 * R;
+    constexpr int CK = strip_ck<T>();
     extern __shared__ __align__(16) unsigned char adj_smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     T *ringc = reinterpret_cast<T *>(adj_smem) + (size_t)warp * adj_warp_elems<T, R, LAM>();
-    T *rings = ringc + NRING * CP;
-    T *bb = rings + NSR * 32 * R;
+    T *bb = ringc + NRING * CP;
     const int64_t total_strips = a.totals[TOT_STRIPS];
 
     for (;;) {
@@ -661,15 +684,19 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
         const int nj = pp.nj;
         const int tend = nj + TH - 1;
         const int nwin = (tend + S - 1) / S;
+        const int nck = (tend + CK - 1) / CK;
         const T *blk = a.cbuf + pp.c_off + (int64_t)s * pp.nw * CP;
-        const T *sst = a.sums + pp.s_off + (int64_t)s * tend * TH;
+        const T *ck = a.ckpt + pp.s_off + (int64_t)s * nck * TH * 2 + lane * (2 * R);
+        const T *topb = s > 0 ? a.bnd + pp.bnd_off + (int64_t)(s - 1) * nj * 2 : nullptr;
+        const T *botb = a.bnd + pp.bnd_off + (int64_t)s * nj * 2;
         const T *below = s < pp.ns - 1 ? a.vbuf + pp.bnd_off / 2 + (int64_t)s * nj : nullptr;
         T *above = s > 0 ? a.vbuf + pp.bnd_off / 2 + (int64_t)(s - 1) * nj : nullptr;
         const int prow0 = s * CP - (pp.pad >> LAM);
 
         T A[R], V[R], cp[R], cn[NG], co[NG], gN[NG], gO[NG];
+        T KS[R], QS[R];   // the forward state after the step about to be undone
 #pragma unroll
-        for (int r = 0; r < R; ++r) { A[r] = 0; V[r] = 0; cp[r] = 0; }
+        for (int r = 0; r < R; ++r) { A[r] = 0; V[r] = 0; cp[r] = 0; KS[r] = 1; QS[r] = 0; }
 #pragma unroll
         for (int g = 0; g < NG; ++g) { gN[g] = 0; gO[g] = 0; }
         bool timed_out = false;
@@ -707,18 +734,12 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
             }
         }
 
-        // one initial group: coefficient diagonals nwin-1 .. nwin-NRING+1 and
-        // the sums of steps tend-1 .. tend-PD; then one group per step
+        // coefficient diagonals nwin-1 .. nwin-NRING+1, then one per window
 #pragma unroll
         for (int k = 0; k < NRING - 1; ++k) {
             const int dg = nwin - 1 - k;
             if (dg >= 0 && dg < pp.nw)
                 ring_fetch<T, NG>(&ringc[((dg + NRING) % NRING) * CP + lane * NG], blk + (int64_t)dg * CP + lane * NG);
-        }
-#pragma unroll
-        for (int k = 0; k < PD; ++k) {
-            const int ts = tend - 1 - k;
-            if (ts >= 0) sums_fetch<T, R>(&rings[(ts % NSR) * 32 * R + lane * R], sst + (int64_t)ts * TH + lane * R);
         }
         ring_commit();
         ring_wait<0>();
@@ -728,12 +749,14 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
             for (int g = 0; g < NG; ++g) co[g] = cw[g];
         }
         for (int w = nwin - 1; w >= 0; --w) {
-            // diagonal w - (NRING - 1) joins this window's first group; diagonal
-            // w - 1 was fetched NRING - 1 windows (>= PD steps) ago and has landed
+            // diagonal w - (NRING - 1) joins the ring; diagonal w - 1 was
+            // fetched NRING - 1 windows ago
             {
                 const int k = w - (NRING - 1);
                 if (k >= 0)
                     ring_fetch<T, NG>(&ringc[(k % NRING) * CP + lane * NG], blk + (int64_t)k * CP + lane * NG);
+                ring_commit();
+                ring_wait<1>();
             }
 #pragma unroll
             for (int g = 0; g < NG; ++g) cn[g] = co[g];
@@ -749,11 +772,12 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
             for (int jj = S - 1; jj >= 0; --jj) {
                 const int t = w * S + jj;
                 if (t >= tend) continue;
-                // this step's group: the sums of step t - PD
-                if (t - PD >= 0)
-                    sums_fetch<T, R>(&rings[((t - PD) % NSR) * 32 * R + lane * R], sst + (int64_t)(t - PD) * TH + lane * R);
-                ring_commit();
-                ring_wait<PD>();   // the sums of step t (fetched PD steps ago) have landed
+                // the forward state after step t: a checkpoint, or the last undo
+                if ((t + 1) % CK == 0 || t == tend - 1) {
+                    const T *src = ck + (int64_t)(t / CK) * TH * 2;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) { KS[r] = src[r]; QS[r] = src[R + r]; }
+                }
                 const int col31 = t - (TH - 1);   // zero-based column of the strip's last row
                 if (below && col31 >= 0 && col31 < nj - CW) {
                     // chunk c = (nj-1-col31)/CW (c >= 1) was loaded half a chunk
@@ -774,21 +798,55 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
                 else
                     vbel = (col31 == nj - 1) ? (T)1 : (T)0;   // seed: V(Ni+1, Nj) = 1
                 const T vnext = __shfl_down_sync(FULL, V[0], 1);
-                const T *srow = &rings[(t % NSR) * 32 * R + lane * R];
-                T sm[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) sm[r] = srow[r];
+                // ---- undo step t: K(a,b-1) = K - Q and the cells' sums
+                T KL[R], sm[R], cw[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int g = r / S, sr = r % S;
-                    const T cown = (jj >= sr) ? cn[g] : co[g];
+                    cw[r] = (jj >= sr) ? cn[g] : co[g];
+                    KL[r] = KS[r] - QS[r];
+                }
+                T kup = __shfl_up_sync(FULL, KL[R - 1], 1);
+                if (lane == 0)   // row 0 of the strip is at column t: the row above is the upper strip's
+                    kup = topb ? (t < nj ? topb[(int64_t)t * 2] : (T)1) : (T)1;
+                sm[0] = KL[0] + kup;
+#pragma unroll
+                for (int r = 1; r < R; ++r) sm[r] = KL[r] + KL[r - 1];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const T cown = cw[r];
                     const T vb = r < R - 1 ? V[r < R - 1 ? r + 1 : 0] : (lane == 31 ? vbel : vnext);
                     const T P = vb + cp[r] * A[r];
                     const T An = A[r] + P;
                     V[r] = P + cown * An;
                     A[r] = An;
                     cp[r] = cown;
+                    const int g = r / S, sr = r % S;
                     if (jj >= sr) gN[g] += An * sm[r]; else gO[g] += An * sm[r];
+                }
+                // ---- the state before step t: Q from the row below's update
+                const T qx = QS[0] - cw[0] * sm[0];   // the row above's Q, for lane - 1
+                const T qlast = __shfl_down_sync(FULL, qx, 1);
+#pragma unroll
+                for (int r = 0; r < R - 1; ++r) QS[r] = QS[r + 1] - cw[r + 1] * sm[r + 1];
+#pragma unroll
+                for (int r = 0; r < R; ++r) KS[r] = KL[r];
+                if (lane == 31) {
+                    // the strip's last row: its own bottom row, kept by the
+                    // forward (beyond the grid's last column every value is
+                    // virtual and meets only zero adjoints)
+                    const int bc = col31 - 1;
+                    if (bc < 0) {
+                        KS[R - 1] = 1;
+                        QS[R - 1] = 0;
+                    } else if (bc < nj) {
+                        KS[R - 1] = botb[(int64_t)bc * 2];
+                        QS[R - 1] = botb[(int64_t)bc * 2 + 1];
+                    } else {
+                        QS[R - 1] = 0;
+                    }
+                } else {
+                    QS[R - 1] = qlast;
                 }
                 // lane 0's first row is at column t: its V goes to the strip above
                 if (above && lane == 0 && t < nj) st_boundary(above + t, V[0]);
@@ -1303,14 +1361,17 @@ struct StripLayout {
     int64_t plan, coef, bnd, incA, incB, total;
     int64_t strips;   // at most this many strips (n x the longest pair's)
     // backward only
-    int64_t vbuf, sums, gbar;
+    int64_t vbuf, ckpt, gbar;
 };
+
 
 static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
 
 // Upper bounds from the longest path length (exact for uniform lengths).
+// bwd: every strip keeps its bottom row (the forward only hands on ns - 1)
 static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R, int lam,
-                                int64_t es, int64_t rowsA, int64_t rowsB, int64_t D4, int shorter_rows = 0) {
+                                int64_t es, int64_t rowsA, int64_t rowsB, int64_t D4, int shorter_rows = 0,
+                                int bwd = 0) {
     const int64_t S = 1LL << lam, TH = 32LL * R, CP = 32LL * (R / S);
     int64_t lx = max_la > max_lb ? max_la : max_lb, ly = max_la > max_lb ? max_lb : max_la;
     if (shorter_rows) { const int64_t t = lx; lx = ly; ly = t; }
@@ -1324,29 +1385,32 @@ static StripLayout strip_layout(int64_t n, int64_t max_la, int64_t max_lb, int R
     L.coef = off;
     off += al256(n * ns * nw * CP * es);
     L.bnd = off;
-    off += al256(n * (ns > 1 ? ns - 1 : 0) * nj * 2 * es + es);
+    off += al256(n * (bwd ? ns : (ns > 1 ? ns - 1 : 0)) * nj * 2 * es + es);
     L.incA = off;
     off += al256(rowsA * D4 * 4 * es);
     L.incB = off;
     off += al256(rowsB * D4 * 4 * es);
     L.total = off;
-    L.vbuf = L.sums = L.gbar = 0;
+    L.vbuf = L.ckpt = L.gbar = 0;
     L.strips = n * ns;
     return L;
 }
 
 static StripLayout strip_layout_bwd(int64_t n, int64_t max_la, int64_t max_lb, int R, int lam,
                                     int64_t es, int64_t rowsA, int64_t rowsB, int64_t D4) {
-    StripLayout L = strip_layout(n, max_la, max_lb, R, lam, es, rowsA, rowsB, D4);
+    StripLayout L = strip_layout(n, max_la, max_lb, R, lam, es, rowsA, rowsB, D4, 0, 1);
     const int64_t S = 1LL << lam, TH = 32LL * R;
     const int64_t lx = max_la > max_lb ? max_la : max_lb, ly = max_la > max_lb ? max_lb : max_la;
     const int64_t nx = lx - 1, ny = ly - 1, ni = nx * S, nj = ny * S;
     const int64_t ns = (ni + TH - 1) / TH;
     int64_t off = L.total;
+    // indexed like the bottom rows (ns per pair; the last strip's is unused)
     L.vbuf = off;
-    off += al256(n * (ns > 1 ? ns - 1 : 0) * nj * es + es);
-    L.sums = off;
-    off += al256(n * ns * (nj + TH - 1) * TH * es);
+    off += al256(n * ns * nj * es + es);
+    // checkpoints: (K, Q) of the strip's 32 R rows after every ck-th step
+    const int64_t ck = strip_ck_of(es);
+    L.ckpt = off;
+    off += al256(n * ns * ((nj + TH - 1 + ck - 1) / ck) * TH * 2 * es);
     L.gbar = off;
     off += al256(n * nx * ny * es);
     L.total = off;
@@ -1523,7 +1587,7 @@ static cudaError_t launch_strip_t(const PairSrc &src, int64_t n, void *ws, T *ou
         inc_kernel<T><<<gb, 256, 0, st>>>((const T *)src.B, rowsB, packed ? src.b_off + nall : nullptr,
                                           src.d, D4, incB);
     }
-    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals, shorter_rows);
+    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals, shorter_rows, 0);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1570,7 +1634,7 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
     cudaError_t e;
     if ((e = cudaMemsetAsync(w, 0, 768, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w + L.bnd, 0xff, (size_t)(L.incA - L.bnd), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w + L.vbuf, 0xff, (size_t)(L.sums - L.vbuf), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w + L.vbuf, 0xff, (size_t)(L.ckpt - L.vbuf), st)) != cudaSuccess) return e;
     {
         const bool packed = src.mode == PM_VARLEN;
         const int64_t na = rowsA * D4 * 4, nbv = rowsB * D4 * 4;
@@ -1584,7 +1648,7 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         inc_kernel<T><<<gb, 256, 0, st>>>((const T *)src.B, rowsB, packed ? src.b_off + nall : nullptr,
                                           src.d, D4, incB);
     }
-    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals, 0);
+    plan_kernel<R, LAM><<<1, 512, 0, st>>>(src, n, plan, totals, 0, strip_ck<T>());
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1605,7 +1669,7 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         a.out = nullptr;
         a.wait_cycles = wait_cycles;
         a.fault_inject = 0;
-        a.sums = (T *)(w + L.sums);
+        a.sums = (T *)(w + L.ckpt);
         auto sk = strip_kernel<T, R, LAM, true>;
         int per_sm = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk, STRIP_WARPS * 32, 0)) != cudaSuccess)
@@ -1619,7 +1683,8 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         a.totals = totals;
         a.n_pairs = n;
         a.cbuf = (const T *)(w + L.coef);
-        a.sums = (const T *)(w + L.sums);
+        a.ckpt = (const T *)(w + L.ckpt);
+        a.bnd = (const T *)(w + L.bnd);
         a.vbuf = (T *)(w + L.vbuf);
         a.counter = counter2;
         a.status = status;

@@ -206,3 +206,17 @@ def test_band_schedule_is_f32_only(libsigk):
     # NG = 8 coarse rows per lane, 512 padded columns -> 32 macro-steps per pair
     n = libsigk.sigk_workspace_bytes(sigk.OP_GRAM, 4, 5, 256, 256, 32, 1, 0, ctypes.byref(o))
     assert n == 256 + 4 * (20 * 32 + 1) * 32 * 64
+
+
+def test_strip_backward_workspace_holds_no_per_cell_values(libsigk):
+    """The strip adjoint reruns the forward backwards between checkpoints:
+    its workspace for 8 long pairs (L = M = 4096, d = 64, dyadic order 1) is
+    the coarse coefficient blocks and dk/dG (0.57 + 0.54 GB) and the strips'
+    bottom rows and checkpoints (under 0.1 GB), not a value per refined cell
+    (2.15 GB of sums on their own)."""
+    from paper_2006_14794_gb300 import sigk
+    o = sigk.SigkOpts()
+    o.rec = sigk.REC_STRIP
+    n = libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_BACKWARD, 8, 0, 4096, 4096, 64, 1, 0, ctypes.byref(o))
+    per_cell = 8 * 8190 * 8190 * 4
+    assert 0 < n < 1.25e9 < per_cell

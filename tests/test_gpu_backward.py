@@ -167,3 +167,22 @@ def test_strip_backward_matches_oracle(lam, L, M, d):
     assert grad_err(dY.cpu(), rY) <= 1e-10
     pX, pY = S().pairs_backward(to_dev(g), to_dev(X32), to_dev(Y32), lam, rec=S().REC_PLAIN)
     assert grad_err(pX.cpu(), rX) <= 1e-4
+
+
+def test_strip_backward_long_pair_at_dyadic_order_1():
+    """One pair of the long-pair workload (L = M = 4096, d = 64, dyadic order
+    1: 8190 x 8190 refined cells, 16 strips of 512 rows): the strip adjoint
+    runs the forward backwards between checkpoints (every 64 steps in FP32,
+    128 in FP64) instead of reading stored per-cell sums."""
+    w = inputs.long_pairs(B=1)
+    X32, X64 = inputs.f32(w["X"])
+    Y32, Y64 = inputs.f32(w["Y"])
+    g = np.array([0.75])
+    rX, rY = oracle.pairs_grad(X64, Y64, 1, g)
+    dX, dY = S().pairs_backward(to_dev(g), to_dev(X32), to_dev(Y32), 1, rec=S().REC_STRIP, check_status=True)
+    assert grad_err(dX.cpu(), rX) <= 1e-4
+    assert grad_err(dY.cpu(), rY) <= 1e-4
+    dX, dY = S().pairs_backward(to_dev(g, torch.float64), to_dev(X64, torch.float64),
+                                to_dev(Y64, torch.float64), 1, rec=S().REC_CHAIN, check_status=True)
+    assert grad_err(dX.cpu(), rX) <= 1e-10
+    assert grad_err(dY.cpu(), rY) <= 1e-10
