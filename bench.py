@@ -458,8 +458,16 @@ def _workload(name, batch=0, cache=None):
 
     if name == "uneven4096":
         # config 3: 4096 pairs, L, M ~ U{16..512}, d=16 walks, dyadic order 1
+        # (batch > 0: the first `batch` pairs, 4096 for all, on the band
+        # schedule, untuned: a case for profilers without the tuner's runs)
         w = inputs.uneven_pairs()
         lam = w["dyadic_order"]
+        np_all = 4096
+        tuned = batch <= 0
+        if 0 < batch < 4096:
+            np_all = batch
+            w = dict(w, Xp=w["Xp"][:w["x_off"][batch]], Yp=w["Yp"][:w["y_off"][batch]],
+                     x_off=w["x_off"][:batch + 1], y_off=w["y_off"][:batch + 1])
         X32, X64 = inputs.f32(w["Xp"])
         Y32, Y64 = inputs.f32(w["Yp"])
         xo, yo = w["x_off"], w["y_off"]
@@ -470,7 +478,10 @@ def _workload(name, batch=0, cache=None):
         xod, yod = torch.as_tensor(xo).cuda(), torch.as_tensor(yo).cuda()
         # the schedule chosen by timing the candidates on these inputs (before
         # the timed region), then the whole call captured as one CUDA graph
-        sched, _ = tune.tune("pairs_varlen", Xd, xod, Yd, yod, lam, 512, store=False)
+        if tuned:
+            sched, _ = tune.tune("pairs_varlen", Xd, xod, Yd, yod, lam, 512, store=False)
+        else:
+            sched = sigk.Schedule(sigk.REC_BAND)
         g = sigk.graphed(sigk.pairs_varlen, Xd, xod, Yd, yod, lam, max_len=512, schedule=sched)
 
         def step():
@@ -482,33 +493,34 @@ def _workload(name, batch=0, cache=None):
 
         def oracle_rate(budget):
             t0 = time.perf_counter(); done = 0; cc = 0
-            while time.perf_counter() - t0 < budget and done < 4096:
-                b = np.arange(done, min(done + 64, 4096))
+            while time.perf_counter() - t0 < budget and done < np_all:
+                b = np.arange(done, min(done + 64, np_all))
                 sub_x = np.concatenate([X64[xo[i]:xo[i + 1]] for i in b])
                 sub_y = np.concatenate([Y64[yo[i]:yo[i + 1]] for i in b])
                 sxo = np.concatenate([[0], np.cumsum(lx[b])]); syo = np.concatenate([[0], np.cumsum(ly[b])])
                 oracle.pairs_varlen(sub_x, sxo, sub_y, syo, lam)
                 cc += int(np.sum(((lx[b] - 1) << lam) * ((ly[b] - 1) << lam))); done = b[-1] + 1
-            return cc / (time.perf_counter() - t0), "pairs 0..%d of 4096" % (done - 1), oracle.num_threads()
+            return cc / (time.perf_counter() - t0), "pairs 0..%d of %d" % (done - 1, np_all), oracle.num_threads()
 
         def parity(out):
             o = out.cpu().numpy()
             cl = (lx - 1) * (ly - 1)
-            idx = _pick(8, 4096, 60, must=(0, 4095, int(np.argmax(cl)), int(np.argmin(cl))))
+            idx = _pick(8, np_all, 60, must=(0, np_all - 1, int(np.argmax(cl)), int(np.argmin(cl))))
             ref = np.array([oracle.sigkernel(X64[xo[b]:xo[b + 1]], Y64[yo[b]:yo[b + 1]], lam) for b in idx])
             return float(np.max(np.abs(o[idx] - ref) / np.maximum(np.abs(ref), 1e-3))), \
                 "%d pairs (60 random, the first, the last, the most and the fewest cells)" % len(idx)
         host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
                 torch.as_tensor(xo).pin_memory(), torch.as_tensor(yo).pin_memory(),
-                torch.empty(4096).pin_memory())
+                torch.empty(np_all).pin_memory())
         return dict(
-            desc="4096 pairs, L,M ~ U{16..512}, d=16 walks, dyadic order 1, fp32; tuned schedule "
+            desc="%d pairs, L,M ~ U{16..512}, d=16 walks, dyadic order 1, fp32; %s schedule "
                  "rec=%d rows_per_lane=%d coef_path=%d orient=%d, one CUDA graph per call"
-                 % (sched.rec, sched.rows_per_lane, sched.coef_path, sched.orient),
-            dtype="f32", step=step, cells=cells, pairs=4096, flop=3 * cells + 2 * 16 * coarse,
+                 % (np_all, "tuned" if tuned else "band", sched.rec, sched.rows_per_lane,
+                    sched.coef_path, sched.orient),
+            dtype="f32", step=step, cells=cells, pairs=np_all, flop=3 * cells + 2 * 16 * coarse,
             kernels=_uneven_kernels(sched), oracle_rate=oracle_rate, parity=parity,
             host_step=host_step, host=host, h2d=X32.nbytes + Y32.nbytes + xo.nbytes + yo.nbytes,
-            d2h=4096 * 4)
+            d2h=np_all * 4)
 
     if name.startswith("long64") and not name.endswith("_grad"):
         # config 5: 64 pairs, L=M=4096, d=64 (time + 63 walks), dyadic order 0 / 1
@@ -1004,7 +1016,8 @@ def main():
     ap.add_argument("--wl-cpu-seconds", type=float, default=3.0,
                     help="oracle time budget per workload where the sample is time-bounded")
     ap.add_argument("--batch", type=int, default=0,
-                    help="long64 / mmd128 / gram256_*: only the first BATCH pairs / paths per batch (profiling)")
+                    help="uneven4096 / long64 / mmd128 / gram256_*: only the first BATCH pairs / paths per batch "
+                         "(profiling)")
     ap.add_argument("--workload", default="gram256",
                     choices=["gram256"] + DEFAULT_WORKLOADS + ["gram256_implicit", "gram256_rbf",
                                                                "surface256", "support_fbm30"])

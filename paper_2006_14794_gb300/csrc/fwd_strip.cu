@@ -871,7 +871,10 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
 // then to the points, atomically (a path appears in many pairs).  Both
 // contractions run on 64 x 64 tiles of Gbar staged in shared memory; thread
 // (t / 8, t % 8) owns rows t/8 and t/8 + 32 of the output tile and 4
-// channels of a 32-channel block.
+// channels of a 32-channel block.  A block takes one (pair, contraction,
+// 64-row output tile, channel block) and walks the reduction: blockIdx.y
+// strides over the pairs, blockIdx.x over a pair's tiles, so a few long
+// pairs still fill the GPU.
 constexpr int CT = 64;
 
 template <typename T>
@@ -888,7 +891,8 @@ __global__ void __launch_bounds__(256) grad_chain_kernel(PairSrc src, const Pair
     const int64_t d = src.d;
     const int64_t D4 = (d + 3) / 4;
     const int rt = threadIdx.x >> 3, ct = threadIdx.x & 7;
-    for (int64_t k = blockIdx.x; k < n_pairs; k += gridDim.x) {
+    const int ncb = (int)((D4 + 7) / 8);
+    for (int64_t k = blockIdx.y; k < n_pairs; k += gridDim.y) {
         const PairPlan pp = plan[k];
         if (pp.ns == 0) continue;
         const T f = gout[pp.out0] * scale;
@@ -897,15 +901,20 @@ __global__ void __launch_bounds__(256) grad_chain_kernel(PairSrc src, const Pair
         const V4 *yi = reinterpret_cast<const V4 *>(pp.swap ? incA : incB) + pp.b_row0 * D4;
         T *gx = pp.swap ? dB : dA;
         T *gy = pp.swap ? dA : dB;
-        for (int pass = 0; pass < 2; ++pass) {
+        const int tx = (pp.nx + CT - 1) / CT, ty = (pp.ny + CT - 1) / CT;
+        for (int64_t wi = blockIdx.x; wi < (int64_t)(tx + ty) * ncb; wi += gridDim.x) {
             // pass 0: rows p of dk/d dx, contracting over q; pass 1: rows q of dk/d dy over p
+            const int pass = wi < (int64_t)tx * ncb ? 0 : 1;
+            const int rem = (int)(pass == 0 ? wi : wi - (int64_t)tx * ncb);
             T *gout_pts = pass == 0 ? gx : gy;
             if (!gout_pts) continue;
             gout_pts += (pass == 0 ? pp.a_row0 : pp.b_row0) * d;
             const int nrow = pass == 0 ? pp.nx : pp.ny, nred = pass == 0 ? pp.ny : pp.nx;
             const V4 *other = pass == 0 ? yi : xi;
-            for (int r0 = 0; r0 < nrow; r0 += CT) {
-                for (int64_t cb = 0; cb < D4; cb += 8) {
+            {
+                const int r0 = (rem / ncb) * CT;
+                const int64_t cb = (int64_t)(rem % ncb) * 8;
+                {
                     T acc[2][4];
                     for (int i = 0; i < 2; ++i)
                         for (int e = 0; e < 4; ++e) acc[i][e] = 0;
@@ -1702,8 +1711,14 @@ static cudaError_t launch_strip_bwd_t(const PairSrc &src, int64_t n, void *ws, c
         ak<<<strip_grid(L, sms, per_sm), STRIP_WARPS * 32, asmem, st>>>(a);
     }
     const T scale = (T)0.5 / (T)(1LL << (2 * LAM));
-    grad_chain_kernel<T><<<sms * 4, 256, 0, st>>>(src, plan, n, (const T *)(w + L.gbar), incA, incB,
-                                                  gout, dA, dB, scale);
+    {
+        // tiles of the longest pair in x, pairs in y
+        const int64_t lx = max_la > max_lb ? max_la : max_lb;
+        const int64_t tiles = 2 * ((lx - 1 + CT - 1) / CT) * ((D4 + 7) / 8);
+        const dim3 grid((unsigned)(tiles < 1 ? 1 : tiles), (unsigned)(n < 65535 ? n : 65535));
+        grad_chain_kernel<T><<<grid, 256, 0, st>>>(src, plan, n, (const T *)(w + L.gbar), incA, incB, gout, dA,
+                                                   dB, scale);
+    }
     return cudaGetLastError();
 }
 
