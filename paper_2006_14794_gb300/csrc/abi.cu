@@ -246,12 +246,15 @@ bool bwd_uses_strip(int lam, int64_t d, int dtype, int rec, int kernel) {
     return dtype == SIGK_F32 ? rec != SIGK_REC_PLAIN : rec == SIGK_REC_CHAIN;
 }
 
+// The strip backward's batches: under 16 GiB, so that the 64 pairs of 4096
+// points at dyadic order 1 (coefficient blocks and dk/dG, 9.7 GB) run as one
+// launch, with all their strips' wavefronts in flight at once.
 void bwd_strip_batch(const PairSrc &src, int64_t n, int lam, int dtype, int64_t &nb, int64_t &bytes) {
     int64_t ra, rb;
     src_rows(src, n, ra, rb);
     nb = n;
     bytes = strip_bwd_workspace_bytes(nb, src.La, src.Lb, lam, dtype, ra, rb, src.d);
-    while (nb > 1 && bytes > STRIP_WS_CAP) {
+    while (nb > 1 && bytes > BAND_BWD_WS_CAP) {
         nb = (nb + 1) / 2;
         bytes = strip_bwd_workspace_bytes(nb, src.La, src.Lb, lam, dtype, ra, rb, src.d);
     }

@@ -697,6 +697,21 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
         T KS[R], QS[R];   // the forward state after the step about to be undone
 #pragma unroll
         for (int r = 0; r < R; ++r) { A[r] = 0; V[r] = 0; cp[r] = 0; KS[r] = 1; QS[r] = 0; }
+        // the bottom rows the undo reads (the upper strip's K at column t for
+        // lane 0, this strip's (K, Q) at column t - 32 R for lane 31), 32
+        // columns a chunk, lane j holding column 32 c + j: the chunk in use
+        // and the next one down, loaded a chunk ahead and read by shuffles
+        T topc = 1, topn = 1, bKc = 1, bQc = 0, bKn = 1, bQn = 0;
+        int tchunk = -1, bchunk = -1;
+        auto top_chunk = [&](int c) -> T {
+            const int col = c * 32 + lane;
+            return (topb && col >= 0 && col < nj) ? topb[(int64_t)col * 2] : (T)1;
+        };
+        auto bot_chunk = [&](int c, T &k, T &q) {
+            const int col = c * 32 + lane;
+            k = (col >= 0 && col < nj) ? botb[(int64_t)col * 2] : (T)1;
+            q = (col >= 0 && col < nj) ? botb[(int64_t)col * 2 + 1] : (T)0;
+        };
 #pragma unroll
         for (int g = 0; g < NG; ++g) { gN[g] = 0; gO[g] = 0; }
         bool timed_out = false;
@@ -806,9 +821,16 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
                     cw[r] = (jj >= sr) ? cn[g] : co[g];
                     KL[r] = KS[r] - QS[r];
                 }
+                if ((t >> 5) != tchunk) {   // warp-uniform: a new chunk of the upper strip's row
+                    const int tc = t >> 5;
+                    topc = tchunk == tc + 1 ? topn : top_chunk(tc);
+                    topn = top_chunk(tc - 1);
+                    tchunk = tc;
+                }
+                const T topv = __shfl_sync(FULL, topc, t & 31);
                 T kup = __shfl_up_sync(FULL, KL[R - 1], 1);
                 if (lane == 0)   // row 0 of the strip is at column t: the row above is the upper strip's
-                    kup = topb ? (t < nj ? topb[(int64_t)t * 2] : (T)1) : (T)1;
+                    kup = topb ? topv : (T)1;
                 sm[0] = KL[0] + kup;
 #pragma unroll
                 for (int r = 1; r < R; ++r) sm[r] = KL[r] + KL[r - 1];
@@ -827,6 +849,18 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
                 // ---- the state before step t: Q from the row below's update
                 const T qx = QS[0] - cw[0] * sm[0];   // the row above's Q, for lane - 1
                 const T qlast = __shfl_down_sync(FULL, qx, 1);
+                const int bc = col31 - 1;   // the last row's column before step t
+                T bkv = 1, bqv = 0;
+                if (bc >= 0) {   // warp-uniform
+                    if ((bc >> 5) != bchunk) {
+                        const int bq = bc >> 5;
+                        if (bchunk == bq + 1) { bKc = bKn; bQc = bQn; } else bot_chunk(bq, bKc, bQc);
+                        bot_chunk(bq - 1, bKn, bQn);
+                        bchunk = bq;
+                    }
+                    bkv = __shfl_sync(FULL, bKc, bc & 31);
+                    bqv = __shfl_sync(FULL, bQc, bc & 31);
+                }
 #pragma unroll
                 for (int r = 0; r < R - 1; ++r) QS[r] = QS[r + 1] - cw[r + 1] * sm[r + 1];
 #pragma unroll
@@ -835,13 +869,12 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_adj_kernel(AdjArgs<T> 
                     // the strip's last row: its own bottom row, kept by the
                     // forward (beyond the grid's last column every value is
                     // virtual and meets only zero adjoints)
-                    const int bc = col31 - 1;
                     if (bc < 0) {
                         KS[R - 1] = 1;
                         QS[R - 1] = 0;
                     } else if (bc < nj) {
-                        KS[R - 1] = botb[(int64_t)bc * 2];
-                        QS[R - 1] = botb[(int64_t)bc * 2 + 1];
+                        KS[R - 1] = bkv;
+                        QS[R - 1] = bqv;
                     } else {
                         QS[R - 1] = 0;
                     }
