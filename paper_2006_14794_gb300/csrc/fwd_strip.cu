@@ -30,6 +30,8 @@
 // (its result is then meaningless and the call reports the timeout).
 #include <string.h>
 
+#include <type_traits>
+
 #include "rbf.cuh"
 #include "sigk_internal.cuh"
 #include "tc5.cuh"
@@ -311,6 +313,17 @@ __device__ __forceinline__ void st_boundary(double *p, double v) {
     const unsigned long long b = ullmin((unsigned long long)__double_as_longlong(v), 0xfffffffffffffffeULL);
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b));
 }
+// the same store under a predicate, without a branch around it
+__device__ __forceinline__ void st_boundary_if(float *p, float v, bool pred) {
+    const unsigned b = umin(__float_as_uint(v), 0xfffffffeu);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.relaxed.gpu.global.b32 [%0], %1;\n\t}"
+                 ::"l"(p), "r"(b), "r"((int)pred));
+}
+__device__ __forceinline__ void st_boundary_if(double *p, double v, bool pred) {
+    const unsigned long long b = ullmin((unsigned long long)__double_as_longlong(v), 0xfffffffffffffffeULL);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.relaxed.gpu.global.b64 [%0], %1;\n\t}"
+                 ::"l"(p), "l"(b), "r"((int)pred));
+}
 
 template <typename T>
 struct StripArgs {
@@ -461,41 +474,68 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
         constexpr int WPC = CW / S;   // windows per chunk of the top row
         static_assert(WPC >= 2 && CW % (2 * S) == 0, "a chunk spans whole windows, half a chunk too");
         const int nwin = (tend + S - 1) / S;
-        for (int w = 0; w < nwin; ++w) {
-            // diagonal w + NRING - 1 into the slot diagonal w - 1 used; then
-            // diagonal w has landed (at most NRING - 1 newer groups in flight)
-            {
-                const int k = w + NRING - 1;
-                if (k < pp.nw)
-                    ring_fetch<T, NG>(&ring[warp][k % NRING][lane * NG], blk + (int64_t)k * CP + lane * NG);
-                ring_commit();
-                ring_wait<NRING - 1>();
-            }
-            const T *cw = &ring[warp][w % NRING][lane * NG];
+        const int nfull = tend / S;   // windows whose S steps all lie before tend
+        // the next window's coefficients, read from the ring one window ahead
+        // so that no step waits on a shared-memory load (diagonal nwin exists:
+        // nw >= nwin + 1)
+        float2 CX[NH > 0 ? NH : 1];
+        T cx[NG];
+        auto read_next = [&](int wn) {
+            const T *cw = &ring[warp][wn % NRING][lane * NG];
             if constexpr (PACK) {
 #pragma unroll
-                for (int g = 0; g < NH; ++g) { CO[g] = CN[g]; CN[g] = make_float2(cw[g], cw[g + NH]); }
+                for (int g = 0; g < NH; ++g) CX[g] = make_float2(cw[g], cw[g + NH]);
             } else {
 #pragma unroll
-                for (int g = 0; g < NG; ++g) { co[g] = cn[g]; cn[g] = cw[g]; }
+                for (int g = 0; g < NG; ++g) cx[g] = cw[g];
             }
+        };
+        ring_wait<NRING - 2>();   // diagonal 0 has landed
+        read_next(0);
+        int tev = top ? WPC : 0x7fffffff;   // the next window with top-row chunk work
+
+        // one window: S steps; TAIL: the last, partial window checks each step
+        auto window = [&](int w, auto tail_tag) {
+            constexpr bool TAIL = decltype(tail_tag)::value;
+            // diagonal w + NRING - 1 into the slot diagonal w - 1 used (read a
+            // window ago); then diagonal w + 1 has landed (at most NRING - 2
+            // newer groups in flight)
+            {
+                // past the last diagonal the copy repeats it: slots of
+                // diagonals >= nw are never read (nw >= nwin + 1), and an
+                // unconditional copy keeps the window free of branches
+                const int k = w + NRING - 1;
+                const int kc = min(k, pp.nw - 1);
+                ring_fetch<T, NG>(&ring[warp][k % NRING][lane * NG], blk + (int64_t)kc * CP + lane * NG);
+                ring_commit();
+                ring_wait<NRING - 2>();
+            }
+            if constexpr (PACK) {
+#pragma unroll
+                for (int g = 0; g < NH; ++g) { CO[g] = CN[g]; CN[g] = CX[g]; }
+            } else {
+#pragma unroll
+                for (int g = 0; g < NG; ++g) { co[g] = cn[g]; cn[g] = cx[g]; }
+            }
+            read_next(w + 1);
             // the top row at the window's first step t = w S: chunk c = t / CW
             // (columns t+1 .. t+CW) was loaded half a chunk ago, publish it;
             // load chunk c + 1 half a chunk on (chunks 0 and 1 were loaded at
             // the start)
-            if (top) {
-                const int c = w / WPC, wc = w % WPC;
-                if (c >= 1 && c * CW < nj) {
-                    if (wc == 0) {
+            if (w == tev) {   // warp-uniform: publish or load, every half chunk from window WPC on
+                const int c = w / WPC;
+                if (w % WPC == 0) {
+                    if (c * CW < nj) {
                         wait_top(c);
                         __syncwarp();
                         tb[2 * lane] = tn0;
                         tb[2 * lane + 1] = tn1;
                         __syncwarp();
-                    } else if (wc == WPC / 2 && (c + 1) * CW < nj) {
-                        load_top(c + 1);
                     }
+                } else if ((c + 1) * CW < nj) {
+                    load_top(c + 1);
                 }
+                tev += WPC / 2;
             }
             // the window's S top-row values (K, Q), read by every lane (one
             // broadcast address) and taken by lane 0 of a strip with a top row
@@ -508,7 +548,9 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
 #pragma unroll
             for (int jj = 0; jj < S; ++jj) {
                 const int t = w * S + jj;
-                if (S > 1 && t >= tend) break;   // only the last window can be partial
+                if constexpr (TAIL) {
+                    if (t >= tend) break;
+                }
                 // lane 0's row 0 is at column t + 1 now
                 if (top0 && t < nj) {
                     pK = topv[2 * jj];
@@ -519,7 +561,6 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                 const int bcol = t - (TH - 1);   // zero-based column of the lane's last row
                 if constexpr (PACK) {
                     const float kH1 = KP[H - 1].x, qH1 = QP[H - 1].x;   // row H-1 before this step
-                    float2 sum[H];
 #pragma unroll
                     for (int i = H - 1; i >= 0; --i) {
                         const int g1 = i / S, s1 = i % S;   // row i; row i+H: group g1+NH, same s1
@@ -532,17 +573,15 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                             ku = make_float2(pK, kH1);
                             qu = make_float2(pQ, qH1);
                         }
-                        sum[i] = __fadd2_rn(KP[i], ku);
-                        const float2 qn = __ffma2_rn(c, sum[i], qu);
+                        const float2 sum = __fadd2_rn(KP[i], ku);
+                        const float2 qn = __ffma2_rn(c, sum, qu);
                         KP[i] = __fadd2_rn(KP[i], qn);
                         QP[i] = qn;
                         if (i == H - 1) {
                             shK = __shfl_up_sync(FULL, KP[i].y, 1);
                             shQ = __shfl_up_sync(FULL, QP[i].y, 1);
-                            if (bstore) {
-                                st_boundary(bot + (int64_t)bcol * 2, KP[i].y);
-                                st_boundary(bot + (int64_t)bcol * 2 + 1, QP[i].y);
-                            }
+                            st_boundary_if(bot + (int64_t)bcol * 2, KP[i].y, bstore);
+                            st_boundary_if(bot + (int64_t)bcol * 2 + 1, QP[i].y, bstore);
                         }
                     }
                     if constexpr (SAVE) {
@@ -558,7 +597,6 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                         }
                     }
                 } else {
-                    T sum[R];
 #pragma unroll
                     for (int r = R - 1; r >= 0; --r) {
                         const int g = r / S, sr = r % S;
@@ -566,17 +604,15 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                         const T kl = K[r];
                         const T ku = r > 0 ? K[r > 0 ? r - 1 : 0] : pK;
                         const T qu = r > 0 ? Q[r > 0 ? r - 1 : 0] : pQ;
-                        sum[r] = kl + ku;
-                        const T qn = qu + c * sum[r];
+                        const T sum = kl + ku;
+                        const T qn = qu + c * sum;
                         K[r] = kl + qn;
                         Q[r] = qn;
                         if (r == R - 1) {
                             shK = __shfl_up_sync(FULL, K[r], 1);
                             shQ = __shfl_up_sync(FULL, Q[r], 1);
-                            if (bstore) {
-                                st_boundary(bot + (int64_t)bcol * 2, K[r]);
-                                st_boundary(bot + (int64_t)bcol * 2 + 1, Q[r]);
-                            }
+                            st_boundary_if(bot + (int64_t)bcol * 2, K[r], bstore);
+                            st_boundary_if(bot + (int64_t)bcol * 2 + 1, Q[r], bstore);
                         }
                     }
                     if constexpr (SAVE) {
@@ -594,7 +630,12 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) strip_kernel(StripArgs<T> a)
                     pQ = shQ;
                 }
             }
-        }
+        };
+        // four windows a loop iteration: the loop's own compare and branch
+        // cost a step about a tenth of its time at one window an iteration
+#pragma unroll 4
+        for (int w = 0; w < nfull; ++w) window(w, std::false_type{});
+        if (nfull < nwin) window(nfull, std::true_type{});
         ring_wait<0>();
         if (a.out && s == pp.ns - 1 && lane == 31) {
             T kc;
