@@ -285,14 +285,14 @@ bool bwd_uses_band(const PairSrc &src, int lam, int dtype, int rec, int rows, Ba
     return band_geometry(la, lb, lam, rows, bp);
 }
 
-int64_t backward_ws_bytes(const PairSrc &src, int64_t n, int lam, int dtype, int rec, int rows = 0) {
+int64_t backward_ws_bytes(const PairSrc &src, int64_t n, int lam, int dtype, int rec, int rows, int coef) {
     if (n == 0 || src.La < 2 || src.Lb < 2) return 0;
     BandPlan bp;
     if (bwd_uses_band(src, lam, dtype, rec, rows, bp)) {
         bool sw;
         const PairSrc o = band_orient(src, n, sw);
         int64_t bytes;
-        band_bwd_batch(o, bp, n, BAND_BWD_WS_CAP, bytes);
+        band_bwd_batch(o, bp, n, BAND_BWD_WS_CAP, bytes, coef);
         return bytes;
     }
     if (rec == SIGK_REC_BAND || src.mode == PM_GRAM_SYM) return -1;
@@ -326,7 +326,7 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
         bool sw;
         const PairSrc o = band_orient(src, n_pairs, sw);
         int64_t bytes;
-        const int64_t nbp = band_bwd_batch(o, bp, n_pairs, BAND_BWD_WS_CAP, bytes);
+        const int64_t nbp = band_bwd_batch(o, bp, n_pairs, BAND_BWD_WS_CAP, bytes, coef_of(opts));
         if (!ws || (int64_t)ws_bytes < bytes) return SIGK_ENOMEM_WS;
         float *dA = (float *)(sw ? dY : dX), *dB = (float *)(sw ? dX : dY);
         return cuda_status(
@@ -422,7 +422,8 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
             bs.mode = PM_GRAM_SYM;
             bs.nb = B_or_Bx;
         }
-        const int64_t need = backward_ws_bytes(bs, n_pairs, dyadic_order, dtype, rec_of(opts), rows_of(opts));
+        const int64_t need = backward_ws_bytes(bs, n_pairs, dyadic_order, dtype, rec_of(opts), rows_of(opts),
+                                               coef_of(opts));
         return need > 0 ? (size_t)need : 0;
     }
     int64_t nb, need;

@@ -1036,84 +1036,136 @@ __global__ void band_inc_kernel(const float *pts, int64_t npaths, int64_t L, int
     }
 }
 
-// C (+)= G B per batch, G read as G[r * ld + k] (or G[k * ld + r] when
-// trans): the chain rule through G(p, q) = <dx_p, dy_q>, summed over the
-// other path's increments.  128 x 32 output tiles, 32-deep K slices staged
-// in shared memory (the next slice is loaded into registers while the current
-// one is used), 4 x 4 outputs per thread; long K ranges are split across
-// blocks that add their partial tiles atomically into a zeroed C.
+// The chain rule through G(p, q) = <dx_p, dy_q>: C (+)= G B per batch, where
+// G is dk/dc read straight from the adjoint's band layout (pair k's value at
+// row-role increment p, column-role increment q sits in slot (k, pos, lane)
+// at [w][gpos(g)] with P = p + vrows = lane NG + g, Q = q + NQV = pos NG + w - g).
+// Not trans: C rows are the row role's increments (all row paths), the sum
+// runs over the column role's; trans: the other way round.  Output tiles are
+// 128 band coordinates (P, or Q when trans) of one output path by 32
+// channels; reduction slices are 32 band coordinates of one reduction path.
+// A slice's slots are staged whole (contiguous 16-byte loads), then
+// transposed into the tile in shared memory; virtual rows and columns (the
+// band's padding) read as zero.  4 x 4 outputs per thread; long reductions
+// are split across blocks whose partial tiles a second kernel sums in order.
 struct GemmArgs {
-    const float *G;
-    int64_t g_ld, g_bstride;
+    const float *G;          // dense dk/dc (the tensor-core contraction only)
+    int64_t g_ld;
     const float *Bm;
     int64_t b_bstride;
     float *C;
     int64_t c_bstride;
-    int64_t M, K;
-    int N, trans, ksplit;   // ksplit > 1 (one batch only): block ks writes its partial
-    float *partial;         // tile to partial[ks][M][N], summed by band_split_sum_kernel
-    // symmetric Gram (blocks of rb x cb, only blocks i <= j stored, the rest
-    // zero): skip the K slices that hold only blocks below the diagonal
-    int64_t tri_rb, tri_cb;  // 0: no skipping
+    int64_t M, K;            // output rows, reduction length (real increments)
+    int N, trans, ksplit;    // ksplit > 1 (one batch only): block ks writes its partial
+    float *partial;          // tile to partial[ks][M][N], summed by band_split_sum_kernel
+    int64_t tri_rb, tri_cb;  // symmetric Gram: only pairs i <= j are stored (tensor-core path)
+    const float *band;
+    int mode;                // PM_PAIRS: batch b is pair b; PM_GRAM / PM_GRAM_SYM: one batch
+    int64_t nb, a0, kbase;   // Gram: column paths, the launch's first row path, its first pair
+    int64_t nA, nB;          // row / column paths of a batch (1 and 1 for pairs)
+    int TperR1, vrows, NQV, nx, ny;
 };
 constexpr int GEMM_MAX_SPLIT = 8;
 constexpr int GT_M = 128, GT_K = 32, GT_N = 32;
 
+// the launch-local pair of row path ia and column path jb (-1: none stored,
+// below a symmetric Gram's diagonal)
+__device__ __forceinline__ int64_t gemm_pair(const GemmArgs &a, int64_t b, int64_t ia, int64_t jb) {
+    if (a.mode == PM_PAIRS) return b;
+    if (a.mode == PM_GRAM) return (a.a0 + ia) * a.nb + jb - a.kbase;
+    if (ia > jb) return -1;
+    return ia * a.nb - ia * (ia - 1) / 2 + (jb - ia) - a.kbase;
+}
+
+template <int NG>
 __global__ void __launch_bounds__(256) band_gemm_kernel(GemmArgs a) {
+    constexpr int SLOT = NG * NG;
+    constexpr int BH = 32 * NG;                                           // band rows of a path
+    constexpr int TL0 = (BH < GT_M ? BH : GT_M) / NG, TP0 = GT_K / NG + 1;   // staged lanes, positions
+    constexpr int TL1 = GT_K / NG, TP1 = GT_M / NG + 1;                      // (trans)
+    constexpr int ST0 = TL0 * TP0 * SLOT, ST1 = TL1 * TP1 * SLOT;
+    constexpr int STF = ST0 > ST1 ? ST0 : ST1;
+    constexpr int SV = (STF / 4 + 255) / 256;   // staged float4s per thread
     __shared__ __align__(16) float Gs[GT_K][GT_M + 4];
     __shared__ __align__(16) float Bs[GT_K][GT_N];
+    __shared__ __align__(16) float St[STF];
+    const bool tr = a.trans != 0;
     const int64_t b = blockIdx.z / a.ksplit;
     const int ks = blockIdx.z - (int)b * a.ksplit;
-    const float *G = a.G + b * a.g_bstride;
     const float *Bm = a.Bm + b * a.b_bstride;
     float *C = a.C + b * a.c_bstride;
-    const int64_t r0 = (int64_t)blockIdx.x * GT_M;
+    const int NQ = (a.TperR1 - 1) * NG;   // band columns of a path
+    const int ocoords = tr ? NQ : BH;     // output band coordinates of a path
+    const int tpp = (ocoords + GT_M - 1) / GT_M;
+    const int64_t opath = blockIdx.x / tpp;
+    const int o0 = (int)(blockIdx.x - opath * tpp) * GT_M;
     const int n0 = blockIdx.y * GT_N;
     const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
-    // this block's K range, in whole slices
-    int64_t kmin = 0, kmax = a.K;
-    if (a.tri_rb > 0) {
-        if (!a.trans) kmin = (r0 / a.tri_rb) * a.tri_cb;   // rows of block i: columns of blocks j >= i
-        else {                                           // columns of block j: rows of blocks i <= j
-            const int64_t rl = (r0 + GT_M - 1 < a.M ? r0 + GT_M - 1 : a.M - 1);
-            kmax = (rl / a.tri_cb + 1) * a.tri_rb;
-            if (kmax > a.K) kmax = a.K;
-        }
+    // the reduction: paths [rlo, rhi) (a symmetric Gram stores pairs i <= j
+    // only), each in spp slices of 32 band coordinates
+    const int rcoords = tr ? BH : NQ;
+    const int spp = (rcoords + GT_K - 1) / GT_K;
+    int64_t rlo = 0, rhi = tr ? a.nA : a.nB;
+    if (a.mode == PM_GRAM_SYM) {
+        if (tr) rhi = opath + 1; else rlo = opath;
     }
-    const int64_t sl0 = kmin / GT_K, nslice = (kmax + GT_K - 1) / GT_K - sl0;
-    const int64_t s_lo = sl0 + nslice * ks / a.ksplit, s_hi = sl0 + nslice * (ks + 1) / a.ksplit;
-    float gr[16], br[4];
-    auto load = [&](int64_t k0) {
+    const int64_t total = (rhi - rlo) * spp;
+    const int64_t s_lo = total * ks / a.ksplit, s_hi = total * (ks + 1) / a.ksplit;
+    const int TL = tr ? TL1 : TL0, TP = tr ? TP1 : TP0;
+    const int SN = TL * TP * SLOT / 4;   // float4s staged a slice
+    const int nrr = tr ? a.nx : a.ny;    // real increments of the reduction role
+    const int nro = tr ? a.ny : a.nx;    // and of the output role
+    const int vro = tr ? a.NQV : a.vrows, vrr = tr ? a.vrows : a.NQV;
+
+    float4 sv[SV];
+    float br[4];
+    int c0n = 0;
+    // slice sidx into registers: its slots (not trans: lanes o0/NG + [0, TL0),
+    // positions c0/NG + [0, TP0); trans: lanes c0/NG + [0, TL1), positions
+    // o0/NG + [0, TP1); positions past the pair's last slot read as zero) and
+    // the reduction role's 32 increments of 32 channels
+    auto load = [&](int64_t sidx) {
+        const int64_t rp = rlo + sidx / spp;
+        const int c0 = (int)(sidx - (rp - rlo) * spp) * GT_K;
+        const int64_t k = tr ? gemm_pair(a, b, rp, opath) : gemm_pair(a, b, opath, rp);
+        const int l0 = (tr ? c0 : o0) / NG, p0 = (tr ? o0 : c0) / NG;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int v = threadIdx.x + 256 * i;
-            int rr, kk;
-            if (!a.trans) { rr = v / GT_K; kk = v % GT_K; } else { kk = v / GT_M; rr = v % GT_M; }
-            const int64_t r = r0 + rr, k = k0 + kk;
-            gr[i] = (r < a.M && k < a.K) ? (a.trans ? G[k * a.g_ld + r] : G[r * a.g_ld + k]) : 0.f;
+        for (int i = 0; i < SV; ++i) {
+            const int u = threadIdx.x + 256 * i;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (u < SN && k >= 0) {
+                const int sl = u / (SLOT / 4), e = u - sl * (SLOT / 4);
+                const int pr = sl / TL, lr = sl - pr * TL;
+                const int pos = p0 + pr;
+                if (pos < a.TperR1)
+                    v = __ldg(reinterpret_cast<const float4 *>(
+                                  a.band + ((k * a.TperR1 + pos) * 32 + l0 + lr) * (int64_t)SLOT) + e);
+            }
+            sv[i] = v;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int v = threadIdx.x + 256 * i;
             const int kk = v / GT_N, nn = v % GT_N;
-            const int64_t k = k0 + kk;
+            const int real = c0 + kk - vrr;
             const int n = n0 + nn;
-            br[i] = (k < a.K && n < a.N) ? Bm[k * a.N + n] : 0.f;
+            br[i] = (real >= 0 && real < nrr && n < a.N && k >= 0) ? Bm[(rp * nrr + real) * a.N + n] : 0.f;
         }
+        c0n = c0;
     };
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jx = 0; jx < 4; ++jx) acc[i][jx] = 0.f;
-    if (s_lo < s_hi) load(s_lo * GT_K);
-    for (int64_t sl = s_lo; sl < s_hi; ++sl) {
+    if (s_lo < s_hi) load(s_lo);
+    for (int64_t sidx = s_lo; sidx < s_hi; ++sidx) {
+        const int c0 = c0n;
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int v = threadIdx.x + 256 * i;
-            if (!a.trans) Gs[v % GT_K][v / GT_K] = gr[i];
-            else Gs[v / GT_M][v % GT_M] = gr[i];
+        for (int i = 0; i < SV; ++i) {
+            const int u = threadIdx.x + 256 * i;
+            if (u < SN) reinterpret_cast<float4 *>(St)[u] = sv[i];
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -1121,12 +1173,26 @@ __global__ void __launch_bounds__(256) band_gemm_kernel(GemmArgs a) {
             Bs[v / GT_N][v % GT_N] = br[i];
         }
         __syncthreads();
-        if (sl + 1 < s_hi) load((sl + 1) * GT_K);
+        // Gs[kk][rr]: output coordinate o0 + rr, reduction coordinate c0 + kk;
+        // virtual rows and columns of the reduction role read as zero
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int v = threadIdx.x + 256 * i;
+            const int rr = v % GT_M, kk = v / GT_M;
+            const int Prel = tr ? kk : rr, Qrel = tr ? rr : kk;
+            const int lr = Prel / NG, g = Prel % NG;
+            const int t = Qrel + g, pr = t / NG, w = t % NG;
+            const int real = c0 + kk - vrr;
+            const bool ok = real >= 0 && real < nrr && (tr || o0 + rr < BH);
+            Gs[kk][rr] = ok ? St[(pr * TL + lr) * SLOT + w * NG + band_gpos<NG>(g)] : 0.f;
+        }
+        if (sidx + 1 < s_hi) load(sidx + 1);
+        __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < GT_K; ++kk) {
-            const float4 g = *reinterpret_cast<const float4 *>(&Gs[kk][4 * ty]);
+            const float4 gv = *reinterpret_cast<const float4 *>(&Gs[kk][4 * ty]);
             const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][4 * tx]);
-            const float gg[4] = {g.x, g.y, g.z, g.w};
+            const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
             const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -1136,8 +1202,10 @@ __global__ void __launch_bounds__(256) band_gemm_kernel(GemmArgs a) {
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int64_t r = r0 + 4 * ty + i;
-        if (r >= a.M) continue;
+        const int oc = o0 + 4 * ty + i;
+        const int real = oc - vro;
+        if (oc >= ocoords || real < 0 || real >= nro) continue;
+        const int64_t r = opath * nro + real;
 #pragma unroll
         for (int jx = 0; jx < 4; ++jx) {
             const int n = n0 + 4 * tx + jx;
@@ -1400,7 +1468,14 @@ struct BwdRegions {
     int64_t total() const { return band + gbar + ckpt + exitk + botq + incA + incB + dincA + dincB + part + gband; }
 };
 
-BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
+// dense: whether a Gram's dk/dc is unpacked into a dense matrix for the
+// tensor-core contraction (coef_path 3); the FP32 contraction reads the band
+bool bwd_dense_gbar(const PairSrc &src, int coef_path) {
+    const bool gram = src.mode == PM_GRAM || src.mode == PM_GRAM_SYM;
+    return gram && coef_path == 3 && chain_gemm_tc5_ok(1, 1, (int)src.d);
+}
+
+BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp, int coef_path) {
     const int64_t nx = src.La - 1, ny = src.Lb - 1, d = src.d;
     const bool sym = src.mode == PM_GRAM_SYM;
     const bool gram = src.mode == PM_GRAM || sym;
@@ -1408,8 +1483,7 @@ BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
     const int64_t nB = gram ? src.nb : nbp;
     BwdRegions r;
     r.band = up4(band_bytes(p, nbp) / (int64_t)sizeof(float));
-    r.gbar = up4(nA * nx * nB * ny);
-    if (!gram) r.gbar = up4(nbp * nx * ny);
+    r.gbar = bwd_dense_gbar(src, coef_path) ? up4(nA * nx * nB * ny) : 0;
     r.ckpt = ((nbp + 1) * ((2 * (int64_t)p.TperR + 32 + BAND_CK) / BAND_CK) + 1) * 32 * 2 * p.R;
     r.exitk = (nbp + 1) * 32 * (int64_t)p.R;
     r.botq = up4((nbp + 1) * ((2 * (int64_t)p.TperR + 32) * p.R + 4));
@@ -1427,20 +1501,20 @@ BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp) {
 }  // namespace
 
 int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t cap_bytes,
-                       int64_t &bytes) {
+                       int64_t &bytes, int coef_path) {
     if (src.mode == PM_GRAM_SYM) {   // one launch: every pair involves the same paths
-        bytes = bwd_regions(src, p, n).total() * (int64_t)sizeof(float);
+        bytes = bwd_regions(src, p, n, coef_path).total() * (int64_t)sizeof(float);
         return n;
     }
     // whole Gram rows per launch: each launch owns its row paths' gradients
     const int64_t unit = src.mode == PM_GRAM ? src.nb : 1;
     int64_t units = (n + unit - 1) / unit;
     int64_t nb = n;
-    bytes = bwd_regions(src, p, nb).total() * (int64_t)sizeof(float);
+    bytes = bwd_regions(src, p, nb, coef_path).total() * (int64_t)sizeof(float);
     while (units > 1 && bytes > cap_bytes) {
         units = (units + 1) / 2;
         nb = units * unit < n ? units * unit : n;
-        bytes = bwd_regions(src, p, nb).total() * (int64_t)sizeof(float);
+        bytes = bwd_regions(src, p, nb, coef_path).total() * (int64_t)sizeof(float);
     }
     return nb;
 }
@@ -1462,7 +1536,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
     if (sym && (dB || nbp != n)) return cudaErrorInvalidValue;
     const int64_t nx = src0.La - 1, ny = src0.Lb - 1, d = src0.d;
     const float scale = 0.5f / (float)(1 << (2 * p.lam));
-    const BwdRegions rg = bwd_regions(src0, p, nbp);
+    const BwdRegions rg = bwd_regions(src0, p, nbp, coef_path);
     float *w = (float *)ws;
     int *status = (int *)ws;
     float *band = w + 64;   // after the 256-byte status header
@@ -1489,8 +1563,6 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         src.kbase = src0.kbase + kb;
         const int64_t a0 = sym ? 0 : gram ? src.kbase / src0.nb : src.kbase;   // first row path
         const int64_t nA = sym ? src0.nb : gram ? m / src0.nb : m;
-        // blocks below the diagonal of a symmetric Gram's dk/dc stay zero
-        if (sym && cudaMemsetAsync(gbar, 0, sizeof(float) * rg.gbar, st) != cudaSuccess) return cudaErrorUnknown;
         // 1. coefficients
         BandCoefArgs c;
         c.src = src;
@@ -1560,8 +1632,17 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         SIGK_BAND_CASES(X)
 #undef X
         if (!launched) return cudaErrorInvalidValue;
-        // 3b. dk/dc from the band layout into the dense Gbar
-        {
+        // a Gram's contractions on the tensor cores (split-TF32) with the
+        // tcgen05 path (coef_path 3), else on the FP32 pipe.  The tensor-core
+        // contraction matches the FP32 one's accuracy but measured slower on
+        // the 128 x 128 MMD Gram (2.6 against 1.5 ms a launch): its chunks run
+        // in lockstep (copy, split, MMAs, read-back behind block barriers)
+        const bool tc = bwd_dense_gbar(src0, coef_path);
+        // 3b. dk/dc from the band layout into the dense Gbar (the tensor-core
+        // contraction reads it; the FP32 one reads the band layout itself)
+        if (tc) {
+            // blocks below the diagonal of a symmetric Gram's dense dk/dc stay zero
+            if (sym && cudaMemsetAsync(gbar, 0, sizeof(float) * rg.gbar, st) != cudaSuccess) return cudaErrorUnknown;
             BandGbarArgs gb;
             memset(&gb, 0, sizeof(gb));   // s_pair = 0: the dense Gbar, not the surface
             gb.src = src;
@@ -1591,6 +1672,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 5. chain rule: dinc_A = gbar inc_B, dinc_B (+)= gbar^T inc_A
         GemmArgs g1;
+        memset(&g1, 0, sizeof(g1));
         g1.G = gbar;
         g1.Bm = sym ? incA : incB;
         g1.C = dincA;
@@ -1606,49 +1688,60 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         if (gram) {
             batches = 1;
             g1.g_ld = g2.g_ld = nBall * ny;
-            g1.g_bstride = g2.g_bstride = 0;
-            g1.b_bstride = g2.b_bstride = 0;
-            g1.c_bstride = g2.c_bstride = 0;
             g1.M = nA * nx; g1.K = nBall * ny;
             g2.M = nBall * ny; g2.K = nA * nx;
+            g1.nA = g2.nA = nA;
+            g1.nB = g2.nB = nBall;
         } else {
             batches = m;
-            g1.g_ld = g2.g_ld = ny;
-            g1.g_bstride = g2.g_bstride = nx * ny;
             g1.b_bstride = ny * d; g2.b_bstride = nx * d;
             g1.c_bstride = nx * d; g2.c_bstride = ny * d;
             g1.M = nx; g1.K = ny;
             g2.M = ny; g2.K = nx;
+            g1.nA = g2.nA = 1;
+            g1.nB = g2.nB = 1;
         }
-        // a Gram's contractions have long K ranges: split them to about four
+        // output tiles: 128 band coordinates of one output path (band rows,
+        // or band columns when trans) by 32 channels
+        const int64_t BHr = 32 * (int64_t)p.NG, NQc = (int64_t)p.TperR * p.NG;
+        const int64_t tiles1 = (gram ? g1.nA : 1) * ((BHr + GT_M - 1) / GT_M);
+        const int64_t tiles2 = (gram ? g2.nB : 1) * ((NQc + GT_M - 1) / GT_M);
+        // a Gram's contractions have long reductions: split them to about four
         // blocks per SM, the partial tiles summed in a fixed order.  The Gram's
         // column-path gradients add up over launches.
-        auto split = [&](const GemmArgs &g) {
+        auto split = [&](int64_t tiles, int64_t nsl) {
             if (!gram) return 1;
-            const int64_t tiles = ((g.M + GT_M - 1) / GT_M) * ((d + GT_N - 1) / GT_N);
+            tiles *= (d + GT_N - 1) / GT_N;
             int64_t ksp = (4 * (int64_t)sms + tiles - 1) / tiles;
-            const int64_t nsl = (g.K + GT_K - 1) / GT_K;
             if (ksp > nsl / 4) ksp = nsl / 4;
             if (ksp > GEMM_MAX_SPLIT) ksp = GEMM_MAX_SPLIT;
             return (int)(ksp < 1 ? 1 : ksp);
         };
-        g1.ksplit = split(g1);
-        g2.ksplit = split(g2);
+        g1.ksplit = split(tiles1, nBall * ((NQc + GT_K - 1) / GT_K));
+        g2.ksplit = split(tiles2, nA * (BHr / GT_K));
         g1.partial = g2.partial = part;
         const bool add_b = (gram && kb > 0) || sym;
         if (sym) g2.C = dincA;   // column-role gradients of the same paths: add them to the row role's
         // the split sum writes the result; an unsplit contraction that must add goes through it too
         if (add_b && g2.ksplit == 1) g2.ksplit = 2;
-        const dim3 gd1((unsigned)((g1.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N),
-                       (unsigned)(batches * g1.ksplit));
-        const dim3 gd2((unsigned)((g2.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N),
-                       (unsigned)(batches * g2.ksplit));
-        // a Gram's contractions on the tensor cores (split-TF32) with the
-        // tcgen05 path (coef_path 3), else on the FP32 pipe.  The tensor-core
-        // contraction matches the FP32 one's accuracy but measured slower on
-        // the 128 x 128 MMD Gram (2.6 against 1.5 ms a launch): its chunks run
-        // in lockstep (copy, split, MMAs, read-back behind block barriers)
-        const bool tc = gram && coef_path == 3 && chain_gemm_tc5_ok(g1.M, g1.K, (int)d);
+        const dim3 gd1((unsigned)tiles1, (unsigned)((d + GT_N - 1) / GT_N), (unsigned)(batches * g1.ksplit));
+        const dim3 gd2((unsigned)tiles2, (unsigned)((d + GT_N - 1) / GT_N), (unsigned)(batches * g2.ksplit));
+        // the FP32 contractions gather dk/dc from the band layout
+        g1.band = g2.band = gband;
+        g1.mode = g2.mode = src.mode;
+        g1.nb = g2.nb = src0.nb;
+        g1.a0 = g2.a0 = a0;
+        g1.kbase = g2.kbase = src.kbase;
+        g1.TperR1 = g2.TperR1 = p.TperR + 1;
+        g1.vrows = g2.vrows = p.vrows;
+        g1.NQV = g2.NQV = p.NQV;
+        g1.nx = g2.nx = (int)nx;
+        g1.ny = g2.ny = (int)ny;
+        auto gemm = [&](const dim3 &gd, const GemmArgs &ga) {
+            if (p.NG == 8) band_gemm_kernel<8><<<gd, 256, 0, st>>>(ga);
+            else if (p.NG == 4) band_gemm_kernel<4><<<gd, 256, 0, st>>>(ga);
+            else band_gemm_kernel<2><<<gd, 256, 0, st>>>(ga);
+        };
         auto as_chain = [&](const GemmArgs &ga, int add) {
             ChainGemm cg;
             cg.G = ga.G;
@@ -1668,7 +1761,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
             if (tc) {
                 if ((e = launch_chain_gemm_tc5(as_chain(g1, 0), status, st)) != cudaSuccess) return e;
             } else {
-                band_gemm_kernel<<<gd1, 256, 0, st>>>(g1);
+                gemm(gd1, g1);
                 if (g1.ksplit > 1)
                     band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g1.ksplit, g1.M * d, 0, dincA);
             }
@@ -1677,7 +1770,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
             if (tc) {
                 if ((e = launch_chain_gemm_tc5(as_chain(g2, add_b ? 1 : 0), status, st)) != cudaSuccess) return e;
             } else {
-                band_gemm_kernel<<<gd2, 256, 0, st>>>(g2);
+                gemm(gd2, g2);
                 if (g2.ksplit > 1)
                     band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g2.ksplit, g2.M * d, add_b ? 1 : 0,
                                                                    g2.C);
@@ -1699,8 +1792,5 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
     return cudaSuccess;
 }
 
-int64_t band_bwd_bytes(const PairSrc &src, const BandPlan &p, int64_t nbp) {
-    return bwd_regions(src, p, nbp).total() * (int64_t)sizeof(float);
-}
 
 }  // namespace sigk

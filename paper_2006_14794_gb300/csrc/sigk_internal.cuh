@@ -180,11 +180,11 @@ cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pai
                             void *ws, cudaStream_t st, int coef_path, float *surf = nullptr,
                             int64_t s_pair = 0, int64_t s_a = 0, int64_t s_b = 0);
 // The band backward (reversible adjoint): pairs per launch (Gram: whole rows)
-// under cap_bytes, with the workspace that needs; then the launches.  src is
+// under cap_bytes, with the workspace that needs (coef_path 3 adds a Gram's
+// dense dk/dc for the tensor-core contraction); then the launches.  src is
 // oriented (rows refine A); dA / dB (either may be null) are overwritten.
 int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t cap_bytes,
-                       int64_t &bytes);
-int64_t band_bwd_bytes(const PairSrc &src, const BandPlan &p, int64_t nbp);
+                       int64_t &bytes, int coef_path);
 // out: null, or where the forward sweep also writes the values; add: the
 // gradients are added to what dA / dB hold instead of overwriting them
 cudaError_t launch_band_bwd_f32(const PairSrc &src, const BandPlan &p, int64_t n, int64_t nbp,
