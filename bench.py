@@ -640,9 +640,13 @@ def _workload(name, batch=0, cache=None):
             oracle_rate=oracle_rate, parity=parity, host_step=host_step, host=host,
             h2d=X32.nbytes + Y32.nbytes, d2h=X32.nbytes)
 
-    if name == "mmd128":
+    if name in ("mmd128", "mmd128_rbf"):
         # config 4: MMD^2 between 128 and 128 paths, L=256, d=32, dyadic order 1;
-        # one step = the loss and dL/dX
+        # one step = the loss and dL/dX.  mmd128_rbf: the same with the RBF
+        # lift (sigma = 1) of Sec. 2.2
+        rbf_sigma = 1.0 if name == "mmd128_rbf" else None
+        var = sigk.Variant(static_kernel="rbf", sigma=rbf_sigma) if rbf_sigma else None
+        okw = dict(static_kernel="rbf", sigma=rbf_sigma) if rbf_sigma else {}
         w = inputs.mmd_batches()
         lam = w["dyadic_order"]
         nb = batch if 1 < batch < 128 else 128
@@ -668,23 +672,29 @@ def _workload(name, batch=0, cache=None):
         nch = 32
         flop = (fwd_pairs * nn * 2 * nch + fwd_pairs * nc * 3 + adj_pairs * nc * 7
                 + 2 * 2 * (255 * nb) ** 2 * nch)
+        if rbf_sigma:
+            # the lift: 9d flop per coarse cell for its coefficient (exponentials
+            # not counted); its chain rule: squared distances (3d per point pair)
+            # and the contractions over points
+            flop = (fwd_pairs * nn * 9 * nch + fwd_pairs * nc * 3 + adj_pairs * nc * 7
+                    + adj_pairs * 256 * 256 * 3 * nch + 2 * 2 * (256 * nb) ** 2 * nch)
 
         def step():
             X = Xd.clone().requires_grad_(True)
-            v = sigk.mmd2_loss(X, Yd, lam)
+            v = sigk.mmd2_loss(X, Yd, lam, variant=var)
             v.backward()
             return X.grad
 
         def host_step(hx, hy, hg):
             X = hx.cuda(non_blocking=True).requires_grad_(True)
-            v = sigk.mmd2_loss(X, hy.cuda(non_blocking=True), lam)
+            v = sigk.mmd2_loss(X, hy.cuda(non_blocking=True), lam, variant=var)
             v.backward()
             hg.copy_(X.grad, non_blocking=True)
 
         rows = [0, min(77, nb - 1)]
 
         def refs():
-            key = ("mmd128", nb)
+            key = (name, nb)
             if key not in cache:
                 m = n = nb
 
@@ -695,8 +705,8 @@ def _workload(name, batch=0, cache=None):
                     for i in rows:
                         gi = gxx.copy()
                         gi[0, i] = 0.0
-                        a, _ = oracle.gram_grad(X64[i:i + 1], X64, lam, gi, want_dy=False)
-                        b, _ = oracle.gram_grad(X64[i:i + 1], Y64, lam, gxy, want_dy=False)
+                        a, _ = oracle.gram_grad(X64[i:i + 1], X64, lam, gi, want_dy=False, **okw)
+                        b, _ = oracle.gram_grad(X64[i:i + 1], Y64, lam, gxy, want_dy=False, **okw)
                         out.append(2.0 * a[0] + b[0])
                     return out
                 cache[key] = _timed_oracle(run)
@@ -717,11 +727,14 @@ def _workload(name, batch=0, cache=None):
         host = (torch.from_numpy(X32).pin_memory(), torch.from_numpy(Y32).pin_memory(),
                 torch.empty(X32.shape).pin_memory())
         return dict(
-            desc="MMD^2 %d vs %d, L=256, d=32 walks + drift, dyadic order 1, loss + dL/dX, fp32 "
-                 "(cells: the forward cells of the U-statistic's %d distinct pairs)" % (nb, nb, u_pairs),
+            desc="MMD^2 %d vs %d, L=256, d=32 walks + drift, dyadic order 1, %sloss + dL/dX, fp32 "
+                 "(cells: the forward cells of the U-statistic's %d distinct pairs)"
+                 % (nb, nb, "RBF lift (sigma 1), " if rbf_sigma else "", u_pairs),
             dtype="f32", step=step, cells=cells, pairs=u_pairs, flop=flop,
-            kernels="chain_band_adj_kernel + band_gemm_kernel + band_coef_kernel + band_gbar_kernel + "
-                    "chain_band_kernel (band form; fused value-and-gradient calls for Kxx and Kxy)",
+            kernels=("rbf_coef_kernel + chain_band_kernel + chain_band_adj_kernel + rbf_wt_kernel + "
+                     "dense_gemm_kernel (band form; fused value-and-gradient calls for Kxx and Kxy)" if rbf_sigma else
+                     "chain_band_adj_kernel + band_gemm_kernel + band_coef_kernel + chain_band_kernel "
+                     "(band form; fused value-and-gradient calls for Kxx and Kxy)"),
             oracle_rate=oracle_rate, parity=parity, host_step=host_step, host=host,
             h2d=X32.nbytes + Y32.nbytes, d2h=X32.nbytes)
 
@@ -1019,7 +1032,7 @@ def main():
                     help="uneven4096 / long64 / mmd128 / gram256_*: only the first BATCH pairs / paths per batch "
                          "(profiling)")
     ap.add_argument("--workload", default="gram256",
-                    choices=["gram256"] + DEFAULT_WORKLOADS + ["gram256_implicit", "gram256_rbf",
+                    choices=["gram256"] + DEFAULT_WORKLOADS + ["gram256_implicit", "gram256_rbf", "mmd128_rbf",
                                                                "surface256", "support_fbm30"])
     args = ap.parse_args()
     if args.warmup < 3:

@@ -213,8 +213,10 @@ int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64
  * <dx_p, dy_q>).  grad_out: [B]; dX: [B, L, d]; dY: [B, M, d] (overwritten).
  * opts->scheme selects the scheme differentiated.  With the RBF lift
  * (opts->static_kernel) the chain rule goes through the second difference of
- * kappa and runs in the one-block-per-pair backward; SIGK_REC_STRIP,
- * SIGK_REC_BAND and the symmetric Gram backward then give SIGK_EUNSUPPORTED. */
+ * kappa over the points (dk/dkappa(i,j) from four neighbouring dk/dc, then
+ * dkappa/dx_i = kappa (y_j - x_i) / sigma^2): in f32 on the band form when
+ * the pair fits it (the symmetric Gram backward included), else in the
+ * one-block-per-pair backward; SIGK_REC_STRIP gives SIGK_EUNSUPPORTED. */
 int sigk_pairs_backward(const void *grad_out, const void *X, const void *Y, int64_t B,
                         int64_t L, int64_t M, int64_t d, int dyadic_order, int dtype,
                         const sigk_opts *opts, void *dX, void *dY, void *ws, size_t ws_bytes,

@@ -279,7 +279,7 @@ PairSrc band_orient(const PairSrc &src, int64_t n, bool &swapped) {
 
 bool bwd_uses_band(const PairSrc &src, int lam, int dtype, int rec, int rows, BandPlan &bp) {
     if (dtype != SIGK_F32 || rec == SIGK_REC_PLAIN || rec == SIGK_REC_STRIP) return false;
-    if (src.kernel != SIGK_KERNEL_LINEAR) return false;
+    if (src.kernel != SIGK_KERNEL_LINEAR && src.kernel != SIGK_KERNEL_RBF) return false;
     if (src.mode != PM_PAIRS && src.mode != PM_GRAM && src.mode != PM_GRAM_SYM) return false;
     const int64_t la = src.La < src.Lb ? src.La : src.Lb, lb = src.La < src.Lb ? src.Lb : src.La;
     return band_geometry(la, lb, lam, rows, bp);
@@ -333,8 +333,8 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
             launch_band_bwd_f32(o, bp, n_pairs, nbp, (const float *)gout, dA, dB, ws, st, coef_of(opts),
                                 (float *)out, acc));
     }
-    // the symmetric backward exists in the band form only, the RBF lift's in
-    // the plain backward only
+    // the symmetric backward exists in the band form only; the RBF lift's in
+    // the band form (FP32, pairs that fit a warp) and the plain backward
     if (rec == SIGK_REC_BAND || src.mode == PM_GRAM_SYM) return SIGK_EUNSUPPORTED;
     if (src.kernel != SIGK_KERNEL_LINEAR && rec == SIGK_REC_STRIP) return SIGK_EUNSUPPORTED;
     if (bwd_uses_strip(lam, src.d, dtype, rec, src.kernel)) {

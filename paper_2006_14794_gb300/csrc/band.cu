@@ -1216,6 +1216,126 @@ __global__ void __launch_bounds__(256) band_gemm_kernel(GemmArgs a) {
     }
 }
 
+// ---- the RBF lift's chain rule (Sec. 2.2) ---------------------------------
+// With c(p, q) = 1/2 4^-lambda (k(p+1,q+1) - k(p+1,q) - k(p,q+1) + k(p,q)),
+// k(i, j) = kappa(x_i, y_j) = exp(-|x_i - y_j|^2 / (2 sigma^2)), the adjoint's
+// dk/dc = Gbar gives dL/dk(i, j) = 1/2 4^-lambda W(i, j) with the second
+// difference W(i, j) = Gbar(i-1,j-1) - Gbar(i-1,j) - Gbar(i,j-1) + Gbar(i,j)
+// (Gbar zero outside the grid), and dk/dx_i = k (y_j - x_i) / sigma^2.  So
+// with Wt = 1/2 4^-lambda W k over the points of every pair,
+//   dL/dx_i = (sum_j Wt(i,j) y_j - x_i sum_j Wt(i,j)) / sigma^2
+// and the mirror for y: a dense contraction of Wt with the points plus the
+// row and column sums of Wt.
+
+// C (+)= G B per batch for a dense G read as G[r * ld + k] (or G[k * ld + r]
+// when trans).  128 x 32 output tiles, 32-deep K slices staged in shared
+// memory (the next slice is loaded into registers while the current one is
+// used), 4 x 4 outputs per thread; long K ranges split across blocks whose
+// partial tiles band_split_sum_kernel adds in order.  A symmetric Gram's Wt
+// holds blocks i <= j only (tri_rb x tri_cb blocks): the K slices of blocks
+// below the diagonal are skipped.
+struct DenseGemmArgs {
+    const float *G;
+    int64_t g_ld, g_bstride;
+    const float *Bm;
+    int64_t b_bstride;
+    float *C;
+    int64_t c_bstride;
+    int64_t M, K;
+    int N, trans, ksplit;
+    float *partial;
+    int64_t tri_rb, tri_cb;
+};
+
+__global__ void __launch_bounds__(256) dense_gemm_kernel(DenseGemmArgs a) {
+    __shared__ __align__(16) float Gs[GT_K][GT_M + 4];
+    __shared__ __align__(16) float Bs[GT_K][GT_N];
+    const int64_t b = blockIdx.z / a.ksplit;
+    const int ks = blockIdx.z - (int)b * a.ksplit;
+    const float *G = a.G + b * a.g_bstride;
+    const float *Bm = a.Bm + b * a.b_bstride;
+    float *C = a.C + b * a.c_bstride;
+    const int64_t r0 = (int64_t)blockIdx.x * GT_M;
+    const int n0 = blockIdx.y * GT_N;
+    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+    // this block's K range, in whole slices
+    int64_t kmin = 0, kmax = a.K;
+    if (a.tri_rb > 0) {
+        if (!a.trans) kmin = (r0 / a.tri_rb) * a.tri_cb;   // rows of block i: columns of blocks j >= i
+        else {                                           // columns of block j: rows of blocks i <= j
+            const int64_t rl = (r0 + GT_M - 1 < a.M ? r0 + GT_M - 1 : a.M - 1);
+            kmax = (rl / a.tri_cb + 1) * a.tri_rb;
+            if (kmax > a.K) kmax = a.K;
+        }
+    }
+    const int64_t sl0 = kmin / GT_K, nslice = (kmax + GT_K - 1) / GT_K - sl0;
+    const int64_t s_lo = sl0 + nslice * ks / a.ksplit, s_hi = sl0 + nslice * (ks + 1) / a.ksplit;
+    float gr[16], br[4];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int v = threadIdx.x + 256 * i;
+            int rr, kk;
+            if (!a.trans) { rr = v / GT_K; kk = v % GT_K; } else { kk = v / GT_M; rr = v % GT_M; }
+            const int64_t r = r0 + rr, k = k0 + kk;
+            gr[i] = (r < a.M && k < a.K) ? (a.trans ? G[k * a.g_ld + r] : G[r * a.g_ld + k]) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int v = threadIdx.x + 256 * i;
+            const int kk = v / GT_N, nn = v % GT_N;
+            const int64_t k = k0 + kk;
+            const int n = n0 + nn;
+            br[i] = (k < a.K && n < a.N) ? Bm[k * a.N + n] : 0.f;
+        }
+    };
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jx = 0; jx < 4; ++jx) acc[i][jx] = 0.f;
+    if (s_lo < s_hi) load(s_lo * GT_K);
+    for (int64_t sl = s_lo; sl < s_hi; ++sl) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int v = threadIdx.x + 256 * i;
+            if (!a.trans) Gs[v % GT_K][v / GT_K] = gr[i];
+            else Gs[v / GT_M][v % GT_M] = gr[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int v = threadIdx.x + 256 * i;
+            Bs[v / GT_N][v % GT_N] = br[i];
+        }
+        __syncthreads();
+        if (sl + 1 < s_hi) load((sl + 1) * GT_K);
+#pragma unroll 8
+        for (int kk = 0; kk < GT_K; ++kk) {
+            const float4 g = *reinterpret_cast<const float4 *>(&Gs[kk][4 * ty]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][4 * tx]);
+            const float gg[4] = {g.x, g.y, g.z, g.w};
+            const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jx = 0; jx < 4; ++jx) acc[i][jx] = fmaf(gg[i], bb[jx], acc[i][jx]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + 4 * ty + i;
+        if (r >= a.M) continue;
+#pragma unroll
+        for (int jx = 0; jx < 4; ++jx) {
+            const int n = n0 + 4 * tx + jx;
+            if (n >= a.N) continue;
+            if (a.ksplit > 1) a.partial[((int64_t)ks * a.M + r) * a.N + n] = acc[i][jx];
+            else C[r * a.N + n] = acc[i][jx];
+        }
+    }
+}
+
 // C = (add ? C : 0) + sum over the splits, in split order (deterministic).
 __global__ void band_split_sum_kernel(const float *partial, int ksplit, int64_t MN, int add, float *C) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < MN; v += (int64_t)gridDim.x * blockDim.x) {
@@ -1240,6 +1360,145 @@ __global__ void band_points_kernel(const float *dinc, int64_t npaths, int64_t L,
         const float hi = p < L - 1 ? di[p * d] : 0.f;
         const float g = scale * (lo - hi);
         dpts[v] = add ? dpts[v] + g : g;
+    }
+}
+
+
+// Wt of every pair's (nx+1) x (ny+1) points (see the RBF chain rule above)
+// and its row and column sums.  Units are (pair, 128 x 32 point tile); a
+// block stages the tile's points channel-major (32 channels a pass) and the
+// 129 x 33 values of dk/dc around it from the band layout; thread t owns
+// points rows 4 (t/8) .. +3 and columns 4 (t%8) .. +3 of the tile.
+struct RbfWtArgs {
+    PairSrc src;             // oriented: rows refine A
+    const float *gband;      // dk/dc in the band layout (TperR1 slots per pair)
+    float *wt;               // Gram: [row path ia][i] x [column path jb][j], ld = ldw; pairs: [k][i][j]
+    float *rsum, *csum;      // sums over j / over i (zeroed before)
+    int64_t n_pairs, ldw, a0;
+    int TperR1, vrows, NQV, tiles_i, tiles_j;
+    float s, scale;          // 1/(2 sigma^2), 1/2 4^-lambda
+};
+constexpr int RW_TI = 128, RW_TJ = 32, RW_CH = 32;
+
+template <int NG>
+__global__ void __launch_bounds__(256) rbf_wt_kernel(RbfWtArgs a) {
+    __shared__ float xs[RW_CH][RW_TI];
+    __shared__ float ys[RW_CH][RW_TJ + 1];
+    __shared__ float gs[RW_TI + 1][RW_TJ + 2];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int r = (tid >> 3) * 4, c0 = (tid & 7) * 4;
+    const int64_t d = a.src.d;
+    const bool gram = a.src.mode != PM_PAIRS;
+    const int per = a.tiles_i * a.tiles_j;
+    for (int64_t u = blockIdx.x; u < a.n_pairs * per; u += gridDim.x) {
+        const int64_t k = u / per;
+        const int t = (int)(u - k * per);
+        const int i0 = (t / a.tiles_j) * RW_TI, j0 = (t % a.tiles_j) * RW_TJ;
+        const PairRef pr = pair_ref(a.src, k);
+        const int nx = (int)pr.la - 1, ny = (int)pr.lb - 1;   // coarse rows / columns; nx + 1 points
+        if (i0 > nx || j0 > ny) continue;   // block-uniform
+        const float *xp = (const float *)a.src.A + pr.a_row0 * d;
+        const float *yp = (const float *)a.src.B + pr.b_row0 * d;
+        __syncthreads();
+        // dk/dc at (p, q) = (i0 - 1 + pi, j0 - 1 + qj), zero outside the grid
+        for (int v = tid; v < (RW_TI + 1) * (RW_TJ + 1); v += 256) {
+            const int pi = v / (RW_TJ + 1), qj = v - pi * (RW_TJ + 1);
+            const int pp = i0 - 1 + pi, qq = j0 - 1 + qj;
+            float gv = 0.f;
+            if (pp >= 0 && pp < nx && qq >= 0 && qq < ny) {
+                const int P = pp + a.vrows, Q = qq + a.NQV;
+                const int l = P / NG, g = P % NG, tq = Q + g;
+                gv = a.gband[((k * a.TperR1 + tq / NG) * 32 + l) * (int64_t)(NG * NG) + (tq % NG) * NG +
+                             band_gpos<NG>(g)];
+            }
+            gs[pi][qj] = gv;
+        }
+        float uu[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) uu[i][j] = 0.f;
+        for (int64_t cb = 0; cb < d; cb += RW_CH) {
+            const int nc = d - cb < RW_CH ? (int)(d - cb) : RW_CH;
+            __syncthreads();
+            for (int v = tid; v < nc * RW_TI; v += 256) {
+                const int i = v / nc, c = v - i * nc;
+                xs[c][i] = i0 + i <= nx ? xp[(int64_t)(i0 + i) * d + cb + c] : 0.f;
+            }
+            for (int v = tid; v < nc * RW_TJ; v += 256) {
+                const int j = v / nc, c = v - j * nc;
+                ys[c][j] = j0 + j <= ny ? yp[(int64_t)(j0 + j) * d + cb + c] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int c = 0; c < nc; ++c) {
+                float xv[4], yv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xv[i] = xs[c][r + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) yv[j] = ys[c][c0 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float e = xv[i] - yv[j];
+                        uu[i][j] = fmaf(e, e, uu[i][j]);
+                    }
+            }
+        }
+        float rs[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
+        const int64_t ia = gram ? pr.a_row0 / pr.la - a.a0 : k;
+        const int64_t jb = gram ? pr.b_row0 / pr.lb : k;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int pi = r + i, ii = i0 + pi;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int qj = c0 + j, jj = j0 + qj;
+                if (ii > nx || jj > ny) continue;
+                const float W = gs[pi][qj] - gs[pi][qj + 1] - gs[pi + 1][qj] + gs[pi + 1][qj + 1];
+                const float wt = a.scale * W * __expf(-a.s * uu[i][j]);
+                if (gram) a.wt[(ia * (nx + 1) + ii) * a.ldw + jb * (ny + 1) + jj] = wt;
+                else a.wt[(k * (nx + 1) + ii) * (int64_t)(ny + 1) + jj] = wt;
+                rs[i] += wt;
+                cs[j] += wt;
+            }
+        }
+        // row sums over the 8 threads of a row group, column sums over the
+        // 4 row groups of the warp; then one atomic add per value
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            rs[i] += __shfl_xor_sync(FULL, rs[i], 1);
+            rs[i] += __shfl_xor_sync(FULL, rs[i], 2);
+            rs[i] += __shfl_xor_sync(FULL, rs[i], 4);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cs[j] += __shfl_xor_sync(FULL, cs[j], 8);
+            cs[j] += __shfl_xor_sync(FULL, cs[j], 16);
+        }
+        if ((lane & 7) == 0)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (i0 + r + i <= nx) atomicAdd(a.rsum + ia * (nx + 1) + i0 + r + i, rs[i]);
+        if (lane < 8)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j0 + c0 + j <= ny) atomicAdd(a.csum + jb * (ny + 1) + j0 + c0 + j, cs[j]);
+    }
+}
+
+// out[v] = (add ? out[v] : 0) + f (C1[v] - s1[row] P[v] (+ C2[v] - s2[row] P[v])),
+// v = row d + channel: the points' gradients from the contraction and the
+// sums (C2, s2: the column role of a symmetric Gram's same paths)
+__global__ void rbf_points_kernel(const float *P, int64_t rows, int64_t d, const float *C1, const float *s1,
+                                  const float *C2, const float *s2, float f, int add, float *out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < rows * d;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = v / d;
+        float g = C1[v] - s1[row] * P[v];
+        if (C2) g += C2[v] - s2[row] * P[v];
+        out[v] = add ? out[v] + f * g : f * g;
     }
 }
 
@@ -1464,15 +1723,17 @@ int64_t up4(int64_t v) { return (v + 3) / 4 * 4; }
 // for any pairs-per-warp split (they are checked against the actual split at
 // launch).
 struct BwdRegions {
-    int64_t band, gbar, ckpt, exitk, botq, incA, incB, dincA, dincB, part, gband;
-    int64_t total() const { return band + gbar + ckpt + exitk + botq + incA + incB + dincA + dincB + part + gband; }
+    int64_t band, gbar, ckpt, exitk, botq, incA, incB, dincA, dincB, part, gband, rsum;
+    int64_t total() const {
+        return band + gbar + ckpt + exitk + botq + incA + incB + dincA + dincB + part + gband + rsum;
+    }
 };
 
 // dense: whether a Gram's dk/dc is unpacked into a dense matrix for the
 // tensor-core contraction (coef_path 3); the FP32 contraction reads the band
 bool bwd_dense_gbar(const PairSrc &src, int coef_path) {
     const bool gram = src.mode == PM_GRAM || src.mode == PM_GRAM_SYM;
-    return gram && coef_path == 3 && chain_gemm_tc5_ok(1, 1, (int)src.d);
+    return gram && src.kernel == SIGK_KERNEL_LINEAR && coef_path == 3 && chain_gemm_tc5_ok(1, 1, (int)src.d);
 }
 
 BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp, int coef_path) {
@@ -1493,6 +1754,19 @@ BwdRegions bwd_regions(const PairSrc &src, const BandPlan &p, int64_t nbp, int c
     r.dincB = r.incB;
     // split-K partial tiles of the Gram's contractions
     r.part = gram ? up4((int64_t)GEMM_MAX_SPLIT * (nA * nx > nB * ny ? nA * nx : nB * ny) * d) : 0;
+    r.rsum = 0;
+    if (src.kernel == SIGK_KERNEL_RBF) {
+        // the lift works on points: Wt of every pair (dense, in gbar), the
+        // contractions' results (dinc), the row and column sums; no increments
+        const int64_t px = nx + 1, py = ny + 1;
+        r.gbar = up4(nA * px * nB * py);
+        if (!gram) r.gbar = up4(nbp * px * py);
+        r.incA = r.incB = 0;
+        r.dincA = up4(nA * px * d);
+        r.dincB = up4(nB * py * d);
+        r.part = gram ? up4((int64_t)GEMM_MAX_SPLIT * (nA * px > nB * py ? nA * px : nB * py) * d) : 0;
+        r.rsum = up4(nA * px) + up4(nB * py);
+    }
     // the adjoint's dk/dc in the band layout: TperR + 1 slots per pair
     r.gband = up4(nbp * ((int64_t)p.TperR + 1) * 32 * p.NG * p.NG);
     return r;
@@ -1517,6 +1791,113 @@ int64_t band_bwd_batch(const PairSrc &src, const BandPlan &p, int64_t n, int64_t
         bytes = bwd_regions(src, p, nb, coef_path).total() * (int64_t)sizeof(float);
     }
     return nb;
+}
+
+// The RBF lift's chain rule for one launch of the band backward (pairs
+// kbase .. kbase + m of the oriented src; Gram: row paths a0 .. a0 + nA
+// against all nB column paths): Wt and its sums, the dense contractions
+// CX = Wt Y and CY = Wt^T X, then the points' gradients.  dA is overwritten
+// (or added to: add); dB likewise on the first launch and added to after.
+cudaError_t rbf_chain_rule(const PairSrc &src, const BandPlan &p, int64_t m, int64_t a0, int64_t nA, int64_t nB,
+                           int64_t kb, const float *gband, float *wt, float *CX, float *CY, float *rsum,
+                           float *part, float *dA, float *dB, bool add, int sms, cudaStream_t st) {
+    const bool sym = src.mode == PM_GRAM_SYM;
+    const bool gram = src.mode == PM_GRAM || sym;
+    const int64_t d = src.d, px = src.La, py = src.Lb;   // points per path
+    const int64_t nrow = gram ? nA : m, ncol = gram ? nB : m;
+    float *csum = rsum + up4(nrow * px);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(rsum, 0, sizeof(float) * (size_t)(up4(nrow * px) + ncol * py), st)) != cudaSuccess)
+        return e;
+    // a symmetric Gram stores pairs i <= j: the blocks below the diagonal stay zero
+    if (sym && (e = cudaMemsetAsync(wt, 0, sizeof(float) * (size_t)(nA * px * nB * py), st)) != cudaSuccess)
+        return e;
+    RbfWtArgs w;
+    w.src = src;
+    w.gband = gband;
+    w.wt = wt;
+    w.rsum = rsum;
+    w.csum = csum;
+    w.n_pairs = m;
+    w.ldw = gram ? nB * py : py;
+    w.a0 = a0;
+    w.TperR1 = p.TperR + 1;
+    w.vrows = p.vrows;
+    w.NQV = p.NQV;
+    w.tiles_i = (int)((px + RW_TI - 1) / RW_TI);
+    w.tiles_j = (int)((py + RW_TJ - 1) / RW_TJ);
+    w.s = (float)(0.5 / (src.sigma * src.sigma));
+    w.scale = 0.5f / (float)(1 << (2 * p.lam));
+    int64_t grid = m * w.tiles_i * w.tiles_j;
+    if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+    if (p.NG == 8) rbf_wt_kernel<8><<<(int)grid, 256, 0, st>>>(w);
+    else if (p.NG == 4) rbf_wt_kernel<4><<<(int)grid, 256, 0, st>>>(w);
+    else rbf_wt_kernel<2><<<(int)grid, 256, 0, st>>>(w);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the contractions
+    const float *Apts = (const float *)src.A + (gram ? a0 : src.kbase) * px * d;
+    const float *Bpts = sym ? (const float *)src.A : (const float *)src.B + (gram ? 0 : src.kbase) * py * d;
+    DenseGemmArgs g1;
+    memset(&g1, 0, sizeof(g1));
+    g1.G = wt;
+    g1.N = (int)d;
+    DenseGemmArgs g2 = g1;
+    g1.Bm = Bpts;
+    g1.C = CX;
+    g1.trans = 0;
+    g2.Bm = Apts;
+    g2.C = CY;
+    g2.trans = 1;
+    int64_t batches = 1;
+    if (gram) {
+        g1.g_ld = g2.g_ld = nB * py;
+        g1.M = nA * px; g1.K = nB * py;
+        g2.M = nB * py; g2.K = nA * px;
+        g1.tri_rb = g2.tri_rb = sym ? px : 0;
+        g1.tri_cb = g2.tri_cb = sym ? py : 0;
+    } else {
+        batches = m;
+        g1.g_ld = g2.g_ld = py;
+        g1.g_bstride = g2.g_bstride = px * py;
+        g1.b_bstride = py * d; g2.b_bstride = px * d;
+        g1.c_bstride = px * d; g2.c_bstride = py * d;
+        g1.M = px; g1.K = py;
+        g2.M = py; g2.K = px;
+    }
+    auto split = [&](const DenseGemmArgs &g) {
+        if (!gram) return 1;
+        const int64_t tiles = ((g.M + GT_M - 1) / GT_M) * ((d + GT_N - 1) / GT_N);
+        int64_t ksp = (4 * (int64_t)sms + tiles - 1) / tiles;
+        const int64_t nsl = (g.K + GT_K - 1) / GT_K;
+        if (ksp > nsl / 4) ksp = nsl / 4;
+        if (ksp > GEMM_MAX_SPLIT) ksp = GEMM_MAX_SPLIT;
+        return (int)(ksp < 1 ? 1 : ksp);
+    };
+    g1.ksplit = split(g1);
+    g2.ksplit = split(g2);
+    g1.partial = g2.partial = part;
+    const bool want_b = dB || sym;
+    for (int pass = 0; pass < (want_b ? 2 : 1); ++pass) {
+        const DenseGemmArgs &g = pass == 0 ? g1 : g2;
+        const dim3 gd((unsigned)((g.M + GT_M - 1) / GT_M), (unsigned)((d + GT_N - 1) / GT_N),
+                      (unsigned)(batches * g.ksplit));
+        dense_gemm_kernel<<<gd, 256, 0, st>>>(g);
+        if (g.ksplit > 1) band_split_sum_kernel<<<sms * 4, 256, 0, st>>>(part, g.ksplit, g.M * d, 0, g.C);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // the points
+    const float f = (float)(1.0 / (src.sigma * src.sigma));
+    if (dA) {
+        float *out = dA + (gram ? a0 : src.kbase) * px * d;
+        rbf_points_kernel<<<sms * 4, 256, 0, st>>>(Apts, nrow * px, d, CX, rsum, sym ? CY : nullptr,
+                                                   sym ? csum : nullptr, f, add ? 1 : 0, out);
+    }
+    if (dB && !sym) {
+        float *out = dB + (gram ? 0 : src.kbase) * py * d;
+        rbf_points_kernel<<<sms * 4, 256, 0, st>>>(Bpts, ncol * py, d, CY, csum, nullptr, nullptr, f,
+                                                   (add || (gram && kb > 0)) ? 1 : 0, out);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t n, int64_t nbp,
@@ -1551,8 +1932,10 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
     float *dincB = dincA + rg.dincA;
     float *part = dincB + rg.dincB;
     float *gband = part + rg.part;
+    float *rsum = gband + rg.gband;   // the RBF lift's row sums, then its column sums
+    const bool rbf = src0.kernel == SIGK_KERNEL_RBF;
     const int64_t nBall = gram ? src0.nb : 0;
-    if (gram) {
+    if (gram && !rbf) {
         // every column path is used by every launch: increments once, gradients summed
         band_inc_kernel<<<sms * 4, 256, 0, st>>>((const float *)src0.B, nBall, src0.Lb, d, incB);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1632,6 +2015,13 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
         SIGK_BAND_CASES(X)
 #undef X
         if (!launched) return cudaErrorInvalidValue;
+        if (rbf) {
+            // the RBF lift: the chain rule through kappa over the points
+            if ((e = rbf_chain_rule(src, p, m, a0, nA, nBall, kb, gband, gbar, dincA, dincB, rsum, part, dA, dB,
+                                    add, sms, st)) != cudaSuccess)
+                return e;
+            continue;
+        }
         // a Gram's contractions on the tensor cores (split-TF32) with the
         // tcgen05 path (coef_path 3), else on the FP32 pipe.  The tensor-core
         // contraction matches the FP32 one's accuracy but measured slower on
@@ -1785,7 +2175,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
                                                       dB + src.kbase * src.Lb * d);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (dB && gram) {
+    if (dB && gram && !rbf) {
         band_points_kernel<<<sms * 4, 256, 0, st>>>(dincB, nBall, src0.Lb, d, scale, add, dB);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -239,12 +239,17 @@ def test_rbf_pairs_and_varlen_match_oracle():
         assert rel_err(got, ref) <= F32_TOL
 
 
-@pytest.mark.parametrize("dtype,scheme", [(torch.float32, "explicit"), (torch.float32, "implicit"),
-                                          (torch.float64, "explicit")])
-def test_rbf_backward_matches_oracle(dtype, scheme):
-    """The RBF lift's gradient (the plain backward: adjoint sweep, then the
-    chain rule through the second difference of kappa)."""
+@pytest.mark.parametrize("dtype,scheme,rec", [(torch.float32, "explicit", "plain"),
+                                              (torch.float32, "implicit", "plain"),
+                                              (torch.float32, "explicit", "band"),
+                                              (torch.float32, "implicit", "band"),
+                                              (torch.float64, "explicit", "plain")])
+def test_rbf_backward_matches_oracle(dtype, scheme, rec):
+    """The RBF lift's gradient: the adjoint sweep (one block per pair, or the
+    band form's chained reverse sweep), then the chain rule through the second
+    difference of kappa over the points."""
     sigk = S()
+    rec = sigk.REC_PLAIN if rec == "plain" else sigk.REC_BAND
     lam, d, L, M, sigma = 1, 7, 50, 40, 0.8
     Bx, By = 4, 3
     X32, X64 = inputs.f32(inputs.random_paths(6700, Bx, L, d, time_channel=True))
@@ -255,13 +260,13 @@ def test_rbf_backward_matches_oracle(dtype, scheme):
     Xd = to_dev(X32 if dtype == torch.float32 else X64, dtype)
     Yd = to_dev(Y32 if dtype == torch.float32 else Y64, dtype)
     v = rbf(sigma, scheme)
-    dX, dY = sigk.gram_backward(to_dev(gout, dtype), Xd, Yd, lam, variant=v)
+    dX, dY = sigk.gram_backward(to_dev(gout, dtype), Xd, Yd, lam, variant=v, rec=rec)
     tol = GRAD_TOL if dtype == torch.float32 else 1e-10
     assert grad_err(dX.cpu(), rX) <= tol
     assert grad_err(dY.cpu(), rY) <= tol
     g = np.random.default_rng(68).normal(size=3)
     pX, pY = oracle.pairs_grad(X64[:3], Y64, lam, g, **kw)
-    dXp, dYp = sigk.pairs_backward(to_dev(g, dtype), Xd[:3], Yd, lam, variant=v)
+    dXp, dYp = sigk.pairs_backward(to_dev(g, dtype), Xd[:3], Yd, lam, variant=v, rec=rec)
     assert grad_err(dXp.cpu(), pX) <= tol
     assert grad_err(dYp.cpu(), pY) <= tol
 
@@ -297,9 +302,60 @@ def test_rbf_unsupported_combinations():
     with pytest.raises(sigk.SigkError) as ei:   # no tensor-core path for the lift
         sigk.gram(X, X, 1, schedule=sigk.Schedule(sigk.REC_STRIP, 0, sigk.COEF_TC), variant=v)
     assert ei.value.status == sigk.SIGK_EUNSUPPORTED
-    with pytest.raises(sigk.SigkError) as ei:   # its gradient runs on the plain backward only
+    with pytest.raises(sigk.SigkError) as ei:   # no strip backward for the lift
         sigk.gram_backward(torch.ones(3, 3, device="cuda"), X, X, 1, rec=sigk.REC_STRIP, variant=v)
     assert ei.value.status == sigk.SIGK_EUNSUPPORTED
-    with pytest.raises(sigk.SigkError) as ei:
-        sigk.gram_backward(torch.ones(3, 3, device="cuda"), X, X, 1, symmetric=True, variant=v)
+    Xl = to_dev(inputs.random_paths(6901, 3, 600, 4, time_channel=True))
+    with pytest.raises(sigk.SigkError) as ei:   # the symmetric backward needs the band form
+        sigk.gram_backward(torch.ones(3, 3, device="cuda"), Xl, Xl, 1, symmetric=True, variant=v)
     assert ei.value.status == sigk.SIGK_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("lam,L,d,sigma", [(1, 60, 6, 0.9), (0, 130, 33, 1.7), (2, 33, 3, 0.6)])
+def test_rbf_symmetric_gram_backward_in_the_band_form(lam, L, d, sigma):
+    """The symmetric Gram's backward with the lift (pairs i <= j, the
+    derivative through both arguments), against the oracle's gradient of the
+    full Gram through both arguments; and autograd through the symmetric
+    forward."""
+    sigk = S()
+    B = 6
+    X32, X64 = inputs.f32(inputs.random_paths(6950 + L, B, L, d, time_channel=True))
+    gout = np.random.default_rng(6951).normal(size=(B, B))
+    kw = dict(static_kernel="rbf", sigma=sigma)
+    rX, rY = oracle.gram_grad(X64, X64, lam, gout, **kw)
+    v = rbf(sigma)
+    dX, none = sigk.gram_backward(to_dev(gout), to_dev(X32), to_dev(X32), lam, symmetric=True, variant=v)
+    assert none is None
+    assert grad_err(dX.cpu(), rX + rY) <= GRAD_TOL
+    X = to_dev(X32).requires_grad_(True)
+    K = sigk.SigKernelGram.apply(X, X, lam, v)
+    K.backward(to_dev(gout))
+    assert grad_err(X.grad.cpu(), rX + rY) <= GRAD_TOL
+
+
+def test_rbf_mmd_loss_in_the_band_form():
+    """The lifted MMD^2 loss of 8 vs 8 paths (L = 96, d = 12, drift), whose
+    fused value-and-gradient calls run the band backward: value and dL/dX
+    against the oracle."""
+    sigk = S()
+    lam, sigma = 1, 1.3
+    w = inputs.mmd_batches(B=8, L=96, d=12)
+    X32, X64 = inputs.f32(w["X"])
+    Y32, Y64 = inputs.f32(w["Y"])
+    v = rbf(sigma)
+    X = to_dev(X32).requires_grad_(True)
+    loss = sigk.mmd2_loss(X, to_dev(Y32), lam, variant=v)
+    kw = dict(static_kernel="rbf", sigma=sigma)
+    m = 8
+    Kxx = oracle.gram(X64, X64, lam, **kw)
+    Kyy = oracle.gram(Y64, Y64, lam, **kw)
+    Kxy = oracle.gram(X64, Y64, lam, **kw)
+    want = ((Kxx.sum() - np.trace(Kxx)) / (m * (m - 1)) + (Kyy.sum() - np.trace(Kyy)) / (m * (m - 1))
+            - 2 * Kxy.sum() / (m * m))
+    assert abs(float(loss.detach()) - want) <= 1e-5 * max(1.0, abs(want))
+    loss.backward()
+    gxx = np.full((m, m), 1.0 / (m * (m - 1)))
+    np.fill_diagonal(gxx, 0.0)
+    a, b = oracle.gram_grad(X64, X64, lam, gxx, **kw)
+    c, _ = oracle.gram_grad(X64, Y64, lam, np.full((m, m), -2.0 / (m * m)), want_dy=False, **kw)
+    assert grad_err(X.grad.cpu(), a + b + c) <= GRAD_TOL
