@@ -978,8 +978,8 @@ def measure_workload(name, args, cache=None, with_e2e=False, with_clocks=True):
 # the configurations of the workload statement besides the headline Gram
 # (configs 1, 3, 4, 5; config 5 in FP32 and FP64 at both dyadic orders, and
 # its backward at dyadic order 1)
-DEFAULT_WORKLOADS = ["gram_small_f64", "gram_small_f32", "uneven4096", "mmd128", "long64_l0", "long64_l1",
-                     "long64_l0_f64", "long64_l1_f64", "long64_l1_grad"]
+DEFAULT_WORKLOADS = ["gram_small_f64", "gram_small_f32", "uneven4096", "mmd128", "mmd128_rbf", "long64_l0",
+                     "long64_l1", "long64_l0_f64", "long64_l1_f64", "long64_l1_grad"]
 
 
 def run_workloads(args):
@@ -1032,7 +1032,7 @@ def main():
                     help="uneven4096 / long64 / mmd128 / gram256_*: only the first BATCH pairs / paths per batch "
                          "(profiling)")
     ap.add_argument("--workload", default="gram256",
-                    choices=["gram256"] + DEFAULT_WORKLOADS + ["gram256_implicit", "gram256_rbf", "mmd128_rbf",
+                    choices=["gram256"] + DEFAULT_WORKLOADS + ["gram256_implicit", "gram256_rbf",
                                                                "surface256", "support_fbm30"])
     args = ap.parse_args()
     if args.warmup < 3:
