@@ -1382,8 +1382,14 @@ constexpr int RW_TI = 128, RW_TJ = 32, RW_CH = 32;
 
 template <int NG>
 __global__ void __launch_bounds__(256) rbf_wt_kernel(RbfWtArgs a) {
-    __shared__ float xs[RW_CH][RW_TI];
-    __shared__ float ys[RW_CH][RW_TJ + 1];
+    constexpr int SLOT = NG * NG;
+    // the band slots around a tile: lanes (rows) and positions (columns)
+    constexpr int SL = RW_TI / NG + 1 < 32 ? RW_TI / NG + 1 : 32, SP = RW_TJ / NG + 2;
+    // the points (channel loop) and the staged slots (before it) share memory
+    constexpr int PTS = RW_CH * RW_TI + RW_CH * (RW_TJ + 1), STG = SL * SP * SLOT;
+    __shared__ __align__(16) float pool[PTS > STG ? PTS : STG];
+    float (*xs)[RW_TI] = reinterpret_cast<float (*)[RW_TI]>(pool);
+    float (*ys)[RW_TJ + 1] = reinterpret_cast<float (*)[RW_TJ + 1]>(pool + RW_CH * RW_TI);
     __shared__ float gs[RW_TI + 1][RW_TJ + 2];
     const int tid = threadIdx.x, lane = tid & 31;
     const int r = (tid >> 3) * 4, c0 = (tid & 7) * 4;
@@ -1400,7 +1406,22 @@ __global__ void __launch_bounds__(256) rbf_wt_kernel(RbfWtArgs a) {
         const float *xp = (const float *)a.src.A + pr.a_row0 * d;
         const float *yp = (const float *)a.src.B + pr.b_row0 * d;
         __syncthreads();
-        // dk/dc at (p, q) = (i0 - 1 + pi, j0 - 1 + qj), zero outside the grid
+        // the slots holding dk/dc at (p, q) = (i0 - 1 + pi, j0 - 1 + qj): lanes
+        // from l0, positions from s0 (for a position, the lanes are one
+        // contiguous run), staged with 16-byte loads; then the tile, zero
+        // outside the grid
+        const int Pf = i0 - 1 + a.vrows, Qf = j0 - 1 + a.NQV;
+        const int l0 = (Pf < 0 ? 0 : Pf) / NG, s0 = (Qf < 0 ? 0 : Qf) / NG;
+        for (int v = tid; v < STG / 4; v += 256) {
+            const int sl = v / (SLOT / 4), e = v - sl * (SLOT / 4);
+            const int pr = sl / SL, lr = sl - pr * SL;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (l0 + lr < 32 && s0 + pr < a.TperR1)
+                x = __ldg(reinterpret_cast<const float4 *>(a.gband + ((k * a.TperR1 + s0 + pr) * 32 + l0 + lr) *
+                                                                        (int64_t)SLOT) + e);
+            reinterpret_cast<float4 *>(pool)[v] = x;
+        }
+        __syncthreads();
         for (int v = tid; v < (RW_TI + 1) * (RW_TJ + 1); v += 256) {
             const int pi = v / (RW_TJ + 1), qj = v - pi * (RW_TJ + 1);
             const int pp = i0 - 1 + pi, qq = j0 - 1 + qj;
@@ -1408,25 +1429,32 @@ __global__ void __launch_bounds__(256) rbf_wt_kernel(RbfWtArgs a) {
             if (pp >= 0 && pp < nx && qq >= 0 && qq < ny) {
                 const int P = pp + a.vrows, Q = qq + a.NQV;
                 const int l = P / NG, g = P % NG, tq = Q + g;
-                gv = a.gband[((k * a.TperR1 + tq / NG) * 32 + l) * (int64_t)(NG * NG) + (tq % NG) * NG +
-                             band_gpos<NG>(g)];
+                gv = pool[((tq / NG - s0) * SL + l - l0) * SLOT + (tq % NG) * NG + band_gpos<NG>(g)];
             }
             gs[pi][qj] = gv;
         }
-        float uu[4][4];
+        // |x_i - y_j|^2 = |x_i|^2 + |y_j|^2 - 2 <x_i, y_j>: one FMA a pair and
+        // channel (only kappa itself is needed here, so the cancellation near
+        // x_i = y_j costs an absolute error of about FP32 epsilon times |x|^2)
+        float xy[4][4], xx[4], yy[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i) {
+            xx[i] = 0.f;
+            yy[i] = 0.f;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) uu[i][j] = 0.f;
+            for (int j = 0; j < 4; ++j) xy[i][j] = 0.f;
+        }
         for (int64_t cb = 0; cb < d; cb += RW_CH) {
             const int nc = d - cb < RW_CH ? (int)(d - cb) : RW_CH;
             __syncthreads();
+            // consecutive threads take consecutive channels of a point (the
+            // full-width passes without a division)
             for (int v = tid; v < nc * RW_TI; v += 256) {
-                const int i = v / nc, c = v - i * nc;
+                const int i = nc == RW_CH ? v >> 5 : v / nc, c = nc == RW_CH ? v & 31 : v - i * nc;
                 xs[c][i] = i0 + i <= nx ? xp[(int64_t)(i0 + i) * d + cb + c] : 0.f;
             }
             for (int v = tid; v < nc * RW_TJ; v += 256) {
-                const int j = v / nc, c = v - j * nc;
+                const int j = nc == RW_CH ? v >> 5 : v / nc, c = nc == RW_CH ? v & 31 : v - j * nc;
                 ys[c][j] = j0 + j <= ny ? yp[(int64_t)(j0 + j) * d + cb + c] : 0.f;
             }
             __syncthreads();
@@ -1438,30 +1466,43 @@ __global__ void __launch_bounds__(256) rbf_wt_kernel(RbfWtArgs a) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) yv[j] = ys[c][c0 + j];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) yy[j] = fmaf(yv[j], yv[j], yy[j]);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float e = xv[i] - yv[j];
-                        uu[i][j] = fmaf(e, e, uu[i][j]);
-                    }
+                for (int i = 0; i < 4; ++i) {
+                    xx[i] = fmaf(xv[i], xv[i], xx[i]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) xy[i][j] = fmaf(xv[i], yv[j], xy[i][j]);
+                }
             }
         }
         float rs[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
         const int64_t ia = gram ? pr.a_row0 / pr.la - a.a0 : k;
         const int64_t jb = gram ? pr.b_row0 / pr.lb : k;
+        // a row's four columns leave as one 16-byte store where the rows are
+        // 16-byte aligned and all four are real
+        const bool vec = ((ny + 1) & 3) == 0 && j0 + c0 + 3 <= ny;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int pi = r + i, ii = i0 + pi;
+            if (ii > nx) continue;
+            float wv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int qj = c0 + j, jj = j0 + qj;
-                if (ii > nx || jj > ny) continue;
+                const int qj = c0 + j;
                 const float W = gs[pi][qj] - gs[pi][qj + 1] - gs[pi + 1][qj] + gs[pi + 1][qj + 1];
-                const float wt = a.scale * W * __expf(-a.s * uu[i][j]);
-                if (gram) a.wt[(ia * (nx + 1) + ii) * a.ldw + jb * (ny + 1) + jj] = wt;
-                else a.wt[(k * (nx + 1) + ii) * (int64_t)(ny + 1) + jj] = wt;
-                rs[i] += wt;
-                cs[j] += wt;
+                const float uu = fmaxf(xx[i] + yy[j] - 2.f * xy[i][j], 0.f);
+                wv[j] = j0 + qj <= ny ? a.scale * W * __expf(-a.s * uu) : 0.f;
+                rs[i] += wv[j];
+                cs[j] += wv[j];
+            }
+            float *row = gram ? a.wt + (ia * (nx + 1) + ii) * a.ldw + jb * (ny + 1)
+                              : a.wt + (k * (nx + 1) + ii) * (int64_t)(ny + 1);
+            if (vec) {
+                *reinterpret_cast<float4 *>(row + j0 + c0) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j0 + c0 + j <= ny) row[j0 + c0 + j] = wv[j];
             }
         }
         // row sums over the 8 threads of a row group, column sums over the
