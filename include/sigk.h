@@ -267,8 +267,7 @@ int sigk_gram_value_and_grad(const void *grad_out, const void *X, const void *Y,
  * exceeds the array.  The first call on each device looks the array's device
  * address up (cudaGetSymbolAddress, with that device current) and keeps it
  * for that device's context; the first call after the context was reset
- * (cudaDeviceReset) looks it up again.  Make that first call before any
- * stream capture.  All calls share the array:
+ * (cudaDeviceReset) looks it up again.  All calls share the array:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller.  No state carries over between calls. */
 int sigk_pairs_backward_noalloc(const void *grad_out, const void *X, const void *Y, int64_t B,
