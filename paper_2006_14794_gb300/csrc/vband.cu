@@ -603,6 +603,131 @@ cudaError_t vb_launch_sweep(const VbArgs &a, int cls, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// The same slots with a thread on WQ windows x 2 HB groups, the HB group
+// pairs (h, h + NG/2) for h = h0 .. h0 + HB - 1: per channel 2 HB of its
+// lane's row increments (two 16-byte loads) and WQ + NG/2 + HB - 1 column
+// increments (a broadcast) for 2 HB WQ products, half the lane-distinct
+// shared-memory reads a product of vb_coef_kernel's NG = 16 instance; and a
+// window row's pairs are 2 HB consecutive floats of the slot.
+template <int NG, int WQ, int HB>
+__global__ void __launch_bounds__(VB_CT) vb_coef_pair_kernel(VbArgs a, int cls, int dc) {
+    extern __shared__ __align__(16) float vcs[];
+    constexpr int NPP = 32 * NG, XL = vb_lane_stride(NG), XS = vb_xstride<NG>(), SLOT = NG * NG;
+    constexpr int NH = NG / 2, NHB = NH / HB, NQW = NG / WQ;
+    constexpr int YN = WQ + NH + HB - 1, YL = (YN + 3) / 4 * 4;
+    static_assert(NH % HB == 0 && HB % 4 == 0 && WQ % 4 == 0 && (NH - HB) % 4 == 0, "aligned vector loads");
+    const VbClassInfo ci = a.cinfo[cls];
+    const int64_t d = a.src.d;
+    float *dxs = vcs;
+    float *dys = vcs + dc * XS;
+    for (int t = blockIdx.x; t < ci.count; t += gridDim.x) {
+        const int pid = a.order[ci.start + t];
+        const VbPair p = a.plan[pid];
+        const float *rows = (const float *)(p.swapped ? a.src.B : a.src.A) + p.r_row0 * d;
+        const float *cols = (const float *)(p.swapped ? a.src.A : a.src.B) + p.c_row0 * d;
+        const int nx = p.lr - 1, ny = p.lc - 1, T = p.T, NQ = T * NG;
+        const int YS = vb_ystride(T, NG);
+        const int nthr = 32 * (T + 1) * NQW * NHB;
+        for (int b0 = 0; b0 < nthr; b0 += VB_CT) {
+            const int u = b0 + (int)threadIdx.x;
+            const int l = u & 31, pq = u >> 5;
+            const int hb = pq % NHB, pq2 = pq / NHB;
+            const int pos = pq2 / NQW, w0 = (pq2 - pos * NQW) * WQ, h0 = hb * HB;
+            float acc[WQ][2 * HB];   // [w][2k]: group h0 + k, [w][2k + 1]: group h0 + k + NH
+#pragma unroll
+            for (int w = 0; w < WQ; ++w)
+#pragma unroll
+                for (int k = 0; k < 2 * HB; ++k) acc[w][k] = 0.f;
+            for (int64_t c0 = 0; c0 < d; c0 += dc) {
+                if (d > dc || b0 == 0) {
+                    __syncthreads();
+                    const int dq = dc / 4;
+                    for (int v = threadIdx.x; v < dq * NPP; v += VB_CT) {
+                        const int P = v / dq, c = 4 * (v - (v / dq) * dq);
+                        const int pr = P - p.vrows;
+                        float e[4] = {0.f, 0.f, 0.f, 0.f};
+                        if (pr >= 0 && pr < nx) vb_inc4(e, rows + (int64_t)pr * d, d, c0 + c);
+                        float *o = dxs + c * XS + (P / NG) * XL + P % NG;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) o[k * XS] = e[k];
+                    }
+                    for (int v = threadIdx.x; v < dq * YS; v += VB_CT) {
+                        const int iq = v / dq, c = 4 * (v - (v / dq) * dq);
+                        const int q = iq - (NG - 1) - p.nqv;   // real column
+                        float e[4] = {0.f, 0.f, 0.f, 0.f};
+                        if (q >= 0 && q < ny && iq - (NG - 1) < NQ) vb_inc4(e, cols + (int64_t)q * d, d, c0 + c);
+                        float *o = dys + c * YS + iq;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) o[k * YS] = e[k];
+                    }
+                    __syncthreads();
+                }
+                if (u < nthr) {
+                    const int cn = (int)(d - c0 < dc ? d - c0 : dc);
+#pragma unroll 2
+                    for (int c = 0; c < cn; ++c) {
+                        float xa[HB], xb[HB], yv[YL];
+                        vb_lds<HB>(xa, dxs + c * XS + l * XL + h0);
+                        vb_lds<HB>(xb, dxs + c * XS + l * XL + h0 + NH);
+                        // column index Q + NG - 1 = pos NG + w - g, from jb = w0 - h0 + NH - HB
+                        vb_lds<YL>(yv, dys + c * YS + pos * NG + w0 - h0 + NH - HB);
+#pragma unroll
+                        for (int w = 0; w < WQ; ++w)
+#pragma unroll
+                            for (int k = 0; k < HB; ++k) {
+                                acc[w][2 * k] = fmaf(xa[k], yv[w - k + NH - 1 + HB], acc[w][2 * k]);
+                                acc[w][2 * k + 1] = fmaf(xb[k], yv[w - k + HB - 1], acc[w][2 * k + 1]);
+                            }
+                    }
+                }
+            }
+            if (u >= nthr) continue;
+#pragma unroll
+            for (int w = 0; w < WQ; ++w)
+#pragma unroll
+                for (int k = 0; k < 2 * HB; ++k) acc[w][k] = scheme_coef(acc[w][k] * a.scale, a.src.scheme);
+            float *dst = a.band + p.base + ((int64_t)pos * 32 + l) * SLOT;   // pos = T: the next slot 0
+            if (pos > 0 && pos < T) {
+#pragma unroll
+                for (int w = 0; w < WQ; ++w)
+#pragma unroll
+                    for (int k = 0; k < 2 * HB; k += 4)
+                        *reinterpret_cast<float4 *>(dst + (w0 + w) * NG + 2 * h0 + k) =
+                            make_float4(acc[w][k], acc[w][k + 1], acc[w][k + 2], acc[w][k + 3]);
+                continue;
+            }
+#pragma unroll
+            for (int w = 0; w < WQ; ++w)
+#pragma unroll
+                for (int k = 0; k < 2 * HB; ++k) {
+                    const int g = (k & 1) ? h0 + (k >> 1) + NH : h0 + (k >> 1);
+                    const int ww = w0 + w;
+                    float *o = dst + ww * NG + 2 * h0 + k;   // vb_gpos(g)
+                    if (pos == 0) {
+                        if (ww >= g) *o = acc[w][k];
+                        else if (p.first) *o = 0.f;
+                    } else {
+                        if (ww < g) *o = acc[w][k];
+                        else if (p.last) *o = 0.f;
+                    }
+                }
+        }
+    }
+}
+
+template <int NG, int WQ, int HB>
+cudaError_t vb_launch_coef_pair(const VbArgs &a, int cls, int dc, int tmax, int sms, cudaStream_t st) {
+    auto kern = vb_coef_pair_kernel<NG, WQ, HB>;
+    const int smem = (int)sizeof(float) * dc * (vb_xstride<NG>() + vb_ystride(tmax, NG));
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, VB_CT, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    kern<<<sms * per_sm, VB_CT, smem, st>>>(a, cls, dc);
+    return cudaGetLastError();
+}
+
 template <int NG, int WQ>
 cudaError_t vb_launch_coef(const VbArgs &a, int cls, int dc, int tmax, int sms, cudaStream_t st) {
     auto kern = vb_coef_kernel<NG, WQ>;
@@ -621,7 +746,7 @@ cudaError_t vb_coef_of(const VbArgs &a, int cls, int NG, int dc, int tmax, int s
         case 2: return vb_launch_coef<2, 2>(a, cls, dc, tmax, sms, st);
         case 4: return vb_launch_coef<4, 4>(a, cls, dc, tmax, sms, st);
         case 8: return vb_launch_coef<8, 8>(a, cls, dc, tmax, sms, st);
-        case 16: return vb_launch_coef<16, 4>(a, cls, dc, tmax, sms, st);
+        case 16: return vb_launch_coef_pair<16, 8, 4>(a, cls, dc, tmax, sms, st);
         default: return cudaErrorInvalidValue;
     }
 }
