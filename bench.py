@@ -458,7 +458,7 @@ def _workload(name, batch=0, cache=None):
 
     if name == "uneven4096":
         # config 3: 4096 pairs, L, M ~ U{16..512}, d=16 walks, dyadic order 1
-        # (batch > 0: the first `batch` pairs, 4096 for all, on the band
+        # (batch > 0: the first `batch` pairs, 4096 for all, on the warp-stack
         # schedule, untuned: a case for profilers without the tuner's runs)
         w = inputs.uneven_pairs()
         lam = w["dyadic_order"]
@@ -481,7 +481,7 @@ def _workload(name, batch=0, cache=None):
         if tuned:
             sched, _ = tune.tune("pairs_varlen", Xd, xod, Yd, yod, lam, 512, store=False)
         else:
-            sched = sigk.Schedule(sigk.REC_BAND)
+            sched = sigk.Schedule(sigk.REC_CHAIN)
         g = sigk.graphed(sigk.pairs_varlen, Xd, xod, Yd, yod, lam, max_len=512, schedule=sched)
 
         def step():
@@ -515,7 +515,7 @@ def _workload(name, batch=0, cache=None):
         return dict(
             desc="%d pairs, L,M ~ U{16..512}, d=16 walks, dyadic order 1, fp32; %s schedule "
                  "rec=%d rows_per_lane=%d coef_path=%d orient=%d, one CUDA graph per call"
-                 % (np_all, "tuned" if tuned else "band", sched.rec, sched.rows_per_lane,
+                 % (np_all, "tuned" if tuned else "warp-stack", sched.rec, sched.rows_per_lane,
                     sched.coef_path, sched.orient),
             dtype="f32", step=step, cells=cells, pairs=np_all, flop=3 * cells + 2 * 16 * coarse,
             kernels=_uneven_kernels(sched), oracle_rate=oracle_rate, parity=parity,
@@ -900,6 +900,9 @@ def _workload(name, batch=0, cache=None):
 
 def _uneven_kernels(sched):
     from paper_2006_14794_gb300 import sigk
+    if sched.rec == sigk.REC_CHAIN:
+        return ("vstack_kernel (one launch per stack height; coefficients formed in the sweep) + "
+                "vs_inc_kernel (increments) + vs_pairs_kernel + vs_plan_kernel (device planning)")
     if sched.rec == sigk.REC_BAND:
         return ("vband_sweep_kernel (one launch per band class) + vb_coef_kernel (FMA contraction into "
                 "the band) + vb_pairs_kernel + vb_plan_kernel (device planning)")

@@ -176,14 +176,18 @@ int sigk_gram(const void *X, const void *Y, int64_t Bx, int64_t By, int64_t L, i
  * Xp [sum L, d]; likewise Y.  x_off, y_off: device int64 [B+1], nondecreasing,
  * x_off[0] = 0.  max_len: an upper bound on every path length (host value).
  * out: [B].  Same scheme as sigk_pairs, per pair.
- * f32 with rec AUTO or BAND (default rows_per_lane, linear static kernel):
- * the band form with every pair's geometry planned on the device (no host
- * round trip; CUDA-graph capturable), when 2^lambda (max_len - 1) refined
- * rows fit its largest band (dyadic order 0: 512, orders 1 and 2: 1024;
- * orders above 2 have none), else the strip path (rec BAND: then
- * SIGK_EUNSUPPORTED).  Its classes run on library-owned streams forked from
- * and joined to `stream` by events, created on the first such call on a
- * device. */
+ * f32 with rec CHAIN (default rows_per_lane, linear static kernel), d <= 16,
+ * dyadic order <= 2 and max_len <= 513: warp stacks, each pair's rows
+ * refining its shorter path in bands of 64 coarse rows, one warp a band, the
+ * coefficients formed inside the sweep (no coefficient in memory); rec AUTO
+ * takes them for d <= 8, or where the band form has no class for max_len.
+ * Otherwise f32 with rec AUTO or BAND: the band form, when 2^lambda
+ * (max_len - 1) refined rows fit its largest band (dyadic order 0: 512,
+ * orders 1 and 2: 1024; orders above 2 have none); else the strip path (rec
+ * BAND: then SIGK_EUNSUPPORTED).  Both forms plan every pair's geometry on the
+ * device (no host round trip; CUDA-graph capturable) and run their stack
+ * heights or band classes on library-owned streams forked from and joined to
+ * `stream` by events, created on the first such call on a device. */
 int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp,
                       const int64_t *y_off, int64_t B, int64_t d, int64_t max_len,
                       int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *ws,

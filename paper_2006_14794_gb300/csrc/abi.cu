@@ -102,6 +102,32 @@ void strip_batch(const PairSrc &src, int64_t n, int64_t la, int64_t lb, int lam,
 
 enum Path { P_FILL, P_CHAIN, P_BAND, P_STRIP, P_PLAIN };
 
+// Pairs of uneven lengths in warp stacks with the coefficients formed in the
+// sweep: f32, the linear static kernel, rec AUTO or CHAIN with the default
+// rows, d <= 16, dyadic order <= 2 and every path of at most 513 points.
+// AUTO takes them for d <= 8, or where the band form has no class for the
+// longest path: at d = 16 the band form's separate FMA contraction is the
+// faster of the two (4096 pairs of 16..512 points at dyadic order 1: 1.48
+// against 1.94 ms), at d = 8 and below the stacks are (1.08 against 1.36 ms
+// at d = 8, 0.87 against 1.40 ms at d = 3).
+bool varlen_uses_band(int64_t d, int64_t max_len, int lam, int dtype, const sigk_opts *o);
+bool varlen_uses_stack(int64_t d, int64_t max_len, int lam, int dtype, const sigk_opts *o) {
+    const int rec = rec_of(o);
+    if (rec != SIGK_REC_AUTO && rec != SIGK_REC_CHAIN) return false;
+    if (rows_of(o) != 0) return false;
+    if (!vstack_supported(lam, d, max_len, dtype, o ? o->static_kernel : SIGK_KERNEL_LINEAR)) return false;
+    return rec == SIGK_REC_CHAIN || d <= 8 || !varlen_uses_band(d, max_len, lam, dtype, o);
+}
+// Pairs per stack launch and the workspace that needs.
+void vstack_batch(int64_t n, int64_t max_len, int64_t d, int64_t &nb, int64_t &bytes) {
+    nb = n;
+    bytes = vstack_workspace_bytes(nb, max_len, d);
+    while (nb > 1 && bytes > STRIP_WS_CAP) {
+        nb = (nb + 1) / 2;
+        bytes = vstack_workspace_bytes(nb, max_len, d);
+    }
+}
+
 // Pairs of uneven lengths in the band form: f32, the linear static kernel,
 // rec AUTO or BAND with the default band heights, and every path short enough
 // for the largest band class.
@@ -428,6 +454,10 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
     }
     int64_t nb, need;
     if (op == SIGK_OP_PAIRS_VARLEN) {
+        if (varlen_uses_stack(d, L, dyadic_order, dtype, opts)) {
+            vstack_batch(n_pairs, L, d, nb, need);
+            return (size_t)need;
+        }
         if (varlen_uses_band(d, L, dyadic_order, dtype, opts)) {
             vband_batch(n_pairs, L, dyadic_order, nb, need);
             return (size_t)need;
@@ -548,6 +578,19 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp, cons
     src.La = max_len; src.Lb = max_len;
     src.d = d;
     const int rec = rec_of(opts);
+    if (varlen_uses_stack(d, max_len, dyadic_order, dtype, opts)) {
+        int64_t nb, need;
+        vstack_batch(B, max_len, d, nb, need);
+        if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
+        for (int64_t k0 = 0; k0 < B; k0 += nb) {
+            PairSrc s2 = src;
+            s2.kbase = k0;
+            const int64_t m = B - k0 < nb ? B - k0 : nb;
+            cudaError_t e = launch_vstack(s2, m, dyadic_order, max_len, (float *)out, ws, (cudaStream_t)stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        return SIGK_OK;
+    }
     if (varlen_uses_band(d, max_len, dyadic_order, dtype, opts)) {
         int64_t nb, need;
         vband_batch(B, max_len, dyadic_order, nb, need);

@@ -224,6 +224,14 @@ int64_t vband_workspace_bytes(int64_t n, int64_t max_len, int lam);
 cudaError_t launch_vband(const PairSrc &src, int64_t n, int lam, int64_t max_len, float *out, void *ws,
                          cudaStream_t st);
 
+// Pairs of uneven lengths with the coefficients formed inside the sweep
+// (vstack.cu): stacks of warps, one 64-coarse-row band each, f32, the linear
+// static kernel, d <= 16, dyadic order <= 2, shorter paths of <= 513 points.
+bool vstack_supported(int lam, int64_t d, int64_t max_len, int dtype, int kernel);
+int64_t vstack_workspace_bytes(int64_t n, int64_t max_len, int64_t d);
+cudaError_t launch_vstack(const PairSrc &src, int64_t n, int lam, int64_t max_len, float *out, void *ws,
+                          cudaStream_t st);
+
 // The band backward's chain rule on the tcgen05 tensor cores (chain_tc5.cu):
 // C = G B (trans = 0) or G^T B (trans = 1), G [M][K] (trans: [K][M]) with row
 // stride g_ld, B [K][N], C [M][N]; add: C += instead of C =; tri_rb > 0: a

@@ -46,14 +46,15 @@ def cache_path() -> str:
 
 def candidates(op: str, dtype: torch.dtype) -> List[Schedule]:
     """Schedules worth timing, roughly fastest-first so that slow ones are cut
-    short.  The uneven-length call has no chained form (its band form
-    plans its own band heights); f64 has neither those nor the tensor-core
-    coefficient kernel."""
+    short.  The uneven-length call plans its own stack and band heights on the
+    device, so it takes no rows_per_lane; f64 has neither those forms nor the
+    tensor-core coefficient kernel."""
     c: List[Schedule] = []
     if op != "pairs_varlen" and dtype == torch.float32:
         c += [Schedule(REC_CHAIN, r, 0) for r in (4, 8, 16)]
         c += [Schedule(REC_BAND, r, 0) for r in (4, 8, 16)]
     if op == "pairs_varlen" and dtype == torch.float32:
+        c.append(Schedule(REC_CHAIN, 0, 0))  # warp stacks, coefficients formed in the sweep
         c.append(Schedule(REC_BAND, 0, 0))   # band classes planned on the device
     for orient in (1, 2):   # rows refine the longer / the shorter path
         if dtype == torch.float32:

@@ -200,6 +200,19 @@ def test_band_schedule_is_f32_only(libsigk):
     assert libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_VARLEN, 3, 0, 514, 514, 16, 1, 0, ctypes.byref(o)) == 0
     assert libsigk.sigk_pairs_varlen(P, P, P, P, 3, 16, 514, 1, 0, ctypes.byref(o), P, P, 1 << 30, None) == \
         sigk.SIGK_EUNSUPPORTED
+    # rec CHAIN (and AUTO) on uneven f32 lengths with d <= 16: the warp
+    # stacks, whose workspace holds the increments of both sides (2 x pairs x
+    # max_len rows of 16-byte channel quads) and the plan
+    o.rec = sigk.REC_CHAIN
+    ws_chain = libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_VARLEN, 3, 0, 513, 513, 16, 1, 0, ctypes.byref(o))
+    assert ws_chain > 2 * 3 * 513 * 64
+    # AUTO takes the stacks for d <= 8 (the band form's contraction wins at d = 16)
+    o.rec = sigk.REC_CHAIN
+    ws8 = libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_VARLEN, 3, 0, 513, 513, 8, 1, 0, ctypes.byref(o))
+    o.rec = sigk.REC_AUTO
+    assert libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_VARLEN, 3, 0, 513, 513, 8, 1, 0, ctypes.byref(o)) == ws8
+    assert libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_VARLEN, 3, 0, 513, 513, 16, 1, 0, ctypes.byref(o)) != ws_chain
+    o.rec = sigk.REC_BAND
     # the band workspace: a 256-byte header, then (pairs x macro-steps + 1)
     # slot rows of 32 x NG^2 floats.
     # 256-point paths at dyadic order 1: 510 refined rows -> 16 rows per lane,

@@ -43,6 +43,8 @@ def _packed(seed, Ls, Ms, d, scale=1.0):
 
 
 def _run(X32, xo, Y32, yo, lam, max_len, **kw):
+    # the band form by name (AUTO takes the warp stacks where they apply)
+    kw.setdefault("rec", S().REC_BAND)
     return S().pairs_varlen(to_dev(X32), torch.as_tensor(xo).cuda(), to_dev(Y32), torch.as_tensor(yo).cuda(),
                             lam, max_len=max_len, **kw).cpu().numpy()
 
@@ -101,6 +103,16 @@ def test_chains_of_several_pairs_of_different_lengths():
     assert rel_err(got, ref, floor=0.25) <= 1e-5
 
 
+@pytest.mark.parametrize("lam", [0, 2])
+def test_sixteen_channels_other_dyadic_orders(lam):
+    rng = np.random.default_rng(85 + lam)
+    Ls = rng.integers(2, 250, size=32)
+    Ms = rng.integers(2, 250, size=32)
+    X32, X64, xo, Y32, Y64, yo = _packed(95 + lam, Ls, Ms, 16)
+    got = _run(X32, xo, Y32, yo, lam, 250)
+    assert rel_err(got, _ref(X64, xo, Y64, yo, lam)) <= 1e-5
+
+
 @pytest.mark.parametrize("d", [1, 16, 45])
 def test_channel_counts(d):
     # one channel; one pass of staged channels; two passes (d > 32)
@@ -144,7 +156,7 @@ def test_graph_replay_with_other_lengths():
     # and with them the static buffers' shapes, stay the same
     b = _packed(72, rng.permutation(Ls), rng.permutation(Ms), 16)
     dev = [to_dev(a[0]), torch.as_tensor(a[2]).cuda(), to_dev(a[3]), torch.as_tensor(a[5]).cuda()]
-    g = S().graphed(S().pairs_varlen, *dev, 1, max_len=512)
+    g = S().graphed(S().pairs_varlen, *dev, 1, max_len=512, rec=S().REC_BAND)
     for X32, X64, xo, Y32, Y64, yo in (a, b, a):
         out = g(to_dev(X32), torch.as_tensor(xo).cuda(), to_dev(Y32), torch.as_tensor(yo).cuda())
         torch.cuda.synchronize()

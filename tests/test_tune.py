@@ -19,9 +19,10 @@ def test_candidates_cover_every_path():
     c64 = tune.candidates("pairs", torch.float64)
     assert all(s.rec not in (REC_CHAIN, sigk.REC_BAND) and s.coef_path != COEF_TC for s in c64)
     cv = tune.candidates("pairs_varlen", torch.float32)
-    # uneven lengths: no chained form; the band form plans its own band heights
-    assert all(s.rec != REC_CHAIN for s in cv)
+    # uneven lengths: the warp stacks and the band form plan their own heights
+    assert [s for s in cv if s.rec == REC_CHAIN] == [Schedule(REC_CHAIN, 0, 0)]
     assert [s for s in cv if s.rec == sigk.REC_BAND] == [Schedule(sigk.REC_BAND, 0, 0)]
+    assert all(s.rec not in (REC_CHAIN, sigk.REC_BAND) for s in tune.candidates("pairs_varlen", torch.float64))
     assert all(s.rec != sigk.REC_BAND for s in tune.candidates("pairs_varlen", torch.float64))
 
 
