@@ -846,7 +846,7 @@ def _workload(name, batch=0, cache=None):
                  "the solution surface on the sample grid (%d x %d nodes per pair, %.2f GB written)"
                  % (B, L, L, B * L * L * 4 / 1e9),
             dtype="f32", step=step, cells=cells, pairs=B, flop=3 * cells + 2 * d * coarse,
-            kernels="chain_band_kernel (surface instance) + band_gbar_kernel (surface unpack)",
+            kernels="chain_f32_kernel (surface instance, inline coefficients) + band_gbar_kernel (surface unpack)",
             oracle_rate=oracle_rate, parity=parity, host_step=host_step, host=(hx, hy, hs),
             h2d=hx.numel() * 4 + hy.numel() * 4, d2h=B * L * L * 4)
 

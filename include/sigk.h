@@ -201,10 +201,14 @@ int sigk_pairs_varlen(const void *Xp, const int64_t *x_off, const void *Yp,
  * and column 0 are the boundary value 1; surf[b][L-1][M-1] = out[b] = k.
  * X: [B, L, d], Y: [B, M, d]; out: [B]; surf: [B, L, M] (both overwritten).
  * opts as for sigk_pairs (scheme and static kernel included).  f32 pairs
- * whose shorter path fits a warp (2^lambda (L-1) <= 512) run the band sweep
- * with its workspace (size it with SIGK_OP_PAIRS_SURFACE); others the plain
- * sweep without one.  SIGK_REC_STRIP gives SIGK_EUNSUPPORTED (the strip path
- * keeps no surface); SIGK_REC_BAND where the band form does not apply too.
+ * whose shorter path fits a warp (2^lambda (L-1) <= 512) run a chained sweep
+ * that keeps the nodes in a band layout in the workspace, then an unpack
+ * into surf (size the workspace with SIGK_OP_PAIRS_SURFACE): with the
+ * coefficients formed inline (rec AUTO or CHAIN, explicit scheme, linear
+ * static kernel, d <= 16 where the chained kernel has an instance), else
+ * from the band form's coefficient band; others run the plain sweep without
+ * a workspace.  SIGK_REC_STRIP gives SIGK_EUNSUPPORTED (the strip path keeps
+ * no surface); SIGK_REC_BAND where the band form does not apply too.
  * Writes B L M elements: HBM-bound once the grid is small. */
 int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64_t M, int64_t d,
                        int dyadic_order, int dtype, const sigk_opts *opts, void *out, void *surf,

@@ -388,6 +388,40 @@ int run_backward(PairSrc src, int64_t n_pairs, int lam, int dtype, const sigk_op
 
 // The surface's path: the band sweep's surface instance for f32 pairs whose
 // shorter path fits a warp (rec AUTO, CHAIN or BAND), else the plain sweep.
+// The surface in the chain schedule (inline coefficients, no coefficient
+// band): f32, the linear static kernel, the explicit scheme, rec AUTO or
+// CHAIN and a chained instance for the shape (d <= 16); bp is the same
+// geometry as the surface unpack reads it.
+bool surface_uses_chain(const PairSrc &src, int lam, int dtype, int rec, int rows, ChainPlan &cp,
+                        BandPlan &bp) {
+    if (dtype != SIGK_F32 || (rec != SIGK_REC_AUTO && rec != SIGK_REC_CHAIN)) return false;
+    if (src.kernel != SIGK_KERNEL_LINEAR || src.scheme != SIGK_SCHEME_EXPLICIT) return false;
+    const int64_t la = src.La < src.Lb ? src.La : src.Lb, lb = src.La < src.Lb ? src.Lb : src.La;
+    if (!chain_geometry(la, lb, src.d, lam, cp, rows)) return false;
+    bp.R = cp.R;
+    bp.lam = lam;
+    bp.NG = cp.R >> lam;
+    bp.TperR = cp.Tper / cp.R;
+    bp.NQ = cp.NQ;
+    bp.NQV = cp.NQV;
+    bp.vrows = cp.vtop >> lam;
+    bp.slot_floats = 32LL * bp.NG * bp.NG;
+    return true;
+}
+// Its workspace: a 256-byte header, then the nodes' band layout (TperR + 1
+// slots a pair); pairs per launch under the cap.
+int64_t chain_surface_bytes(const BandPlan &bp, int64_t n) {
+    return 256 + (int64_t)sizeof(float) * n * (bp.TperR + 1) * bp.slot_floats;
+}
+void chain_surface_batch(const BandPlan &bp, int64_t n, int64_t &nb, int64_t &bytes) {
+    nb = n;
+    bytes = chain_surface_bytes(bp, nb);
+    while (nb > 1 && bytes > STRIP_WS_CAP) {
+        nb = (nb + 1) / 2;
+        bytes = chain_surface_bytes(bp, nb);
+    }
+}
+
 bool surface_uses_band(const PairSrc &src, int lam, int dtype, int rec, int rows, BandPlan &bp) {
     if (dtype != SIGK_F32 || rec == SIGK_REC_PLAIN || rec == SIGK_REC_STRIP) return false;
     const int64_t la = src.La < src.Lb ? src.La : src.Lb, lb = src.La < src.Lb ? src.Lb : src.La;
@@ -431,8 +465,13 @@ size_t sigk_workspace_bytes(int op, int64_t B_or_Bx, int64_t By, int64_t L, int6
         ss.mode = PM_PAIRS;
         ss.La = L; ss.Lb = M; ss.d = d;
         BandPlan bp;
-        if (!surface_uses_band(ss, dyadic_order, dtype, rec_of(opts), rows_of(opts), bp)) return 0;
+        ChainPlan cp;
         int64_t nb, need;
+        if (surface_uses_chain(ss, dyadic_order, dtype, rec_of(opts), rows_of(opts), cp, bp)) {
+            chain_surface_batch(bp, n_pairs, nb, need);
+            return (size_t)need;
+        }
+        if (!surface_uses_band(ss, dyadic_order, dtype, rec_of(opts), rows_of(opts), bp)) return 0;
         band_surface_batch(bp, n_pairs, nb, need);
         return (size_t)need;
     }
@@ -634,11 +673,14 @@ int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64
     src.A = X; src.B = Y;
     src.La = L; src.Lb = M; src.d = d;
     BandPlan bp;
-    const bool band = surface_uses_band(src, dyadic_order, dtype, rec, rows_of(opts), bp);
+    ChainPlan cp;
+    const bool chain = surface_uses_chain(src, dyadic_order, dtype, rec, rows_of(opts), cp, bp);
+    const bool band = !chain && surface_uses_band(src, dyadic_order, dtype, rec, rows_of(opts), bp);
     if (rec == SIGK_REC_BAND && !band) return SIGK_EUNSUPPORTED;
-    if (band) {
+    if (chain || band) {
         int64_t nb, need;
-        band_surface_batch(bp, B, nb, need);
+        if (chain) chain_surface_batch(bp, B, nb, need);
+        else band_surface_batch(bp, B, nb, need);
         if (!ws || (int64_t)ws_bytes < need) return SIGK_ENOMEM_WS;
     }
     // boundary nodes (row and column 0) are 1; the sweeps write the others
@@ -649,7 +691,7 @@ int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64
     }
     cudaError_t e = launch_surface_border(surf, B, L, M, dtype, st);
     if (e != cudaSuccess) return cuda_status(e);
-    if (!band) return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, st, surf));
+    if (!band && !chain) return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, st, surf));
     // rows refine the shorter path: node (i, j) of the sweep is surface (i, j),
     // or (j, i) when X and Y swap places
     PairSrc s2 = src;
@@ -660,6 +702,23 @@ int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64
         sa = 1; sb = M;
     }
     int64_t nb, need;
+    if (chain) {
+        // the chained sweep writes the nodes' band layout, the unpack the surface
+        chain_surface_batch(bp, B, nb, need);
+        float *sband = (float *)((unsigned char *)ws + 256);
+        if ((e = cudaMemsetAsync(ws, 0, sizeof(int), st)) != cudaSuccess) return cuda_status(e);
+        for (int64_t k0 = 0; k0 < B; k0 += nb) {
+            PairSrc s3 = s2;
+            s3.kbase = k0;
+            const int64_t m = B - k0 < nb ? B - k0 : nb;
+            ChainPlan c2;
+            if (!chain_plan(m, s2.La, s2.Lb, d, dyadic_order, c2, rows_of(opts))) return SIGK_EUNSUPPORTED;
+            if ((e = launch_chain_f32(s3, c2, m, (float *)out, st, sband)) != cudaSuccess) return cuda_status(e);
+            if ((e = launch_surface_unpack(s3, bp, m, sband, (float *)surf, L * M, sa, sb, st)) != cudaSuccess)
+                return cuda_status(e);
+        }
+        return SIGK_OK;
+    }
     band_surface_batch(bp, B, nb, need);
     for (int64_t k0 = 0; k0 < B; k0 += nb) {
         PairSrc s3 = s2;

@@ -1714,11 +1714,20 @@ cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pai
 #undef X
     if (!launched) return cudaErrorInvalidValue;
     if ((e = cudaGetLastError()) != cudaSuccess || !surf) return e;
+    return launch_surface_unpack(src, p, n_pairs, a.sband, surf, s_pair, s_a, s_b, st);
+}
+
+cudaError_t launch_surface_unpack(const PairSrc &src, const BandPlan &p, int64_t n_pairs, const float *sband,
+                                  float *surf, int64_t s_pair, int64_t s_a, int64_t s_b, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     // the surface from the band layout into [pair][L][M]
     BandGbarArgs gb;
     memset(&gb, 0, sizeof(gb));
     gb.src = src;
-    gb.gband = a.sband;
+    gb.gband = sband;
     gb.gbar = surf;
     gb.n_pairs = n_pairs;
     gb.TperR = p.TperR;

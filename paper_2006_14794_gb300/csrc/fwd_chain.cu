@@ -62,6 +62,11 @@ struct ChainArgs {
     int yunits, xunits;      // their sizes (float4)
     int warp_units;          // float4 units of shared memory per warp (incl. output slots)
     float scale;             // 1/2 * 4^-lambda
+    // the solution surface on the sample grid (SURF instances): each lane's
+    // values at the sample-grid nodes, a window row per window, in the band
+    // layout with Tper/R + 1 slots per pair (the last: the pair's tail), as
+    // band.cu's surface sweep writes them for its unpack kernel
+    float *sband;
 };
 
 __device__ __forceinline__ int swz(int u) { return u ^ ((u >> 3) & 7); }
@@ -113,19 +118,44 @@ __device__ __forceinline__ float dot_inc(const float4 (&dx)[D4], const float4 (&
     return acc.x + acc.y;
 }
 
+// A window row of NG values (NH float2: groups g, g + NH) to 8- or 16-byte
+// aligned memory.
+template <int NG>
+__device__ __forceinline__ void chain_store_window(float *dst, const float2 (&v)[NG / 2]) {
+    if constexpr (NG == 8) {
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        reinterpret_cast<float4 *>(dst)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    } else if constexpr (NG == 4) {
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    } else {
+        reinterpret_cast<float2 *>(dst)[0] = v[0];
+    }
+}
+
 // MINB: CTAs per SM the register allocation must allow (6 two-warp CTAs =
 // 12 warps at <= 168 registers measured fastest for the 256x256 Gram; 1 where
 // that cap would spill).
 // IMPL: the implicit scheme's coefficient map (scheme_coef) on every coarse
 // cell, a compile-time choice so that the explicit scheme's loop carries none
 // of it.
-template <int R, int LAM, int D4, int MINB, bool IMPL>
+// SURF: also keep the solution at the sample-grid nodes.  Row r of lane l is
+// refined node row R l + r + 1 - vtop and at step j of position pos computes
+// node column pos R + j - r + 1 - vpad (the previous pair's when that is <=
+// 0); vtop and vpad are multiples of 2^lambda, so the node is on the sample
+// grid exactly for the last row of each coarse group (r % 2^lambda =
+// 2^lambda - 1) at step j % 2^lambda = 2^lambda - 2 of each window (0 at
+// dyadic orders 0 and 1).  There group g of window w holds node (p + 1, q)
+// (order 0: (p + 1, q + 1)) of coarse cell (p, q) = (P - vrows, Q - NQV),
+// (P, Q) = (lane NG + g, pos NG + w - g): the band layout's cell, so the lane
+// stores its NG values as one window row.
+template <int R, int LAM, int D4, int MINB, bool IMPL, bool SURF = false>
 __global__ void __launch_bounds__(CHAIN_WARPS * 32, MINB) chain_f32_kernel(ChainArgs a) {
     constexpr int S = 1 << LAM;
     constexpr int NG = R / S;        // coarse rows (groups) per lane = windows per macro-step
     constexpr int H = R / 2;         // rows i and i + H share a float2
     constexpr int NH = NG / 2;       // groups g and g + NH share a float2 of coefficients
     constexpr int JOUT = R - 2;      // step of the corner in a turn-over macro-step
+    constexpr int SLOT = NG * NG;    // floats a lane's window rows take in a surface slot
     static_assert(R % S == 0 && NG % 2 == 0, "rows per lane: an even number of coarse rows");
     extern __shared__ float4 smem[];
 
@@ -253,6 +283,21 @@ __global__ void __launch_bounds__(CHAIN_WARPS * 32, MINB) chain_f32_kernel(Chain
                         }
                     }
                 }
+                if constexpr (SURF) {
+                    constexpr int JS = S >= 2 ? S - 2 : 0;
+                    if (jj == JS) {
+                        // rows g S + S - 1 (packed with g + NH) are at their group's node
+                        float2 sv[NH];
+#pragma unroll
+                        for (int g = 0; g < NH; ++g) sv[g] = KP[g * S + S - 1];
+                        if (kl >= 0 && kl < np)
+                            chain_store_window<NG>(a.sband + (((k0 + kl) * (TperR + 1) + pos) * 32 + lane) *
+                                                                 (int64_t)SLOT + w * NG, sv);
+                        if (trans && kl >= 1 && kl <= np)   // the previous pair's tail
+                            chain_store_window<NG>(a.sband + (((k0 + kl - 1) * (TperR + 1) + TperR) * 32 + lane) *
+                                                                 (int64_t)SLOT + w * NG, sv);
+                    }
+                }
                 pK = (lane == 0) ? 1.f : shK;
                 pQ = (lane == 0) ? 0.f : shQ;
             }
@@ -270,8 +315,9 @@ __global__ void __launch_bounds__(CHAIN_WARPS * 32, MINB) chain_f32_kernel(Chain
 
 template <int R, int LAM, int D4, int MINB>
 cudaError_t launch_one(const ChainArgs &args, const ChainPlan &p, cudaStream_t st) {
-    auto kern = args.src.scheme == SIGK_SCHEME_IMPLICIT ? chain_f32_kernel<R, LAM, D4, MINB, true>
-                                                        : chain_f32_kernel<R, LAM, D4, MINB, false>;
+    auto kern = args.sband ? chain_f32_kernel<R, LAM, D4, MINB, false, true>
+                           : args.src.scheme == SIGK_SCHEME_IMPLICIT ? chain_f32_kernel<R, LAM, D4, MINB, true>
+                                                                     : chain_f32_kernel<R, LAM, D4, MINB, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          p.smem_bytes);
     if (e != cudaSuccess) return e;
@@ -313,9 +359,8 @@ int occupancy_of(int R, int lam, int D4, int smem) {
 
 }  // namespace
 
-bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p,
-                int rows_per_lane) {
-    if (La < 2 || Lb < 2 || lam > 3 || d < 1 || n_pairs < 1) return false;
+bool chain_geometry(int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p, int rows_per_lane) {
+    if (La < 2 || Lb < 2 || lam > 3 || d < 1) return false;
     const int64_t S = 1LL << lam;
     const int64_t Ni = S * (La - 1), Nj = S * (Lb - 1);
     int D4 = (int)((d + 3) / 4);
@@ -352,6 +397,13 @@ bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, Cha
     const int64_t cta_smem = (int64_t)CHAIN_WARPS * p.warp_units * 16;
     if (cta_smem > 200 * 1024) return false;
     p.smem_bytes = (int)cta_smem;
+    return true;
+}
+
+bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p,
+                int rows_per_lane) {
+    if (n_pairs < 1 || !chain_geometry(La, Lb, d, lam, p, rows_per_lane)) return false;
+    const int R = p.R, D4 = p.D4;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
@@ -365,7 +417,8 @@ bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, Cha
 }
 
 cudaError_t launch_chain_f32(const PairSrc &src, const ChainPlan &p, int64_t n_pairs, float *out,
-                             cudaStream_t st) {
+                             cudaStream_t st, float *sband) {
+    if (sband && src.scheme == SIGK_SCHEME_IMPLICIT) return cudaErrorInvalidValue;   // no such instance
     ChainArgs a;
     a.src = src;
     a.out = out;
@@ -382,6 +435,7 @@ cudaError_t launch_chain_f32(const PairSrc &src, const ChainPlan &p, int64_t n_p
     a.xunits = p.xunits;
     a.warp_units = p.warp_units;
     a.scale = 0.5f / (float)(1 << (2 * p.lam));
+    a.sband = sband;
 #define X(r, l, dd, mb) \
     if (p.R == r && p.lam == l && p.D4 == dd) return launch_one<r, l, dd, mb>(a, p, st);
     SIGK_CHAIN_CASES(X)

@@ -152,11 +152,17 @@ struct ChainPlan {
     int grid, smem_bytes;
 };
 
+// Geometry and shared memory of the chained kernel, with no device query;
+// false when it has no instance for these sizes.
+bool chain_geometry(int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p, int rows_per_lane = 0);
 // Returns false when the chained kernel has no instance for these sizes.
 bool chain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, ChainPlan &p,
                 int rows_per_lane = 0);
+// sband (explicit scheme only): also the solution surface's sample-grid
+// nodes in the band layout of the surface unpack (launch_surface_unpack),
+// Tper/R + 1 slots of 32 (R/2^lambda)^2 floats a pair.
 cudaError_t launch_chain_f32(const PairSrc &src, const ChainPlan &p, int64_t n_pairs,
-                             float *out, cudaStream_t st);
+                             float *out, cudaStream_t st, float *sband = nullptr);
 
 // The band form (fwd_band.cu): the row chain reading coefficients that a
 // contraction kernel formed beforehand into a banded buffer (the workspace).
@@ -179,6 +185,10 @@ int64_t band_surface_bytes(const BandPlan &p, int64_t n_pairs);
 cudaError_t launch_band_f32(const PairSrc &src, const BandPlan &p, int64_t n_pairs, float *out,
                             void *ws, cudaStream_t st, int coef_path, float *surf = nullptr,
                             int64_t s_pair = 0, int64_t s_a = 0, int64_t s_b = 0);
+// The surface from its band-layout node values (written by a SURF sweep,
+// band or chain, with geometry p) into surf[k s_pair + i s_a + j s_b].
+cudaError_t launch_surface_unpack(const PairSrc &src, const BandPlan &p, int64_t n_pairs, const float *sband,
+                                  float *surf, int64_t s_pair, int64_t s_a, int64_t s_b, cudaStream_t st);
 // The band backward (reversible adjoint): pairs per launch (Gram: whole rows)
 // under cap_bytes, with the workspace that needs (coef_path 3 adds a Gram's
 // dense dk/dc for the tensor-core contraction); then the launches.  src is

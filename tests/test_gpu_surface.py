@@ -1,8 +1,8 @@
 """The solution surface on the sample grid (sigk_pairs_surface) through the C
-ABI against the FP64 oracle: the band sweep's surface instance for every
-(rows per lane, dyadic order) family, both orientations, pair turnovers inside
-a warp's chain, the plain sweep (f32 and f64, long pairs), both variants, and
-the degenerate and refused cases."""
+ABI against the FP64 oracle: the band sweep's and the chained sweep's surface
+instances for every (rows per lane, dyadic order) family, both orientations,
+pair turnovers inside a warp's chain, the plain sweep (f32 and f64, long
+pairs), both variants, and the degenerate and refused cases."""
 import numpy as np
 import pytest
 import torch
@@ -51,6 +51,36 @@ def test_band_surface_matches_oracle(R, lam, L, M, d):
     assert rel_err(k.cpu().numpy(), rk) <= F32_TOL
     np.testing.assert_array_equal(surf[:, :, -1][:, -1], k.cpu().numpy())
     assert np.all(surf[:, 0, :] == 1.0) and np.all(surf[:, :, 0] == 1.0)
+
+
+@pytest.mark.parametrize("R,lam,L,M,d", [
+    (16, 2, 128, 128, 8),    # the bench shape
+    (16, 1, 200, 150, 4),    # L > M: rows refine Y, the surface is transposed back
+    (8, 0, 230, 256, 5),     # every refined node is a sample-grid node
+    (8, 2, 60, 50, 13),      # four channel quads
+    (16, 3, 40, 61, 3),
+    (4, 1, 60, 70, 16),
+])
+def test_chain_surface_matches_oracle(R, lam, L, M, d):
+    # the chained sweep (coefficients formed inline) writes the nodes' band
+    # layout, which the surface unpack reads
+    sigk = S()
+    B = 23   # several pairs per warp: turnovers inside the chain
+    X32, X64 = inputs.f32(inputs.random_paths(7700 + R + lam, B, L, d, time_channel=True))
+    Y32, Y64 = inputs.f32(inputs.random_paths(7800 + R + lam, B, M, d, time_channel=True))
+    rk, rs = oracle.pairs_surface(X64, Y64, lam)
+    k, surf = sigk.pairs_surface(to_dev(X32), to_dev(Y32), lam,
+                                 schedule=sigk.Schedule(sigk.REC_CHAIN, R, 0))
+    surf = surf.cpu().numpy()
+    assert surf.shape == (B, L, M)
+    assert rel_err(surf, rs) <= F32_TOL
+    assert rel_err(k.cpu().numpy(), rk) <= F32_TOL
+    np.testing.assert_array_equal(surf[:, :, -1][:, -1], k.cpu().numpy())
+    assert np.all(surf[:, 0, :] == 1.0) and np.all(surf[:, :, 0] == 1.0)
+    if R == 16 and lam == 2:
+        # AUTO takes the chained surface: the same bits
+        k2, s2 = sigk.pairs_surface(to_dev(X32), to_dev(Y32), lam)
+        np.testing.assert_array_equal(s2.cpu().numpy(), surf)
 
 
 @pytest.mark.parametrize("dtype,L,M,lam", [(torch.float32, 50, 70, 1), (torch.float64, 50, 70, 1),
