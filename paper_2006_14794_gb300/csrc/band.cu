@@ -690,16 +690,18 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // contractions read: [row path * nx][column path * ny] (Gram: every column
 // path of the call; pairs: one nx x ny block per pair).  Pair k's cell (P, Q)
 // = (l NG + g, Q) is in slot (k, pos) window w with pos NG + w = Q + g (slot
-// TperR: the tail).  A block takes GB_POS positions of one pair: it stages
-// those slots and the next one in shared memory (coalesced), then writes the
-// real cells of columns Q in [pos0 NG, (pos0 + GB_POS) NG) row by row, each
-// row a contiguous run (window rows staged NG + 1 floats apart).
-constexpr int GB_POS = 4;
+// TperR: the tail).  A block takes gb_pos(NG) positions of one pair: it
+// stages those slots and the next one in shared memory (coalesced), then
+// writes the real cells of columns Q in [pos0 NG, (pos0 + gb_pos) NG) row by
+// row, each row a contiguous run (window rows staged NG + 1 floats apart):
+// 32 columns (128 bytes) a row for NG <= 4, 32 for NG = 8 (four positions,
+// the static shared memory's limit).
+__host__ __device__ constexpr int gb_pos(int NG) { return NG <= 4 ? 8 : 4; }
 constexpr int GB_THREADS = 256;
 // position groups per pair: the columns Q < NQ = TperR NG, and for the
 // surface also Q = NQ (its last node column, in the tail slot)
-__host__ __device__ inline int gb_groups(int TperR, bool surf) {
-    return (TperR + (surf ? 1 : 0) + GB_POS - 1) / GB_POS;
+__host__ __device__ inline int gb_groups(int TperR, bool surf, int NG) {
+    return (TperR + (surf ? 1 : 0) + gb_pos(NG) - 1) / gb_pos(NG);
 }
 
 struct BandGbarArgs {
@@ -724,12 +726,13 @@ template <int NG>
 __global__ void __launch_bounds__(GB_THREADS) band_gbar_kernel(BandGbarArgs a) {
     constexpr int SLOT = NG * NG;
     constexpr int NP = 32 * NG;                 // padded rows
+    constexpr int GB_POS = gb_pos(NG);
     constexpr int SPAN = GB_POS * NG;           // columns per block task
     constexpr int WS = NG + 1;                  // staged window row stride: consecutive
                                                 // columns of a row hit distinct banks
     constexpr int SS = NG * WS;                 // staged slot stride
     __shared__ float sl[(GB_POS + 1) * 32 * SS];
-    const int ngroups = gb_groups(a.TperR, a.s_pair > 0);
+    const int ngroups = gb_groups(a.TperR, a.s_pair > 0, NG);
     const int64_t tasks = a.n_pairs * ngroups;
     for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
         const int64_t k = t / ngroups;
@@ -1739,7 +1742,7 @@ cudaError_t launch_surface_unpack(const PairSrc &src, const BandPlan &p, int64_t
     gb.s_a = s_a;
     gb.s_b = s_b;
     gb.q_off = p.lam == 0 ? 1 : 0;
-    const int64_t tasks = n_pairs * gb_groups(p.TperR, true);
+    const int64_t tasks = n_pairs * gb_groups(p.TperR, true, p.NG);
     const int ggrid = (int)(tasks < (int64_t)sms * 8 ? tasks : (int64_t)sms * 8);
     if (p.NG == 8) band_gbar_kernel<8><<<ggrid, GB_THREADS, 0, st>>>(gb);
     else if (p.NG == 4) band_gbar_kernel<4><<<ggrid, GB_THREADS, 0, st>>>(gb);
@@ -2097,7 +2100,7 @@ cudaError_t launch_band_bwd_f32(const PairSrc &src0, const BandPlan &p, int64_t 
             gb.vrows = p.vrows;
             gb.nx = (int)nx;
             gb.ny = (int)ny;
-            const int64_t tasks = m * gb_groups(p.TperR, false);
+            const int64_t tasks = m * gb_groups(p.TperR, false, p.NG);
             const int ggrid = (int)(tasks < (int64_t)sms * 8 ? tasks : (int64_t)sms * 8);
             if (p.NG == 8) band_gbar_kernel<8><<<ggrid, GB_THREADS, 0, st>>>(gb);
             else if (p.NG == 4) band_gbar_kernel<4><<<ggrid, GB_THREADS, 0, st>>>(gb);
