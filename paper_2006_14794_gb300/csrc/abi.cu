@@ -689,7 +689,11 @@ int sigk_pairs_surface(const void *X, const void *Y, int64_t B, int64_t L, int64
         if (e != cudaSuccess) return cuda_status(e);
         return cuda_status(launch_fill_one(out, B, dtype, st));
     }
-    cudaError_t e = launch_surface_border(surf, B, L, M, dtype, st);
+    // the unpack of the chain and band forms writes the sweep's column 0 at
+    // dyadic orders >= 1 when the pairs have virtual left columns: the
+    // surface's column 0 unless the rows refine Y
+    const bool col0 = !(chain || band) || dyadic_order == 0 || bp.NQV == 0 || L > M;
+    cudaError_t e = launch_surface_border(surf, B, L, M, dtype, st, col0);
     if (e != cudaSuccess) return cuda_status(e);
     if (!band && !chain) return cuda_status(launch_plain(src, B, dyadic_order, dtype, out, st, surf));
     // rows refine the shorter path: node (i, j) of the sweep is surface (i, j),

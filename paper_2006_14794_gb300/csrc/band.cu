@@ -763,7 +763,13 @@ __global__ void __launch_bounds__(GB_THREADS) band_gbar_kernel(BandGbarArgs a) {
             const int64_t jb = a.gram ? pr.b_row0 / a.src.Lb : 0;
             base = a.gbar + ia * a.nx * a.g_ld + jb * a.ny;
         }
-        const int qlo = surf ? 1 - a.q_off : 0, qhi = surf ? a.ny - a.q_off : a.ny - 1;
+        // surface: column 0 too when the pairs have virtual columns at the
+        // left (NQV >= 1 at dyadic orders >= 1): there the stored node is the
+        // boundary value, exactly 1 (c = 0 keeps K = 1 and Q = 0), and the
+        // border fill need not write that strided column; without them the
+        // slot holds the previous pair's last column instead
+        const int qlo = surf && a.q_off == 0 && a.NQV == 0 ? 1 : 0;
+        const int qhi = surf ? a.ny - a.q_off : a.ny - 1;
         if (surf) base += (int64_t)a.q_off * sc;
         const int Qlo = pos0 * NG;
         for (int v = threadIdx.x; v < NP * SPAN; v += GB_THREADS) {

@@ -196,8 +196,8 @@ cudaError_t launch_fill_one(void *out, int64_t n, int dtype, cudaStream_t st) {
 // Row 0 and column 0 of B surfaces [L][M]: the boundary value 1 (the sweeps
 // write every other node).
 template <typename T>
-__global__ void surface_border_kernel(T *surf, int64_t B, int64_t L, int64_t M) {
-    const int64_t per = L + M - 1;
+__global__ void surface_border_kernel(T *surf, int64_t B, int64_t L, int64_t M, bool col0) {
+    const int64_t per = col0 ? L + M - 1 : M;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B * per;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = i / per, j = i - b * per;
@@ -207,14 +207,15 @@ __global__ void surface_border_kernel(T *surf, int64_t B, int64_t L, int64_t M) 
     }
 }
 
-cudaError_t launch_surface_border(void *surf, int64_t B, int64_t L, int64_t M, int dtype, cudaStream_t st) {
-    const int64_t n = B * (L + M - 1);
+cudaError_t launch_surface_border(void *surf, int64_t B, int64_t L, int64_t M, int dtype, cudaStream_t st,
+                                  bool col0) {
+    const int64_t n = B * (col0 ? L + M - 1 : M);
     if (n <= 0) return cudaSuccess;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     if (dtype == SIGK_F64)
-        surface_border_kernel<double><<<grid, 256, 0, st>>>((double *)surf, B, L, M);
+        surface_border_kernel<double><<<grid, 256, 0, st>>>((double *)surf, B, L, M, col0);
     else
-        surface_border_kernel<float><<<grid, 256, 0, st>>>((float *)surf, B, L, M);
+        surface_border_kernel<float><<<grid, 256, 0, st>>>((float *)surf, B, L, M, col0);
     return cudaGetLastError();
 }
 

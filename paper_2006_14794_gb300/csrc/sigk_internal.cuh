@@ -205,8 +205,9 @@ cudaError_t launch_plain(const PairSrc &src, int64_t n_pairs, int lam, int dtype
                          cudaStream_t st, void *surf = nullptr);
 
 cudaError_t launch_fill_one(void *out, int64_t n, int dtype, cudaStream_t st);
-// row 0 and column 0 of B solution surfaces [L][M] set to 1
-cudaError_t launch_surface_border(void *surf, int64_t B, int64_t L, int64_t M, int dtype, cudaStream_t st);
+// row 0 and (col0) column 0 of B solution surfaces [L][M] set to 1
+cudaError_t launch_surface_border(void *surf, int64_t B, int64_t L, int64_t M, int dtype, cudaStream_t st,
+                                  bool col0 = true);
 
 bool bwd_plain_plan(int64_t n_pairs, int64_t La, int64_t Lb, int64_t d, int lam, int dtype,
                     int64_t &grid, int64_t &slot_bytes, int64_t &smem);
