@@ -233,3 +233,28 @@ def test_strip_backward_workspace_holds_no_per_cell_values(libsigk):
     n = libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_BACKWARD, 8, 0, 4096, 4096, 64, 1, 0, ctypes.byref(o))
     per_cell = 8 * 8190 * 8190 * 4
     assert 0 < n < 1.25e9 < per_cell
+
+
+def test_surface_workspace_follows_the_schedule(libsigk):
+    """The solution surface's workspace (no device needed): the chained sweep
+    (f32, explicit scheme, linear kernel, d <= 16) keeps only the nodes' band
+    layout, Tper/R + 1 slots of 32 NG^2 floats a pair; the band form adds the
+    coefficient band before it."""
+    from paper_2006_14794_gb300 import sigk
+    o = sigk.SigkOpts()
+    B, L, M, d, lam = 3, 128, 128, 8, 2
+    # 127 coarse rows at order 2: 508 refined rows -> 16 rows a lane, NG = 4
+    # coarse rows a lane; 508 refined columns padded to 512: Tper/R = 32
+    chain = libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_SURFACE, B, 0, L, M, d, lam, 0, ctypes.byref(o))
+    assert chain == 256 + 4 * B * (32 + 1) * 32 * 4 * 4
+    o.rec = sigk.REC_BAND
+    band = libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_SURFACE, B, 0, L, M, d, lam, 0, ctypes.byref(o))
+    assert band > chain
+    # the implicit scheme and d > 16 take the band form under AUTO too
+    o.rec = sigk.REC_AUTO
+    o.scheme = sigk.SCHEMES["implicit"]
+    assert libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_SURFACE, B, 0, L, M, d, lam, 0, ctypes.byref(o)) == band
+    o.scheme = 0
+    wide = libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_SURFACE, B, 0, L, M, 17, lam, 0, ctypes.byref(o))
+    o.rec = sigk.REC_BAND
+    assert wide == libsigk.sigk_workspace_bytes(sigk.OP_PAIRS_SURFACE, B, 0, L, M, 17, lam, 0, ctypes.byref(o))
