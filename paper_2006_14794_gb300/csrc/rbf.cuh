@@ -58,6 +58,90 @@ __global__ void __launch_bounds__(RBF_THREADS) rbf_coef_kernel(Layout lay, int64
         const typename Layout::Geo g = lay.geo(k);
         const int p0 = (t / tiles_c) * TR, q0 = (t - (t / tiles_c) * tiles_c) * RBF_TC;
         if (p0 >= g.nx || q0 >= g.ny) continue;   // block-uniform
+        // points p0 .. p0 + TR and q0 .. q0 + 32 (0 past the path's last
+        // point), channels cb .. cb + nc - 1: consecutive threads read
+        // consecutive channels of a point
+        auto stage = [&](int64_t cb, int nc) {
+            __syncthreads();
+            for (int v = tid; v < nc * (TR + 1); v += RBF_THREADS) {
+                const int i = v / nc, c = v - i * nc;
+                xs[c][i] = p0 + i <= g.nx ? g.rows[(int64_t)(p0 + i) * d + cb + c] : (T)0;
+            }
+            for (int v = tid; v < nc * (RBF_TC + 1); v += RBF_THREADS) {
+                const int i = v / nc, c = v - i * nc;
+                ys[c][i] = q0 + i <= g.ny ? g.cols[(int64_t)(q0 + i) * d + cb + c] : (T)0;
+            }
+            __syncthreads();
+        };
+        if constexpr (sizeof(T) == 4) {
+            // f32: columns (j, j + 1) of a row share a float2, each sum a packed
+            // FMA (the same operations per cell as the scalar loop below)
+            float2 uu2[NR][2], ux2[NR][2], uy2[NR][2], xy2[NR][2], ny2[2];
+            float nxs[NR];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                ny2[h] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    uu2[i][h] = ny2[h]; ux2[i][h] = ny2[h]; uy2[i][h] = ny2[h]; xy2[i][h] = ny2[h];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NR; ++i) nxs[i] = 0.f;
+            for (int64_t cb = 0; cb < d; cb += RBF_CH) {
+                const int nc = d - cb < RBF_CH ? (int)(d - cb) : RBF_CH;
+                stage(cb, nc);
+#pragma unroll 2
+                for (int c = 0; c < nc; ++c) {
+                    float xv[NR + 1], yv[5];
+#pragma unroll
+                    for (int i = 0; i <= NR; ++i) xv[i] = xs[c][r + i];
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) yv[j] = ys[c][c0 + j];
+                    float2 ny_[2], dy2[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        ny_[h] = make_float2(-yv[2 * h], -yv[2 * h + 1]);
+                        dy2[h] = make_float2(yv[2 * h + 1] - yv[2 * h], yv[2 * h + 2] - yv[2 * h + 1]);
+                        ny2[h] = __ffma2_rn(dy2[h], dy2[h], ny2[h]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < NR; ++i) {
+                        const float dxv = xv[i + 1] - xv[i];
+                        nxs[i] = fmaf(dxv, dxv, nxs[i]);
+                        const float2 x2 = make_float2(xv[i], xv[i]), d2 = make_float2(dxv, dxv);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float2 uv = __fadd2_rn(x2, ny_[h]);
+                            uu2[i][h] = __ffma2_rn(uv, uv, uu2[i][h]);
+                            ux2[i][h] = __ffma2_rn(uv, d2, ux2[i][h]);
+                            uy2[i][h] = __ffma2_rn(uv, dy2[h], uy2[i][h]);
+                            xy2[i][h] = __ffma2_rn(d2, dy2[h], xy2[i][h]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const int p = p0 + r + i;
+                if (p >= g.nx) break;
+                const typename Layout::Row row = lay.row(g, p);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int q = q0 + c0 + j;
+                    if (q < g.ny) {
+                        const int h = j >> 1;
+                        const bool hi = j & 1;
+                        const float G = rbf_second_difference(
+                            hi ? uu2[i][h].y : uu2[i][h].x, hi ? ux2[i][h].y : ux2[i][h].x,
+                            hi ? uy2[i][h].y : uy2[i][h].x, hi ? xy2[i][h].y : xy2[i][h].x, nxs[i],
+                            hi ? ny2[h].y : ny2[h].x, (float)s);
+                        lay.store(g, row, q, scheme_coef(G * (float)scale, scheme));
+                    }
+                }
+            }
+            continue;
+        }
         T uu[NR][4], ux[NR][4], uy[NR][4], xy[NR][4], ny[4], nx[NR];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -69,19 +153,7 @@ __global__ void __launch_bounds__(RBF_THREADS) rbf_coef_kernel(Layout lay, int64
         for (int i = 0; i < NR; ++i) nx[i] = 0;
         for (int64_t cb = 0; cb < d; cb += RBF_CH) {
             const int nc = d - cb < RBF_CH ? (int)(d - cb) : RBF_CH;
-            __syncthreads();
-            // points p0 .. p0 + TR and q0 .. q0 + 32 (0 past the path's last
-            // point), channels cb .. cb + nc - 1: consecutive threads read
-            // consecutive channels of a point
-            for (int v = tid; v < nc * (TR + 1); v += RBF_THREADS) {
-                const int i = v / nc, c = v - i * nc;
-                xs[c][i] = p0 + i <= g.nx ? g.rows[(int64_t)(p0 + i) * d + cb + c] : (T)0;
-            }
-            for (int v = tid; v < nc * (RBF_TC + 1); v += RBF_THREADS) {
-                const int i = v / nc, c = v - i * nc;
-                ys[c][i] = q0 + i <= g.ny ? g.cols[(int64_t)(q0 + i) * d + cb + c] : (T)0;
-            }
-            __syncthreads();
+            stage(cb, nc);
 #pragma unroll 2
             for (int c = 0; c < nc; ++c) {
                 T xv[NR + 1], dxv[NR];
