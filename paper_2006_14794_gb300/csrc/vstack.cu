@@ -37,22 +37,23 @@
 // chain column and window 1 an odd one, at the same index (the lane's macro-
 // step), so the ring keeps even and odd columns apart, each column padded to
 // an odd number of 16-byte units: the 32 lanes, one column apart, then read
-// distinct bank quads with one address a macro-step.  A lane's row increments for its next pair
-// wait in a 2-row slot of shared memory, fetched by the lane itself with
-// cp.async when it enters the current pair.
+// distinct bank quads with one address a macro-step.  A lane's row
+// increments for its next pair wait in a 2-row slot of shared memory, fetched
+// by the lane itself with cp.async when it enters the current pair.
 //
 // The increments themselves, x[p+1] - x[p] for every point row of the call,
 // are formed once by vs_inc_kernel into the workspace (16-byte rows of
 // channel quads, zero-padded), so that every later copy is a plain 16-byte
 // cp.async; those of the X side are scaled by 1/2 4^-lambda there (a power
 // of two: exact), so every pair, whichever side its rows refine, forms
-// c = <dx, dy> with exactly one factor scaled.  Planning happens on the device from the offsets (no host round
-// trip; a CUDA graph replays it for any lengths up to max_len):
+// c = <dx, dy> with exactly one factor scaled.  Planning happens on the
+// device from the offsets (no host round trip; a CUDA graph replays it for
+// any lengths up to max_len):
 //   vs_pairs_kernel: per pair, orientation, stack height, macro-steps T;
 //   vs_plan_kernel (one block): pairs sorted by (stack height, T descending),
 //     the number of chains of each height chosen so that every chain ends at
-//     about the same time with all of them resident, pairs dealt to chains in
-//     snake order;
+//     about the same time with all of them resident in three quarters of the
+//     register file, pairs dealt to chains in snake order;
 //   vstack_kernel, one launch per stack height on library streams.
 #include <string.h>
 
